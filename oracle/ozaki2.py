@@ -1,0 +1,441 @@
+"""CPU oracle of the Ozaki-II scheme (arXiv 2602.02549), Algorithms 1-3.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this module.  It shares no code
+with the GPU library; the loops live in oracle/oz2_oracle.c (plain C) and the
+constants in oracle/constants.py (Python integers).
+
+The steps below follow the paper's order and notation:
+  Algorithm 2 (Scaling):  mu', Abar, nu', Bbar, Cbar = Abar Bbar,
+      Dbar = single_up(Cbar), e = log2f(max dbar), f likewise,
+      mu = mu' + floor(fma_down(c, e, P')), A' = trunc(2^mu A), B' likewise.
+  Algorithm 3 (CRT):  A'_l = mod(A', p_l), B'_l, C'_l = A'_l B'_l,
+      W_l = mod(C'_l, p_l), C'(1), C'(2), Q, C''.
+  Algorithm 1:  C = diag(2^-mu) C'' diag(2^-nu).
+
+Readings where the paper is silent (each also listed in the design doc):
+  * floor(fl_down(fma(c, e, P'))) equals floor(c*e + P') taken exactly, because
+    rounding down never crosses the integer below; c*e + P' is exact in FP64.
+  * A zero row of A (zero column of B) gets mu' = 0; a row whose Cbar row is
+    all zero uses max dbar = 1 (e = 0).  The output there is exactly 0.
+  * C'(1) and C'(2) are fma chains in ascending l from +0.
+  * The final scaling is one ldexp by -(mu_i + nu_j).  For b = 32 the
+    rounding single(C'') of Algorithm 3 is applied after that scaling, which
+    changes nothing unless single(C'') would overflow (P > 2^128, N >= 17) or
+    C is subnormal.
+  * e = log2f(.) is the C library's log2f unless exponents are injected.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from fractions import Fraction
+
+import numpy as np
+
+from . import build as _build
+from .constants import MODULI, K_MAX, N_MAX, N_MIN, U32, bound_terms, constants
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_build.build())
+        P = ctypes.c_void_p
+        i32, i64, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
+        _lib.oz2o_floor_log2_absmax.argtypes = [i32, i32, P, i64, i64, P]
+        _lib.oz2o_ceil_scaled_abs.argtypes = [i32, i32, P, i64, i64, P, P]
+        _lib.oz2o_gemm_i8_i64.argtypes = [i32, i32, i32, P, P, P]
+        _lib.oz2o_trunc_scaled.argtypes = [i32, i32, P, i64, i64, P, P]
+        _lib.oz2o_residues.argtypes = [i64, P, i32, P]
+        _lib.oz2o_mod_i64.argtypes = [i64, P, i32, P]
+        _lib.oz2o_crt.argtypes = [i64, i32, P, P, P, d, d, d, i32, P, P, P, P]
+        _lib.oz2o_unscale.argtypes = [i32, i32, P, P, P, i32, P]
+        _lib.oz2o_log2f.argtypes = [i64, P, P]
+        _lib.oz2o_exact_residual.argtypes = [i32, i32, i32, P, i64, i64, P, i64, i64, P, P]
+        _lib.oz2o_exact_abs_sums.argtypes = [i32, i32, P, i64, i64, P]
+        _lib.oz2o_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _strides(X: np.ndarray):
+    return X.strides[0] // X.itemsize, X.strides[1] // X.itemsize
+
+
+INT32_MIN = -(1 << 31)
+
+
+# --------------------------------------------------------------------------- #
+# Small elementwise helpers (exact)
+# --------------------------------------------------------------------------- #
+def floor_log2_absmax(X: np.ndarray, axis: int) -> np.ndarray:
+    """floor(log2 max |x|) along `axis` (alpha_i / beta_j of Theorem 2); INT32_MIN if zero."""
+    X = np.asarray(X, dtype=np.float64)
+    V = X if axis == 1 else X.T
+    out = np.empty(V.shape[0], dtype=np.int32)
+    rs, cs = _strides(V)
+    lib().oz2o_floor_log2_absmax(V.shape[0], V.shape[1], _p(V), rs, cs, _p(out))
+    return out
+
+
+def single_up(v: np.ndarray) -> np.ndarray:
+    """single_up(.) of nonnegative integers below 2^31 (Algorithm 2, Dbar)."""
+    v = np.asarray(v, dtype=np.float64)
+    f = v.astype(np.float32)
+    low = f.astype(np.float64) < v
+    f[low] = np.nextafter(f[low], np.float32(np.inf))
+    return f
+
+
+def log2f(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty_like(x)
+    lib().oz2o_log2f(x.size, _p(x), _p(out))
+    return out
+
+
+def exponent_shift(c: np.float32, e: np.ndarray, Pprime: np.float32) -> np.ndarray:
+    """floor(fl_down(fma(c, e, P'))) of Algorithm 2 = floor(c*e + P') exactly.
+
+    c and e are FP32, so c*e has at most 48 significant bits and |c*e| < 16;
+    P' < 200 is a multiple of 2^-16 at worst.  The sum therefore fits the 53
+    bits of FP64 and both operations below are exact.
+    """
+    v = np.float64(c) * e.astype(np.float64) + np.float64(Pprime)
+    return np.floor(v).astype(np.int64)
+
+
+# --------------------------------------------------------------------------- #
+# Algorithm 2: Scaling
+# --------------------------------------------------------------------------- #
+def scaling(A: np.ndarray, B: np.ndarray, N: int, b: int = 64,
+            mu_in: np.ndarray | None = None, nu_in: np.ndarray | None = None) -> dict:
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    C = constants(N, b)
+    L = lib()
+    # mu'_i = 5 - floor(log2 max_h |a_ih|); nu'_j likewise (eq. mu'nu')
+    alpha = floor_log2_absmax(A, axis=1)
+    beta = floor_log2_absmax(B, axis=0)
+    mu_p = np.where(alpha == INT32_MIN, 0, 5 - alpha.astype(np.int64)).astype(np.int32)
+    nu_p = np.where(beta == INT32_MIN, 0, 5 - beta.astype(np.int64)).astype(np.int32)
+    # Abar = ceil(diag(2^mu') |A|), Bbar = ceil(|B| diag(2^nu'))
+    Abar = np.empty((m, k), dtype=np.int8)
+    rs, cs = _strides(A)
+    L.oz2o_ceil_scaled_abs(m, k, _p(A), rs, cs, _p(mu_p), _p(Abar))
+    BbarT = np.empty((n, k), dtype=np.int8)
+    BT = B.T
+    rs, cs = _strides(BT)
+    L.oz2o_ceil_scaled_abs(n, k, _p(BT), rs, cs, _p(nu_p), _p(BbarT))
+    Bbar = np.ascontiguousarray(BbarT.T)
+    # Cbar = Abar Bbar, exact
+    Cbar = gemm_i8(Abar, Bbar)
+    # Dbar = single_up(Cbar); e_i = log2f(max_h dbar_ih); f_j = log2f(max_h dbar_hj)
+    Dbar = single_up(Cbar)
+    drow = Dbar.max(axis=1) if n > 0 else np.zeros(m, np.float32)
+    dcol = Dbar.max(axis=0) if m > 0 else np.zeros(n, np.float32)
+    drow = np.where(drow == 0, np.float32(1), drow)          # reading: empty row -> 1
+    dcol = np.where(dcol == 0, np.float32(1), dcol)
+    e = log2f(drow)
+    f = log2f(dcol)
+    mu = (mu_p + exponent_shift(C.c, e, C.Pprime)).astype(np.int32)
+    nu = (nu_p + exponent_shift(C.c, f, C.Pprime)).astype(np.int32)
+    own_mu, own_nu = mu, nu
+    if mu_in is not None:
+        mu = np.asarray(mu_in, dtype=np.int32)
+    if nu_in is not None:
+        nu = np.asarray(nu_in, dtype=np.int32)
+    # A' = trunc(diag(2^mu) A), B' = trunc(B diag(2^nu))
+    Ap = trunc_scaled_rows(A, mu)
+    Bp = np.ascontiguousarray(trunc_scaled_rows(B.T, nu).T)
+    return dict(alpha=alpha, beta=beta, mu_p=mu_p, nu_p=nu_p, Abar=Abar, Bbar=Bbar,
+                Cbar=Cbar, cmax_row=Cbar.max(axis=1) if n else np.zeros(m, np.int64),
+                cmax_col=Cbar.max(axis=0) if m else np.zeros(n, np.int64),
+                e=e, f=f, mu=mu, nu=nu, own_mu=own_mu, own_nu=own_nu, Ap=Ap, Bp=Bp)
+
+
+def trunc_scaled_rows(X: np.ndarray, shift: np.ndarray) -> np.ndarray:
+    X = np.asarray(X, dtype=np.float64)
+    rows, cols = X.shape
+    out = np.empty((rows, cols), dtype=np.float64)
+    rs, cs = _strides(X)
+    sh = np.ascontiguousarray(shift, dtype=np.int32)
+    lib().oz2o_trunc_scaled(rows, cols, _p(X), rs, cs, _p(sh), _p(out))
+    return out
+
+
+def gemm_i8(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.int8)
+    Y = np.ascontiguousarray(Y, dtype=np.int8)
+    m, k = X.shape
+    n = Y.shape[1]
+    Z = np.empty((m, n), dtype=np.int64)
+    lib().oz2o_gemm_i8_i64(m, n, k, _p(X), _p(Y), _p(Z))
+    return Z
+
+
+def residues(X: np.ndarray, p: int) -> np.ndarray:
+    """mod(X, p) of Algorithm 3 as INT8 (X integer-valued doubles)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.empty(X.shape, dtype=np.int8)
+    lib().oz2o_residues(X.size, _p(X), p, _p(out))
+    return out
+
+
+def mod_i64(X: np.ndarray, p: int) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.int64)
+    out = np.empty(X.shape, dtype=np.int8)
+    lib().oz2o_mod_i64(X.size, _p(X), p, _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------- #
+# Algorithm 3: CRT
+# --------------------------------------------------------------------------- #
+def crt(Ap: np.ndarray, Bp: np.ndarray, N: int, b: int = 64, keep_residues: bool = False,
+        consts=None) -> dict:
+    C = consts if consts is not None else constants(N, b)
+    m, k = Ap.shape
+    n = Bp.shape[1]
+    W = np.empty((N, m, n), dtype=np.int8)
+    Ares = np.empty((N, m, k), dtype=np.int8) if keep_residues else None
+    Bres = np.empty((N, k, n), dtype=np.int8) if keep_residues else None
+    for l, pl in enumerate(C.p):
+        Al = residues(Ap, pl)                 # A'_l = mod(A', p_l)
+        Bl = residues(Bp, pl)                 # B'_l = mod(B', p_l)
+        if keep_residues:
+            Ares[l], Bres[l] = Al, Bl
+        W[l] = mod_i64(gemm_i8(Al, Bl), pl)   # W_l = mod(A'_l B'_l, p_l)
+    out = crt_from_W(W, N, b, consts=C)
+    out.update(W=W, Ares=Ares, Bres=Bres)
+    return out
+
+
+def crt_from_W(W: np.ndarray, N: int, b: int = 64, consts=None) -> dict:
+    """Algorithm 3 from W_l on; `consts` replaces the tables (tests plant mistakes with it)."""
+    C = consts if consts is not None else constants(N, b)
+    shape = W.shape[1:]
+    count = int(np.prod(shape))
+    W = np.ascontiguousarray(W, dtype=np.int8)
+    s1 = np.array(C.s1, dtype=np.float64)
+    s2 = np.array(C.s2, dtype=np.float64)
+    C1 = np.empty(count); C2 = np.empty(count); Q = np.empty(count); Cpp = np.empty(count)
+    lib().oz2o_crt(count, N, _p(W), _p(s1), _p(s2), C.P1, C.P2, C.Pinv, b,
+                   _p(C1), _p(C2), _p(Q), _p(Cpp))
+    return dict(C1=C1.reshape(shape), C2=C2.reshape(shape), Q=Q.reshape(shape),
+                Cpp=Cpp.reshape(shape))
+
+
+def unscale(Cpp: np.ndarray, mu: np.ndarray, nu: np.ndarray, b: int = 64) -> np.ndarray:
+    Cpp = np.ascontiguousarray(Cpp, dtype=np.float64)
+    m, n = Cpp.shape
+    out = np.empty((m, n), dtype=np.float64)
+    lib().oz2o_unscale(m, n, _p(Cpp), _p(np.ascontiguousarray(mu, np.int32)),
+                       _p(np.ascontiguousarray(nu, np.int32)), b, _p(out))
+    return out if b == 64 else out.astype(np.float32)
+
+
+# --------------------------------------------------------------------------- #
+# Algorithm 1: OS_II
+# --------------------------------------------------------------------------- #
+def os_ii(A: np.ndarray, B: np.ndarray, N: int, b: int = 64,
+          mu_in=None, nu_in=None, keep_residues: bool = False, consts=None) -> dict:
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    if not (N_MIN <= N <= N_MAX):
+        raise ValueError("N out of range")
+    if A.shape[1] > K_MAX:
+        raise ValueError("k > 2^17")
+    s = scaling(A, B, N, b, mu_in, nu_in)
+    r = crt(s["Ap"], s["Bp"], N, b, keep_residues, consts)
+    s.update(r)
+    s["C"] = unscale(r["Cpp"], s["mu"], s["nu"], b)
+    s["N"], s["b"] = N, b
+    return s
+
+
+def os_ii_block(A_rows: np.ndarray, B_cols: np.ndarray, mu: np.ndarray, nu: np.ndarray,
+                N: int, b: int = 64) -> np.ndarray:
+    """Entries C_ij for the given rows of A and columns of B with injected mu, nu.
+
+    Algorithm 2 only fixes mu and nu; once they are given, each entry depends on
+    row i of A and column j of B alone (A' rows, B' columns, Algorithm 3 and the
+    final scaling), so sampled entries of a large product can be checked one by one.
+    """
+    Ap = trunc_scaled_rows(A_rows, mu)
+    Bp = np.ascontiguousarray(trunc_scaled_rows(np.asarray(B_cols, np.float64).T, nu).T)
+    r = crt(Ap, Bp, N, b)
+    return unscale(r["Cpp"], mu, nu, b)
+
+
+# --------------------------------------------------------------------------- #
+# Exact products, errors and the bounds of Theorem 2
+# --------------------------------------------------------------------------- #
+def exact_residual(X: np.ndarray, Y: np.ndarray, Cm: np.ndarray | None = None) -> np.ndarray:
+    """RN(X Y - Cm), computed exactly and rounded once (X m x k, Y k x n doubles)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    m, k = X.shape
+    n = Y.shape[1]
+    out = np.empty((m, n), dtype=np.float64)
+    xr, xc = _strides(X)
+    yr, yc = _strides(Y)
+    Cm = None if Cm is None else np.ascontiguousarray(Cm, dtype=np.float64)
+    lib().oz2o_exact_residual(m, n, k, _p(X), xr, xc, _p(Y), yr, yc, _p(Cm), _p(out))
+    return out
+
+
+def exact_product(A, B):
+    return exact_residual(A, B, None)
+
+
+def abs_sums(X: np.ndarray, axis: int) -> np.ndarray:
+    """Correctly rounded sum_h |x| along `axis`."""
+    X = np.asarray(X, dtype=np.float64)
+    V = X if axis == 1 else X.T
+    out = np.empty(V.shape[0])
+    rs, cs = _strides(V)
+    lib().oz2o_exact_abs_sums(V.shape[0], V.shape[1], _p(V), rs, cs, _p(out))
+    return out
+
+
+_UP = 1.0 + 2.0 ** -40
+
+
+def pow2_prime(alpha: np.ndarray, cmax: np.ndarray) -> np.ndarray:
+    """2^alpha' = 2^alpha * sqrt(max cbar) (Theorem 2), rounded up; 0 for empty rows."""
+    out = np.zeros(alpha.shape[0])
+    ok = (alpha != INT32_MIN) & (cmax > 0)
+    out[ok] = np.ldexp(np.sqrt(cmax[ok].astype(np.float64)), alpha[ok]) * _UP
+    return out
+
+
+def bounds(A: np.ndarray, B: np.ndarray, res: dict) -> tuple[np.ndarray, np.ndarray]:
+    """Upper bounds of |AB - C| per entry: eq. thm:err-1 and eq. thm:err-2."""
+    N, b = res["N"], res["b"]
+    k = A.shape[1]
+    bt = bound_terms(N, b)
+    t = bt["t"]
+    R = abs_sums(A, axis=1) * _UP            # |A| v
+    K = abs_sums(B, axis=0) * _UP            # v^T |B|
+    a2 = pow2_prime(res["alpha"], res["cmax_row"])
+    b2 = pow2_prime(res["beta"], res["cmax_col"])
+    absApBp = np.abs(exact_residual(res["Ap"], res["Bp"])) * _UP
+    common = t * np.outer(R, b2) + t * np.outer(a2, K)
+    t2ab = (t * t) * np.outer(a2, b2)
+    err1 = (common + (k + bt["gN"] + bt["h"] * absApBp) * t2ab) * _UP
+    err2 = (common + (k + bt["rb"]) * t2ab) * _UP
+    return err1, err2
+
+
+# --------------------------------------------------------------------------- #
+# Exponent checks against the paper's definitions
+# --------------------------------------------------------------------------- #
+def mu_band(mu_p: np.ndarray, cmax: np.ndarray, N: int, b: int = 64) -> tuple[np.ndarray, np.ndarray]:
+    """Range of mu allowed by Algorithm 2 under assumption (1) on log2f.
+
+    With d = max dbar (1 for an empty row), any FP32 e with
+    |e - log2 d| <= 4 u32 log2 d gives mu = mu' + floor(c e + P'); c < 0 makes
+    this non-increasing in e, so the extremes come from the smallest and the
+    largest admissible FP32 e.
+    """
+    C = constants(N, b)
+    d = single_up(cmax).astype(np.float64)
+    d = np.where(d == 0, 1.0, d)
+    lo = np.empty(len(d), np.int64)
+    hi = np.empty(len(d), np.int64)
+    u4 = 4 * float(U32)
+    for i, di in enumerate(d):
+        lg = math.log2(di)
+        e_lo = np.float32(lg * (1 - u4))
+        if float(e_lo) < lg * (1 - u4) * (1 - 1e-15):
+            e_lo = np.nextafter(e_lo, np.float32(np.inf))
+        e_hi = np.float32(lg * (1 + u4))
+        if float(e_hi) > lg * (1 + u4) * (1 + 1e-15):
+            e_hi = np.nextafter(e_hi, np.float32(-np.inf))
+        if lg == 0.0:
+            e_lo = e_hi = np.float32(0.0)
+        hi[i] = exponent_shift(C.c, np.array([e_lo], np.float32), C.Pprime)[0]
+        lo[i] = exponent_shift(C.c, np.array([e_hi], np.float32), C.Pprime)[0]
+    return mu_p + lo, mu_p + hi
+
+
+# --------------------------------------------------------------------------- #
+# Bound-chosen N (reading of the paper's motivation)
+# --------------------------------------------------------------------------- #
+def choose_N(A: np.ndarray, B: np.ndarray, alpha, beta, cmax_row, cmax_col,
+             tau: float, nmax: int, b: int = 64) -> tuple[int, dict]:
+    """Smallest N in [2, nmax] whose N-dependent part of eq. thm:err-2 is <= tau * L.
+
+    T_N = t (max_i R_i)(max_j 2^beta'_j) + t (max_i 2^alpha'_i)(max_j K_j)
+          + (k + g_N) t^2 (max_i 2^alpha'_i)(max_j 2^beta'_j)
+    with R = |A| v, K = v^T |B|, g_N the P-proportional part of R_b (Lemma 4),
+    and L = max(L1, L2) a lower bound of max_ij (|A||B|)_ij:
+      L1 = max_h (max_i |a_ih|)(max_j |b_hj|),  L2 = max_i (|A| (|B| 1))_i / n.
+    Returns (N, info); nmax is returned when no N qualifies.
+    """
+    A = np.asarray(A, np.float64)
+    B = np.asarray(B, np.float64)
+    m, k = A.shape
+    n = B.shape[1]
+    R = abs_sums(A, 1)
+    K = abs_sums(B, 0)
+    a2 = pow2_prime(np.asarray(alpha), np.asarray(cmax_row))
+    b2 = pow2_prime(np.asarray(beta), np.asarray(cmax_col))
+    absA, absB = np.abs(A), np.abs(B)
+    L1 = float(np.max(absA.max(axis=0) * absB.max(axis=1))) if m and n and k else 0.0
+    rB = abs_sums(B, 1)
+    L2 = float(np.max(absA @ rB)) / n if m and n and k else 0.0
+    Lnorm = max(L1, L2)
+    maxR, maxK, ma2, mb2 = float(R.max(initial=0)), float(K.max(initial=0)), float(a2.max(initial=0)), float(b2.max(initial=0))
+    chosen, ratios = nmax, {}
+    for N in range(N_MIN, nmax + 1):
+        bt = bound_terms(N, b)
+        t = bt["t"]
+        T = t * (maxR * mb2 + ma2 * maxK) + (k + bt["gN"]) * t * t * ma2 * mb2
+        ratios[N] = T / Lnorm if Lnorm > 0 else 0.0
+        if T <= tau * Lnorm:
+            chosen = N
+            break
+    return chosen, dict(L=Lnorm, L1=L1, L2=L2, ratios=ratios, maxR=maxR, maxK=maxK,
+                        max2a=ma2, max2b=mb2)
+
+
+# --------------------------------------------------------------------------- #
+# Exact integer checks (Lemmas 0, 2, 3; Theorem 1)
+# --------------------------------------------------------------------------- #
+def crt_exact(W: np.ndarray, N: int) -> tuple[list, list]:
+    """A'B' = mod(sum_l P/p_l q_l W_l, P) (Lemma 3 proof) and Q_exact, as Python ints."""
+    C = constants(N, 64)
+    P = C.P
+    flat = W.reshape(N, -1)
+    AB, Qx = [], []
+    for e in range(flat.shape[1]):
+        S = sum(int(x) * int(w) for x, w in zip(C.x, flat[:, e]))
+        q = (2 * S + P) // (2 * P)            # round(S/P); ties cannot occur (Lemma 3)
+        AB.append(S - P * q)
+        Qx.append(q)
+    return AB, Qx
+
+
+def ozaki_exponent_floor_ok(mu, alpha, cmax, N) -> np.ndarray:
+    """Lemma 1, eq. (mu_i lower bound): 2^(2 mu_i + 2 alpha_i - 5) * max cbar_i >= P - 1."""
+    P = constants(N, 64).P
+    ok = []
+    for mi, ai, ci in zip(mu, alpha, cmax):
+        if ai == INT32_MIN or ci == 0:
+            ok.append(True)
+            continue
+        ex = 2 * int(mi) + 2 * int(ai) - 5
+        lhs = Fraction(int(ci)) * (Fraction(2) ** ex)
+        ok.append(lhs >= P - 1)
+    return np.array(ok)
