@@ -1,0 +1,355 @@
+"""Benchmark: emulated DGEMM TFLOPS at the bound-chosen N, and the error of the
+result against the exact product, on one B300 (or N independent replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl oz2|reference]
+
+Workload (default): square FP64 DGEMM m = n = k = 16384, entries from the
+paper's generator (Section 5) with phi = 1, seeds 0 (A) and 1 (B), accurate
+scaling, N chosen by the bound rule for a normwise target of 1e-15 (N <= 20).
+A step is one full call of the emulated GEMM (all kernels).  Inputs are
+resident in HBM for `value`; `e2e` adds the host->device copy of A and B from
+pinned memory and the device->host copy of C to every step.
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Emulated DGEMM TFLOPS at bound-chosen N & max rel err vs exact, 1 B300"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="oz2", choices=["oz2", "reference"])
+    p.add_argument("--size", type=int, default=16384)
+    p.add_argument("--phi", type=float, default=1.0)
+    p.add_argument("--target", type=float, default=1e-15)
+    p.add_argument("--nmax", type=int, default=20)
+    p.add_argument("--nmoduli", type=int, default=0, help="fixed N instead of the bound rule")
+    p.add_argument("--cpu-sample", type=int, default=192, help="rows/cols of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--acc-samples", type=int, default=256)
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("oz2_kernels.cuh", "oz2_ptx.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2602_02549_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, units: float):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "gemm_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("kernel_hash") != kernel_hash() or kernel not in d:
+        return None
+    e = d[kernel]
+    return e["dram_bytes"] / e["units"] * units
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_config(args, m, n, k, N, world=1):
+    nmax = args.nmoduli or args.nmax
+    return {"workload": f"dgemm_square_{m}_phi{args.phi}_tau{args.target:g}_accurate",
+            "m": m, "n": n, "k": k, "phi": args.phi, "target": args.target, "nmax": nmax,
+            "nmoduli": N, "mode": "accurate",
+            "l2": "inputs larger than L2 (A, B 2 GiB each; residues 1 GiB per modulus)",
+            "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
+# --------------------------------------------------------------------------- #
+def cpu_baseline(A_host, B_host, N: int, sample: int, phi: float):
+    """The oracle as it stands, on a sample: rows[:s] of A times cols[:s] of B."""
+    import numpy as np
+    from oracle import ozaki2
+    s = sample
+    a = np.ascontiguousarray(A_host[:s])
+    b = np.ascontiguousarray(B_host[:, :s])
+    k = a.shape[1]
+    t0 = time.perf_counter()
+    ozaki2.os_ii(a, b, N, 64)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * s * s * k / dt / 1e12, "unit": "TFLOPS", "cores": int(ozaki2.lib().oz2o_num_threads()),
+            "kind": "oracle",
+            "sample": f"Algorithms 1-3 on A[:{s}, :] x B[:, :{s}] (k={k}, N={N}, phi={phi}), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on the host cores, a bounded sample per step."""
+    from paper_2602_02549_b300.inputs import paper_matrix
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    k = args.size
+    s = 128
+    A = paper_matrix(s, k, args.phi, 0)
+    B = paper_matrix(k, s, args.phi, 1)
+    from oracle import ozaki2
+    N = args.nmoduli or 17
+    for _ in range(args.warmup):
+        ozaki2.os_ii(A[:32], B[:, :32], N)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ozaki2.os_ii(A, B, N)
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times)
+    v = 2.0 * s * s * k / t / 1e12
+    cores = int(ozaki2.lib().oz2o_num_threads())
+    sample = f"A[:{s}, :] x B[:, :{s}] of the {k}^3 workload (phi={args.phi}), N={N}, per step"
+    config = workload_config(args, k, k, k, N)
+    config.update(sample=sample)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config,
+        "cpu_baseline": {"value": v, "unit": "TFLOPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "TFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# --------------------------------------------------------------------------- #
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.build import build
+    from paper_2602_02549_b300.inputs import paper_matrix_torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    build()
+    m = n = k = args.size
+    A = paper_matrix_torch(m, k, args.phi, 0, dev)
+    Bm = paper_matrix_torch(k, n, args.phi, 1, dev)
+    C = torch.empty((m, n), dtype=torch.float64, device=dev)
+    nmax = args.nmoduli or args.nmax
+    ws = torch.empty(B.workspace_size(m, n, k, nmax, 0, False), dtype=torch.uint8, device=dev)
+    nout = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    tgt = args.target if not args.nmoduli else 0.0
+    nmx = args.nmax if not args.nmoduli else 0
+
+    def step(events=None, a=A, b=Bm):
+        rc = B.gemm_ex(a, b, C, args.nmoduli, 0, target=tgt, nmax=nmx, workspace=ws, stream=stream,
+                       n_out=nout, phase_events=events)
+        if rc:
+            raise B.Oz2Error(rc, "oz2_gemm_ex")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert B.sync(stream) == 0
+    N_used = int(nout.item())
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(B.NPHASES + 1)] for _ in range(args.steps)]
+    for evs in ev:
+        for e in evs:
+            e.record(stream)          # create the CUDA events before the timed region
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        barrier()
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for s in range(args.steps):
+            step(ev[s])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    assert B.sync(stream) == 0
+    phase_ms = [statistics.mean(ev[s][p].elapsed_time(ev[s][p + 1]) for s in range(args.steps))
+                for p in range(B.NPHASES)]
+    flops = 2.0 * m * n * k
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # dominant kernel: the N residue GEMMs (tcgen05, BF16 operands, FP32 accumulate)
+    peaks, peak_kind = load_peaks()
+    gemm_ms = phase_ms[5]
+    achieved = N_used * flops / (gemm_ms * 1e-3) / 1e12
+    peak = float(peaks["bf16_tflops_sustained"])
+    roofline = {"bound": "tensor", "kernel": "k_gemm<EPI_MOD>", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"bf16_tflops_sustained ({peak_kind})",
+                "traffic": traffic_for("k_gemm_mod", N_used * m * n * k),
+                "emulated_roofline_tflops": peak / (N_used + 1),
+                "emulated_frac": value / world / (peak / (N_used + 1))}
+
+    # end to end through the C ABI: pinned host A, B -> device, GEMM, C -> host
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.empty((m, k), dtype=torch.float64, pin_memory=True)
+        hB = torch.empty((k, n), dtype=torch.float64, pin_memory=True)
+        hC = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        hA.copy_(A)
+        hB.copy_(Bm)
+        dA, dB = torch.empty_like(A), torch.empty_like(Bm)
+
+        def e2e_step():
+            dA.copy_(hA, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+            step(None, dA, dB)
+            hC.copy_(C, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * flops / (e_ms * 1e-3) / 1e12, "unit": "TFLOPS", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": 8 * (m * k + k * n), "d2h_bytes_per_step": 8 * m * n}
+        del hA, hB, hC, dA, dB
+
+    # accuracy against the exact product on sampled entries
+    from paper_2602_02549_b300.accuracy import sampled_errors
+    g = torch.Generator(device="cpu").manual_seed(1234)
+    ii = torch.randint(0, m, (args.acc_samples,), generator=g).to(dev)
+    jj = torch.randint(0, n, (args.acc_samples,), generator=g).to(dev)
+    step()
+    torch.cuda.synchronize()
+    rows = A[ii].cpu().numpy()
+    cols = Bm[:, jj].t().contiguous().cpu().numpy()
+    vals = C[ii, jj].cpu().numpy()
+    acc = sampled_errors(rows, cols, vals)
+
+    # native FP64 GEMM (cuBLAS through torch) for context, at 4096^3
+    ns = min(4096, m)
+    a4, b4 = A[:ns, :ns].contiguous(), Bm[:ns, :ns].contiguous()
+    torch.matmul(a4, b4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    torch.matmul(a4, b4)
+    torch.cuda.synchronize()
+    native_tflops = 2.0 * ns ** 3 / (time.perf_counter() - t0) / 1e12
+    del a4, b4
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = args.cpu_sample
+        cpu = cpu_baseline(A[:s].cpu().numpy(), Bm[:, :s].cpu().numpy(), N_used, s, args.phi)
+
+    if rank == 0:
+        launches_per_step = 12 if args.nmoduli == 0 else 11
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, m, n, k, N_used, world),
+            "n_moduli": N_used,
+            "accuracy": acc,
+            "phase_ms": dict(zip(B.PHASE_NAMES, phase_ms)),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "native_fp64_tflops": {"value": native_tflops, "size": ns, "note": "torch.matmul float64, context"},
+            "clocks": clk.summary(),
+        }))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

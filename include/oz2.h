@@ -1,0 +1,149 @@
+/*
+ * oz2 — Ozaki-II emulation of FP64 / FP32 matrix multiplication on one B300.
+ *
+ * C ABI of liboz2.so.  Method: Uchino, Ozaki, Imamura, "Error Analysis of
+ * Matrix Multiplication Emulation Using Ozaki-II Scheme", arXiv 2602.02549.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major: X[i*ldx + j].  A is m x k (lda >= k), B is k x n
+ *     (ldb >= n), C is m x n (ldc >= n).  With OZ2_TRANS_A the array passed as
+ *     A holds A^T (k x m, lda >= m); with OZ2_TRANS_B it holds B^T (n x k,
+ *     ldb >= k).  These are the only transposes; there is no alpha/beta.
+ *   - A, B, C, the workspace and every optional output are DEVICE pointers
+ *     owned by the caller.  Nothing is freed by the library.
+ *   - All work is enqueued on opts->stream (NULL: the legacy default stream)
+ *     and the call returns without synchronising.  Argument errors are
+ *     returned before anything is enqueued, and C is then left untouched.
+ *   - Return value: OZ2_OK (0) or one of the negative OZ2_E* codes.
+ *   - NaN or Inf inputs violate the paper's preconditions (A, B finite); the
+ *     result for them is unspecified but no out-of-bounds access occurs.
+ */
+#ifndef OZ2_H
+#define OZ2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OZ2_API __attribute__((visibility("default")))
+#else
+#define OZ2_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define OZ2_OK          0
+#define OZ2_EINVAL     -1   /* bad dimension, leading dimension, N, mode or null pointer */
+#define OZ2_ERANGE     -2   /* k > 2^17 (Section 3: k <= 2^17 keeps INT32 sums exact)    */
+#define OZ2_ENOMEM     -3   /* workspace smaller than oz2_workspace_size()               */
+#define OZ2_ECUDA      -4   /* a CUDA runtime or driver call failed                      */
+#define OZ2_ETIMEOUT   -5   /* a bounded device-side wait gave up (see oz2_sync)         */
+#define OZ2_ENOTSUP    -6   /* combination not supported                                 */
+
+/* mode bits */
+#define OZ2_ACCURATE    0   /* Algorithm 2 as printed: Cbar = Abar*Bbar on the tensor cores */
+#define OZ2_FAST        1   /* Cbar replaced by a Cauchy-Schwarz majorant (no extra GEMM)    */
+#define OZ2_TRANS_A     2
+#define OZ2_TRANS_B     4
+
+/* Limits stated by the paper (Section 3, Algorithm 1). */
+#define OZ2_K_MAX   131072  /* k <= 2^17 */
+#define OZ2_N_MIN   2
+#define OZ2_N_MAX   49      /* p_l <= 256 pairwise coprime, eq. (p_list) */
+
+/* Phases of one call, in launch order (for oz2_opts.phase_events). */
+#define OZ2_PHASE_STATS     0   /* max |x| per row/column, sums for the N rule   */
+#define OZ2_PHASE_QUANT     1   /* Abar, Bbar (Algorithm 2)                       */
+#define OZ2_PHASE_SCALEGEMM 2   /* Cbar = Abar Bbar, row/column maxima            */
+#define OZ2_PHASE_EXPONENTS 3   /* N rule, mu, nu                                 */
+#define OZ2_PHASE_RESIDUES  4   /* A'_l, B'_l (Algorithm 3)                       */
+#define OZ2_PHASE_GEMM      5   /* C'_l = A'_l B'_l, W_l = mod(C'_l, p_l)         */
+#define OZ2_PHASE_CRT       6   /* C'(1), C'(2), Q, C'', inverse scaling          */
+#define OZ2_NPHASES         7
+
+typedef struct oz2_opts {
+    void   *stream;          /* cudaStream_t; NULL = legacy default stream                 */
+    void   *workspace;       /* device scratch of >= oz2_workspace_size(...) bytes,
+                                256-byte aligned.  NULL: the library uses a per-device
+                                cached buffer it grows with cudaMalloc.                    */
+    size_t  workspace_bytes;
+    double  target;          /* nmoduli == 0: target normwise relative error tau           */
+    int     nmax;            /* nmoduli == 0: largest N tried (0 = 20 DGEMM, 14 SGEMM)     */
+    int    *n_out;           /* optional device int: the N used                            */
+    int32_t *mu_out;         /* optional device int32[m]: the exponents mu of Algorithm 2  */
+    int32_t *nu_out;         /* optional device int32[n]: the exponents nu                  */
+    const int32_t *mu_in;    /* optional device int32[m] and int32[n]: use these exponents  */
+    const int32_t *nu_in;    /*   instead of Algorithm 2's (both or neither; needs N > 0)  */
+    int8_t *w_out;           /* optional device int8[N*m*n]: the residue products W_l of
+                                Algorithm 3, plane l at w_out + l*m*n, row-major m x n     */
+    void  **phase_events;    /* optional cudaEvent_t[OZ2_NPHASES + 1], created by the
+                                caller: event i is recorded on the stream before phase i,
+                                event OZ2_NPHASES after the last one (for timing)          */
+} oz2_opts;
+
+/*
+ * C = OS_II(A, B): Algorithm 1 of the paper (Scaling, Algorithm 2; CRT,
+ * Algorithm 3; inverse scaling) for FP64 A, B, C (DGEMM emulation, b = 64).
+ *   nmoduli  N in [2, 49] uses the first N moduli of eq. (p_list);
+ *            0 picks the smallest N in [2, opts->nmax] whose N-dependent part
+ *            of the Theorem 2 bound (eq. thm:err-2) is <= opts->target times a
+ *            lower bound of max_ij (|A||B|)_ij (requires opts with target > 0).
+ *   k        must be <= 2^17 (OZ2_ERANGE otherwise).
+ *   m, n, k  >= 1.
+ * oz2_gemm uses the library-managed workspace and the legacy default stream.
+ */
+OZ2_API int oz2_gemm(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                     double *C, int ldc, int nmoduli, int mode);
+OZ2_API int oz2_gemm_ex(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                        double *C, int ldc, int nmoduli, int mode, const oz2_opts *opts);
+
+/* FP32 A, B, C (SGEMM emulation, b = 32): Section 3.1 constants for b = 32
+ * (P2 = 0, s_l1 = double(P/p_l q_l), s_l2 = 0).  C'' is rounded to FP32 after
+ * the inverse scaling (identical to Algorithm 3's order unless single(C'')
+ * would overflow, which happens once P > 2^128, N >= 17). */
+OZ2_API int oz2_sgemm(int m, int n, int k, const float *A, int lda, const float *B, int ldb,
+                      float *C, int ldc, int nmoduli, int mode);
+OZ2_API int oz2_sgemm_ex(int m, int n, int k, const float *A, int lda, const float *B, int ldb,
+                         float *C, int ldc, int nmoduli, int mode, const oz2_opts *opts);
+
+/* Bytes of device workspace a call with these sizes needs; nmax is the largest
+ * N the call may use (its nmoduli, or opts->nmax when nmoduli == 0).  Returns 0
+ * for invalid sizes.  Host-only; touches no GPU. */
+OZ2_API size_t oz2_workspace_size(int m, int n, int k, int nmax, int mode, int fp32);
+
+/* Waits for `stream` and reports device-side status collected since the last
+ * call: OZ2_ETIMEOUT if a kernel's bounded wait expired (the kernel then
+ * stopped early and C is invalid), OZ2_ECUDA on a CUDA error, else OZ2_OK.
+ * The status word is cleared. */
+OZ2_API int oz2_sync(void *stream);
+
+/* Host-only: the library's own constant tables for N moduli (Section 3.1,
+ * Algorithm 2 first line, Algorithm 3), for tests.  fp32 = 0: DGEMM tables,
+ * 1: SGEMM tables.  Fills s1[N], s2[N] (doubles), scal[6] = {P1, P2, Pinv, g,
+ * t, gN} (g = grid of s_l1, 0 for SGEMM; t = 1/sqrt(32(P-1)) rounded up; gN =
+ * the P-proportional part of R_b in Lemma 4, rounded up) and *pprime = P'.
+ * Returns OZ2_OK or OZ2_EINVAL.  Touches no GPU. */
+OZ2_API int oz2_tables(int N, int fp32, double *s1, double *s2, double *scal, float *pprime);
+
+/* Diagnostic for assumption (1) of Section 1.2 (|log2f(x) - log2 x| <=
+ * 4 u32 log2 x, which Lemmas 0 and 1 rely on), for the __log2f used by the
+ * exponent kernel: enqueues a check of every FP32 value that is an integer in
+ * [1, 2^29] (the values Dbar can take).  dev_out: device uint64[2]; on
+ * completion dev_out[0] = number of violations, dev_out[1] = bits of the
+ * largest |__log2f(x) - log2 x| / (u32 log2 x) seen (a double). */
+OZ2_API int oz2_check_log2f(void *stream, unsigned long long *dev_out);
+
+/* Human-readable name of a status code (static string). */
+OZ2_API const char *oz2_status_str(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+OZ2_API int oz2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OZ2_H */

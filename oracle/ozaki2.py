@@ -379,9 +379,10 @@ def choose_N(A: np.ndarray, B: np.ndarray, alpha, beta, cmax_row, cmax_col,
     T_N = t (max_i R_i)(max_j 2^beta'_j) + t (max_i 2^alpha'_i)(max_j K_j)
           + (k + g_N) t^2 (max_i 2^alpha'_i)(max_j 2^beta'_j)
     with R = |A| v, K = v^T |B|, g_N the P-proportional part of R_b (Lemma 4),
-    and L = max(L1, L2) a lower bound of max_ij (|A||B|)_ij:
-      L1 = max_h (max_i |a_ih|)(max_j |b_hj|),  L2 = max_i (|A| (|B| 1))_i / n.
-    Returns (N, info); nmax is returned when no N qualifies.
+    and L = max_h (max_i |a_ih|)(max_j |b_hj|), a lower bound of
+    max_ij (|A||B|)_ij.  Every maximum of a sum of nonnegative terms is bounded
+    by the sum of the maxima, so T_N bounds the N-dependent part of the bound
+    on every entry.  Returns (N, info); nmax when no N qualifies.
     """
     A = np.asarray(A, np.float64)
     B = np.asarray(B, np.float64)
@@ -391,23 +392,20 @@ def choose_N(A: np.ndarray, B: np.ndarray, alpha, beta, cmax_row, cmax_col,
     K = abs_sums(B, 0)
     a2 = pow2_prime(np.asarray(alpha), np.asarray(cmax_row))
     b2 = pow2_prime(np.asarray(beta), np.asarray(cmax_col))
-    absA, absB = np.abs(A), np.abs(B)
-    L1 = float(np.max(absA.max(axis=0) * absB.max(axis=1))) if m and n and k else 0.0
-    rB = abs_sums(B, 1)
-    L2 = float(np.max(absA @ rB)) / n if m and n and k else 0.0
-    Lnorm = max(L1, L2)
-    maxR, maxK, ma2, mb2 = float(R.max(initial=0)), float(K.max(initial=0)), float(a2.max(initial=0)), float(b2.max(initial=0))
+    L = float(np.max(np.abs(A).max(axis=0) * np.abs(B).max(axis=1))) if m and n and k else 0.0
+    maxR, maxK = float(R.max(initial=0)), float(K.max(initial=0))
+    ma2, mb2 = float(a2.max(initial=0)), float(b2.max(initial=0))
     chosen, ratios = nmax, {}
     for N in range(N_MIN, nmax + 1):
         bt = bound_terms(N, b)
         t = bt["t"]
         T = t * (maxR * mb2 + ma2 * maxK) + (k + bt["gN"]) * t * t * ma2 * mb2
-        ratios[N] = T / Lnorm if Lnorm > 0 else 0.0
-        if T <= tau * Lnorm:
+        ratios[N] = T / L if L > 0 else 0.0
+    for N in range(N_MIN, nmax + 1):
+        if ratios[N] <= tau:
             chosen = N
             break
-    return chosen, dict(L=Lnorm, L1=L1, L2=L2, ratios=ratios, maxR=maxR, maxK=maxK,
-                        max2a=ma2, max2b=mb2)
+    return chosen, dict(L=L, ratios=ratios, maxR=maxR, maxK=maxK, max2a=ma2, max2b=mb2)
 
 
 # --------------------------------------------------------------------------- #
@@ -439,3 +437,36 @@ def ozaki_exponent_floor_ok(mu, alpha, cmax, N) -> np.ndarray:
         lhs = Fraction(int(ci)) * (Fraction(2) ** ex)
         ok.append(lhs >= P - 1)
     return np.array(ok)
+
+
+def bound_from_exponents(A_rows: np.ndarray, B_cols: np.ndarray, mu: np.ndarray, nu: np.ndarray,
+                         Ap_rows: np.ndarray, Bp_cols: np.ndarray, N: int, b: int = 64) -> np.ndarray:
+    """Upper bound of |AB - C| per entry given the exponents actually used.
+
+    The proof of Lemma 1 bounds the truncation error with |Delta_A|, |Delta_B| < 1:
+      |AB - 2^-mu A'B' 2^-nu| <= 2^-nu_j (|A| v)_i + 2^-mu_i (v^T |B|)_j + k 2^-(mu_i+nu_j),
+    and Lemma 4 adds 2^-(mu_i+nu_j) R_b.  Valid whenever Lemma 0 holds for the
+    entries (checked separately), so it applies to injected exponents too.
+    """
+    A_rows = np.asarray(A_rows, np.float64)
+    B_cols = np.asarray(B_cols, np.float64)
+    k = A_rows.shape[1]
+    bt = bound_terms(N, b)
+    R = abs_sums(A_rows, 1) * _UP
+    K = abs_sums(B_cols, 0) * _UP
+    absApBp = np.abs(exact_residual(Ap_rows, Bp_cols)) * _UP
+    smu = np.ldexp(1.0, -np.asarray(mu, np.int64))
+    snu = np.ldexp(1.0, -np.asarray(nu, np.int64))
+    Rb = bt["gN"] + bt["h"] * absApBp
+    return (np.outer(R, snu) + np.outer(smu, K) + (k + Rb) * np.outer(smu, snu)) * _UP
+
+
+def lemma0_holds(Ap_rows: np.ndarray, Bp_cols: np.ndarray, N: int) -> bool:
+    """Lemma 0: |A'||B'| < P/2 on every entry (FP64 upper bound, exact fallback)."""
+    P = constants(N, 64).P
+    ub = exact_product(np.abs(Ap_rows), np.abs(Bp_cols)) * (1 + 2.0 ** -40)
+    if (ub < float(P) / 2 * (1 - 2.0 ** -40)).all():
+        return True
+    IA = [[int(v) for v in row] for row in np.abs(Ap_rows)]
+    IB = [[int(v) for v in col] for col in np.abs(Bp_cols).T]
+    return all(2 * sum(a * b for a, b in zip(ra, cb)) < P for ra in IA for cb in IB)

@@ -1,0 +1,207 @@
+"""Python binding of liboz2.so (ctypes): argument marshalling only.
+
+Every step of the emulated GEMM runs in the library's CUDA kernels; this module
+turns torch tensors into device pointers, leading dimensions and a stream, and
+allocates the workspace through PyTorch's caching allocator.  There is no CPU
+fallback: without the built library (python -m paper_2602_02549_b300.build)
+or without a CUDA device, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from .build import LIB
+
+OZ2_OK, OZ2_EINVAL, OZ2_ERANGE, OZ2_ENOMEM, OZ2_ECUDA, OZ2_ETIMEOUT, OZ2_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+OZ2_ACCURATE, OZ2_FAST, OZ2_TRANS_A, OZ2_TRANS_B = 0, 1, 2, 4
+K_MAX, N_MIN, N_MAX = 131072, 2, 49
+NPHASES = 7
+PHASE_NAMES = ("stats", "quant", "scale_gemm", "exponents", "residues", "gemm", "crt")
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "oz2.h")
+
+
+class Oz2Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+        self.status = status
+
+
+class oz2_opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t),
+                ("target", ctypes.c_double),
+                ("nmax", ctypes.c_int),
+                ("n_out", ctypes.c_void_p),
+                ("mu_out", ctypes.c_void_p),
+                ("nu_out", ctypes.c_void_p),
+                ("mu_in", ctypes.c_void_p),
+                ("nu_in", ctypes.c_void_p),
+                ("w_out", ctypes.c_void_p),
+                ("phase_events", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load liboz2.so from the package directory (built in-tree)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing; build it with `python -m paper_2602_02549_b300.build`")
+        L = ctypes.CDLL(LIB)
+        i, P, sz = ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+        gemm_args = [i, i, i, P, i, P, i, P, i, i, i]
+        for name in ("oz2_gemm", "oz2_sgemm"):
+            getattr(L, name).argtypes = gemm_args
+            getattr(L, name).restype = i
+        for name in ("oz2_gemm_ex", "oz2_sgemm_ex"):
+            getattr(L, name).argtypes = gemm_args + [ctypes.POINTER(oz2_opts)]
+            getattr(L, name).restype = i
+        L.oz2_workspace_size.argtypes = [i, i, i, i, i, i]
+        L.oz2_workspace_size.restype = sz
+        L.oz2_sync.argtypes = [P]
+        L.oz2_sync.restype = i
+        L.oz2_tables.argtypes = [i, i, P, P, P, P]
+        L.oz2_tables.restype = i
+        L.oz2_check_log2f.argtypes = [P, P]
+        L.oz2_check_log2f.restype = i
+        L.oz2_status_str.argtypes = [i]
+        L.oz2_status_str.restype = ctypes.c_char_p
+        L.oz2_version.restype = i
+        _lib = L
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Names of the entry points declared in include/oz2.h."""
+    text = open(HEADER).read()
+    return re.findall(r"OZ2_API\s+[\w\s\*]+?\b(oz2_\w+)\s*\(", text)
+
+
+def status_str(status: int) -> str:
+    return lib().oz2_status_str(status).decode()
+
+
+def workspace_size(m: int, n: int, k: int, nmax: int, mode: int = 0, fp32: bool = False) -> int:
+    return int(lib().oz2_workspace_size(m, n, k, nmax, mode, int(fp32)))
+
+
+def tables(N: int, fp32: bool = False) -> dict:
+    """The library's own constant tables for N moduli (host-only)."""
+    import numpy as np
+    s1 = np.zeros(N)
+    s2 = np.zeros(N)
+    scal = np.zeros(6)
+    pp = ctypes.c_float()
+    rc = lib().oz2_tables(N, int(fp32), s1.ctypes.data, s2.ctypes.data, scal.ctypes.data, ctypes.addressof(pp))
+    if rc:
+        raise Oz2Error(rc, "oz2_tables")
+    return dict(s1=s1, s2=s2, P1=scal[0], P2=scal[1], Pinv=scal[2], g=scal[3], t=scal[4], gN=scal[5],
+                Pprime=np.float32(pp.value))
+
+
+# --------------------------------------------------------------------------- #
+# torch-facing calls
+# --------------------------------------------------------------------------- #
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _ld(t, name):
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if t.stride(1) != 1 and t.size(1) > 1:
+        raise ValueError(f"{name} must have unit column stride (row-major)")
+    return max(t.stride(0), t.size(1), 1)
+
+
+def gemm_ex(A, B, C, nmoduli: int = 0, mode: int = 0, *, target: float = 0.0, nmax: int = 0,
+            workspace=None, stream=None, n_out=None, mu_out=None, nu_out=None,
+            mu_in=None, nu_in=None, w_out=None, phase_events=None) -> int:
+    """oz2_gemm_ex / oz2_sgemm_ex on torch CUDA tensors; returns the status code.
+
+    A is m x k (or k x m with OZ2_TRANS_A), B is k x n (or n x k with
+    OZ2_TRANS_B), C is m x n; float64 calls oz2_gemm_ex, float32 oz2_sgemm_ex.
+    """
+    import torch
+    fp32 = A.dtype == torch.float32
+    if A.dtype not in (torch.float32, torch.float64) or B.dtype != A.dtype or C.dtype != A.dtype:
+        raise TypeError("A, B, C must all be float64 or all float32")
+    for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+        if not t.is_cuda:
+            raise ValueError(f"{nm} must be a CUDA tensor (no CPU path)")
+    ta, tb = bool(mode & OZ2_TRANS_A), bool(mode & OZ2_TRANS_B)
+    m = A.size(1) if ta else A.size(0)
+    k = A.size(0) if ta else A.size(1)
+    n = B.size(0) if tb else B.size(1)
+    kb = B.size(1) if tb else B.size(0)
+    if kb != k or tuple(C.shape) != (m, n):
+        raise ValueError("shape mismatch")
+    o = oz2_opts()
+    s = stream if stream is not None else torch.cuda.current_stream(A.device)
+    o.stream = ctypes.c_void_p(s.cuda_stream)
+    n_eff = nmoduli if nmoduli else (nmax if nmax else (14 if fp32 else 20))
+    if workspace is None and m > 0 and n > 0 and k > 0 and n_eff >= 2:
+        size = workspace_size(m, n, k, n_eff, mode, fp32)
+        if size:
+            workspace = torch.empty(size, dtype=torch.uint8, device=A.device)
+    if workspace is not None:
+        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    o.target = float(target)
+    o.nmax = int(nmax)
+    o.n_out, o.mu_out, o.nu_out = _ptr(n_out), _ptr(mu_out), _ptr(nu_out)
+    o.mu_in, o.nu_in, o.w_out = _ptr(mu_in), _ptr(nu_in), _ptr(w_out)
+    arr = None
+    if phase_events is not None:
+        # torch.cuda.Event handles, NPHASES + 1 of them, created with timing enabled;
+        # torch creates the CUDA event lazily at its first record
+        for e in phase_events:
+            if not e.cuda_event:
+                e.record(s)
+        arr = (ctypes.c_void_p * (NPHASES + 1))(*[ctypes.c_void_p(e.cuda_event) for e in phase_events])
+        o.phase_events = ctypes.cast(arr, ctypes.c_void_p)
+    fn = lib().oz2_sgemm_ex if fp32 else lib().oz2_gemm_ex
+    with torch.cuda.device(A.device):
+        return fn(m, n, k, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), _ptr(C), _ld(C, "C"),
+                  nmoduli, mode, ctypes.byref(o))
+
+
+def matmul(A, B, nmoduli: int = 0, *, target: float = 1e-15, nmax: int = 0, trans_a: bool = False,
+           trans_b: bool = False, fast: bool = False, out=None, **kw):
+    """C = A @ B through the Ozaki-II emulation (raises on any non-OK status)."""
+    import torch
+    m = A.size(1) if trans_a else A.size(0)
+    n = B.size(0) if trans_b else B.size(1)
+    C = out if out is not None else torch.empty((m, n), dtype=A.dtype, device=A.device)
+    mode = (OZ2_FAST if fast else 0) | (OZ2_TRANS_A if trans_a else 0) | (OZ2_TRANS_B if trans_b else 0)
+    rc = gemm_ex(A, B, C, nmoduli, mode, target=target if nmoduli == 0 else 0.0, nmax=nmax, **kw)
+    if rc:
+        raise Oz2Error(rc, "oz2 gemm")
+    return C
+
+
+def sync(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return lib().oz2_sync(ctypes.c_void_p(s.cuda_stream))
+
+
+def check_log2f(stream=None):
+    """Run the assumption-(1) diagnostic; returns (violations, max ratio)."""
+    import struct
+    import torch
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().oz2_check_log2f(ctypes.c_void_p(s.cuda_stream), ctypes.c_void_p(out.data_ptr()))
+    if rc:
+        raise Oz2Error(rc, "oz2_check_log2f")
+    s.synchronize()
+    v = out.cpu().tolist()
+    ratio = struct.unpack("<d", struct.pack("<q", v[1]))[0]
+    return v[0], ratio

@@ -1,0 +1,443 @@
+// C ABI of the Ozaki-II emulated GEMM (arXiv 2602.02549): argument checks,
+// workspace layout, constant upload and the launch sequence.  The kernels are
+// in oz2_kernels.cuh, included here so that one translation unit owns the
+// __constant__ tables.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "oz2.h"
+#include "oz2_kernels.cuh"
+
+namespace oz2 {
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------------------ per-device state
+struct DeviceState {
+    bool tables = false;
+    bool smem_attr = false;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+};
+std::mutex g_mu;
+DeviceState g_dev[kMaxDevices];
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return OZ2_OK;
+    (void)cudaGetLastError();
+    return OZ2_ECUDA;
+}
+
+// Upload the host-built tables to this device's constant memory (once).
+int ensure_device(int *dev_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+    if (dev < 0 || dev >= kMaxDevices) return OZ2_ENOTSUP;
+    *dev_out = dev;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState &st = g_dev[dev];
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return OZ2_ECUDA;
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    if (!st.tables) {
+        const Tables &T = tables();
+        DevN n64[kNMax + 1], n32[kNMax + 1];
+        for (int N = 0; N <= kNMax; N++) {
+            const NTable &a = T.n64[N], &b = T.n32[N];
+            n64[N] = DevN{a.P1, a.P2, a.Pinv, a.g, a.t, a.gN, a.Pprime, a.offset};
+            n32[N] = DevN{b.P1, b.P2, b.Pinv, b.g, b.t, b.gN, b.Pprime, b.offset};
+        }
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_n64, n64, sizeof n64);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_n32, n32, sizeof n32);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_s1i, T.s1i, sizeof T.s1i);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_s2d, T.s2d, sizeof T.s2d);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_s1f, T.s1f, sizeof T.s1f);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_p, T.mod.p, sizeof T.mod.p);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_magic, T.mod.magic, sizeof T.mod.magic);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c16, T.mod.c16, sizeof T.mod.c16);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c24, T.mod.c24, sizeof T.mod.c24);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c48, T.mod.c48, sizeof T.mod.c48);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cneg, &T.c, sizeof T.c);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_pow2, T.mod.pow2, sizeof T.mod.pow2);
+        if (e != cudaSuccess) return cuda_fail(e);
+        st.tables = true;
+    }
+    if (!st.smem_attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<EPI_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(gemm::kSmemBytes));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm<EPI_MOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(gemm::kSmemBytes));
+        if (e != cudaSuccess) return cuda_fail(e);
+        st.smem_attr = true;
+    }
+    return OZ2_OK;
+}
+
+// ------------------------------------------------------------------ workspace layout
+struct Dims {
+    int m, n, k, m_pad, n_pad, k_pad, nmax;
+};
+
+Dims make_dims(int m, int n, int k, int nmax) {
+    Dims d;
+    d.m = m; d.n = n; d.k = k;
+    d.m_pad = int(round_up(size_t(m), gemm::BM));
+    d.n_pad = int(round_up(size_t(n), gemm::BN));
+    d.k_pad = int(round_up(size_t(k), gemm::BK));
+    d.nmax = nmax;
+    return d;
+}
+
+struct Layout {
+    // the block up to zero_end is cleared at the start of every call
+    size_t hmaxA, hmaxB, cmax_row, cmax_col, red, zero_end;
+    size_t rmaxA, rmaxB, rsumA, rsumB, mu, nu, ndev, resA, resB, W, total;
+};
+
+Layout make_layout(const Dims &d) {
+    Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = round_up(o + bytes, 256); return at; };
+    L.hmaxA = take(sizeof(unsigned long long) * size_t(d.k_pad));
+    L.hmaxB = take(sizeof(unsigned long long) * size_t(d.k_pad));
+    L.cmax_row = take(sizeof(int) * size_t(d.m_pad));
+    L.cmax_col = take(sizeof(int) * size_t(d.n_pad));
+    L.red = take(sizeof(unsigned long long) * 8);
+    L.zero_end = o;
+    L.rmaxA = take(sizeof(unsigned long long) * size_t(d.m_pad));
+    L.rmaxB = take(sizeof(unsigned long long) * size_t(d.n_pad));
+    L.rsumA = take(sizeof(double) * size_t(d.m_pad));
+    L.rsumB = take(sizeof(double) * size_t(d.n_pad));
+    L.mu = take(sizeof(int32_t) * size_t(d.m_pad));
+    L.nu = take(sizeof(int32_t) * size_t(d.n_pad));
+    L.ndev = take(sizeof(int) * 4);
+    L.resA = take(size_t(2) * size_t(d.nmax) * size_t(d.m_pad) * size_t(d.k_pad));
+    L.resB = take(size_t(2) * size_t(d.nmax) * size_t(d.n_pad) * size_t(d.k_pad));
+    L.W = take(size_t(d.nmax) * size_t(d.m_pad) * size_t(d.n_pad));
+    L.total = o;
+    return L;
+}
+
+// ------------------------------------------------------------------ tensor maps
+int encode_bf16_2d(CUtensorMap *tm, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 2};
+    const cuuint32_t box[2] = {uint32_t(gemm::BK), box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? OZ2_OK : OZ2_ECUDA;
+}
+
+int grid_rows(int rows) { return std::max(1, std::min(rows, 65535)); }
+
+// ------------------------------------------------------------------ launches
+template <typename T>
+int launch_stats(const Operand<T> &X, int k, unsigned long long *row_max, double *row_sum,
+                 unsigned long long *h_max, cudaStream_t st) {
+    if (X.kcontig) {
+        const int blocks = (X.R + kStatsRows - 1) / kStatsRows;
+        k_stats_kc<T><<<blocks, 256, 0, st>>>(X, k, row_max, row_sum, h_max);
+    } else {
+        const int blocks = (X.R + 31) / 32;
+        k_stats_rc<T><<<blocks, 256, 0, st>>>(X, k, row_max, row_sum, h_max);
+    }
+    return cuda_fail(cudaGetLastError());
+}
+
+template <int MODE, typename T>
+int launch_planes(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
+    if (X.kcontig) {
+        dim3 grid((a.k_pad / 8 + 255) / 256, grid_rows(a.R_pad));
+        k_planes_kc<MODE, T><<<grid, 256, 0, st>>>(X, a);
+    } else {
+        dim3 grid(a.k_pad / 64, a.R_pad / 64);
+        k_planes_rc<MODE, T><<<grid, 256, 0, st>>>(X, a);
+    }
+    return cuda_fail(cudaGetLastError());
+}
+
+template <int EPI>
+int launch_gemm(const CUtensorMap &tA, const CUtensorMap &tB, const GemmArgs &g, int planes, cudaStream_t st) {
+    dim3 grid(g.n_pad / gemm::BN, g.m_pad / gemm::BM, planes);
+    k_gemm<EPI><<<grid, gemm::kThreads, gemm::kSmemBytes, st>>>(tA, tB, g);
+    return cuda_fail(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ validation
+int validate(int m, int n, int k, const void *A, int lda, const void *B, int ldb, const void *C, int ldc,
+             int nmoduli, int mode, const oz2_opts *o) {
+    if (m < 1 || n < 1 || k < 1) return OZ2_EINVAL;
+    if (!A || !B || !C) return OZ2_EINVAL;
+    if (mode & ~(OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B)) return OZ2_EINVAL;
+    const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
+    if (lda < (ta ? m : k) || ldb < (tb ? k : n) || ldc < n) return OZ2_EINVAL;
+    if (nmoduli != 0 && (nmoduli < OZ2_N_MIN || nmoduli > OZ2_N_MAX)) return OZ2_EINVAL;
+    if (nmoduli == 0) {
+        if (!o || !(o->target > 0.0)) return OZ2_EINVAL;
+        if (o->nmax != 0 && (o->nmax < OZ2_N_MIN || o->nmax > OZ2_N_MAX)) return OZ2_EINVAL;
+    }
+    if (o && ((o->mu_in == nullptr) != (o->nu_in == nullptr))) return OZ2_EINVAL;
+    if (o && o->mu_in && nmoduli == 0) return OZ2_EINVAL;
+    if (k > OZ2_K_MAX) return OZ2_ERANGE;
+    return OZ2_OK;
+}
+
+int resolve_nmax(int nmoduli, const oz2_opts *o, bool fp32) {
+    if (nmoduli) return nmoduli;
+    return (o && o->nmax) ? o->nmax : (fp32 ? 14 : 20);
+}
+
+// ------------------------------------------------------------------ the pipeline
+template <typename T>
+int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, int nmoduli, int mode,
+        const oz2_opts *o) {
+    constexpr bool fp32 = sizeof(T) == 4;
+    int rc = validate(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o);
+    if (rc) return rc;
+    if (mode & OZ2_FAST) return OZ2_ENOTSUP;
+    const int nmax = resolve_nmax(nmoduli, o, fp32);
+    const Dims d = make_dims(m, n, k, nmax);
+    const Layout L = make_layout(d);
+    int dev = 0;
+    if ((rc = ensure_device(&dev))) return rc;
+    cudaStream_t st = o ? static_cast<cudaStream_t>(o->stream) : nullptr;
+
+    uint8_t *ws = nullptr;
+    if (o && o->workspace) {
+        if (o->workspace_bytes < L.total) return OZ2_ENOMEM;
+        if (reinterpret_cast<uintptr_t>(o->workspace) & 255u) return OZ2_EINVAL;
+        ws = static_cast<uint8_t *>(o->workspace);
+    } else {
+        std::lock_guard<std::mutex> lk(g_mu);
+        DeviceState &s = g_dev[dev];
+        if (s.ws_bytes < L.total) {
+            if (s.ws) {
+                cudaDeviceSynchronize();
+                cudaFree(s.ws);
+                s.ws = nullptr;
+                s.ws_bytes = 0;
+            }
+            if (cudaMalloc(&s.ws, L.total) != cudaSuccess) return cuda_fail(cudaErrorMemoryAllocation);
+            s.ws_bytes = L.total;
+        }
+        ws = static_cast<uint8_t *>(s.ws);
+    }
+    auto at = [&](size_t off) { return ws + off; };
+    auto *hmaxA = reinterpret_cast<unsigned long long *>(at(L.hmaxA));
+    auto *hmaxB = reinterpret_cast<unsigned long long *>(at(L.hmaxB));
+    auto *cmax_row = reinterpret_cast<int *>(at(L.cmax_row));
+    auto *cmax_col = reinterpret_cast<int *>(at(L.cmax_col));
+    auto *red = reinterpret_cast<unsigned long long *>(at(L.red));
+    auto *rmaxA = reinterpret_cast<unsigned long long *>(at(L.rmaxA));
+    auto *rmaxB = reinterpret_cast<unsigned long long *>(at(L.rmaxB));
+    auto *rsumA = reinterpret_cast<double *>(at(L.rsumA));
+    auto *rsumB = reinterpret_cast<double *>(at(L.rsumB));
+    auto *mu = reinterpret_cast<int32_t *>(at(L.mu));
+    auto *nu = reinterpret_cast<int32_t *>(at(L.nu));
+    auto *ndev = reinterpret_cast<int *>(at(L.ndev));
+    auto *resA = reinterpret_cast<__nv_bfloat16 *>(at(L.resA));
+    auto *resB = reinterpret_cast<__nv_bfloat16 *>(at(L.resB));
+    auto *W = reinterpret_cast<int8_t *>(at(L.W));
+
+    const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
+    // A's logical rows are the rows of A; B's are the columns of B.
+    const Operand<T> opA{A, long(lda), m, ta ? 0 : 1};
+    const Operand<T> opB{B, long(ldb), n, tb ? 1 : 0};
+    const long planeA = long(d.m_pad) * d.k_pad, planeB = long(d.n_pad) * d.k_pad;
+
+    CUtensorMap tA, tB;
+    if ((rc = encode_bf16_2d(&tA, resA, uint64_t(nmax) * d.m_pad, uint64_t(d.k_pad), gemm::BM))) return rc;
+    if ((rc = encode_bf16_2d(&tB, resB, uint64_t(nmax) * d.n_pad, uint64_t(d.k_pad), gemm::BN))) return rc;
+
+    const bool inject = o && o->mu_in;
+    const int32_t *mu_use = inject ? o->mu_in : mu;
+    const int32_t *nu_use = inject ? o->nu_in : nu;
+
+    auto mark = [&](int phase) -> int {
+        if (!o || !o->phase_events) return OZ2_OK;
+        return cuda_fail(cudaEventRecord(static_cast<cudaEvent_t>(o->phase_events[phase]), st));
+    };
+    if ((rc = mark(OZ2_PHASE_STATS))) return rc;
+    if ((rc = cuda_fail(cudaMemsetAsync(ws, 0, L.zero_end, st)))) return rc;
+    if (!inject) {
+        // Algorithm 2: mu', nu' (and the N-rule inputs)
+        if ((rc = launch_stats(opA, k, rmaxA, rsumA, hmaxA, st))) return rc;
+        if ((rc = launch_stats(opB, k, rmaxB, rsumB, hmaxB, st))) return rc;
+        // Abar, Bbar
+        if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
+        PlaneArgs qa{resA, planeA, d.m_pad, k, d.k_pad, rmaxA, nullptr, nullptr};
+        PlaneArgs qb{resB, planeB, d.n_pad, k, d.k_pad, rmaxB, nullptr, nullptr};
+        if ((rc = launch_planes<MODE_QUANT>(opA, qa, st))) return rc;
+        if ((rc = launch_planes<MODE_QUANT>(opB, qb, st))) return rc;
+        // Cbar = Abar Bbar: row and column maxima only
+        if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
+        GemmArgs g{d.m_pad, d.n_pad, d.k_pad / gemm::BK, nullptr, nullptr, 0, cmax_row, cmax_col};
+        if ((rc = launch_gemm<EPI_MAX>(tA, tB, g, 1, st))) return rc;
+        // the N rule, then mu and nu
+        if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
+        if (nmoduli == 0) {
+            BoundArgs ba{m, n, k, rmaxA, rmaxB, hmaxA, hmaxB, rsumA, rsumB, cmax_row, cmax_col, red};
+            k_bound_reduce<<<148, 256, 0, st>>>(ba);
+            if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+        }
+        k_choose_n<<<1, 32, 0, st>>>(red, k, nmoduli ? 0.0 : o->target, nmax, nmoduli, fp32 ? 1 : 0, ndev,
+                                     o ? o->n_out : nullptr);
+        if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+        k_mu_nu<<<std::min(1184, (m + n + 255) / 256), 256, 0, st>>>(
+            m, n, rmaxA, rmaxB, cmax_row, cmax_col, ndev, fp32 ? 1 : 0, mu, nu, o ? o->mu_out : nullptr,
+            o ? o->nu_out : nullptr);
+        if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+    } else {
+        for (int ph = OZ2_PHASE_QUANT; ph <= OZ2_PHASE_EXPONENTS; ph++)
+            if ((rc = mark(ph))) return rc;
+        k_choose_n<<<1, 32, 0, st>>>(red, k, 0.0, nmax, nmoduli, fp32 ? 1 : 0, ndev, o->n_out);
+        if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+    }
+    // Algorithm 3: residues, N products, W_l
+    if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
+    PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, nullptr, mu_use, ndev};
+    PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, nullptr, nu_use, ndev};
+    if ((rc = launch_planes<MODE_RESID>(opA, ra, st))) return rc;
+    if ((rc = launch_planes<MODE_RESID>(opB, rb, st))) return rc;
+    const long w_plane = long(d.m_pad) * d.n_pad;
+    if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
+    GemmArgs g{d.m_pad, d.n_pad, d.k_pad / gemm::BK, ndev, W, w_plane, nullptr, nullptr};
+    if ((rc = launch_gemm<EPI_MOD>(tA, tB, g, nmax, st))) return rc;
+    // CRT and inverse scaling
+    if ((rc = mark(OZ2_PHASE_CRT))) return rc;
+    {
+        dim3 grid((n + 1023) / 1024, grid_rows(m));
+        if constexpr (fp32)
+            k_crt<T, 32><<<grid, 256, 0, st>>>(W, w_plane, d.n_pad, ndev, mu_use, nu_use, C, long(ldc), m, n);
+        else
+            k_crt<T, 64><<<grid, 256, 0, st>>>(W, w_plane, d.n_pad, ndev, mu_use, nu_use, C, long(ldc), m, n);
+        if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+    }
+    if ((rc = mark(OZ2_NPHASES))) return rc;
+    if (o && o->w_out) {
+        // export W_l (test aid): plane l, m x n row-major, from the padded layout
+        for (int l = 0; l < nmax; l++) {
+            rc = cuda_fail(cudaMemcpy2DAsync(o->w_out + size_t(l) * m * n, size_t(n), W + size_t(l) * w_plane,
+                                             size_t(d.n_pad), size_t(n), size_t(m), cudaMemcpyDeviceToDevice, st));
+            if (rc) return rc;
+        }
+    }
+    return OZ2_OK;
+}
+
+}  // namespace
+}  // namespace oz2
+
+using namespace oz2;
+
+extern "C" {
+
+int oz2_gemm_ex(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+                int nmoduli, int mode, const oz2_opts *opts) {
+    return run<double>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, opts);
+}
+
+int oz2_gemm(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+             int nmoduli, int mode) {
+    return run<double>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, nullptr);
+}
+
+int oz2_sgemm_ex(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                 int nmoduli, int mode, const oz2_opts *opts) {
+    return run<float>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, opts);
+}
+
+int oz2_sgemm(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+              int nmoduli, int mode) {
+    return run<float>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, nullptr);
+}
+
+size_t oz2_workspace_size(int m, int n, int k, int nmax, int mode, int fp32) {
+    (void)mode;
+    (void)fp32;
+    if (m < 1 || n < 1 || k < 1 || k > OZ2_K_MAX || nmax < OZ2_N_MIN || nmax > OZ2_N_MAX) return 0;
+    return make_layout(make_dims(m, n, k, nmax)).total;
+}
+
+int oz2_sync(void *stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e);
+    int s = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&s, g_status, sizeof s) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+    if (s) {
+        if (cudaMemcpyToSymbol(g_status, &zero, sizeof zero) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+        return OZ2_ETIMEOUT;
+    }
+    return OZ2_OK;
+}
+
+int oz2_tables(int N, int fp32, double *s1, double *s2, double *scal, float *pprime) {
+    if (N < OZ2_N_MIN || N > OZ2_N_MAX || !s1 || !s2 || !scal || !pprime) return OZ2_EINVAL;
+    const Tables &T = tables();
+    const NTable &t = fp32 ? T.n32[N] : T.n64[N];
+    for (int l = 0; l < N; l++) {
+        s1[l] = fp32 ? T.s1f[t.offset + l] : T.s1d[t.offset + l];
+        s2[l] = fp32 ? 0.0 : T.s2d[t.offset + l];
+    }
+    scal[0] = t.P1;
+    scal[1] = t.P2;
+    scal[2] = t.Pinv;
+    scal[3] = fp32 ? 0.0 : t.g;
+    scal[4] = t.t;
+    scal[5] = t.gN;
+    *pprime = t.Pprime;
+    return OZ2_OK;
+}
+
+int oz2_check_log2f(void *stream, unsigned long long *dev_out) {
+    if (!dev_out) return OZ2_EINVAL;
+    int dev = 0, rc = ensure_device(&dev);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float lo = 1.0f, hi = 536870912.0f;   // 2^29
+    uint32_t b0, b1;
+    std::memcpy(&b0, &lo, 4);
+    std::memcpy(&b1, &hi, 4);
+    rc = cuda_fail(cudaMemsetAsync(dev_out, 0, 2 * sizeof(unsigned long long), st));
+    if (rc) return rc;
+    k_log2f_check<<<148 * 8, 256, 0, st>>>(b0, b1 - b0 + 1, dev_out);
+    return cuda_fail(cudaGetLastError());
+}
+
+const char *oz2_status_str(int s) {
+    switch (s) {
+    case OZ2_OK: return "OZ2_OK";
+    case OZ2_EINVAL: return "OZ2_EINVAL: invalid argument";
+    case OZ2_ERANGE: return "OZ2_ERANGE: k exceeds 2^17";
+    case OZ2_ENOMEM: return "OZ2_ENOMEM: workspace too small";
+    case OZ2_ECUDA: return "OZ2_ECUDA: CUDA call failed";
+    case OZ2_ETIMEOUT: return "OZ2_ETIMEOUT: a device-side wait gave up";
+    case OZ2_ENOTSUP: return "OZ2_ENOTSUP: not supported";
+    default: return "unknown status";
+    }
+}
+
+int oz2_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,784 @@
+// Device code of the Ozaki-II path (arXiv 2602.02549) for sm_103a.
+//
+// Included once, by oz2_api.cu, so that the __constant__ tables below live in a
+// single translation unit with every kernel that reads them.
+//
+//   k_stats_kc / k_stats_rc   Algorithm 2 inputs: max |x| per row of A (per
+//                             column of B) -> mu', nu'; |A| v, v^T |B| and
+//                             per-k maxima for the N rule (one HBM read)
+//   k_planes<QUANT>           Abar = ceil(2^mu' |A|), Bbar likewise, as BF16
+//   k_gemm<EPI_MAX>           Cbar = Abar Bbar on tcgen05, keeping only the row
+//                             and column maxima of Cbar
+//   k_bound_reduce, k_choose_n, k_mu_nu
+//                             Dbar, e, f, mu, nu (Algorithm 2) and the N rule
+//   k_planes<RESID>           A'_l = mod(trunc(2^mu A), p_l) as BF16, N planes
+//   k_gemm<EPI_MOD>           C'_l = A'_l B'_l on tcgen05, W_l = mod(C'_l, p_l)
+//   k_crt                     C'(1), C'(2), Q, C'' (Algorithm 3) and the
+//                             inverse scaling of Algorithm 1
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "oz2_ptx.cuh"
+#include "oz2_tables.h"
+
+namespace oz2 {
+
+// ============================================================= constant tables
+struct DevN {
+    double P1, P2, Pinv, g, t, gN;
+    float Pprime;
+    int offset;
+};
+
+__constant__ DevN c_n64[kNMax + 1];
+__constant__ DevN c_n32[kNMax + 1];
+__constant__ long long c_s1i[kPackedLen];
+__constant__ double c_s2d[kPackedLen];
+__constant__ double c_s1f[kPackedLen];
+__constant__ int c_p[kNMax];
+__constant__ uint32_t c_magic[kNMax];
+__constant__ uint32_t c_c16[kNMax];
+__constant__ uint32_t c_c24[kNMax];
+__constant__ uint32_t c_c48[kNMax];
+__constant__ float c_cneg;                 // single_down(-0.5/(1-4 u32))
+__device__ uint8_t g_pow2[kNMax][256];     // 2^E mod p_l
+
+// Device status word: bit 0 = a bounded wait expired.
+__device__ int g_status;
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
+
+// ============================================================= small helpers
+__device__ __forceinline__ uint32_t mod_small(uint32_t t, uint32_t p, uint32_t magic) {
+    // t < 2^24, p <= 256: floor(t/p) = umulhi(t, ceil(2^32/p))
+    return t - __umulhi(t, magic) * p;
+}
+
+// floor(log2 x) of a positive double given by its bits.
+__device__ __forceinline__ int floor_log2_bits(uint64_t b) {
+    int ex = int(b >> 52);
+    if (ex) return ex - 1023;
+    uint64_t m = b & ((1ull << 52) - 1);
+    return -1074 + (63 - __clzll((long long)m));
+}
+
+template <typename T> __device__ __forceinline__ double absd(T x) { return fabs(double(x)); }
+
+// x = (-1)^neg * M * 2^e with M an integer (< 2^53), from the bits of x.
+struct Split {
+    uint64_t M;
+    int e;
+    bool neg;
+};
+__device__ __forceinline__ Split split_bits(double x) {
+    uint64_t b = (uint64_t)__double_as_longlong(x);
+    Split s;
+    s.neg = (b >> 63) != 0;
+    int ex = int((b >> 52) & 0x7FF);
+    uint64_t man = b & ((1ull << 52) - 1);
+    if (ex == 0) { s.M = man; s.e = -1074; }
+    else { s.M = man | (1ull << 52); s.e = ex - 1075; }
+    if (ex == 0x7FF) s.M = 0;                  // non-finite: precondition violated
+    return s;
+}
+__device__ __forceinline__ Split split_bits(float x) {
+    uint32_t b = __float_as_uint(x);
+    Split s;
+    s.neg = (b >> 31) != 0;
+    int ex = int((b >> 23) & 0xFF);
+    uint32_t man = b & ((1u << 23) - 1);
+    if (ex == 0) { s.M = man; s.e = -149; }
+    else { s.M = man | (1u << 23); s.e = ex - 150; }
+    if (ex == 0xFF) s.M = 0;
+    return s;
+}
+
+// Algorithm 2: xbar = ceil(2^shift |x|), 0 <= xbar <= 64 for shift = 5 - floor(log2 max).
+template <typename T>
+__device__ __forceinline__ uint32_t ceil_scaled_abs(T x, int shift) {
+    Split s = split_bits(x);
+    if (s.M == 0) return 0;
+    int sh = s.e + shift;
+    if (sh >= 0) return sh > 10 ? 127u : uint32_t(s.M << sh);
+    int r = -sh;
+    if (r >= 64) return 1;
+    uint64_t q = s.M >> r;
+    return uint32_t(q + ((s.M & ((1ull << r) - 1)) != 0));
+}
+
+// Algorithm 2: x' = trunc(2^shift x) = (-1)^neg * M * 2^E, E >= 0.
+struct Int {
+    uint64_t M;
+    int E;
+    bool neg;
+};
+template <typename T>
+__device__ __forceinline__ Int trunc_scaled(T x, int shift) {
+    Split s = split_bits(x);
+    Int v;
+    v.neg = s.neg;
+    int sh = s.e + shift;
+    if (sh >= 0) { v.M = s.M; v.E = sh; }
+    else { v.M = (-sh >= 64) ? 0 : (s.M >> (-sh)); v.E = 0; }
+    return v;
+}
+
+// mod(x', p_l) of Algorithm 3 (balanced; p = 256 stores class 128 as -128).
+__device__ __forceinline__ int residue(const Int &v, int l, const uint8_t (*pow2)[256]) {
+    if (v.M == 0) return 0;
+    if (l == 0) {                              // p = 256: the low byte
+        if (v.E >= 8) return 0;
+        uint32_t lo = (uint32_t(v.M) << v.E) & 255u;
+        if (v.neg) lo = (256u - lo) & 255u;
+        return int(int8_t(lo));
+    }
+    const uint32_t p = uint32_t(c_p[l]), mg = c_magic[l];
+    const uint32_t m0 = uint32_t(v.M & 0xFFFFFFu), m1 = uint32_t((v.M >> 24) & 0xFFFFFFu),
+                   m2 = uint32_t(v.M >> 48);
+    uint32_t t = mod_small(m0, p, mg) + mod_small(m1, p, mg) * c_c24[l] + m2 * c_c48[l];
+    uint32_t r = mod_small(t, p, mg);
+    r = mod_small(r * pow2[l][v.E > 255 ? 255 : v.E], p, mg);
+    int sr = int(r) > int(p >> 1) ? int(r) - int(p) : int(r);
+    return v.neg ? -sr : sr;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(int a, int b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(float(a), float(b));
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// ============================================================= operand views
+// Logical matrix X[r][h], r < R, h < k: A rows (r = i) or B columns (r = j).
+// kcontig: element at ptr[r*ld + h]; else at ptr[h*ld + r].
+template <typename T>
+struct Operand {
+    const T *ptr;
+    long ld;
+    int R;
+    int kcontig;
+};
+
+// ============================================================= stats
+// Per logical row r: bits of max |x| (row_max) and the FP64 sum of |x|
+// (row_sum, a fixed summation order); per h: atomicMax of |x| bits (h_max).
+constexpr int kStatsRows = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_stats_kc(Operand<T> X, int k, unsigned long long *row_max,
+                                                  double *row_sum, unsigned long long *h_max) {
+    const int r0 = blockIdx.x * kStatsRows;
+    double sum[kStatsRows];
+    unsigned long long mx[kStatsRows];
+#pragma unroll
+    for (int i = 0; i < kStatsRows; i++) { sum[i] = 0.0; mx[i] = 0ull; }
+    for (int h = threadIdx.x; h < k; h += 256) {
+        unsigned long long hm = 0;
+#pragma unroll
+        for (int i = 0; i < kStatsRows; i++) {
+            if (r0 + i < X.R) {
+                double v = absd(X.ptr[(long)(r0 + i) * X.ld + h]);
+                unsigned long long b = (unsigned long long)__double_as_longlong(v);
+                sum[i] += v;
+                mx[i] = b > mx[i] ? b : mx[i];
+                hm = b > hm ? b : hm;
+            }
+        }
+        if (hm) atomicMax(h_max + h, hm);
+    }
+    __shared__ double ssum[8][kStatsRows];
+    __shared__ unsigned long long smax[8][kStatsRows];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kStatsRows; i++) {
+        double s = sum[i];
+        unsigned long long m = mx[i];
+        for (int o = 16; o; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            unsigned long long mo = __shfl_xor_sync(0xffffffffu, m, o);
+            m = mo > m ? mo : m;
+        }
+        if (lane == 0) { ssum[w][i] = s; smax[w][i] = m; }
+    }
+    __syncthreads();
+    if (threadIdx.x < kStatsRows && r0 + threadIdx.x < X.R) {
+        double s = 0.0;
+        unsigned long long m = 0;
+        for (int ww = 0; ww < 8; ww++) {
+            s += ssum[ww][threadIdx.x];
+            m = smax[ww][threadIdx.x] > m ? smax[ww][threadIdx.x] : m;
+        }
+        row_sum[r0 + threadIdx.x] = s;
+        row_max[r0 + threadIdx.x] = m;
+    }
+}
+
+// R-contiguous storage: 32 logical rows per block, 8 phases over h.
+template <typename T>
+__global__ void __launch_bounds__(256) k_stats_rc(Operand<T> X, int k, unsigned long long *row_max,
+                                                  double *row_sum, unsigned long long *h_max) {
+    const int lane = threadIdx.x & 31, ph = threadIdx.x >> 5;
+    const int r = blockIdx.x * 32 + lane;
+    const bool live = r < X.R;
+    double s = 0.0;
+    unsigned long long m = 0;
+    for (int h = ph; h < k; h += 8) {
+        double v = live ? absd(X.ptr[(long)h * X.ld + r]) : 0.0;
+        unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        s += v;
+        m = b > m ? b : m;
+        unsigned long long hm = b;
+        for (int o = 16; o; o >>= 1) {
+            unsigned long long t = __shfl_xor_sync(0xffffffffu, hm, o);
+            hm = t > hm ? t : hm;
+        }
+        if (lane == 0 && hm) atomicMax(h_max + h, hm);
+    }
+    __shared__ double ssum[8][32];
+    __shared__ unsigned long long smax[8][32];
+    ssum[ph][lane] = s;
+    smax[ph][lane] = m;
+    __syncthreads();
+    if (ph == 0 && live) {
+        double t = 0.0;
+        unsigned long long mm = 0;
+        for (int q = 0; q < 8; q++) {
+            t += ssum[q][lane];
+            mm = smax[q][lane] > mm ? smax[q][lane] : mm;
+        }
+        row_sum[r] = t;
+        row_max[r] = mm;
+    }
+}
+
+// ============================================================= planes
+// MODE_QUANT: plane 0 = BF16(ceil(2^shift |x|)), shift_r = mu'_r.
+// MODE_RESID: planes l < N = BF16(mod(trunc(2^shift x), p_l)), shift_r = mu_r.
+// Output: out[l*plane + r*k_pad + h], K-major, zeros in the padding.
+enum { MODE_QUANT = 0, MODE_RESID = 1 };
+
+struct PlaneArgs {
+    __nv_bfloat16 *out;
+    long plane;          // elements between planes
+    int R_pad, k, k_pad;
+    const unsigned long long *row_max;   // MODE_QUANT: shift = 5 - floor(log2 max)
+    const int32_t *shift;                 // MODE_RESID: mu or nu
+    const int *n_dev;                     // MODE_RESID: number of planes
+};
+
+__device__ __forceinline__ int quant_shift(const unsigned long long *row_max, int r) {
+    unsigned long long b = row_max[r];
+    return b ? 5 - floor_log2_bits(b) : 0;     // zero row: mu' = 0
+}
+
+template <int MODE, typename T>
+__device__ __forceinline__ void emit8(const PlaneArgs &a, const T (&x)[8], int shift, int r, int h0,
+                                      int N, const uint8_t (*pow2)[256]) {
+    __nv_bfloat16 *base = a.out + (long)r * a.k_pad + h0;
+    if (MODE == MODE_QUANT) {
+        uint4 v;
+        v.x = pack_bf16x2(ceil_scaled_abs(x[0], shift), ceil_scaled_abs(x[1], shift));
+        v.y = pack_bf16x2(ceil_scaled_abs(x[2], shift), ceil_scaled_abs(x[3], shift));
+        v.z = pack_bf16x2(ceil_scaled_abs(x[4], shift), ceil_scaled_abs(x[5], shift));
+        v.w = pack_bf16x2(ceil_scaled_abs(x[6], shift), ceil_scaled_abs(x[7], shift));
+        *reinterpret_cast<uint4 *>(base) = v;
+    } else {
+        Int iv[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) iv[e] = trunc_scaled(x[e], shift);
+        for (int l = 0; l < N; l++) {
+            uint4 v;
+            v.x = pack_bf16x2(residue(iv[0], l, pow2), residue(iv[1], l, pow2));
+            v.y = pack_bf16x2(residue(iv[2], l, pow2), residue(iv[3], l, pow2));
+            v.z = pack_bf16x2(residue(iv[4], l, pow2), residue(iv[5], l, pow2));
+            v.w = pack_bf16x2(residue(iv[6], l, pow2), residue(iv[7], l, pow2));
+            *reinterpret_cast<uint4 *>(base + (long)l * a.plane) = v;
+        }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void zero8(const PlaneArgs &a, int r, int h0, int N) {
+    __nv_bfloat16 *base = a.out + (long)r * a.k_pad + h0;
+    const int np = MODE == MODE_QUANT ? 1 : N;
+    for (int l = 0; l < np; l++) *reinterpret_cast<uint4 *>(base + (long)l * a.plane) = make_uint4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ void load_pow2(uint8_t (*s)[256], int N) {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(g_pow2);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(s);
+    for (int i = threadIdx.x; i < N * 64; i += blockDim.x) dst[i] = src[i];
+}
+
+// K-contiguous source: one row per blockIdx.y (grid-stride), 8 h per thread.
+template <int MODE, typename T>
+__global__ void __launch_bounds__(256) k_planes_kc(Operand<T> X, PlaneArgs a) {
+    __shared__ __align__(16) uint8_t pow2[MODE == MODE_RESID ? kNMax : 1][256];
+    const int N = MODE == MODE_RESID ? *a.n_dev : 1;
+    if (MODE == MODE_RESID) load_pow2(pow2, N);
+    __syncthreads();
+    const int h0 = (blockIdx.x * 256 + threadIdx.x) * 8;
+    if (h0 >= a.k_pad) return;
+    for (int r = blockIdx.y; r < a.R_pad; r += gridDim.y) {
+        if (r >= X.R) { zero8<MODE>(a, r, h0, N); continue; }
+        const int shift = MODE == MODE_QUANT ? quant_shift(a.row_max, r) : a.shift[r];
+        T x[8];
+        const T *src = X.ptr + (long)r * X.ld + h0;
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[e] = (h0 + e < a.k) ? src[e] : T(0);
+        emit8<MODE>(a, x, shift, r, h0, N, pow2);
+    }
+}
+
+// R-contiguous source: 64 (h) x 64 (r) tiles transposed through shared memory.
+template <int MODE, typename T>
+__global__ void __launch_bounds__(256) k_planes_rc(Operand<T> X, PlaneArgs a) {
+    __shared__ __align__(16) uint8_t pow2[MODE == MODE_RESID ? kNMax : 1][256];
+    __shared__ T tile[64][65];
+    const int N = MODE == MODE_RESID ? *a.n_dev : 1;
+    if (MODE == MODE_RESID) load_pow2(pow2, N);
+    const int h_base = blockIdx.x * 64, r_base = blockIdx.y * 64;
+    {
+        const int rr = threadIdx.x & 63;
+        const int r = r_base + rr;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int hh = (threadIdx.x >> 6) + 4 * i;
+            const int h = h_base + hh;
+            tile[hh][rr] = (r < X.R && h < a.k) ? X.ptr[(long)h * X.ld + r] : T(0);
+        }
+    }
+    __syncthreads();
+    const int rr = threadIdx.x >> 2, hq = threadIdx.x & 3;
+    const int r = r_base + rr;
+    if (r >= a.R_pad) return;
+    const bool live = r < X.R;
+    const int shift = !live ? 0 : (MODE == MODE_QUANT ? quant_shift(a.row_max, r) : a.shift[r]);
+#pragma unroll
+    for (int g = 0; g < 2; g++) {
+        const int hh0 = hq * 16 + g * 8;
+        const int h0 = h_base + hh0;
+        if (h0 >= a.k_pad) continue;
+        if (!live) { zero8<MODE>(a, r, h0, N); continue; }
+        T x[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[e] = tile[hh0 + e][rr];
+        emit8<MODE>(a, x, shift, r, h0, N, pow2);
+    }
+}
+
+// ============================================================= tcgen05 GEMM
+namespace gemm {
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int SEG_KB = 16;                       // 1024 K per FP32-exact segment
+constexpr int kThreads = 320;                    // w0 TMA, w1 MMA, w2..w9 epilogue
+constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t kSmemBytes = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t IDESC = ptx::idesc_bf16_f32<BM, BN>();
+}  // namespace gemm
+
+enum { EPI_MAX = 0, EPI_MOD = 1 };
+
+struct GemmArgs {
+    int m_pad, n_pad, kb_total;
+    const int *n_dev;          // EPI_MOD: planes l >= *n_dev exit at once
+    int8_t *W;                 // EPI_MOD: W[l*w_plane + row*n_pad + col]
+    long w_plane;
+    int *row_max, *col_max;    // EPI_MAX
+};
+
+__device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = ptx::globaltimer();
+    while (true) {
+        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (ptx::globaltimer() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            atomicOr(&g_status, 1);
+            return false;
+        }
+    }
+}
+
+// Every lane waits (each gets the barrier's acquire); the warp proceeds only if
+// all lanes saw the phase complete, so .sync.aligned tcgen05 instructions that
+// follow are always executed by the whole warp.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    const bool ok = bounded_wait(bar, parity, abort_flag);
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
+// One CTA computes a 128 x 256 tile of X_l Y_l^T (X_l, Y_l: BF16, K-major,
+// integer-valued), l = blockIdx.z.  K runs in segments of <= 1024 elements:
+// each segment starts a fresh FP32 accumulator in TMEM, so every partial sum
+// is an integer of magnitude <= 1024 * 2^14 = 2^24 and therefore exact; the
+// epilogue warps turn each segment into INT32 and add it up (double-buffered
+// accumulators let the next segment's MMAs overlap the read-out).
+template <int EPI>
+__global__ void __launch_bounds__(gemm::kThreads, 1)
+    k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs args) {
+    using namespace gemm;
+    const int l = blockIdx.z;
+    if (EPI == EPI_MOD && args.n_dev && l >= *args.n_dev) return;
+
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = ptx::smem_addr(smem_raw);
+    const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+    uint8_t *smem = smem_raw + pad;
+    const uint32_t sbase = raw + pad;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    auto bar_full = [&](int s) { return ptx::smem_addr(bars + s); };
+    auto bar_empty = [&](int s) { return ptx::smem_addr(bars + STAGES + s); };
+    auto bar_accf = [&](int b) { return ptx::smem_addr(bars + 2 * STAGES + b); };
+    auto bar_acce = [&](int b) { return ptx::smem_addr(bars + 2 * STAGES + 2 + b); };
+    auto sA = [&](int s) { return sbase + uint32_t(s) * STAGE_BYTES; };
+    auto sB = [&](int s) { return sbase + uint32_t(s) * STAGE_BYTES + A_BYTES; };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) { ptx::mbar_init(bar_full(s), 1); ptx::mbar_init(bar_empty(s), 1); }
+        for (int b = 0; b < 2; b++) { ptx::mbar_init(bar_accf(b), 1); ptx::mbar_init(bar_acce(b), 8); }
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+        ptx::tma_prefetch_desc(&tmA);
+        ptx::tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc<512>(ptx::smem_addr(tmem_slot));
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int kb_total = args.kb_total;
+    const int nseg = (kb_total + SEG_KB - 1) / SEG_KB;
+    const int row_a = l * args.m_pad + blockIdx.y * BM;
+    const int row_b = l * args.n_pad + blockIdx.x * BN;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < kb_total; kb++) {
+                const int s = kb % STAGES;
+                const uint32_t ph = uint32_t(kb / STAGES) & 1u;
+                if (kb >= STAGES && !bounded_wait(bar_empty(s), ph ^ 1u, abort_flag)) break;
+                ptx::mbar_arrive_expect_tx(bar_full(s), STAGE_BYTES);
+                ptx::tma_load_2d(sA(s), &tmA, kb * BK, row_a, bar_full(s));
+                ptx::tma_load_2d(sB(s), &tmB, kb * BK, row_b, bar_full(s));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = true;
+            for (int seg = 0; seg < nseg && ok; seg++) {
+                const int buf = seg & 1;
+                if (seg >= 2 && !bounded_wait(bar_acce(buf), uint32_t((seg >> 1) - 1) & 1u, abort_flag)) break;
+                ptx::tc_fence_after();
+                const uint32_t d = tmem + uint32_t(buf * BN);
+                const int kb0 = seg * SEG_KB;
+                const int kb1 = min(kb_total, kb0 + SEG_KB);
+                for (int kb = kb0; kb < kb1; kb++) {
+                    const int s = kb % STAGES;
+                    const uint32_t ph = uint32_t(kb / STAGES) & 1u;
+                    if (!bounded_wait(bar_full(s), ph, abort_flag)) { ok = false; break; }
+                    ptx::tc_fence_after();
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++) {
+                        const uint64_t ad = ptx::sdesc_sw128_kmajor(sA(s) + uint32_t(kk * 32));
+                        const uint64_t bd = ptx::sdesc_sw128_kmajor(sB(s) + uint32_t(kk * 32));
+                        ptx::mma_bf16(d, ad, bd, IDESC, (kb > kb0 || kk > 0) ? 1u : 0u);
+                    }
+                    ptx::mma_commit(bar_empty(s));
+                }
+                if (ok) ptx::mma_commit(bar_accf(buf));
+            }
+        }
+    } else {
+        const int q = warp & 3;                 // TMEM lanes 32q..32q+31 (warp rank mod 4)
+        const int half = (warp - 2) >> 2;       // columns [128 half, 128 half + 128)
+        int acc[128];
+#pragma unroll
+        for (int i = 0; i < 128; i++) acc[i] = 0;
+        bool ok = true;
+        for (int seg = 0; seg < nseg; seg++) {
+            const int buf = seg & 1;
+            if (!warp_wait(bar_accf(buf), uint32_t(seg >> 1) & 1u, abort_flag)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + half * 128);
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                uint32_t v[32];
+                ptx::tmem_ld_32x32b_x32(taddr + uint32_t(c * 32), v);
+                ptx::tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 32; i++) acc[c * 32 + i] += __float2int_rn(__uint_as_float(v[i]));
+            }
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(bar_acce(buf));
+        }
+        if (ok) {
+            const int row = blockIdx.y * BM + q * 32 + lane;
+            const int col0 = blockIdx.x * BN + half * 128;
+            if (EPI == EPI_MOD) {
+                int8_t *dst = args.W + (long)l * args.w_plane + (long)row * args.n_pad + col0;
+                if (l == 0) {                            // p = 256: low byte
+#pragma unroll
+                    for (int g = 0; g < 8; g++) {
+                        uint32_t w4[4];
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            const int b = g * 16 + j * 4;
+                            w4[j] = (uint32_t(acc[b]) & 255u) | ((uint32_t(acc[b + 1]) & 255u) << 8) |
+                                    ((uint32_t(acc[b + 2]) & 255u) << 16) | ((uint32_t(acc[b + 3]) & 255u) << 24);
+                        }
+                        *reinterpret_cast<uint4 *>(dst + g * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                    }
+                } else {
+                    const uint32_t p = uint32_t(c_p[l]), mg = c_magic[l], c16 = c_c16[l];
+                    const int hp = int(p >> 1);
+#pragma unroll
+                    for (int g = 0; g < 8; g++) {
+                        uint32_t w4[4];
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            uint32_t word = 0;
+#pragma unroll
+                            for (int e = 0; e < 4; e++) {
+                                const int x = acc[g * 16 + j * 4 + e];
+                                const uint32_t u = uint32_t(x < 0 ? -x : x);
+                                uint32_t r = mod_small((u >> 16) * c16 + (u & 0xFFFFu), p, mg);
+                                int sr = int(r) > hp ? int(r) - int(p) : int(r);
+                                if (x < 0) sr = -sr;
+                                word |= (uint32_t(sr) & 255u) << (8 * e);
+                            }
+                            w4[j] = word;
+                        }
+                        *reinterpret_cast<uint4 *>(dst + g * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                    }
+                }
+            } else {
+                int rm = 0;
+#pragma unroll
+                for (int i = 0; i < 128; i++) rm = max(rm, acc[i]);
+                atomicMax(args.row_max + row, rm);
+                int mine[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int c = 0; c < 128; c++) {
+                    const int v = __reduce_max_sync(0xffffffffu, acc[c]);
+                    if (lane == (c & 31)) mine[c >> 5] = v;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; j++) atomicMax(args.col_max + col0 + j * 32 + lane, mine[j]);
+            }
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc<512>(tmem);
+    }
+}
+
+// ============================================================= exponents and N
+// red[] holds bits of nonnegative doubles (order-independent atomicMax):
+// 0 max_i |A|v, 1 max_j v^T|B|, 2 max_i 2^alpha'_i, 3 max_j 2^beta'_j, 4 L.
+struct BoundArgs {
+    int m, n, k;
+    const unsigned long long *rmaxA, *rmaxB, *hmaxA, *hmaxB;
+    const double *rsumA, *rsumB;
+    const int *cmax_row, *cmax_col;
+    unsigned long long *red;
+};
+
+__device__ __forceinline__ double pow2_prime(unsigned long long rmax_bits, int cmax) {
+    // 2^alpha' = 2^alpha sqrt(max cbar) (Theorem 2); 0 for an empty row
+    if (rmax_bits == 0 || cmax <= 0) return 0.0;
+    return ldexp(sqrt(double(cmax)), floor_log2_bits(rmax_bits)) * (1.0 + 0x1p-40);
+}
+
+__device__ __forceinline__ void block_max_to(unsigned long long v, unsigned long long *dst) {
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = t > v ? t : v;
+    }
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(dst, v);
+}
+
+__global__ void __launch_bounds__(256) k_bound_reduce(BoundArgs a) {
+    unsigned long long mR = 0, mK = 0, m2a = 0, m2b = 0, mL = 0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.m; i += stride) {
+        unsigned long long v = (unsigned long long)__double_as_longlong(a.rsumA[i]);
+        mR = v > mR ? v : mR;
+        v = (unsigned long long)__double_as_longlong(pow2_prime(a.rmaxA[i], a.cmax_row[i]));
+        m2a = v > m2a ? v : m2a;
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += stride) {
+        unsigned long long v = (unsigned long long)__double_as_longlong(a.rsumB[j]);
+        mK = v > mK ? v : mK;
+        v = (unsigned long long)__double_as_longlong(pow2_prime(a.rmaxB[j], a.cmax_col[j]));
+        m2b = v > m2b ? v : m2b;
+    }
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < a.k; h += stride) {
+        double v = __longlong_as_double((long long)a.hmaxA[h]) * __longlong_as_double((long long)a.hmaxB[h]);
+        unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        mL = b > mL ? b : mL;
+    }
+    block_max_to(mR, a.red + 0);
+    block_max_to(mK, a.red + 1);
+    block_max_to(m2a, a.red + 2);
+    block_max_to(m2b, a.red + 3);
+    block_max_to(mL, a.red + 4);
+}
+
+// The N rule: smallest N in [2, nmax] with
+//   t_N (maxR max2b + max2a maxK) + (k + gN_N) t_N^2 max2a max2b <= tau * L,
+// else nmax.  fixed > 0 bypasses the rule.
+__global__ void k_choose_n(const unsigned long long *red, int k, double tau, int nmax, int fixed, int fp32,
+                           int *n_dev, int *n_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int N = fixed;
+    if (N <= 0) {
+        const double maxR = __longlong_as_double((long long)red[0]);
+        const double maxK = __longlong_as_double((long long)red[1]);
+        const double m2a = __longlong_as_double((long long)red[2]);
+        const double m2b = __longlong_as_double((long long)red[3]);
+        const double L = __longlong_as_double((long long)red[4]);
+        N = nmax;
+        for (int c = 2; c <= nmax; c++) {
+            const DevN &d = fp32 ? c_n32[c] : c_n64[c];
+            const double T = d.t * (maxR * m2b + m2a * maxK) + (double(k) + d.gN) * d.t * d.t * m2a * m2b;
+            if (T <= tau * L) { N = c; break; }
+        }
+    }
+    *n_dev = N;
+    if (n_out) *n_out = N;
+}
+
+// Algorithm 2, mu/nu lines: d = single_up(max cbar) (1 for an empty row),
+// e = log2f(d) with CUDA's fast __log2f as in the paper,
+// mu = mu' + floor(fl_down(fma(c, e, P'))).
+__global__ void __launch_bounds__(256) k_mu_nu(int m, int n, const unsigned long long *rmaxA,
+                                               const unsigned long long *rmaxB, const int *cmax_row,
+                                               const int *cmax_col, const int *n_dev, int fp32, int32_t *mu,
+                                               int32_t *nu, int32_t *mu_out, int32_t *nu_out) {
+    const int N = *n_dev;
+    const float Pp = fp32 ? c_n32[N].Pprime : c_n64[N].Pprime;
+    const float c = c_cneg;
+    const int stride = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m + n; t += stride) {
+        const bool isrow = t < m;
+        const int i = isrow ? t : t - m;
+        const unsigned long long b = isrow ? rmaxA[i] : rmaxB[i];
+        const int mp = b ? 5 - floor_log2_bits(b) : 0;
+        const int cm = isrow ? cmax_row[i] : cmax_col[i];
+        const float d = cm > 0 ? __int2float_ru(cm) : 1.0f;
+        const float e = __log2f(d);
+        const int v = mp + int(floorf(__fmaf_rd(c, e, Pp)));
+        if (isrow) { mu[i] = v; if (mu_out) mu_out[i] = v; }
+        else { nu[i] = v; if (nu_out) nu_out[i] = v; }
+    }
+}
+
+// ============================================================= CRT
+// Algorithm 3 after the products, then Algorithm 1's inverse scaling:
+//   C'(1) = sum_l s_l1 W_l   (b = 64: exact, kept as the integer sum of
+//                             s_l1/g times W_l, then times g; b = 32: FP64 fma
+//                             chain in ascending l),
+//   C'(2) = fma chain of s_l2 W_l in ascending l (b = 64),
+//   Q = rint(P_inv C'(1)),  C'' = fma(-Q, P2, fma(-Q, P1, C'(1)) + C'(2)),
+//   C = RN(2^-(mu_i + nu_j) C'')  (b = 32: rounded once to FP32).
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+    // RN(x * 2^e) for an integer-valued x with |x| < 2^400
+    if (x == 0.0) return x;
+    if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+    if (e > 1023) return x * 0x1p1023 * 0x1p1023;                 // overflows to +-inf as ldexp does
+    const double y = x * 0x1p-1022;                               // exact: |x| >= 1
+    const int e2 = e + 1022;
+    if (e2 < -1022) return copysign(0.0, x);
+    return y * __longlong_as_double((long long)(e2 + 1023) << 52);
+}
+
+template <typename TO, int B>
+__global__ void __launch_bounds__(256) k_crt(const int8_t *W, long w_plane, int n_pad, const int *n_dev,
+                                             const int32_t *mu, const int32_t *nu, TO *C, long ldc, int m, int n) {
+    const int N = *n_dev;
+    const DevN d = B == 64 ? c_n64[N] : c_n32[N];
+    const int j0 = (blockIdx.x * 256 + threadIdx.x) * 4;
+    if (j0 >= n) return;
+    for (int i = blockIdx.y; i < m; i += gridDim.y) {
+        const int8_t *wp = W + (long)i * n_pad + j0;
+        long long a1[4] = {0, 0, 0, 0};
+        double f1[4] = {0.0, 0.0, 0.0, 0.0}, f2[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int l = 0; l < N; l++) {
+            const char4 w = *reinterpret_cast<const char4 *>(wp + (long)l * w_plane);
+            const int wv[4] = {w.x, w.y, w.z, w.w};
+            if (B == 64) {
+                const long long s1 = c_s1i[d.offset + l];
+                const double s2 = c_s2d[d.offset + l];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    a1[e] += s1 * wv[e];
+                    f2[e] = fma(s2, double(wv[e]), f2[e]);
+                }
+            } else {
+                const double s1 = c_s1f[d.offset + l];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    f1[e] = fma(s1, double(wv[e]), f1[e]);
+                    f2[e] = fma(0.0, double(wv[e]), f2[e]);
+                }
+            }
+        }
+        const int mi = mu[i];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int j = j0 + e;
+            if (j >= n) break;
+            const double c1 = B == 64 ? __ll2double_rn(a1[e]) * d.g : f1[e];
+            const double q = rint(d.Pinv * c1);
+            const double cpp = fma(-q, d.P2, fma(-q, d.P1, c1) + f2[e]);
+            const double v = scale_pow2(cpp, -(mi + nu[j]));
+            if (B == 64) C[(long)i * ldc + j] = TO(v);
+            else C[(long)i * ldc + j] = TO(__double2float_rn(v));
+        }
+    }
+}
+
+// ============================================================= diagnostics
+// Assumption (1), Section 1.2: |log2f(x) - log2 x| <= 4 u32 log2 x, checked
+// for CUDA's __log2f on every FP32 value x that is an integer in [1, 2^29]
+// (the values Dbar can take).  out[0] += violations, out[1] = max ratio
+// |err| / (u32 log2 x) as double bits (atomicMax).
+__global__ void __launch_bounds__(256) k_log2f_check(uint32_t first_bits, uint32_t count,
+                                                     unsigned long long *out) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    unsigned long long bad = 0, worst = 0;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += stride) {
+        const float x = __uint_as_float(first_bits + t);
+        if (x != truncf(x)) continue;
+        const double lx = log2(double(x));
+        const double err = fabs(double(__log2f(x)) - lx);
+        if (err > 4.0 * 0x1p-24 * lx) bad++;
+        if (lx > 0) {
+            const double ratio = err / (0x1p-24 * lx);
+            const unsigned long long b = (unsigned long long)__double_as_longlong(ratio);
+            worst = b > worst ? b : worst;
+        }
+    }
+    if (bad) atomicAdd(out, bad);
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long t2 = __shfl_xor_sync(0xffffffffu, worst, o);
+        worst = t2 > worst ? t2 : worst;
+    }
+    if ((threadIdx.x & 31) == 0 && worst) atomicMax(out + 1, worst);
+}
+
+}  // namespace oz2

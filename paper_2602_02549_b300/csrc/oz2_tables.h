@@ -1,0 +1,45 @@
+// Host-side constant tables of the Ozaki-II scheme, generated at load time
+// from the moduli of eq. (p_list) with a small multi-precision integer.
+#pragma once
+#include <cstdint>
+
+namespace oz2 {
+
+constexpr int kNMax = 49;
+constexpr int kPackedLen = (kNMax * (kNMax + 1)) / 2;  // sum_{N=1}^{49} N entries
+
+// Per-modulus reduction constants (index l = 0..48).
+struct ModTable {
+    int p[kNMax];
+    uint32_t magic[kNMax];   // ceil(2^32 / p): floor(t/p) = umulhi(t, magic) for t < 2^24
+    uint32_t c16[kNMax];     // 2^16 mod p
+    uint32_t c24[kNMax];     // 2^24 mod p
+    uint32_t c48[kNMax];     // 2^48 mod p
+    uint8_t pow2[kNMax][256];// 2^E mod p, E = 0..255
+};
+
+// Per-N scalars for one precision (b = 64 or 32).
+struct NTable {
+    double P1, P2, Pinv;     // P1 + P2 ~ P (P2 = 0 for b = 32), Pinv = double(1/P)
+    double g;                // grid of s_l1 (b = 64); 1 for b = 32 (unused)
+    double t;                // 1/sqrt(32 (P-1)), rounded up
+    double gN;               // P-proportional part of R_b (Lemma 4), rounded up
+    float Pprime;            // single_down(log2(P-1)/2 - 0.5)
+    int offset;              // start of this N's entries in the packed arrays
+};
+
+struct Tables {
+    ModTable mod;
+    NTable n64[kNMax + 1];
+    NTable n32[kNMax + 1];
+    long long s1i[kPackedLen];   // b = 64: s_l1 / g, an integer below 2^53
+    double s1d[kPackedLen];      // b = 64: s_l1
+    double s2d[kPackedLen];      // b = 64: s_l2
+    double s1f[kPackedLen];      // b = 32: s_l1 = double(P/p_l q_l)
+    float c;                     // single_down(-0.5 / (1 - 4 u32))
+};
+
+// Built once (thread-safe); never fails for N in [2, 49].
+const Tables &tables();
+
+}  // namespace oz2

@@ -1,0 +1,107 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/oz2.h declares, rejects bad arguments before touching
+CUDA, sizes its workspace, and its independently generated constant tables
+equal the oracle's exact ones."""
+import ctypes
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle.constants import bound_terms, constants
+from paper_2602_02549_b300 import binding as B
+from paper_2602_02549_b300.build import LIB, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return B.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = B.header_symbols()
+    assert {"oz2_gemm", "oz2_gemm_ex", "oz2_sgemm", "oz2_sgemm_ex", "oz2_workspace_size", "oz2_sync",
+            "oz2_tables", "oz2_status_str", "oz2_version", "oz2_check_log2f"} <= set(names)
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    for n in names:
+        assert n in exported, n
+        assert hasattr(lib, n)
+
+
+def test_version_and_status(lib):
+    assert lib.oz2_version() >= 100
+    assert B.status_str(0) == "OZ2_OK"
+    assert "2^17" in B.status_str(B.OZ2_ERANGE)
+
+
+FAKE = ctypes.c_void_p(0x10000)   # never dereferenced: validation fails first
+
+
+def call(lib, m=8, n=8, k=8, lda=8, ldb=8, ldc=8, N=14, mode=0, opts=None, A=FAKE, Bp=FAKE, C=FAKE, fp32=False):
+    fn = lib.oz2_sgemm_ex if fp32 else lib.oz2_gemm_ex
+    return fn(m, n, k, A, lda, Bp, ldb, C, ldc, N, mode, ctypes.byref(opts) if opts else None)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_argument_validation(lib, fp32):
+    E, R = B.OZ2_EINVAL, B.OZ2_ERANGE
+    assert call(lib, m=0, fp32=fp32) == E
+    assert call(lib, n=-1, fp32=fp32) == E
+    assert call(lib, k=0, fp32=fp32) == E
+    assert call(lib, lda=7, fp32=fp32) == E
+    assert call(lib, ldb=7, fp32=fp32) == E
+    assert call(lib, ldc=7, fp32=fp32) == E
+    assert call(lib, N=1, fp32=fp32) == E
+    assert call(lib, N=50, fp32=fp32) == E
+    assert call(lib, mode=8, fp32=fp32) == E
+    assert call(lib, A=None, fp32=fp32) == E
+    assert call(lib, C=None, fp32=fp32) == E
+    assert call(lib, k=(1 << 17) + 1, lda=(1 << 17) + 1, fp32=fp32) == R
+    # transposed leading dimensions: A^T is k x m, B^T is n x k
+    assert call(lib, m=16, k=8, lda=8, mode=B.OZ2_TRANS_A, ldc=8, fp32=fp32) == E
+    assert call(lib, n=16, k=8, ldb=4, ldc=16, mode=B.OZ2_TRANS_B, fp32=fp32) == E
+    # N = 0 needs a positive target
+    assert call(lib, N=0, fp32=fp32) == E
+    o = B.oz2_opts()
+    o.target = 0.0
+    assert call(lib, N=0, opts=o, fp32=fp32) == E
+    o.target, o.nmax = 1e-15, 50
+    assert call(lib, N=0, opts=o, fp32=fp32) == E
+    # injected exponents: both or neither, and a fixed N
+    o = B.oz2_opts()
+    o.mu_in = ctypes.c_void_p(0x1000)
+    assert call(lib, opts=o, fp32=fp32) == E
+    o.nu_in = ctypes.c_void_p(0x2000)
+    o.target = 1e-15
+    assert call(lib, N=0, opts=o, fp32=fp32) == E
+
+
+def test_workspace_size(lib):
+    assert B.workspace_size(0, 8, 8, 14) == 0
+    assert B.workspace_size(8, 8, (1 << 17) + 1, 14) == 0
+    assert B.workspace_size(8, 8, 8, 1) == 0
+    a = B.workspace_size(100, 100, 100, 14)
+    b = B.workspace_size(100, 100, 100, 20)
+    c = B.workspace_size(1000, 1000, 1000, 20)
+    assert 0 < a < b < c
+    # dominated by N BF16 residue planes of the padded operands and N INT8 W planes
+    m_pad, n_pad, k_pad = 1024, 1024, 1024
+    assert c >= 20 * (2 * (m_pad + n_pad) * k_pad + m_pad * n_pad)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("N", list(range(2, 50)))
+def test_tables_match_oracle(lib, N, fp32):
+    t = B.tables(N, fp32)
+    C = constants(N, 32 if fp32 else 64)
+    assert np.array_equal(t["s1"], np.array(C.s1))
+    assert np.array_equal(t["s2"], np.array(C.s2))
+    assert t["P1"] == C.P1 and t["P2"] == C.P2 and t["Pinv"] == C.Pinv
+    assert t["Pprime"] == C.Pprime
+    if not fp32:
+        assert t["g"] == float(C.g)
+    bt = bound_terms(N, 32 if fp32 else 64)
+    assert abs(t["t"] / bt["t"] - 1) < 1e-12
+    assert abs(t["gN"] / bt["gN"] - 1) < 1e-10

@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bars (the tolerances are written in each test):
+  * W_l = mod(A'_l B'_l, p_l): bit-exact (integer work);
+  * mu, nu: inside the band Algorithm 2 allows under assumption (1) on log2f;
+  * C with the GPU's exponents injected into the oracle: within 2 ulp (both
+    sides run the same FP64 operation sequence, so 0 is expected);
+  * |AB - C| within the Theorem 2 bound on every entry (plus half an ulp of
+    the smallest subnormal where the output underflows, which the paper's
+    analysis leaves out).
+"""
+import numpy as np
+import pytest
+
+from paper_2602_02549_b300.inputs import integer_matrix, paper_pair, wide_exponent_matrix
+
+from _gpu_util import run_gpu, ulp_distance
+
+pytestmark = pytest.mark.gpu
+
+ULP_TOL = 2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2602_02549_b300.build import build
+    build()
+
+
+def check_against_oracle(oracle, A, Bm, g, b=64, bound=True):
+    """Oracle with the GPU's mu, nu, N: W bit-exact, C within ULP_TOL, bound holds."""
+    N = g["N"]
+    r = oracle.os_ii(A, Bm, N, b, mu_in=g["mu"], nu_in=g["nu"])
+    assert np.array_equal(g["W"], r["W"]), "W_l differs"
+    d = ulp_distance(g["C"], r["C"], fp32=(b == 32))
+    assert d.max() <= ULP_TOL, f"max ulp distance {d.max()}"
+    assert oracle.lemma0_holds(r["Ap"], r["Bp"], N)
+    if bound:
+        eb = oracle.bound_from_exponents(A, Bm, g["mu"], g["nu"], r["Ap"], r["Bp"], N, b)
+        eb = eb + (2.0 ** -1075 if b == 64 else 2.0 ** -150)
+        err = np.abs(oracle.exact_residual(A, Bm, g["C"]))
+        assert (err <= eb).all(), f"bound violated: max ratio {(err / eb).max()}"
+    return r
+
+
+SHAPES = [(1, 1, 1), (1, 7, 5), (9, 1, 3), (33, 65, 17), (128, 256, 64), (129, 257, 65),
+          (200, 300, 1500), (256, 256, 256), (130, 40, 2049)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("N", [2, 14])
+def test_dgemm_parity(oracle, shape, N):
+    m, n, k = shape
+    A, Bm = paper_pair(m, n, k, 0.5, seed=m + n + k)
+    g = run_gpu(A, Bm, N)
+    assert g["N"] == N
+    r = check_against_oracle(oracle, A, Bm, g)
+    # the exponents satisfy Algorithm 2 within the log2f band
+    lo, hi = oracle.mu_band(r["mu_p"], r["cmax_row"], N)
+    assert ((g["mu"] >= lo) & (g["mu"] <= hi)).all()
+    lo, hi = oracle.mu_band(r["nu_p"], r["cmax_col"], N)
+    assert ((g["nu"] >= lo) & (g["nu"] <= hi)).all()
+
+
+@pytest.mark.parametrize("N", [3, 5, 6, 8, 20, 33, 49])
+def test_dgemm_parity_moduli(oracle, N):
+    A, Bm = paper_pair(150, 170, 700, 1.0, seed=N)
+    g = run_gpu(A, Bm, N)
+    check_against_oracle(oracle, A, Bm, g)
+
+
+@pytest.mark.parametrize("phi", [0.5, 1.0, 2.0, 4.0])
+def test_dgemm_phi(oracle, phi):
+    A, Bm = paper_pair(96, 80, 1100, phi, seed=int(phi * 8))
+    g = run_gpu(A, Bm, 16)
+    check_against_oracle(oracle, A, Bm, g)
+
+
+def test_exponents_match_oracle_log2f(oracle):
+    # GPU __log2f vs the C library's log2f: mu, nu agree except in rows where
+    # the two round across an integer boundary (counted; at most 2 allowed)
+    A, Bm = paper_pair(256, 256, 512, 1.0, seed=5)
+    g = run_gpu(A, Bm, 14)
+    s = oracle.scaling(A, Bm, 14)
+    mism = int((g["mu"] != s["own_mu"]).sum() + (g["nu"] != s["own_nu"]).sum())
+    assert mism <= 2
+
+
+@pytest.mark.parametrize("tr", [(True, False), (False, True), (True, True)])
+def test_transposes(tr):
+    ta, tb = tr
+    A, Bm = paper_pair(70, 90, 300, 1.0, seed=3)
+    As = np.ascontiguousarray(A.T) if ta else A
+    Bs = np.ascontiguousarray(Bm.T) if tb else Bm
+    g = run_gpu(As, Bs, 14, trans_a=ta, trans_b=tb)
+    ref = run_gpu(A, Bm, 14)
+    assert np.array_equal(g["C"], ref["C"])
+    assert np.array_equal(g["mu"], ref["mu"]) and np.array_equal(g["nu"], ref["nu"])
+
+
+@pytest.mark.parametrize("N", [2, 8, 14, 20])
+def test_sgemm_parity(oracle, N):
+    A, Bm = paper_pair(100, 140, 900, 1.0, seed=N, dtype=np.float32)
+    g = run_gpu(A, Bm, N, fp32=True)
+    check_against_oracle(oracle, A.astype(np.float64), Bm.astype(np.float64), g, b=32)
+
+
+def test_integer_inputs_exact():
+    # A' = 2^mu A exactly when mu >= 0; for N <= 5 every step is exact
+    A = integer_matrix(90, 70, -30, 30, seed=1)
+    Bm = integer_matrix(70, 110, -30, 30, seed=2)
+    g = run_gpu(A, Bm, 5)
+    assert (g["mu"] >= 0).all() and (g["nu"] >= 0).all()
+    assert np.array_equal(g["C"], A @ Bm)
+
+
+def test_extreme_residues_long_k(oracle):
+    # injected mu = nu = 0 keeps A' = A; entries 127 / -128 drive every residue
+    # to (near) its extreme, and k = 2^17 makes C'_1 = 2^31 (wraps in INT32 for
+    # p = 256, still exact mod 256); closed form: every entry is k*a*b.
+    k = 1 << 17
+    for a, b in ((127.0, 127.0), (-128.0, -128.0), (127.0, -128.0)):
+        A = np.full((4, k), a)
+        Bm = np.full((k, 3), b)
+        N = 8
+        g = run_gpu(A, Bm, N, mu_in=np.zeros(4, np.int32), nu_in=np.zeros(3, np.int32))
+        assert (g["C"] == k * a * b).all()
+        r = oracle.os_ii(A, Bm, N, mu_in=np.zeros(4, np.int32), nu_in=np.zeros(3, np.int32))
+        assert np.array_equal(g["W"], r["W"])
+
+
+def test_random_integer_residue_products(oracle):
+    # injected mu = nu = 0: A' = A, so W_l checks the tensor-core products alone
+    A = integer_matrix(130, 3000, -(1 << 40), 1 << 40, seed=7)
+    Bm = integer_matrix(3000, 260, -(1 << 40), 1 << 40, seed=8)
+    g = run_gpu(A, Bm, 12, mu_in=np.zeros(130, np.int32), nu_in=np.zeros(260, np.int32))
+    r = oracle.os_ii(A, Bm, 12, mu_in=np.zeros(130, np.int32), nu_in=np.zeros(260, np.int32))
+    assert np.array_equal(g["W"], r["W"])
+    assert ulp_distance(g["C"], r["C"]).max() <= ULP_TOL
+
+
+def test_wide_exponents_and_zeros(oracle):
+    A = wide_exponent_matrix(70, 300, -1060, 400, seed=9, zero_frac=0.3)
+    Bm = wide_exponent_matrix(300, 50, -900, 400, seed=10, zero_frac=0.3)
+    A[5, :] = 0.0
+    Bm[:, 7] = 0.0
+    g = run_gpu(A, Bm, 20)
+    check_against_oracle(oracle, A, Bm, g)
+    assert (g["C"][5] == 0).all() and (g["C"][:, 7] == 0).all()
+
+
+def test_subnormal_outputs(oracle):
+    # tiny inputs make C subnormal: the single final rounding must match ldexp
+    A, Bm = paper_pair(40, 30, 200, 1.0, seed=4)
+    A = np.ldexp(A, -530)
+    Bm = np.ldexp(Bm, -530)
+    g = run_gpu(A, Bm, 14)
+    assert (np.abs(g["C"]) < 2.0 ** -1022).mean() > 0.5
+    check_against_oracle(oracle, A, Bm, g)
+
+
+def test_auto_N_rule(oracle):
+    for phi, tau in ((0.5, 1e-15), (1.0, 1e-15), (2.0, 1e-12), (1.0, 1e-8)):
+        A, Bm = paper_pair(128, 128, 1024, phi, seed=int(phi * 3))
+        g = run_gpu(A, Bm, 0, target=tau, nmax=40)
+        s = oracle.scaling(A, Bm, 14)
+        N, info = oracle.choose_N(A, Bm, s["alpha"], s["beta"], s["cmax_row"], s["cmax_col"], tau, 40)
+        rat = info["ratios"]
+        slack = 1e-9
+        assert rat[g["N"]] <= tau * (1 + slack) or g["N"] == 40
+        if g["N"] > 2:
+            assert rat[g["N"] - 1] > tau * (1 - slack)
+        check_against_oracle(oracle, A, Bm, g)
+
+
+def test_deterministic():
+    A, Bm = paper_pair(300, 200, 800, 1.0, seed=1)
+    a = run_gpu(A, Bm, 0, target=1e-15)
+    b = run_gpu(A, Bm, 0, target=1e-15)
+    assert a["N"] == b["N"]
+    assert np.array_equal(a["C"].view(np.int64), b["C"].view(np.int64))
+
+
+def test_log2f_assumption():
+    # Section 1.2, assumption (1), for the __log2f the exponent kernel uses
+    from paper_2602_02549_b300 import binding as B
+    viol, ratio = B.check_log2f()
+    assert viol == 0, f"{viol} violations, max |err|/(u32 log2 x) = {ratio}"
+    assert ratio <= 4.0
