@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--target", type=float, default=1e-15)
     p.add_argument("--nmax", type=int, default=20)
     p.add_argument("--nmoduli", type=int, default=0, help="fixed N instead of the bound rule")
-    p.add_argument("--cpu-sample", type=int, default=192, help="rows/cols of the oracle sample")
+    p.add_argument("--cpu-sample", type=int, default=640, help="rows/cols of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--acc-samples", type=int, default=256)
@@ -62,8 +62,9 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, units: float):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+def traffic_for(kernel: str, alg_bytes: float):
+    """DRAM bytes per launch, scaled from the committed ncu capture of a smaller case
+    by the algorithmic bytes, or None once the kernel source has changed."""
     path = os.path.join(ROOT, "profiles", "gemm_traffic.json")
     if not os.path.exists(path):
         return None
@@ -71,7 +72,7 @@ def traffic_for(kernel: str, units: float):
     if d.get("kernel_hash") != kernel_hash() or kernel not in d:
         return None
     e = d[kernel]
-    return e["dram_bytes"] / e["units"] * units
+    return e["dram_bytes"] / e["alg_bytes"] * alg_bytes
 
 
 class ClockSampler:
@@ -265,7 +266,8 @@ def main():
     roofline = {"bound": "tensor", "kernel": "k_gemm<EPI_MOD>", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": f"bf16_tflops_sustained ({peak_kind})",
-                "traffic": traffic_for("k_gemm_mod", N_used * m * n * k),
+                "traffic": traffic_for("k_gemm_mod", N_used * (2 * (m * k + k * n) + m * n)),
+                "algorithmic_bytes": N_used * (2 * (m * k + k * n) + m * n),
                 "emulated_roofline_tflops": peak / (N_used + 1),
                 "emulated_frac": value / world / (peak / (N_used + 1))}
 
