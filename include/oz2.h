@@ -136,6 +136,35 @@ OZ2_API int oz2_tables(int N, int fp32, double *s1, double *s2, double *scal, fl
  * largest |__log2f(x) - log2 x| / (u32 log2 x) seen (a double). */
 OZ2_API int oz2_check_log2f(void *stream, unsigned long long *dev_out);
 
+/* Size of the fixed device scratch used by oz2_gemm_noalloc (32 MiB). */
+#define OZ2_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * oz2_gemm_noalloc: the same emulated DGEMM as oz2_gemm_ex, for callers that
+ * cannot have any device memory allocated for them, e.g. an application that
+ * owns all device memory through its own pool under a hard budget, or a
+ * latency-critical loop that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation, and that cannot hand over a workspace either.  (The paper
+ * has no counterpart; this is an interface convenience.)
+ *   - Works in a fixed OZ2_NOALLOC_SCRATCH_BYTES array that this library
+ *     places in the device memory of every GPU it is loaded on, held until the
+ *     process exits.  Nothing is allocated or freed per call.
+ *   - Problems whose workspace (oz2_workspace_size with nmax = nmoduli, or 20
+ *     when nmoduli == 0) exceeds that size are rejected with OZ2_ENOMEM before
+ *     anything is enqueued.  For 512^3 at N = 20 the workspace is 25 MiB.
+ *   - nmoduli: N in [2, 49], or 0 for the bound rule with `target` and N <= 20.
+ *   - The first call on a device looks up the array's device address; make that
+ *     first call before any stream capture.
+ *   - All calls share the one array, which keeps the previous call's contents
+ *     (each call clears what must start at zero).  Calls whose work overlaps
+ *     on the GPU (different streams, or different host threads) race on it:
+ *     serialise them.
+ * Other conventions as for oz2_gemm_ex (device pointers, row-major, `stream`
+ * is a cudaStream_t or NULL for the legacy default stream).
+ */
+OZ2_API int oz2_gemm_noalloc(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                             double *C, int ldc, int nmoduli, int mode, double target, void *stream);
+
 /* Human-readable name of a status code (static string). */
 OZ2_API const char *oz2_status_str(int status);
 

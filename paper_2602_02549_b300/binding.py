@@ -205,3 +205,22 @@ def check_log2f(stream=None):
     v = out.cpu().tolist()
     ratio = struct.unpack("<d", struct.pack("<q", v[1]))[0]
     return v[0], ratio
+
+
+def gemm_noalloc(A, B, C, nmoduli: int = 0, mode: int = 0, *, target: float = 0.0, stream=None) -> int:
+    """oz2_gemm_noalloc on float64 torch CUDA tensors (no workspace is passed or
+    allocated; the library's fixed device scratch is used).  Returns the status."""
+    import torch
+    L = lib()
+    fn = L.oz2_gemm_noalloc
+    fn.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int] * 3 + \
+        [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    ta, tb = bool(mode & OZ2_TRANS_A), bool(mode & OZ2_TRANS_B)
+    m = A.size(1) if ta else A.size(0)
+    k = A.size(0) if ta else A.size(1)
+    n = B.size(0) if tb else B.size(1)
+    s = stream if stream is not None else torch.cuda.current_stream(A.device)
+    with torch.cuda.device(A.device):
+        return fn(m, n, k, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), _ptr(C), _ld(C, "C"),
+                  nmoduli, mode, float(target), ctypes.c_void_p(s.cuda_stream))

@@ -14,7 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liboz2.so")
-SOURCES = [os.path.join(CSRC, "oz2_api.cu"), os.path.join(CSRC, "oz2_tables.cpp")]
+SOURCES = [os.path.join(CSRC, "oz2_api.cu"), os.path.join(CSRC, "oz2_noalloc.cu"),
+           os.path.join(CSRC, "oz2_tables.cpp")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
