@@ -73,10 +73,10 @@ int ensure_device(int *dev_out) {
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_p, T.mod.p, sizeof T.mod.p);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_magic, T.mod.magic, sizeof T.mod.magic);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c16, T.mod.c16, sizeof T.mod.c16);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c24, T.mod.c24, sizeof T.mod.c24);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c48, T.mod.c48, sizeof T.mod.c48);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cneg, &T.c, sizeof T.c);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_pow2, T.mod.pow2, sizeof T.mod.pow2);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w12, T.mod.w12, sizeof T.mod.w12);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_pf, T.mod.pf, sizeof T.mod.pf);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_invp, T.mod.invp, sizeof T.mod.invp);
         if (e != cudaSuccess) return cuda_fail(e);
         st.tables = true;
     }
@@ -165,15 +165,37 @@ int launch_stats(const Operand<T> &X, int k, unsigned long long *row_max, double
     return cuda_fail(cudaGetLastError());
 }
 
-template <int MODE, typename T>
-int launch_planes(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
+template <typename T>
+int launch_quant(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
     if (X.kcontig) {
         dim3 grid((a.k_pad / 8 + 255) / 256, grid_rows(a.R_pad));
-        k_planes_kc<MODE, T><<<grid, 256, 0, st>>>(X, a);
+        k_planes_kc<T><<<grid, 256, 0, st>>>(X, a);
     } else {
         dim3 grid(a.k_pad / 64, a.R_pad / 64);
-        k_planes_rc<MODE, T><<<grid, 256, 0, st>>>(X, a);
+        k_planes_rc<T><<<grid, 256, 0, st>>>(X, a);
     }
+    return cuda_fail(cudaGetLastError());
+}
+
+template <int J, typename T>
+void launch_resid_j(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
+    if (X.kcontig) {
+        dim3 grid((a.k_pad / 2 + 255) / 256, grid_rows(a.R_pad));
+        k_resid_kc<J, T><<<grid, 256, 0, st>>>(X, a);
+    } else {
+        dim3 grid(a.k_pad / 64, a.R_pad / 64);
+        k_resid_rc<J, T><<<grid, 256, 0, st>>>(X, a);
+    }
+}
+
+// Limbs of 12 bits covering |x'|: |x'| < 2^(P'+6) when mu, nu come from
+// Algorithm 2 (mu_i <= 5 - alpha_i + P'); injected exponents get the maximum.
+template <typename T>
+int launch_resid(const Operand<T> &X, const PlaneArgs &a, int bits, cudaStream_t st) {
+    const int J = (bits + kLimbBits - 1) / kLimbBits;
+    if (J <= 8) launch_resid_j<8>(X, a, st);
+    else if (J <= 12) launch_resid_j<12>(X, a, st);
+    else launch_resid_j<16>(X, a, st);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -288,8 +310,8 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
         if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
         PlaneArgs qa{resA, planeA, d.m_pad, k, d.k_pad, rmaxA, nullptr, nullptr};
         PlaneArgs qb{resB, planeB, d.n_pad, k, d.k_pad, rmaxB, nullptr, nullptr};
-        if ((rc = launch_planes<MODE_QUANT>(opA, qa, st))) return rc;
-        if ((rc = launch_planes<MODE_QUANT>(opB, qb, st))) return rc;
+        if ((rc = launch_quant(opA, qa, st))) return rc;
+        if ((rc = launch_quant(opB, qb, st))) return rc;
         // Cbar = Abar Bbar: row and column maxima only
         if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
         GemmArgs g{d.m_pad, d.n_pad, d.k_pad / gemm::BK, nullptr, nullptr, 0, cmax_row, cmax_col};
@@ -318,8 +340,10 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
     if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
     PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, nullptr, mu_use, ndev};
     PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, nullptr, nu_use, ndev};
-    if ((rc = launch_planes<MODE_RESID>(opA, ra, st))) return rc;
-    if ((rc = launch_planes<MODE_RESID>(opB, rb, st))) return rc;
+    const float pp = fp32 ? tables().n32[nmax].Pprime : tables().n64[nmax].Pprime;
+    const int bits = inject ? kLimbBits * kMaxLimbs : int(pp) + 8;
+    if ((rc = launch_resid(opA, ra, bits, st))) return rc;
+    if ((rc = launch_resid(opB, rb, bits, st))) return rc;
     const long w_plane = long(d.m_pad) * d.n_pad;
     if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
     GemmArgs g{d.m_pad, d.n_pad, d.k_pad / gemm::BK, ndev, W, w_plane, nullptr, nullptr};

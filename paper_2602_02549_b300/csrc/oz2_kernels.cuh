@@ -6,12 +6,12 @@
 //   k_stats_kc / k_stats_rc   Algorithm 2 inputs: max |x| per row of A (per
 //                             column of B) -> mu', nu'; |A| v, v^T |B| and
 //                             per-k maxima for the N rule (one HBM read)
-//   k_planes<QUANT>           Abar = ceil(2^mu' |A|), Bbar likewise, as BF16
+//   k_planes_kc / k_planes_rc Abar = ceil(2^mu' |A|), Bbar likewise, as BF16
 //   k_gemm<EPI_MAX>           Cbar = Abar Bbar on tcgen05, keeping only the row
 //                             and column maxima of Cbar
 //   k_bound_reduce, k_choose_n, k_mu_nu
 //                             Dbar, e, f, mu, nu (Algorithm 2) and the N rule
-//   k_planes<RESID>           A'_l = mod(trunc(2^mu A), p_l) as BF16, N planes
+//   k_resid_kc / k_resid_rc   A'_l = mod(trunc(2^mu A), p_l) as BF16, N planes
 //   k_gemm<EPI_MOD>           C'_l = A'_l B'_l on tcgen05, W_l = mod(C'_l, p_l)
 //   k_crt                     C'(1), C'(2), Q, C'' (Algorithm 3) and the
 //                             inverse scaling of Algorithm 1
@@ -39,10 +39,10 @@ __constant__ double c_s1f[kPackedLen];
 __constant__ int c_p[kNMax];
 __constant__ uint32_t c_magic[kNMax];
 __constant__ uint32_t c_c16[kNMax];
-__constant__ uint32_t c_c24[kNMax];
-__constant__ uint32_t c_c48[kNMax];
 __constant__ float c_cneg;                 // single_down(-0.5/(1-4 u32))
-__device__ uint8_t g_pow2[kNMax][256];     // 2^E mod p_l
+__constant__ float c_w12[kNMax][kMaxLimbs];// 2^(12 j) mod p_l
+__constant__ float c_pf[kNMax];            // p_l
+__constant__ float c_invp[kNMax];          // RN_f32(1/p_l)
 
 // Device status word: bit 0 = a bounded wait expired.
 __device__ int g_status;
@@ -124,23 +124,50 @@ __device__ __forceinline__ Int trunc_scaled(T x, int shift) {
     return v;
 }
 
-// mod(x', p_l) of Algorithm 3 (balanced; p = 256 stores class 128 as -128).
-__device__ __forceinline__ int residue(const Int &v, int l, const uint8_t (*pow2)[256]) {
-    if (v.M == 0) return 0;
-    if (l == 0) {                              // p = 256: the low byte
-        if (v.E >= 8) return 0;
-        uint32_t lo = (uint32_t(v.M) << v.E) & 255u;
-        if (v.neg) lo = (256u - lo) & 255u;
-        return int(int8_t(lo));
+// Residues of x' = trunc(2^shift x) (Algorithm 3, A'_l = mod(A', p_l)).
+// |x'| < 2^(P'+6) <= 2^177 is cut into J limbs of 12 bits at fixed bit
+// positions 12 j, carrying the sign of x'.  For odd p_l,
+//   t = sum_j d_j (2^(12 j) mod p_l)
+// is congruent to x' and |t| < J 2^12 2^8 <= 2^24, so t and every partial sum
+// are exact in FP32; q = rint(t / p_l) (FP32 reciprocal; off by at most one)
+// and one correction give the balanced residue in [-(p-1)/2, (p-1)/2].
+// p = 256 takes the low byte of x' in two's complement (class 128 -> -128).
+template <int J, typename T>
+__device__ __forceinline__ void limbs_of(T x, int shift, float (&d)[J], int &res256) {
+    const Int v = trunc_scaled(x, shift);
+#pragma unroll
+    for (int j = 0; j < J; j++) {
+        const int s = kLimbBits * j - v.E;
+        uint64_t q = 0;
+        if (s >= 0) {
+            if (s < 64) q = v.M >> s;
+        } else if (-s < kLimbBits) {
+            q = v.M << (-s);
+        }
+        const float f = float(uint32_t(q) & 4095u);
+        d[j] = v.neg ? -f : f;
     }
-    const uint32_t p = uint32_t(c_p[l]), mg = c_magic[l];
-    const uint32_t m0 = uint32_t(v.M & 0xFFFFFFu), m1 = uint32_t((v.M >> 24) & 0xFFFFFFu),
-                   m2 = uint32_t(v.M >> 48);
-    uint32_t t = mod_small(m0, p, mg) + mod_small(m1, p, mg) * c_c24[l] + m2 * c_c48[l];
-    uint32_t r = mod_small(t, p, mg);
-    r = mod_small(r * pow2[l][v.E > 255 ? 255 : v.E], p, mg);
-    int sr = int(r) > int(p >> 1) ? int(r) - int(p) : int(r);
-    return v.neg ? -sr : sr;
+    uint32_t lo = uint32_t(v.E >= 8 ? 0ull : (v.M << v.E)) & 255u;
+    if (v.neg) lo = (256u - lo) & 255u;
+    res256 = int(int8_t(lo));
+}
+
+template <int J>
+__device__ __forceinline__ float residue_odd(const float (&d)[J], int l) {
+    float t = 0.0f;
+#pragma unroll
+    for (int j = 0; j < J; j++) t = fmaf(d[j], c_w12[l][j], t);
+    const float p = c_pf[l];
+    const float q = rintf(t * c_invp[l]);
+    float r = fmaf(-q, p, t);
+    if (r > 0.5f * p) r -= p;
+    else if (r < -0.5f * p) r += p;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2f(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(int a, int b) {
@@ -252,18 +279,16 @@ __global__ void __launch_bounds__(256) k_stats_rc(Operand<T> X, int k, unsigned 
 }
 
 // ============================================================= planes
-// MODE_QUANT: plane 0 = BF16(ceil(2^shift |x|)), shift_r = mu'_r.
-// MODE_RESID: planes l < N = BF16(mod(trunc(2^shift x), p_l)), shift_r = mu_r.
-// Output: out[l*plane + r*k_pad + h], K-major, zeros in the padding.
-enum { MODE_QUANT = 0, MODE_RESID = 1 };
-
+// k_planes_*: Abar = BF16(ceil(2^mu' |x|)), plane 0, K-major, zeros in the padding.
+// k_resid_*: planes l < N = BF16(mod(trunc(2^mu x), p_l)), K-major, zeros in padding.
+// Output element (l, r, h) at out[l*plane + r*k_pad + h].
 struct PlaneArgs {
     __nv_bfloat16 *out;
     long plane;          // elements between planes
     int R_pad, k, k_pad;
-    const unsigned long long *row_max;   // MODE_QUANT: shift = 5 - floor(log2 max)
-    const int32_t *shift;                 // MODE_RESID: mu or nu
-    const int *n_dev;                     // MODE_RESID: number of planes
+    const unsigned long long *row_max;   // quantisation: shift = 5 - floor(log2 max)
+    const int32_t *shift;                 // residues: mu or nu
+    const int *n_dev;                     // residues: number of planes
 };
 
 __device__ __forceinline__ int quant_shift(const unsigned long long *row_max, int r) {
@@ -271,72 +296,39 @@ __device__ __forceinline__ int quant_shift(const unsigned long long *row_max, in
     return b ? 5 - floor_log2_bits(b) : 0;     // zero row: mu' = 0
 }
 
-template <int MODE, typename T>
-__device__ __forceinline__ void emit8(const PlaneArgs &a, const T (&x)[8], int shift, int r, int h0,
-                                      int N, const uint8_t (*pow2)[256]) {
-    __nv_bfloat16 *base = a.out + (long)r * a.k_pad + h0;
-    if (MODE == MODE_QUANT) {
-        uint4 v;
-        v.x = pack_bf16x2(ceil_scaled_abs(x[0], shift), ceil_scaled_abs(x[1], shift));
-        v.y = pack_bf16x2(ceil_scaled_abs(x[2], shift), ceil_scaled_abs(x[3], shift));
-        v.z = pack_bf16x2(ceil_scaled_abs(x[4], shift), ceil_scaled_abs(x[5], shift));
-        v.w = pack_bf16x2(ceil_scaled_abs(x[6], shift), ceil_scaled_abs(x[7], shift));
-        *reinterpret_cast<uint4 *>(base) = v;
-    } else {
-        Int iv[8];
-#pragma unroll
-        for (int e = 0; e < 8; e++) iv[e] = trunc_scaled(x[e], shift);
-        for (int l = 0; l < N; l++) {
-            uint4 v;
-            v.x = pack_bf16x2(residue(iv[0], l, pow2), residue(iv[1], l, pow2));
-            v.y = pack_bf16x2(residue(iv[2], l, pow2), residue(iv[3], l, pow2));
-            v.z = pack_bf16x2(residue(iv[4], l, pow2), residue(iv[5], l, pow2));
-            v.w = pack_bf16x2(residue(iv[6], l, pow2), residue(iv[7], l, pow2));
-            *reinterpret_cast<uint4 *>(base + (long)l * a.plane) = v;
-        }
-    }
-}
-
-template <int MODE>
-__device__ __forceinline__ void zero8(const PlaneArgs &a, int r, int h0, int N) {
-    __nv_bfloat16 *base = a.out + (long)r * a.k_pad + h0;
-    const int np = MODE == MODE_QUANT ? 1 : N;
-    for (int l = 0; l < np; l++) *reinterpret_cast<uint4 *>(base + (long)l * a.plane) = make_uint4(0, 0, 0, 0);
-}
-
-__device__ __forceinline__ void load_pow2(uint8_t (*s)[256], int N) {
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(g_pow2);
-    uint32_t *dst = reinterpret_cast<uint32_t *>(s);
-    for (int i = threadIdx.x; i < N * 64; i += blockDim.x) dst[i] = src[i];
+template <typename T>
+__device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8], int shift, int r, int h0) {
+    uint4 v;
+    v.x = pack_bf16x2(ceil_scaled_abs(x[0], shift), ceil_scaled_abs(x[1], shift));
+    v.y = pack_bf16x2(ceil_scaled_abs(x[2], shift), ceil_scaled_abs(x[3], shift));
+    v.z = pack_bf16x2(ceil_scaled_abs(x[4], shift), ceil_scaled_abs(x[5], shift));
+    v.w = pack_bf16x2(ceil_scaled_abs(x[6], shift), ceil_scaled_abs(x[7], shift));
+    *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = v;
 }
 
 // K-contiguous source: one row per blockIdx.y (grid-stride), 8 h per thread.
-template <int MODE, typename T>
+template <typename T>
 __global__ void __launch_bounds__(256) k_planes_kc(Operand<T> X, PlaneArgs a) {
-    __shared__ __align__(16) uint8_t pow2[MODE == MODE_RESID ? kNMax : 1][256];
-    const int N = MODE == MODE_RESID ? *a.n_dev : 1;
-    if (MODE == MODE_RESID) load_pow2(pow2, N);
-    __syncthreads();
     const int h0 = (blockIdx.x * 256 + threadIdx.x) * 8;
     if (h0 >= a.k_pad) return;
     for (int r = blockIdx.y; r < a.R_pad; r += gridDim.y) {
-        if (r >= X.R) { zero8<MODE>(a, r, h0, N); continue; }
-        const int shift = MODE == MODE_QUANT ? quant_shift(a.row_max, r) : a.shift[r];
+        if (r >= X.R) {
+            *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
+            continue;
+        }
+        const int shift = quant_shift(a.row_max, r);
         T x[8];
         const T *src = X.ptr + (long)r * X.ld + h0;
 #pragma unroll
         for (int e = 0; e < 8; e++) x[e] = (h0 + e < a.k) ? src[e] : T(0);
-        emit8<MODE>(a, x, shift, r, h0, N, pow2);
+        emit_quant8(a, x, shift, r, h0);
     }
 }
 
 // R-contiguous source: 64 (h) x 64 (r) tiles transposed through shared memory.
-template <int MODE, typename T>
+template <typename T>
 __global__ void __launch_bounds__(256) k_planes_rc(Operand<T> X, PlaneArgs a) {
-    __shared__ __align__(16) uint8_t pow2[MODE == MODE_RESID ? kNMax : 1][256];
     __shared__ T tile[64][65];
-    const int N = MODE == MODE_RESID ? *a.n_dev : 1;
-    if (MODE == MODE_RESID) load_pow2(pow2, N);
     const int h_base = blockIdx.x * 64, r_base = blockIdx.y * 64;
     {
         const int rr = threadIdx.x & 63;
@@ -353,17 +345,82 @@ __global__ void __launch_bounds__(256) k_planes_rc(Operand<T> X, PlaneArgs a) {
     const int r = r_base + rr;
     if (r >= a.R_pad) return;
     const bool live = r < X.R;
-    const int shift = !live ? 0 : (MODE == MODE_QUANT ? quant_shift(a.row_max, r) : a.shift[r]);
+    const int shift = live ? quant_shift(a.row_max, r) : 0;
 #pragma unroll
     for (int g = 0; g < 2; g++) {
         const int hh0 = hq * 16 + g * 8;
         const int h0 = h_base + hh0;
         if (h0 >= a.k_pad) continue;
-        if (!live) { zero8<MODE>(a, r, h0, N); continue; }
         T x[8];
 #pragma unroll
-        for (int e = 0; e < 8; e++) x[e] = tile[hh0 + e][rr];
-        emit8<MODE>(a, x, shift, r, h0, N, pow2);
+        for (int e = 0; e < 8; e++) x[e] = live ? tile[hh0 + e][rr] : T(0);
+        emit_quant8(a, x, shift, r, h0);
+    }
+}
+
+// Residues of two neighbouring elements of row r for every modulus: one
+// 32-bit store (two BF16) per plane.
+template <int J, typename T>
+__device__ __forceinline__ void emit_resid2(uint32_t *dst, long pw, int N, T x0, T x1, int shift) {
+    float d0[J], d1[J];
+    int b0, b1;
+    limbs_of<J>(x0, shift, d0, b0);
+    limbs_of<J>(x1, shift, d1, b1);
+    dst[0] = pack_bf16x2f(float(b0), float(b1));
+    for (int l = 1; l < N; l++) dst[(long)l * pw] = pack_bf16x2f(residue_odd<J>(d0, l), residue_odd<J>(d1, l));
+}
+
+template <int J, typename T>
+__global__ void __launch_bounds__(256) k_resid_kc(Operand<T> X, PlaneArgs a) {
+    const int N = *a.n_dev;
+    const long pw = a.plane / 2;
+    const int h0 = (blockIdx.x * 256 + threadIdx.x) * 2;
+    if (h0 >= a.k_pad) return;
+    for (int r = blockIdx.y; r < a.R_pad; r += gridDim.y) {
+        uint32_t *dst = reinterpret_cast<uint32_t *>(a.out + (long)r * a.k_pad + h0);
+        if (r >= X.R) {
+            for (int l = 0; l < N; l++) dst[(long)l * pw] = 0u;
+            continue;
+        }
+        const T *src = X.ptr + (long)r * X.ld + h0;
+        const T x0 = h0 < a.k ? src[0] : T(0);
+        const T x1 = h0 + 1 < a.k ? src[1] : T(0);
+        emit_resid2<J>(dst, pw, N, x0, x1, a.shift[r]);
+    }
+}
+
+// R-contiguous source: a 64 (r) x 64 (h) tile transposed through shared
+// memory; each warp then writes 128 contiguous bytes of one row per plane.
+template <int J, typename T>
+__global__ void __launch_bounds__(256) k_resid_rc(Operand<T> X, PlaneArgs a) {
+    __shared__ T tile[64][65];               // [r][h]
+    const int N = *a.n_dev;
+    const long pw = a.plane / 2;
+    const int h_base = blockIdx.x * 64, r_base = blockIdx.y * 64;
+    {
+        const int rr = threadIdx.x & 63;
+        const int r = r_base + rr;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int hh = (threadIdx.x >> 6) + 4 * i;
+            const int h = h_base + hh;
+            tile[rr][hh] = (r < X.R && h < a.k) ? X.ptr[(long)h * X.ld + r] : T(0);
+        }
+    }
+    __syncthreads();
+    const int pi = threadIdx.x & 31;
+    const int h0 = h_base + 2 * pi;
+#pragma unroll 1
+    for (int i = 0; i < 8; i++) {
+        const int rr = (threadIdx.x >> 5) + 8 * i;
+        const int r = r_base + rr;
+        if (r >= a.R_pad || h0 >= a.k_pad) continue;
+        uint32_t *dst = reinterpret_cast<uint32_t *>(a.out + (long)r * a.k_pad + h0);
+        if (r >= X.R) {
+            for (int l = 0; l < N; l++) dst[(long)l * pw] = 0u;
+            continue;
+        }
+        emit_resid2<J>(dst, pw, N, tile[rr][2 * pi], tile[rr][2 * pi + 1], a.shift[r]);
     }
 }
 
@@ -709,6 +766,11 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
 template <typename TO, int B>
 __global__ void __launch_bounds__(256) k_crt(const int8_t *W, long w_plane, int n_pad, const int *n_dev,
                                              const int32_t *mu, const int32_t *nu, TO *C, long ldc, int m, int n) {
+    // double(w) for every INT8 w, read from shared memory instead of converting
+    // on the (slow) FP64 pipe
+    __shared__ double wd[256];
+    wd[threadIdx.x] = double(int(int8_t(uint8_t(threadIdx.x))));
+    __syncthreads();
     const int N = *n_dev;
     const DevN d = B == 64 ? c_n64[N] : c_n32[N];
     const int j0 = (blockIdx.x * 256 + threadIdx.x) * 4;
@@ -718,22 +780,22 @@ __global__ void __launch_bounds__(256) k_crt(const int8_t *W, long w_plane, int 
         long long a1[4] = {0, 0, 0, 0};
         double f1[4] = {0.0, 0.0, 0.0, 0.0}, f2[4] = {0.0, 0.0, 0.0, 0.0};
         for (int l = 0; l < N; l++) {
-            const char4 w = *reinterpret_cast<const char4 *>(wp + (long)l * w_plane);
-            const int wv[4] = {w.x, w.y, w.z, w.w};
+            const uint32_t w4 = *reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane);
             if (B == 64) {
                 const long long s1 = c_s1i[d.offset + l];
                 const double s2 = c_s2d[d.offset + l];
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    a1[e] += s1 * wv[e];
-                    f2[e] = fma(s2, double(wv[e]), f2[e]);
+                    const uint32_t b = (w4 >> (8 * e)) & 255u;
+                    a1[e] += s1 * int(int8_t(b));
+                    f2[e] = fma(s2, wd[b], f2[e]);
                 }
             } else {
                 const double s1 = c_s1f[d.offset + l];
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    f1[e] = fma(s1, double(wv[e]), f1[e]);
-                    f2[e] = fma(0.0, double(wv[e]), f2[e]);
+                    const uint32_t b = (w4 >> (8 * e)) & 255u;
+                    f1[e] = fma(s1, wd[b], f1[e]);
                 }
             }
         }
@@ -744,7 +806,8 @@ __global__ void __launch_bounds__(256) k_crt(const int8_t *W, long w_plane, int 
             if (j >= n) break;
             const double c1 = B == 64 ? __ll2double_rn(a1[e]) * d.g : f1[e];
             const double q = rint(d.Pinv * c1);
-            const double cpp = fma(-q, d.P2, fma(-q, d.P1, c1) + f2[e]);
+            // b = 32: P2 = 0 and C'(2) = +0, so fma(-q, 0, x + 0) = x + 0 as in the b = 64 form
+            const double cpp = B == 64 ? fma(-q, d.P2, fma(-q, d.P1, c1) + f2[e]) : fma(-q, d.P1, c1) + 0.0;
             const double v = scale_pow2(cpp, -(mi + nu[j]));
             if (B == 64) C[(long)i * ldc + j] = TO(v);
             else C[(long)i * ldc + j] = TO(__double2float_rn(v));

@@ -205,6 +205,13 @@ void build(Tables &T) {
         T.mod.c48[l] = uint32_t((uint64_t(1) << 48) % p);
         uint32_t v = 1 % p;
         for (int e = 0; e < 256; e++) { T.mod.pow2[l][e] = uint8_t(v); v = (v * 2) % p; }
+        v = 1 % p;
+        for (int j = 0; j < kMaxLimbs; j++) {
+            T.mod.w12[l][j] = float(v);
+            v = uint32_t((uint64_t(v) << kLimbBits) % p);
+        }
+        T.mod.pf[l] = float(p);
+        T.mod.invp[l] = 1.0f / float(p);
     }
     const long double u64 = 0x1p-53L, u32 = 0x1p-24L;
     T.c = f32_down(-0.5L / (1.0L - 4.0L * u32));

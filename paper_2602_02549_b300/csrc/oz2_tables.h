@@ -6,6 +6,8 @@
 namespace oz2 {
 
 constexpr int kNMax = 49;
+constexpr int kLimbBits = 12;                           // residue limbs of |A'|, 12 bits each
+constexpr int kMaxLimbs = 16;                           // 192 bits >= |A'| < 2^(P'+6), N <= 49
 constexpr int kPackedLen = (kNMax * (kNMax + 1)) / 2;  // sum_{N=1}^{49} N entries
 
 // Per-modulus reduction constants (index l = 0..48).
@@ -16,6 +18,9 @@ struct ModTable {
     uint32_t c24[kNMax];     // 2^24 mod p
     uint32_t c48[kNMax];     // 2^48 mod p
     uint8_t pow2[kNMax][256];// 2^E mod p, E = 0..255
+    float w12[kNMax][kMaxLimbs];  // 2^(12 j) mod p
+    float pf[kNMax];         // p as float
+    float invp[kNMax];       // RN_f32(1/p)
 };
 
 // Per-N scalars for one precision (b = 64 or 32).
