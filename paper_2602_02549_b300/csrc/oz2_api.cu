@@ -77,6 +77,7 @@ int ensure_device(int *dev_out) {
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w12, T.mod.w12, sizeof T.mod.w12);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_pf, T.mod.pf, sizeof T.mod.pf);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_invp, T.mod.invp, sizeof T.mod.invp);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_pow2, T.mod.pow2, sizeof T.mod.pow2);
         if (e != cudaSuccess) return cuda_fail(e);
         st.tables = true;
     }
@@ -177,25 +178,15 @@ int launch_quant(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
     return cuda_fail(cudaGetLastError());
 }
 
-template <int J, typename T>
-void launch_resid_j(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
+template <typename T>
+int launch_resid(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
     if (X.kcontig) {
         dim3 grid((a.k_pad / 2 + 255) / 256, grid_rows(a.R_pad));
-        k_resid_kc<J, T><<<grid, 256, 0, st>>>(X, a);
+        k_resid_kc<T><<<grid, 256, 0, st>>>(X, a);
     } else {
         dim3 grid(a.k_pad / 64, a.R_pad / 64);
-        k_resid_rc<J, T><<<grid, 256, 0, st>>>(X, a);
+        k_resid_rc<T><<<grid, 256, 0, st>>>(X, a);
     }
-}
-
-// Limbs of 12 bits covering |x'|: |x'| < 2^(P'+6) when mu, nu come from
-// Algorithm 2 (mu_i <= 5 - alpha_i + P'); injected exponents get the maximum.
-template <typename T>
-int launch_resid(const Operand<T> &X, const PlaneArgs &a, int bits, cudaStream_t st) {
-    const int J = (bits + kLimbBits - 1) / kLimbBits;
-    if (J <= 8) launch_resid_j<8>(X, a, st);
-    else if (J <= 12) launch_resid_j<12>(X, a, st);
-    else launch_resid_j<16>(X, a, st);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -340,10 +331,8 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
     if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
     PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, nullptr, mu_use, ndev};
     PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, nullptr, nu_use, ndev};
-    const float pp = fp32 ? tables().n32[nmax].Pprime : tables().n64[nmax].Pprime;
-    const int bits = inject ? kLimbBits * kMaxLimbs : int(pp) + 8;
-    if ((rc = launch_resid(opA, ra, bits, st))) return rc;
-    if ((rc = launch_resid(opB, rb, bits, st))) return rc;
+    if ((rc = launch_resid(opA, ra, st))) return rc;
+    if ((rc = launch_resid(opB, rb, st))) return rc;
     const long w_plane = long(d.m_pad) * d.n_pad;
     if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
     GemmArgs g{d.m_pad, d.n_pad, d.k_pad / gemm::BK, ndev, W, w_plane, nullptr, nullptr};

@@ -40,7 +40,8 @@ __constant__ int c_p[kNMax];
 __constant__ uint32_t c_magic[kNMax];
 __constant__ uint32_t c_c16[kNMax];
 __constant__ float c_cneg;                 // single_down(-0.5/(1-4 u32))
-__constant__ float c_w12[kNMax][kMaxLimbs];// 2^(12 j) mod p_l
+__constant__ float c_w12[kNMax][kLimbs];   // balanced 2^(12 j) mod p_l
+__device__ uint8_t g_pow2[kNMax][256];     // 2^E mod p_l
 __constant__ float c_pf[kNMax];            // p_l
 __constant__ float c_invp[kNMax];          // RN_f32(1/p_l)
 
@@ -125,44 +126,47 @@ __device__ __forceinline__ Int trunc_scaled(T x, int shift) {
 }
 
 // Residues of x' = trunc(2^shift x) (Algorithm 3, A'_l = mod(A', p_l)).
-// |x'| < 2^(P'+6) <= 2^177 is cut into J limbs of 12 bits at fixed bit
-// positions 12 j, carrying the sign of x'.  For odd p_l,
-//   t = sum_j d_j (2^(12 j) mod p_l)
-// is congruent to x' and |t| < J 2^12 2^8 <= 2^24, so t and every partial sum
-// are exact in FP32; q = rint(t / p_l) (FP32 reciprocal; off by at most one)
-// and one correction give the balanced residue in [-(p-1)/2, (p-1)/2].
+// x' = (-1)^neg M 2^E with M < 2^53.  M is cut once into five 12-bit limbs d_i
+// (with the sign of x'); for odd p_l and balanced weights w_i = 2^(12 i) mod p_l
+// in [-(p-1)/2, (p-1)/2]:
+//   t  = sum_i d_i w_i,  |t| < 5 * 2^12 * 127 < 2^22, exact in FP32 (every
+//        product and partial sum is an integer below 2^24);
+//   r1 = t - p rint(t / p),    balanced residue of M (with sign);
+//   v  = r1 (2^E mod p_l),     |v| < 2^15, exact;
+//   r  = v - p rint(v / p),    the balanced residue of x'.
+// rint(t * RN(1/p)) equals round(t / p) because t / p lies at least 1/(2p) from
+// a half-integer (p odd) while the FP32 error is below |t| 2^-23 / p < 1/(2p).
 // p = 256 takes the low byte of x' in two's complement (class 128 -> -128).
-template <int J, typename T>
-__device__ __forceinline__ void limbs_of(T x, int shift, float (&d)[J], int &res256) {
+struct Limbs {
+    float d[kLimbs];
+    int E;       // table index (clamped to 255)
+    int r256;    // residue modulo 256
+};
+
+template <typename T>
+__device__ __forceinline__ Limbs limbs_of(T x, int shift) {
     const Int v = trunc_scaled(x, shift);
+    const uint32_t lo = uint32_t(v.M), hi = uint32_t(v.M >> 32);
+    const uint32_t e[kLimbs] = {lo & 0xFFFu, (lo >> 12) & 0xFFFu, ((lo >> 24) | (hi << 8)) & 0xFFFu,
+                                (hi >> 4) & 0xFFFu, (hi >> 16) & 0xFFFu};
+    Limbs L;
 #pragma unroll
-    for (int j = 0; j < J; j++) {
-        const int s = kLimbBits * j - v.E;
-        uint64_t q = 0;
-        if (s >= 0) {
-            if (s < 64) q = v.M >> s;
-        } else if (-s < kLimbBits) {
-            q = v.M << (-s);
-        }
-        const float f = float(uint32_t(q) & 4095u);
-        d[j] = v.neg ? -f : f;
-    }
-    uint32_t lo = uint32_t(v.E >= 8 ? 0ull : (v.M << v.E)) & 255u;
-    if (v.neg) lo = (256u - lo) & 255u;
-    res256 = int(int8_t(lo));
+    for (int i = 0; i < kLimbs; i++) L.d[i] = v.neg ? -float(e[i]) : float(e[i]);
+    L.E = v.E > 255 ? 255 : v.E;
+    uint32_t b = v.E >= 8 ? 0u : ((lo << v.E) & 255u);
+    if (v.neg) b = (256u - b) & 255u;
+    L.r256 = int(int8_t(b));
+    return L;
 }
 
-template <int J>
-__device__ __forceinline__ float residue_odd(const float (&d)[J], int l) {
+__device__ __forceinline__ float residue_odd(const Limbs &L, int l, const uint8_t (*pow2)[256]) {
     float t = 0.0f;
 #pragma unroll
-    for (int j = 0; j < J; j++) t = fmaf(d[j], c_w12[l][j], t);
-    const float p = c_pf[l];
-    const float q = rintf(t * c_invp[l]);
-    float r = fmaf(-q, p, t);
-    if (r > 0.5f * p) r -= p;
-    else if (r < -0.5f * p) r += p;
-    return r;
+    for (int i = 0; i < kLimbs; i++) t = fmaf(L.d[i], c_w12[l][i], t);
+    const float p = c_pf[l], ip = c_invp[l];
+    const float r1 = fmaf(-rintf(t * ip), p, t);
+    const float v = r1 * float(pow2[l][L.E]);
+    return fmaf(-rintf(v * ip), p, v);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2f(float a, float b) {
@@ -360,19 +364,27 @@ __global__ void __launch_bounds__(256) k_planes_rc(Operand<T> X, PlaneArgs a) {
 
 // Residues of two neighbouring elements of row r for every modulus: one
 // 32-bit store (two BF16) per plane.
-template <int J, typename T>
-__device__ __forceinline__ void emit_resid2(uint32_t *dst, long pw, int N, T x0, T x1, int shift) {
-    float d0[J], d1[J];
-    int b0, b1;
-    limbs_of<J>(x0, shift, d0, b0);
-    limbs_of<J>(x1, shift, d1, b1);
-    dst[0] = pack_bf16x2f(float(b0), float(b1));
-    for (int l = 1; l < N; l++) dst[(long)l * pw] = pack_bf16x2f(residue_odd<J>(d0, l), residue_odd<J>(d1, l));
+template <typename T>
+__device__ __forceinline__ void emit_resid2(uint32_t *dst, long pw, int N, T x0, T x1, int shift,
+                                            const uint8_t (*pow2)[256]) {
+    const Limbs a = limbs_of(x0, shift), b = limbs_of(x1, shift);
+    dst[0] = pack_bf16x2f(float(a.r256), float(b.r256));
+    for (int l = 1; l < N; l++)
+        dst[(long)l * pw] = pack_bf16x2f(residue_odd(a, l, pow2), residue_odd(b, l, pow2));
 }
 
-template <int J, typename T>
+__device__ __forceinline__ void load_pow2(uint8_t (*s)[256], int N) {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(g_pow2);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(s);
+    for (int i = threadIdx.x; i < N * 64; i += blockDim.x) dst[i] = src[i];
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_resid_kc(Operand<T> X, PlaneArgs a) {
+    __shared__ __align__(16) uint8_t pow2[kNMax][256];
     const int N = *a.n_dev;
+    load_pow2(pow2, N);
+    __syncthreads();
     const long pw = a.plane / 2;
     const int h0 = (blockIdx.x * 256 + threadIdx.x) * 2;
     if (h0 >= a.k_pad) return;
@@ -385,16 +397,18 @@ __global__ void __launch_bounds__(256) k_resid_kc(Operand<T> X, PlaneArgs a) {
         const T *src = X.ptr + (long)r * X.ld + h0;
         const T x0 = h0 < a.k ? src[0] : T(0);
         const T x1 = h0 + 1 < a.k ? src[1] : T(0);
-        emit_resid2<J>(dst, pw, N, x0, x1, a.shift[r]);
+        emit_resid2(dst, pw, N, x0, x1, a.shift[r], pow2);
     }
 }
 
 // R-contiguous source: a 64 (r) x 64 (h) tile transposed through shared
 // memory; each warp then writes 128 contiguous bytes of one row per plane.
-template <int J, typename T>
+template <typename T>
 __global__ void __launch_bounds__(256) k_resid_rc(Operand<T> X, PlaneArgs a) {
+    __shared__ __align__(16) uint8_t pow2[kNMax][256];
     __shared__ T tile[64][65];               // [r][h]
     const int N = *a.n_dev;
+    load_pow2(pow2, N);
     const long pw = a.plane / 2;
     const int h_base = blockIdx.x * 64, r_base = blockIdx.y * 64;
     {
@@ -420,7 +434,7 @@ __global__ void __launch_bounds__(256) k_resid_rc(Operand<T> X, PlaneArgs a) {
             for (int l = 0; l < N; l++) dst[(long)l * pw] = 0u;
             continue;
         }
-        emit_resid2<J>(dst, pw, N, tile[rr][2 * pi], tile[rr][2 * pi + 1], a.shift[r]);
+        emit_resid2(dst, pw, N, tile[rr][2 * pi], tile[rr][2 * pi + 1], a.shift[r], pow2);
     }
 }
 

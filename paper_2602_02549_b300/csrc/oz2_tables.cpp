@@ -206,9 +206,10 @@ void build(Tables &T) {
         uint32_t v = 1 % p;
         for (int e = 0; e < 256; e++) { T.mod.pow2[l][e] = uint8_t(v); v = (v * 2) % p; }
         v = 1 % p;
-        for (int j = 0; j < kMaxLimbs; j++) {
-            T.mod.w12[l][j] = float(v);
-            v = uint32_t((uint64_t(v) << kLimbBits) % p);
+        for (int j = 0; j < kLimbs; j++) {
+            const int bal = 2 * v > p ? int(v) - int(p) : int(v);
+            T.mod.w12[l][j] = float(bal);
+            v = uint32_t((uint64_t(v) << 12) % p);
         }
         T.mod.pf[l] = float(p);
         T.mod.invp[l] = 1.0f / float(p);

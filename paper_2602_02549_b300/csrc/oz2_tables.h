@@ -6,8 +6,7 @@
 namespace oz2 {
 
 constexpr int kNMax = 49;
-constexpr int kLimbBits = 12;                           // residue limbs of |A'|, 12 bits each
-constexpr int kMaxLimbs = 16;                           // 192 bits >= |A'| < 2^(P'+6), N <= 49
+constexpr int kLimbs = 5;                               // 12-bit limbs of a 53-bit mantissa
 constexpr int kPackedLen = (kNMax * (kNMax + 1)) / 2;  // sum_{N=1}^{49} N entries
 
 // Per-modulus reduction constants (index l = 0..48).
@@ -18,7 +17,7 @@ struct ModTable {
     uint32_t c24[kNMax];     // 2^24 mod p
     uint32_t c48[kNMax];     // 2^48 mod p
     uint8_t pow2[kNMax][256];// 2^E mod p, E = 0..255
-    float w12[kNMax][kMaxLimbs];  // 2^(12 j) mod p
+    float w12[kNMax][kLimbs];     // balanced 2^(12 j) mod p, in [-(p-1)/2, (p-1)/2] (odd p)
     float pf[kNMax];         // p as float
     float invp[kNMax];       // RN_f32(1/p)
 };
