@@ -65,6 +65,15 @@ def test_dgemm_parity(oracle, shape, N):
     assert ((g["nu"] >= lo) & (g["nu"] <= hi)).all()
 
 
+@pytest.mark.parametrize("shape,N", [((4200, 300, 200), 5), ((8300, 70, 130), 14), ((16390, 33, 40), 17)])
+def test_tall_problems(oracle, shape, N):
+    # many row tiles (up to 129) and ragged last tiles in both directions
+    m, n, k = shape
+    A, Bm = paper_pair(m, n, k, 1.0, seed=m)
+    g = run_gpu(A, Bm, N)
+    check_against_oracle(oracle, A, Bm, g, bound=(m * n * k < 2e8))
+
+
 @pytest.mark.parametrize("N", [3, 5, 6, 8, 20, 33, 49])
 def test_dgemm_parity_moduli(oracle, N):
     A, Bm = paper_pair(150, 170, 700, 1.0, seed=N)
