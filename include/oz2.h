@@ -165,6 +165,11 @@ OZ2_API int oz2_check_log2f(void *stream, unsigned long long *dev_out);
 OZ2_API int oz2_gemm_noalloc(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
                              double *C, int ldc, int nmoduli, int mode, double target, void *stream);
 
+/* The last CUDA failure behind an OZ2_ECUDA: returns the cudaError_t value
+ * (or 10000 + a CUresult of a driver call), 0 if none; *line (optional) gets
+ * the library source line that caught it.  For diagnostics. */
+OZ2_API int oz2_last_error(int *line);
+
 /* Human-readable name of a status code (static string). */
 OZ2_API const char *oz2_status_str(int status);
 

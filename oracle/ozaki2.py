@@ -114,8 +114,28 @@ def exponent_shift(c: np.float32, e: np.ndarray, Pprime: np.float32) -> np.ndarr
 # --------------------------------------------------------------------------- #
 # Algorithm 2: Scaling
 # --------------------------------------------------------------------------- #
+def ceil_sqrt(x: int) -> int:
+    """ceil(sqrt(x)) of a nonnegative integer, exactly."""
+    r = math.isqrt(x)
+    return r if r * r == x else r + 1
+
+
+def fast_cbar_maxima(Abar: np.ndarray, Bbar: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Fast mode (reading; the paper only names the mode): row and column maxima
+    of the Cauchy-Schwarz majorant chat_ij = ceil(||Abar_i||_2 ||Bbar_j||_2) >= cbar_ij,
+    i.e. ceil(sqrt(ssA_i * max_j ssB_j)) and ceil(sqrt(max_i ssA_i * ssB_j)), with
+    ssA_i = sum_h abar_ih^2 and ssB_j = sum_h bbar_hj^2 exact integers."""
+    ssA = [int(v) for v in (Abar.astype(np.int64) ** 2).sum(axis=1)]
+    ssB = [int(v) for v in (Bbar.astype(np.int64) ** 2).sum(axis=0)]
+    mA = max(ssA, default=0)
+    mB = max(ssB, default=0)
+    row = np.array([ceil_sqrt(a * mB) for a in ssA], dtype=np.int64)
+    col = np.array([ceil_sqrt(mA * b) for b in ssB], dtype=np.int64)
+    return row, col
+
+
 def scaling(A: np.ndarray, B: np.ndarray, N: int, b: int = 64,
-            mu_in: np.ndarray | None = None, nu_in: np.ndarray | None = None) -> dict:
+            mu_in: np.ndarray | None = None, nu_in: np.ndarray | None = None, fast: bool = False) -> dict:
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
     m, k = A.shape
@@ -137,12 +157,20 @@ def scaling(A: np.ndarray, B: np.ndarray, N: int, b: int = 64,
     rs, cs = _strides(BT)
     L.oz2o_ceil_scaled_abs(n, k, _p(BT), rs, cs, _p(nu_p), _p(BbarT))
     Bbar = np.ascontiguousarray(BbarT.T)
-    # Cbar = Abar Bbar, exact
-    Cbar = gemm_i8(Abar, Bbar)
-    # Dbar = single_up(Cbar); e_i = log2f(max_h dbar_ih); f_j = log2f(max_h dbar_hj)
-    Dbar = single_up(Cbar)
-    drow = Dbar.max(axis=1) if n > 0 else np.zeros(m, np.float32)
-    dcol = Dbar.max(axis=0) if m > 0 else np.zeros(n, np.float32)
+    if not fast:
+        # Cbar = Abar Bbar, exact
+        Cbar = gemm_i8(Abar, Bbar)
+        cmax_row = Cbar.max(axis=1) if n else np.zeros(m, np.int64)
+        cmax_col = Cbar.max(axis=0) if m else np.zeros(n, np.int64)
+        # Dbar = single_up(Cbar); e_i = log2f(max_h dbar_ih); f_j = log2f(max_h dbar_hj)
+        Dbar = single_up(Cbar)
+        drow = Dbar.max(axis=1) if n > 0 else np.zeros(m, np.float32)
+        dcol = Dbar.max(axis=0) if m > 0 else np.zeros(n, np.float32)
+    else:
+        Cbar = None
+        cmax_row, cmax_col = fast_cbar_maxima(Abar, Bbar)
+        drow = single_up(cmax_row)
+        dcol = single_up(cmax_col)
     drow = np.where(drow == 0, np.float32(1), drow)          # reading: empty row -> 1
     dcol = np.where(dcol == 0, np.float32(1), dcol)
     e = log2f(drow)
@@ -158,8 +186,7 @@ def scaling(A: np.ndarray, B: np.ndarray, N: int, b: int = 64,
     Ap = trunc_scaled_rows(A, mu)
     Bp = np.ascontiguousarray(trunc_scaled_rows(B.T, nu).T)
     return dict(alpha=alpha, beta=beta, mu_p=mu_p, nu_p=nu_p, Abar=Abar, Bbar=Bbar,
-                Cbar=Cbar, cmax_row=Cbar.max(axis=1) if n else np.zeros(m, np.int64),
-                cmax_col=Cbar.max(axis=0) if m else np.zeros(n, np.int64),
+                Cbar=Cbar, cmax_row=cmax_row, cmax_col=cmax_col,
                 e=e, f=f, mu=mu, nu=nu, own_mu=own_mu, own_nu=own_nu, Ap=Ap, Bp=Bp)
 
 
@@ -248,14 +275,14 @@ def unscale(Cpp: np.ndarray, mu: np.ndarray, nu: np.ndarray, b: int = 64) -> np.
 # Algorithm 1: OS_II
 # --------------------------------------------------------------------------- #
 def os_ii(A: np.ndarray, B: np.ndarray, N: int, b: int = 64,
-          mu_in=None, nu_in=None, keep_residues: bool = False, consts=None) -> dict:
+          mu_in=None, nu_in=None, keep_residues: bool = False, consts=None, fast: bool = False) -> dict:
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
     if not (N_MIN <= N <= N_MAX):
         raise ValueError("N out of range")
     if A.shape[1] > K_MAX:
         raise ValueError("k > 2^17")
-    s = scaling(A, B, N, b, mu_in, nu_in)
+    s = scaling(A, B, N, b, mu_in, nu_in, fast=fast)
     r = crt(s["Ap"], s["Bp"], N, b, keep_residues, consts)
     s.update(r)
     s["C"] = unscale(r["Cpp"], s["mu"], s["nu"], b)

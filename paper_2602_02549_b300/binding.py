@@ -25,7 +25,12 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 class Oz2Error(RuntimeError):
     def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: {status_str(status)} ({status})")
+        detail = ""
+        if status == OZ2_ECUDA:
+            line = ctypes.c_int()
+            err = lib().oz2_last_error(ctypes.byref(line))
+            detail = f" [CUDA error {err} caught at oz2_api.cu:{line.value}]"
+        super().__init__(f"{where}: {status_str(status)} ({status}){detail}")
         self.status = status
 
 
@@ -73,6 +78,8 @@ def lib() -> ctypes.CDLL:
         L.oz2_status_str.argtypes = [i]
         L.oz2_status_str.restype = ctypes.c_char_p
         L.oz2_version.restype = i
+        L.oz2_last_error.argtypes = [P]
+        L.oz2_last_error.restype = i
         _lib = L
     return _lib
 

@@ -7,6 +7,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -33,17 +34,30 @@ DeviceState g_dev[kMaxDevices];
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-int cuda_fail(cudaError_t e) {
+// Last CUDA failure seen by the library (for oz2_last_error): the error code
+// and the source line of the check that caught it.
+std::atomic<int> g_last_cuda_error{0};
+std::atomic<int> g_last_cuda_line{0};
+
+int cuda_fail_at(cudaError_t e, int line) {
     if (e == cudaSuccess) return OZ2_OK;
+    g_last_cuda_error.store(int(e));
+    g_last_cuda_line.store(line);
     (void)cudaGetLastError();
     return OZ2_ECUDA;
 }
+#define cuda_fail(e) cuda_fail_at((e), __LINE__)
 
 // Upload the host-built tables to this device's constant memory (once).
 int ensure_device(int *dev_out) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail(cudaErrorUnknown);
+    cudaError_t ge = cudaGetDevice(&dev);
+    if (ge != cudaSuccess) return cuda_fail(ge);
     if (dev < 0 || dev >= kMaxDevices) return OZ2_ENOTSUP;
+    // binds the device's primary context to this host thread: the driver call
+    // cuTensorMapEncodeTiled needs a current context, which a thread that has
+    // only made runtime calls (e.g. torch's autograd worker) may not have yet
+    if ((ge = cudaSetDevice(dev)) != cudaSuccess) return cuda_fail(ge);
     *dev_out = dev;
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceState &st = g_dev[dev];
@@ -110,7 +124,7 @@ Dims make_dims(int m, int n, int k, int nmax) {
 
 struct Layout {
     // the block up to zero_end is cleared at the start of every call
-    size_t hmaxA, hmaxB, cmax_row, cmax_col, red, zero_end;
+    size_t hmaxA, hmaxB, cmax_row, cmax_col, red, ssA, ssB, zero_end;
     size_t rmaxA, rmaxB, rsumA, rsumB, mu, nu, ndev, resA, resB, W, total;
 };
 
@@ -123,6 +137,8 @@ Layout make_layout(const Dims &d) {
     L.cmax_row = take(sizeof(int) * size_t(d.m_pad));
     L.cmax_col = take(sizeof(int) * size_t(d.n_pad));
     L.red = take(sizeof(unsigned long long) * 8);
+    L.ssA = take(sizeof(int) * size_t(d.m_pad));
+    L.ssB = take(sizeof(int) * size_t(d.n_pad));
     L.zero_end = o;
     L.rmaxA = take(sizeof(unsigned long long) * size_t(d.m_pad));
     L.rmaxB = take(sizeof(unsigned long long) * size_t(d.n_pad));
@@ -147,7 +163,12 @@ int encode_bf16_2d(CUtensorMap *tm, const void *base, uint64_t rows, uint64_t co
     CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? OZ2_OK : OZ2_ECUDA;
+    if (r != CUDA_SUCCESS) {
+        g_last_cuda_error.store(10000 + int(r));   // driver result, offset to tell it apart
+        g_last_cuda_line.store(__LINE__);
+        return OZ2_ECUDA;
+    }
+    return OZ2_OK;
 }
 
 int grid_rows(int rows) { return std::max(1, std::min(rows, 65535)); }
@@ -228,7 +249,6 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
     constexpr bool fp32 = sizeof(T) == 4;
     int rc = validate(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o);
     if (rc) return rc;
-    if (mode & OZ2_FAST) return OZ2_ENOTSUP;
     const int nmax = resolve_nmax(nmoduli, o, fp32);
     const Dims d = make_dims(m, n, k, nmax);
     const Layout L = make_layout(d);
@@ -262,6 +282,9 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
     auto *cmax_row = reinterpret_cast<int *>(at(L.cmax_row));
     auto *cmax_col = reinterpret_cast<int *>(at(L.cmax_col));
     auto *red = reinterpret_cast<unsigned long long *>(at(L.red));
+    auto *ssA = reinterpret_cast<int *>(at(L.ssA));
+    auto *ssB = reinterpret_cast<int *>(at(L.ssB));
+    const bool fast = mode & OZ2_FAST;
     auto *rmaxA = reinterpret_cast<unsigned long long *>(at(L.rmaxA));
     auto *rmaxB = reinterpret_cast<unsigned long long *>(at(L.rmaxB));
     auto *rsumA = reinterpret_cast<double *>(at(L.rsumA));
@@ -299,14 +322,24 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
         if ((rc = launch_stats(opB, k, rmaxB, rsumB, hmaxB, st))) return rc;
         // Abar, Bbar
         if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
-        PlaneArgs qa{resA, planeA, d.m_pad, k, d.k_pad, rmaxA, nullptr, nullptr};
-        PlaneArgs qb{resB, planeB, d.n_pad, k, d.k_pad, rmaxB, nullptr, nullptr};
+        PlaneArgs qa{resA, planeA, d.m_pad, k, d.k_pad, rmaxA, nullptr, nullptr, fast ? ssA : nullptr, !fast};
+        PlaneArgs qb{resB, planeB, d.n_pad, k, d.k_pad, rmaxB, nullptr, nullptr, fast ? ssB : nullptr, !fast};
         if ((rc = launch_quant(opA, qa, st))) return rc;
         if ((rc = launch_quant(opB, qb, st))) return rc;
-        // Cbar = Abar Bbar: row and column maxima only
         if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
-        GemmArgs g{d.m_pad, d.n_pad, d.k_pad / gemm::BK, nullptr, nullptr, 0, cmax_row, cmax_col};
-        if ((rc = launch_gemm<EPI_MAX>(tA, tB, g, 1, st))) return rc;
+        if (!fast) {
+            // Cbar = Abar Bbar: row and column maxima only
+            GemmArgs g{d.m_pad, d.n_pad, d.k_pad / gemm::BK, nullptr, nullptr, 0, cmax_row, cmax_col};
+            if ((rc = launch_gemm<EPI_MAX>(tA, tB, g, 1, st))) return rc;
+        } else {
+            // fast mode: Cauchy-Schwarz majorant of Cbar from the sums of squares
+            int *mx = reinterpret_cast<int *>(red + 6);
+            k_fast_max<<<std::min(148, (std::max(m, n) + 255) / 256), 256, 0, st>>>(ssA, m, ssB, n, mx);
+            if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+            k_fast_cmax<<<std::min(1184, (m + n + 255) / 256), 256, 0, st>>>(ssA, m, ssB, n, mx, cmax_row,
+                                                                              cmax_col);
+            if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+        }
         // the N rule, then mu and nu
         if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
         if (nmoduli == 0) {
@@ -436,6 +469,11 @@ int oz2_check_log2f(void *stream, unsigned long long *dev_out) {
     if (rc) return rc;
     k_log2f_check<<<148 * 8, 256, 0, st>>>(b0, b1 - b0 + 1, dev_out);
     return cuda_fail(cudaGetLastError());
+}
+
+int oz2_last_error(int *line) {
+    if (line) *line = g_last_cuda_line.load();
+    return g_last_cuda_error.load();
 }
 
 const char *oz2_status_str(int s) {

@@ -293,6 +293,8 @@ struct PlaneArgs {
     const unsigned long long *row_max;   // quantisation: shift = 5 - floor(log2 max)
     const int32_t *shift;                 // residues: mu or nu
     const int *n_dev;                     // residues: number of planes
+    int *sumsq;                           // quantisation, fast mode: sum_h xbar^2 per row (atomicAdd)
+    int write;                            // quantisation: store the BF16 plane (accurate mode)
 };
 
 __device__ __forceinline__ int quant_shift(const unsigned long long *row_max, int r) {
@@ -300,32 +302,53 @@ __device__ __forceinline__ int quant_shift(const unsigned long long *row_max, in
     return b ? 5 - floor_log2_bits(b) : 0;     // zero row: mu' = 0
 }
 
+// Stores 8 values of Abar (accurate mode) and returns their sum of squares
+// (fast mode's Cauchy-Schwarz majorant; exact: xbar <= 64, k <= 2^17).
 template <typename T>
-__device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8], int shift, int r, int h0) {
-    uint4 v;
-    v.x = pack_bf16x2(ceil_scaled_abs(x[0], shift), ceil_scaled_abs(x[1], shift));
-    v.y = pack_bf16x2(ceil_scaled_abs(x[2], shift), ceil_scaled_abs(x[3], shift));
-    v.z = pack_bf16x2(ceil_scaled_abs(x[4], shift), ceil_scaled_abs(x[5], shift));
-    v.w = pack_bf16x2(ceil_scaled_abs(x[6], shift), ceil_scaled_abs(x[7], shift));
-    *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = v;
+__device__ __forceinline__ int emit_quant8(const PlaneArgs &a, const T (&x)[8], int shift, int r, int h0) {
+    uint32_t q[8];
+    int ss = 0;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        q[e] = ceil_scaled_abs(x[e], shift);
+        ss += int(q[e] * q[e]);
+    }
+    if (a.write) {
+        uint4 v;
+        v.x = pack_bf16x2(q[0], q[1]);
+        v.y = pack_bf16x2(q[2], q[3]);
+        v.z = pack_bf16x2(q[4], q[5]);
+        v.w = pack_bf16x2(q[6], q[7]);
+        *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = v;
+    }
+    return ss;
 }
 
 // K-contiguous source: one row per blockIdx.y (grid-stride), 8 h per thread.
+// Every lane stays to the end of each row (the fast-mode sum of squares is
+// reduced across the warp).
 template <typename T>
 __global__ void __launch_bounds__(256) k_planes_kc(Operand<T> X, PlaneArgs a) {
     const int h0 = (blockIdx.x * 256 + threadIdx.x) * 8;
-    if (h0 >= a.k_pad) return;
+    const bool act = h0 < a.k_pad;
     for (int r = blockIdx.y; r < a.R_pad; r += gridDim.y) {
-        if (r >= X.R) {
-            *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
-            continue;
-        }
-        const int shift = quant_shift(a.row_max, r);
-        T x[8];
-        const T *src = X.ptr + (long)r * X.ld + h0;
+        int ss = 0;
+        if (act) {
+            if (r >= X.R) {
+                if (a.write) *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
+            } else {
+                const int shift = quant_shift(a.row_max, r);
+                T x[8];
+                const T *src = X.ptr + (long)r * X.ld + h0;
 #pragma unroll
-        for (int e = 0; e < 8; e++) x[e] = (h0 + e < a.k) ? src[e] : T(0);
-        emit_quant8(a, x, shift, r, h0);
+                for (int e = 0; e < 8; e++) x[e] = (h0 + e < a.k) ? src[e] : T(0);
+                ss = emit_quant8(a, x, shift, r, h0);
+            }
+        }
+        if (a.sumsq) {
+            for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            if ((threadIdx.x & 31) == 0 && ss) atomicAdd(a.sumsq + r, ss);
+        }
     }
 }
 
@@ -347,18 +370,22 @@ __global__ void __launch_bounds__(256) k_planes_rc(Operand<T> X, PlaneArgs a) {
     __syncthreads();
     const int rr = threadIdx.x >> 2, hq = threadIdx.x & 3;
     const int r = r_base + rr;
-    if (r >= a.R_pad) return;
     const bool live = r < X.R;
     const int shift = live ? quant_shift(a.row_max, r) : 0;
+    int ss = 0;
 #pragma unroll
     for (int g = 0; g < 2; g++) {
         const int hh0 = hq * 16 + g * 8;
         const int h0 = h_base + hh0;
-        if (h0 >= a.k_pad) continue;
         T x[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) x[e] = live ? tile[hh0 + e][rr] : T(0);
-        emit_quant8(a, x, shift, r, h0);
+        ss += emit_quant8(a, x, shift, r, h0);
+    }
+    if (a.sumsq) {   // the 4 threads of row rr are adjacent lanes
+        ss += __shfl_xor_sync(0xffffffffu, ss, 1);
+        ss += __shfl_xor_sync(0xffffffffu, ss, 2);
+        if (hq == 0 && live && ss) atomicAdd(a.sumsq + r, ss);
     }
 }
 
@@ -755,6 +782,41 @@ __global__ void __launch_bounds__(256) k_mu_nu(int m, int n, const unsigned long
         const int v = mp + int(floorf(__fmaf_rd(c, e, Pp)));
         if (isrow) { mu[i] = v; if (mu_out) mu_out[i] = v; }
         else { nu[i] = v; if (nu_out) nu_out[i] = v; }
+    }
+}
+
+// Fast mode (a reading; the paper only names the mode): Cbar is replaced by
+// its Cauchy-Schwarz majorant chat_ij = ceil(||Abar_i||_2 ||Bbar_j||_2), whose
+// row maxima are ceil(sqrt(ssA_i max_j ssB_j)) and column maxima
+// ceil(sqrt(max_i ssA_i ssB_j)).  Lemma 0 only needs Dbar >= Cbar and the
+// maxima <= 2^12 k, which the majorant satisfies.
+__global__ void __launch_bounds__(256) k_fast_max(const int *ssA, int m, const int *ssB, int n, int *mx) {
+    int a = 0, b = 0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) a = max(a, ssA[i]);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) b = max(b, ssB[j]);
+    a = __reduce_max_sync(0xffffffffu, a);
+    b = __reduce_max_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicMax(mx, a);
+        if (b) atomicMax(mx + 1, b);
+    }
+}
+
+__device__ __forceinline__ int ceil_sqrt_u64(unsigned long long x) {
+    unsigned long long r = (unsigned long long)sqrt(double(x));
+    while (r * r > x) r--;
+    while ((r + 1) * (r + 1) <= x) r++;
+    return int(r * r == x ? r : r + 1);
+}
+
+__global__ void __launch_bounds__(256) k_fast_cmax(const int *ssA, int m, const int *ssB, int n, const int *mx,
+                                                   int *cmax_row, int *cmax_col) {
+    const unsigned long long mA = (unsigned long long)mx[0], mB = (unsigned long long)mx[1];
+    const int stride = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m + n; t += stride) {
+        if (t < m) cmax_row[t] = ceil_sqrt_u64((unsigned long long)ssA[t] * mB);
+        else cmax_col[t - m] = ceil_sqrt_u64(mA * (unsigned long long)ssB[t - m]);
     }
 }
 

@@ -6,7 +6,8 @@ from paper_2602_02549_b300 import binding as B
 
 
 def run_gpu(A: np.ndarray, Bm: np.ndarray, N: int = 0, *, fp32: bool = False, target: float = 0.0,
-            nmax: int = 0, trans_a: bool = False, trans_b: bool = False, mu_in=None, nu_in=None):
+            nmax: int = 0, trans_a: bool = False, trans_b: bool = False, mu_in=None, nu_in=None,
+            fast: bool = False):
     """Run the emulated GEMM on cuda:0; returns dict(C, mu, nu, N, W) as numpy.
 
     A and Bm are the arrays as stored (A^T / B^T when trans_a / trans_b).
@@ -28,7 +29,7 @@ def run_gpu(A: np.ndarray, Bm: np.ndarray, N: int = 0, *, fp32: bool = False, ta
                   nu_in=torch.tensor(nu_in, dtype=torch.int32, device="cuda"))
     else:
         kw.update(mu_out=mu, nu_out=nu)
-    C = B.matmul(At, Bt, N, target=target, nmax=nmax, trans_a=trans_a, trans_b=trans_b, **kw)
+    C = B.matmul(At, Bt, N, target=target, nmax=nmax, trans_a=trans_a, trans_b=trans_b, fast=fast, **kw)
     torch.cuda.synchronize()
     assert B.sync() == 0
     Nused = int(nout.item())

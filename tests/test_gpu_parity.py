@@ -199,3 +199,29 @@ def test_log2f_assumption():
     viol, ratio = B.check_log2f()
     assert viol == 0, f"{viol} violations, max |err|/(u32 log2 x) = {ratio}"
     assert ratio <= 4.0
+
+
+@pytest.mark.parametrize("b", [64, 32])
+@pytest.mark.parametrize("phi,N", [(0.5, 8), (1.0, 14), (2.0, 17), (4.0, 20)])
+def test_fast_mode(oracle, phi, N, b):
+    # fast mode: Cbar replaced by its Cauchy-Schwarz majorant (no scaling GEMM)
+    dt = np.float64 if b == 64 else np.float32
+    A, Bm = paper_pair(150, 210, 900, phi, seed=int(phi * 5) + N, dtype=dt)
+    A, Bm = A.astype(np.float64), Bm.astype(np.float64)
+    g = run_gpu(A.astype(dt), Bm.astype(dt), N, fp32=(b == 32), fast=True)
+    check_against_oracle(oracle, A, Bm, g, b=b)
+    s = oracle.scaling(A, Bm, N, b, fast=True)
+    lo, hi = oracle.mu_band(s["mu_p"], s["cmax_row"], N, b)
+    assert ((g["mu"] >= lo) & (g["mu"] <= hi)).all()
+    lo, hi = oracle.mu_band(s["nu_p"], s["cmax_col"], N, b)
+    assert ((g["nu"] >= lo) & (g["nu"] <= hi)).all()
+
+
+def test_fast_mode_auto_N(oracle):
+    A, Bm = paper_pair(128, 160, 700, 1.0, seed=9)
+    g = run_gpu(A, Bm, 0, target=1e-14, nmax=30, fast=True)
+    s = oracle.scaling(A, Bm, 14, fast=True)
+    _, info = oracle.choose_N(A, Bm, s["alpha"], s["beta"], s["cmax_row"], s["cmax_col"], 1e-14, 30)
+    assert info["ratios"][g["N"]] <= 1e-14 * (1 + 1e-9)
+    assert info["ratios"][g["N"] - 1] > 1e-14 * (1 - 1e-9)
+    check_against_oracle(oracle, A, Bm, g)

@@ -289,3 +289,36 @@ def test_planted_mistakes_are_caught(oracle):
     r = oracle.os_ii(A, B, N, mu_in=s["mu"] + 2, nu_in=s["nu"] + 2)
     _, absApBp = int_matmul(r["Ap"], r["Bp"])
     assert max(max(row) for row in absApBp) * 2 >= good.P
+
+
+# --------------------------------------------------------------------------- #
+# Fast mode (a reading: Cbar replaced by its Cauchy-Schwarz majorant)
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("b", [64, 32])
+@pytest.mark.parametrize("N", [2, 6, 14, 20, 49])
+@pytest.mark.parametrize("phi", [0.5, 2.0, 4.0])
+def test_fast_mode_bound_and_lemma0(oracle, phi, N, b):
+    dt = np.float64 if b == 64 else np.float32
+    A, B = paper_pair(20, 24, 260, phi, seed=int(phi * 7) + N, dtype=dt)
+    A, B = A.astype(np.float64), B.astype(np.float64)
+    r = oracle.os_ii(A, B, N, b, fast=True)
+    exact = oracle.scaling(A, B, N, b)
+    # the majorant dominates Cbar (Cauchy-Schwarz) and stays <= 2^12 k
+    assert (r["cmax_row"] >= exact["cmax_row"]).all() and (r["cmax_col"] >= exact["cmax_col"]).all()
+    assert r["cmax_row"].max() <= 4096 * A.shape[1]
+    assert oracle.lemma0_holds(r["Ap"], r["Bp"], N)
+    assert oracle.ozaki_exponent_floor_ok(r["mu"], r["alpha"], r["cmax_row"], N).all()
+    err = np.abs(oracle.exact_residual(A, B, r["C"]))
+    e1, _ = oracle.bounds(A, B, r)
+    assert (err <= e1).all()
+
+
+def test_fast_mode_sum_of_squares_by_hand(oracle):
+    # Abar rows (1, 2, 2) and (3, 0, 4): ||.||^2 = 9 and 25; Bbar columns
+    # (2, 2, 1) and (0, 4, 3): 9 and 25.  Row maxima ceil(sqrt(9*25)) = 15 and
+    # ceil(sqrt(25*25)) = 25, column maxima ceil(sqrt(25*9)) = 15 and 25.
+    Abar = np.array([[1, 2, 2], [3, 0, 4]], np.int8)
+    Bbar = np.array([[2, 0], [2, 4], [1, 3]], np.int8)
+    row, col = oracle.fast_cbar_maxima(Abar, Bbar)
+    assert list(row) == [15, 25] and list(col) == [15, 25]
+    assert oracle.ceil_sqrt(10) == 4 and oracle.ceil_sqrt(16) == 4 and oracle.ceil_sqrt(0) == 0
