@@ -26,6 +26,7 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct DeviceState {
     bool tables = false;
     bool smem_attr = false;
+    int sms = 0;
     void *ws = nullptr;
     size_t ws_bytes = 0;
 };
@@ -94,6 +95,10 @@ int ensure_device(int *dev_out) {
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_pow2, T.mod.pow2, sizeof T.mod.pow2);
         if (e != cudaSuccess) return cuda_fail(e);
         st.tables = true;
+    }
+    if (!st.sms) {
+        cudaError_t e = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e);
     }
     if (!st.smem_attr) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm<EPI_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -211,10 +216,20 @@ int launch_resid(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
     return cuda_fail(cudaGetLastError());
 }
 
+// One persistent launch over the problems of `G` (item counts filled in here):
+// one CTA per SM, or fewer when there are fewer work items.
 template <int EPI>
-int launch_gemm(const CUtensorMap &tA, const CUtensorMap &tB, const GemmArgs &g, int planes, cudaStream_t st) {
-    dim3 grid(g.n_pad / gemm::BN, g.m_pad / gemm::BM, planes);
-    k_gemm<EPI><<<grid, gemm::kThreads, gemm::kSmemBytes, st>>>(tA, tB, g);
+int launch_gemm(GemmGroup &G, int sms, cudaStream_t st) {
+    long long items = 0;
+    for (int p = 0; p < G.count; p++) {
+        GemmProblem &P = G.p[p];
+        P.item_begin = items;
+        items += (long long)P.tiles_m * P.tiles_n * P.planes;
+    }
+    G.total_items = items;
+    if (items == 0) return OZ2_OK;
+    const int grid = int(std::min<long long>(items, sms));
+    k_gemm<EPI><<<grid, gemm::kThreads, gemm::kSmemBytes, st>>>(G);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -302,9 +317,18 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
     const Operand<T> opB{B, long(ldb), n, tb ? 1 : 0};
     const long planeA = long(d.m_pad) * d.k_pad, planeB = long(d.n_pad) * d.k_pad;
 
-    CUtensorMap tA, tB;
-    if ((rc = encode_bf16_2d(&tA, resA, uint64_t(nmax) * d.m_pad, uint64_t(d.k_pad), gemm::BM))) return rc;
-    if ((rc = encode_bf16_2d(&tB, resB, uint64_t(nmax) * d.n_pad, uint64_t(d.k_pad), gemm::BN))) return rc;
+    static thread_local GemmGroup G;       // 24 KB: passed by value as the kernel parameter
+    std::memset(&G, 0, sizeof G);
+    G.count = 1;
+    GemmProblem &GP = G.p[0];
+    if ((rc = encode_bf16_2d(&GP.tmA, resA, uint64_t(nmax) * d.m_pad, uint64_t(d.k_pad), gemm::BM))) return rc;
+    if ((rc = encode_bf16_2d(&GP.tmB, resB, uint64_t(nmax) * d.n_pad, uint64_t(d.k_pad), gemm::BN))) return rc;
+    GP.m_pad = d.m_pad;
+    GP.n_pad = d.n_pad;
+    GP.kb_total = d.k_pad / gemm::BK;
+    GP.tiles_m = d.m_pad / gemm::BM;
+    GP.tiles_n = d.n_pad / gemm::BN;
+    const int sms = g_dev[dev].sms;
 
     const bool inject = o && o->mu_in;
     const int32_t *mu_use = inject ? o->mu_in : mu;
@@ -329,8 +353,11 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
         if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
         if (!fast) {
             // Cbar = Abar Bbar: row and column maxima only
-            GemmArgs g{d.m_pad, d.n_pad, d.k_pad / gemm::BK, nullptr, nullptr, 0, cmax_row, cmax_col};
-            if ((rc = launch_gemm<EPI_MAX>(tA, tB, g, 1, st))) return rc;
+            GP.planes = 1;
+            GP.n_dev = nullptr;
+            GP.row_max = cmax_row;
+            GP.col_max = cmax_col;
+            if ((rc = launch_gemm<EPI_MAX>(G, sms, st))) return rc;
         } else {
             // fast mode: Cauchy-Schwarz majorant of Cbar from the sums of squares
             int *mx = reinterpret_cast<int *>(red + 6);
@@ -368,8 +395,12 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
     if ((rc = launch_resid(opB, rb, st))) return rc;
     const long w_plane = long(d.m_pad) * d.n_pad;
     if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
-    GemmArgs g{d.m_pad, d.n_pad, d.k_pad / gemm::BK, ndev, W, w_plane, nullptr, nullptr};
-    if ((rc = launch_gemm<EPI_MOD>(tA, tB, g, nmax, st))) return rc;
+    GP.planes = nmax;
+    GP.n_dev = ndev;
+    GP.W = W;
+    GP.w_plane = w_plane;
+    GP.row_max = GP.col_max = nullptr;
+    if ((rc = launch_gemm<EPI_MOD>(G, sms, st))) return rc;
     // CRT and inverse scaling
     if ((rc = mark(OZ2_PHASE_CRT))) return rc;
     {

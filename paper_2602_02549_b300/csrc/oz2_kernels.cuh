@@ -469,7 +469,9 @@ __global__ void __launch_bounds__(256) k_resid_rc(Operand<T> X, PlaneArgs a) {
 namespace gemm {
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int SEG_KB = 16;                       // 1024 K per FP32-exact segment
+constexpr int GROUP_M = 8;                       // raster: 8 row tiles per column sweep
 constexpr int kThreads = 320;                    // w0 TMA, w1 MMA, w2..w9 epilogue
+constexpr int kMaxGroup = 64;                    // problems per launch (kernel parameter space)
 constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t kSmemBytes = STAGES * STAGE_BYTES + 1024 + 256;
@@ -478,13 +480,53 @@ constexpr uint32_t IDESC = ptx::idesc_bf16_f32<BM, BN>();
 
 enum { EPI_MAX = 0, EPI_MOD = 1 };
 
-struct GemmArgs {
+// One GEMM problem of a launch: X_l (rows l*m_pad ..) times Y_l^T for the planes
+// l < planes (and l < *n_dev when n_dev is set), 128 x 256 output tiles.
+struct alignas(64) GemmProblem {
+    CUtensorMap tmA, tmB;      // BF16, K-major, 128B-swizzled boxes of 64 x 128 / 64 x 256
     int m_pad, n_pad, kb_total;
-    const int *n_dev;          // EPI_MOD: planes l >= *n_dev exit at once
+    int tiles_m, tiles_n, planes;
+    long long item_begin;      // first work item of this problem in the launch
+    const int *n_dev;          // EPI_MOD: planes l >= *n_dev are skipped
     int8_t *W;                 // EPI_MOD: W[l*w_plane + row*n_pad + col]
-    long w_plane;
+    long long w_plane;
     int *row_max, *col_max;    // EPI_MAX
 };
+
+struct GemmGroup {
+    GemmProblem p[gemm::kMaxGroup];
+    int count;
+    long long total_items;
+};
+
+struct WorkItem {
+    int p, l, tile_m, tile_n;
+    bool skip;
+};
+
+// Work item g -> (problem, plane, tile).  Planes run in order; inside a plane
+// the tiles go column by column through groups of GROUP_M row tiles, so the
+// CTAs working at the same time share few A and B panels (L2 reuse).
+__device__ __forceinline__ WorkItem decode_item(const GemmGroup &G, long long g) {
+    WorkItem w;
+    int p = 0;
+    while (p + 1 < G.count && G.p[p + 1].item_begin <= g) p++;
+    const GemmProblem &P = G.p[p];
+    const long long li = g - P.item_begin;
+    const int per_plane = P.tiles_m * P.tiles_n;
+    w.p = p;
+    w.l = int(li / per_plane);
+    const int t = int(li - (long long)w.l * per_plane);
+    const int span = gemm::GROUP_M * P.tiles_n;
+    const int grp = t / span;
+    const int first_m = grp * gemm::GROUP_M;
+    const int gm = min(gemm::GROUP_M, P.tiles_m - first_m);
+    const int tin = t - grp * span;
+    w.tile_m = first_m + tin % gm;
+    w.tile_n = tin / gm;
+    w.skip = P.n_dev != nullptr && w.l >= *P.n_dev;
+    return w;
+}
 
 __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
     if (ptx::mbar_try_wait(bar, parity)) return true;
@@ -508,19 +550,75 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
     return __all_sync(0xffffffffu, ok) != 0;
 }
 
-// One CTA computes a 128 x 256 tile of X_l Y_l^T (X_l, Y_l: BF16, K-major,
-// integer-valued), l = blockIdx.z.  K runs in segments of <= 1024 elements:
-// each segment starts a fresh FP32 accumulator in TMEM, so every partial sum
-// is an integer of magnitude <= 1024 * 2^14 = 2^24 and therefore exact; the
-// epilogue warps turn each segment into INT32 and add it up (double-buffered
-// accumulators let the next segment's MMAs overlap the read-out).
+// Epilogue of one output tile for one epilogue thread: 128 INT32 sums of row
+// `row`, columns col0 .. col0+127.
 template <int EPI>
-__global__ void __launch_bounds__(gemm::kThreads, 1)
-    k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs args) {
-    using namespace gemm;
-    const int l = blockIdx.z;
-    if (EPI == EPI_MOD && args.n_dev && l >= *args.n_dev) return;
+__device__ __forceinline__ void tile_epilogue(const GemmProblem &P, int l, int row, int col0, int lane,
+                                              const int (&acc)[128]) {
+    if (EPI == EPI_MOD) {
+        int8_t *dst = P.W + (long long)l * P.w_plane + (long long)row * P.n_pad + col0;
+        if (l == 0) {                            // p = 256: low byte
+#pragma unroll
+            for (int g = 0; g < 8; g++) {
+                uint32_t w4[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int b = g * 16 + j * 4;
+                    w4[j] = (uint32_t(acc[b]) & 255u) | ((uint32_t(acc[b + 1]) & 255u) << 8) |
+                            ((uint32_t(acc[b + 2]) & 255u) << 16) | ((uint32_t(acc[b + 3]) & 255u) << 24);
+                }
+                *reinterpret_cast<uint4 *>(dst + g * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+        } else {
+            const uint32_t p = uint32_t(c_p[l]), mg = c_magic[l], c16 = c_c16[l];
+            const int hp = int(p >> 1);
+#pragma unroll
+            for (int g = 0; g < 8; g++) {
+                uint32_t w4[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int x = acc[g * 16 + j * 4 + e];
+                        const uint32_t u = uint32_t(x < 0 ? -x : x);
+                        uint32_t r = mod_small((u >> 16) * c16 + (u & 0xFFFFu), p, mg);
+                        int sr = int(r) > hp ? int(r) - int(p) : int(r);
+                        if (x < 0) sr = -sr;
+                        word |= (uint32_t(sr) & 255u) << (8 * e);
+                    }
+                    w4[j] = word;
+                }
+                *reinterpret_cast<uint4 *>(dst + g * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+        }
+    } else {
+        int rm = 0;
+#pragma unroll
+        for (int i = 0; i < 128; i++) rm = max(rm, acc[i]);
+        atomicMax(P.row_max + row, rm);
+        int mine[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < 128; c++) {
+            const int v = __reduce_max_sync(0xffffffffu, acc[c]);
+            if (lane == (c & 31)) mine[c >> 5] = v;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) atomicMax(P.col_max + col0 + j * 32 + lane, mine[j]);
+    }
+}
 
+// Persistent CTA (one per SM) working through the items g = blockIdx.x,
+// blockIdx.x + gridDim.x, ... of one or more problems.  Each item is a 128 x 256
+// tile of X_l Y_l^T (BF16, K-major, integer-valued).  K runs in segments of
+// <= 1024 elements: each segment starts a fresh FP32 accumulator in TMEM, so
+// every partial sum is an integer of magnitude <= 1024 * 2^14 = 2^24 and exact;
+// the epilogue warps turn each segment into INT32 and add it up.  The shared
+// memory stage ring and the two TMEM accumulators run on across items, so the
+// epilogue of one tile overlaps the MMAs of the next.
+template <int EPI>
+__global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constant__ GemmGroup G) {
+    using namespace gemm;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -542,8 +640,6 @@ __global__ void __launch_bounds__(gemm::kThreads, 1)
         for (int b = 0; b < 2; b++) { ptx::mbar_init(bar_accf(b), 1); ptx::mbar_init(bar_acce(b), 8); }
         *abort_flag = 0;
         ptx::fence_mbar_init();
-        ptx::tma_prefetch_desc(&tmA);
-        ptx::tma_prefetch_desc(&tmB);
     }
     if (warp == 1) {
         ptx::tmem_alloc<512>(ptx::smem_addr(tmem_slot));
@@ -553,127 +649,96 @@ __global__ void __launch_bounds__(gemm::kThreads, 1)
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-
-    const int kb_total = args.kb_total;
-    const int nseg = (kb_total + SEG_KB - 1) / SEG_KB;
-    const int row_a = l * args.m_pad + blockIdx.y * BM;
-    const int row_b = l * args.n_pad + blockIdx.x * BN;
+    const long long total = G.total_items;
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int kb = 0; kb < kb_total; kb++) {
-                const int s = kb % STAGES;
-                const uint32_t ph = uint32_t(kb / STAGES) & 1u;
-                if (kb >= STAGES && !bounded_wait(bar_empty(s), ph ^ 1u, abort_flag)) break;
-                ptx::mbar_arrive_expect_tx(bar_full(s), STAGE_BYTES);
-                ptx::tma_load_2d(sA(s), &tmA, kb * BK, row_a, bar_full(s));
-                ptx::tma_load_2d(sB(s), &tmB, kb * BK, row_b, bar_full(s));
+            uint32_t kbc = 0;                    // stage ring position, across items
+            bool ok = true;
+            for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
+                const WorkItem w = decode_item(G, g);
+                if (w.skip) continue;
+                const GemmProblem &P = G.p[w.p];
+                const int row_a = w.l * P.m_pad + w.tile_m * BM;
+                const int row_b = w.l * P.n_pad + w.tile_n * BN;
+                for (int kb = 0; kb < P.kb_total; kb++, kbc++) {
+                    const int s = int(kbc % STAGES);
+                    const uint32_t ph = (kbc / STAGES) & 1u;
+                    if (kbc >= STAGES && !bounded_wait(bar_empty(s), ph ^ 1u, abort_flag)) { ok = false; break; }
+                    ptx::mbar_arrive_expect_tx(bar_full(s), STAGE_BYTES);
+                    ptx::tma_load_2d(sA(s), &P.tmA, kb * BK, row_a, bar_full(s));
+                    ptx::tma_load_2d(sB(s), &P.tmB, kb * BK, row_b, bar_full(s));
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            uint32_t kbc = 0, segc = 0;
             bool ok = true;
-            for (int seg = 0; seg < nseg && ok; seg++) {
-                const int buf = seg & 1;
-                if (seg >= 2 && !bounded_wait(bar_acce(buf), uint32_t((seg >> 1) - 1) & 1u, abort_flag)) break;
-                ptx::tc_fence_after();
-                const uint32_t d = tmem + uint32_t(buf * BN);
-                const int kb0 = seg * SEG_KB;
-                const int kb1 = min(kb_total, kb0 + SEG_KB);
-                for (int kb = kb0; kb < kb1; kb++) {
-                    const int s = kb % STAGES;
-                    const uint32_t ph = uint32_t(kb / STAGES) & 1u;
-                    if (!bounded_wait(bar_full(s), ph, abort_flag)) { ok = false; break; }
-                    ptx::tc_fence_after();
-#pragma unroll
-                    for (int kk = 0; kk < BK / 16; kk++) {
-                        const uint64_t ad = ptx::sdesc_sw128_kmajor(sA(s) + uint32_t(kk * 32));
-                        const uint64_t bd = ptx::sdesc_sw128_kmajor(sB(s) + uint32_t(kk * 32));
-                        ptx::mma_bf16(d, ad, bd, IDESC, (kb > kb0 || kk > 0) ? 1u : 0u);
+            for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
+                const WorkItem w = decode_item(G, g);
+                if (w.skip) continue;
+                const GemmProblem &P = G.p[w.p];
+                const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
+                for (int seg = 0; seg < nseg && ok; seg++, segc++) {
+                    const int buf = int(segc & 1u);
+                    if (segc >= 2 && !bounded_wait(bar_acce(buf), ((segc >> 1) - 1) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
                     }
-                    ptx::mma_commit(bar_empty(s));
+                    ptx::tc_fence_after();
+                    const uint32_t d = tmem + uint32_t(buf * BN);
+                    const int kb0 = seg * SEG_KB;
+                    const int kb1 = min(P.kb_total, kb0 + SEG_KB);
+                    for (int kb = kb0; kb < kb1; kb++, kbc++) {
+                        const int s = int(kbc % STAGES);
+                        const uint32_t ph = (kbc / STAGES) & 1u;
+                        if (!bounded_wait(bar_full(s), ph, abort_flag)) { ok = false; break; }
+                        ptx::tc_fence_after();
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; kk++) {
+                            const uint64_t ad = ptx::sdesc_sw128_kmajor(sA(s) + uint32_t(kk * 32));
+                            const uint64_t bd = ptx::sdesc_sw128_kmajor(sB(s) + uint32_t(kk * 32));
+                            ptx::mma_bf16(d, ad, bd, IDESC, (kb > kb0 || kk > 0) ? 1u : 0u);
+                        }
+                        ptx::mma_commit(bar_empty(s));
+                    }
+                    if (ok) ptx::mma_commit(bar_accf(buf));
                 }
-                if (ok) ptx::mma_commit(bar_accf(buf));
             }
         }
     } else {
         const int q = warp & 3;                 // TMEM lanes 32q..32q+31 (warp rank mod 4)
         const int half = (warp - 2) >> 2;       // columns [128 half, 128 half + 128)
-        int acc[128];
-#pragma unroll
-        for (int i = 0; i < 128; i++) acc[i] = 0;
+        uint32_t segc = 0;
         bool ok = true;
-        for (int seg = 0; seg < nseg; seg++) {
-            const int buf = seg & 1;
-            if (!warp_wait(bar_accf(buf), uint32_t(seg >> 1) & 1u, abort_flag)) { ok = false; break; }
-            ptx::tc_fence_after();
-            const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + half * 128);
+        for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
+            const WorkItem w = decode_item(G, g);
+            if (w.skip) continue;
+            const GemmProblem &P = G.p[w.p];
+            const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
+            int acc[128];
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
-                uint32_t v[32];
-                ptx::tmem_ld_32x32b_x32(taddr + uint32_t(c * 32), v);
-                ptx::tmem_wait_ld();
+            for (int i = 0; i < 128; i++) acc[i] = 0;
+            for (int seg = 0; seg < nseg; seg++, segc++) {
+                const int buf = int(segc & 1u);
+                if (!warp_wait(bar_accf(buf), (segc >> 1) & 1u, abort_flag)) { ok = false; break; }
+                ptx::tc_fence_after();
+                const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + half * 128);
 #pragma unroll
-                for (int i = 0; i < 32; i++) acc[c * 32 + i] += __float2int_rn(__uint_as_float(v[i]));
-            }
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(bar_acce(buf));
-        }
-        if (ok) {
-            const int row = blockIdx.y * BM + q * 32 + lane;
-            const int col0 = blockIdx.x * BN + half * 128;
-            if (EPI == EPI_MOD) {
-                int8_t *dst = args.W + (long)l * args.w_plane + (long)row * args.n_pad + col0;
-                if (l == 0) {                            // p = 256: low byte
+                for (int c = 0; c < 4; c++) {
+                    uint32_t v[32];
+                    ptx::tmem_ld_32x32b_x32(taddr + uint32_t(c * 32), v);
+                    ptx::tmem_wait_ld();
 #pragma unroll
-                    for (int g = 0; g < 8; g++) {
-                        uint32_t w4[4];
-#pragma unroll
-                        for (int j = 0; j < 4; j++) {
-                            const int b = g * 16 + j * 4;
-                            w4[j] = (uint32_t(acc[b]) & 255u) | ((uint32_t(acc[b + 1]) & 255u) << 8) |
-                                    ((uint32_t(acc[b + 2]) & 255u) << 16) | ((uint32_t(acc[b + 3]) & 255u) << 24);
-                        }
-                        *reinterpret_cast<uint4 *>(dst + g * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                    }
-                } else {
-                    const uint32_t p = uint32_t(c_p[l]), mg = c_magic[l], c16 = c_c16[l];
-                    const int hp = int(p >> 1);
-#pragma unroll
-                    for (int g = 0; g < 8; g++) {
-                        uint32_t w4[4];
-#pragma unroll
-                        for (int j = 0; j < 4; j++) {
-                            uint32_t word = 0;
-#pragma unroll
-                            for (int e = 0; e < 4; e++) {
-                                const int x = acc[g * 16 + j * 4 + e];
-                                const uint32_t u = uint32_t(x < 0 ? -x : x);
-                                uint32_t r = mod_small((u >> 16) * c16 + (u & 0xFFFFu), p, mg);
-                                int sr = int(r) > hp ? int(r) - int(p) : int(r);
-                                if (x < 0) sr = -sr;
-                                word |= (uint32_t(sr) & 255u) << (8 * e);
-                            }
-                            w4[j] = word;
-                        }
-                        *reinterpret_cast<uint4 *>(dst + g * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                    }
+                    for (int i = 0; i < 32; i++) acc[c * 32 + i] += __float2int_rn(__uint_as_float(v[i]));
                 }
-            } else {
-                int rm = 0;
-#pragma unroll
-                for (int i = 0; i < 128; i++) rm = max(rm, acc[i]);
-                atomicMax(args.row_max + row, rm);
-                int mine[4] = {0, 0, 0, 0};
-#pragma unroll
-                for (int c = 0; c < 128; c++) {
-                    const int v = __reduce_max_sync(0xffffffffu, acc[c]);
-                    if (lane == (c & 31)) mine[c >> 5] = v;
-                }
-#pragma unroll
-                for (int j = 0; j < 4; j++) atomicMax(args.col_max + col0 + j * 32 + lane, mine[j]);
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(bar_acce(buf));
             }
+            if (!ok) break;
+            tile_epilogue<EPI>(P, w.l, w.tile_m * BM + q * 32 + lane, w.tile_n * BN + half * 128, lane, acc);
         }
     }
     ptx::tc_fence_before();
