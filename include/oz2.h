@@ -109,6 +109,39 @@ OZ2_API int oz2_sgemm(int m, int n, int k, const float *A, int lda, const float 
 OZ2_API int oz2_sgemm_ex(int m, int n, int k, const float *A, int lda, const float *B, int ldb,
                          float *C, int ldc, int nmoduli, int mode, const oz2_opts *opts);
 
+/*
+ * Batched emulated DGEMM: many independent problems of uneven shapes, each
+ * with its own exponents and its own N (fixed, or the bound rule for its own
+ * target).  The scaling GEMMs of all problems run as one persistent tcgen05
+ * launch and the N residue GEMMs of all problems as another (64 problems per
+ * launch; heaviest first); the light phases of the problems run concurrently
+ * on library-owned streams forked from and joined back to opts->stream.  With
+ * a caller workspace the call allocates nothing and enqueues only stream work
+ * and event records/waits, so it can be captured into a CUDA graph and
+ * replayed as one launch.  Each result is bit-identical to oz2_gemm_ex on the
+ * same problem.  opts: stream, workspace, phase_events are used; the other
+ * fields are ignored (per-problem settings live in oz2_problem).
+ */
+typedef struct oz2_problem {
+    int m, n, k;
+    const double *A;
+    int lda;
+    const double *B;
+    int ldb;
+    double *C;
+    int ldc;
+    int nmoduli;       /* N in [2, 49], or 0 for the bound rule with `target`  */
+    double target;     /* nmoduli == 0: target normwise relative error         */
+    int nmax;          /* nmoduli == 0: largest N tried (0 = 20)               */
+    int mode;          /* OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B                 */
+    int *n_out;        /* optional device int: the N used                      */
+} oz2_problem;
+
+OZ2_API int oz2_gemm_batched(int count, const oz2_problem *problems, const oz2_opts *opts);
+
+/* Workspace bytes of oz2_gemm_batched for these problems (0 if any is invalid). */
+OZ2_API size_t oz2_batched_workspace_size(int count, const oz2_problem *problems);
+
 /* Bytes of device workspace a call with these sizes needs; nmax is the largest
  * N the call may use (its nmoduli, or opts->nmax when nmoduli == 0).  Returns 0
  * for invalid sizes.  Host-only; touches no GPU. */

@@ -231,3 +231,71 @@ def gemm_noalloc(A, B, C, nmoduli: int = 0, mode: int = 0, *, target: float = 0.
     with torch.cuda.device(A.device):
         return fn(m, n, k, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), _ptr(C), _ld(C, "C"),
                   nmoduli, mode, float(target), ctypes.c_void_p(s.cuda_stream))
+
+
+class oz2_problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_int),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int),
+                ("nmoduli", ctypes.c_int), ("target", ctypes.c_double), ("nmax", ctypes.c_int),
+                ("mode", ctypes.c_int), ("n_out", ctypes.c_void_p)]
+
+
+def _problem_array(problems):
+    arr = (oz2_problem * len(problems))()
+    for q, d in zip(arr, problems):
+        A, Bm, C = d["A"], d["B"], d["C"]
+        for t in (A, Bm, C):
+            if t.dtype.itemsize != 8 or not t.is_cuda:
+                raise TypeError("batched problems are float64 CUDA tensors")
+        mode = (OZ2_FAST if d.get("fast") else 0) | (OZ2_TRANS_A if d.get("trans_a") else 0) | \
+            (OZ2_TRANS_B if d.get("trans_b") else 0)
+        q.m = A.size(1) if d.get("trans_a") else A.size(0)
+        q.k = A.size(0) if d.get("trans_a") else A.size(1)
+        q.n = Bm.size(0) if d.get("trans_b") else Bm.size(1)
+        q.A, q.lda = A.data_ptr(), _ld(A, "A")
+        q.B, q.ldb = Bm.data_ptr(), _ld(Bm, "B")
+        q.C, q.ldc = C.data_ptr(), _ld(C, "C")
+        q.nmoduli = int(d.get("nmoduli", 0))
+        q.target = float(d.get("target", 0.0))
+        q.nmax = int(d.get("nmax", 0))
+        q.mode = mode
+        q.n_out = d["n_out"].data_ptr() if d.get("n_out") is not None else None
+    return arr
+
+
+def batched_workspace_size(problems) -> int:
+    L = lib()
+    L.oz2_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    L.oz2_batched_workspace_size.restype = ctypes.c_size_t
+    arr = _problem_array(problems)
+    return int(L.oz2_batched_workspace_size(len(problems), ctypes.cast(arr, ctypes.c_void_p)))
+
+
+def gemm_batched(problems, *, workspace=None, stream=None, phase_events=None) -> int:
+    """oz2_gemm_batched on a list of problems, each a dict with float64 CUDA
+    tensors A, B, C and optional nmoduli, target, nmax, trans_a, trans_b, fast,
+    n_out (device int32[1]).  Returns the status code."""
+    import torch
+    L = lib()
+    L.oz2_gemm_batched.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(oz2_opts)]
+    L.oz2_gemm_batched.restype = ctypes.c_int
+    arr = _problem_array(problems)
+    o = oz2_opts()
+    dev = problems[0]["A"].device
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    o.stream = ctypes.c_void_p(s.cuda_stream)
+    if workspace is None:
+        workspace = torch.empty(max(batched_workspace_size(problems), 256), dtype=torch.uint8, device=dev)
+    o.workspace = ctypes.c_void_p(workspace.data_ptr())
+    o.workspace_bytes = workspace.numel()
+    ev = None
+    if phase_events is not None:
+        for e in phase_events:
+            if not e.cuda_event:
+                e.record(s)
+        ev = (ctypes.c_void_p * (NPHASES + 1))(*[ctypes.c_void_p(e.cuda_event) for e in phase_events])
+        o.phase_events = ctypes.cast(ev, ctypes.c_void_p)
+    with torch.cuda.device(dev):
+        return L.oz2_gemm_batched(len(problems), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(o))

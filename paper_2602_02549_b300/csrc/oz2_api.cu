@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "oz2.h"
 #include "oz2_kernels.cuh"
@@ -23,10 +24,15 @@ constexpr int kMaxDevices = 64;
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ------------------------------------------------------------------ per-device state
+constexpr int kPool = 8;   // streams that run the light phases of a batch concurrently
+
 struct DeviceState {
     bool tables = false;
     bool smem_attr = false;
     int sms = 0;
+    cudaStream_t pool[kPool] = {};
+    cudaEvent_t fork = nullptr, done[kPool] = {};
+    std::mutex batch_mu;
     void *ws = nullptr;
     size_t ws_bytes = 0;
 };
@@ -95,6 +101,15 @@ int ensure_device(int *dev_out) {
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_pow2, T.mod.pow2, sizeof T.mod.pow2);
         if (e != cudaSuccess) return cuda_fail(e);
         st.tables = true;
+    }
+    if (!st.pool[0]) {
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < kPool && e == cudaSuccess; i++) {
+            e = cudaStreamCreateWithFlags(&st.pool[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.done[i], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e);
     }
     if (!st.sms) {
         cudaError_t e = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, dev);
@@ -252,114 +267,122 @@ int validate(int m, int n, int k, const void *A, int lda, const void *B, int ldb
     return OZ2_OK;
 }
 
-int resolve_nmax(int nmoduli, const oz2_opts *o, bool fp32) {
-    if (nmoduli) return nmoduli;
-    return (o && o->nmax) ? o->nmax : (fp32 ? 14 : 20);
-}
-
 // ------------------------------------------------------------------ the pipeline
+// One emulated GEMM, split into the phases that surround the two tensor-core
+// GEMMs so that a batch can run the phases of many problems concurrently and
+// each GEMM of all problems as one persistent launch.
 template <typename T>
-int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, int nmoduli, int mode,
-        const oz2_opts *o) {
-    constexpr bool fp32 = sizeof(T) == 4;
-    int rc = validate(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o);
-    if (rc) return rc;
-    const int nmax = resolve_nmax(nmoduli, o, fp32);
-    const Dims d = make_dims(m, n, k, nmax);
-    const Layout L = make_layout(d);
-    int dev = 0;
-    if ((rc = ensure_device(&dev))) return rc;
-    cudaStream_t st = o ? static_cast<cudaStream_t>(o->stream) : nullptr;
-
+struct Job {
+    static constexpr bool fp32 = sizeof(T) == 4;
+    // arguments
+    int m = 0, n = 0, k = 0, lda = 0, ldb = 0, ldc = 0, nmoduli = 0, mode = 0, nmax = 0;
+    const T *A = nullptr, *B = nullptr;
+    T *C = nullptr;
+    double target = 0.0;
+    int *n_out = nullptr;
+    int32_t *mu_out = nullptr, *nu_out = nullptr;
+    const int32_t *mu_in = nullptr, *nu_in = nullptr;
+    // workspace views
+    Dims d{};
+    Layout L{};
     uint8_t *ws = nullptr;
-    if (o && o->workspace) {
-        if (o->workspace_bytes < L.total) return OZ2_ENOMEM;
-        if (reinterpret_cast<uintptr_t>(o->workspace) & 255u) return OZ2_EINVAL;
-        ws = static_cast<uint8_t *>(o->workspace);
-    } else {
-        std::lock_guard<std::mutex> lk(g_mu);
-        DeviceState &s = g_dev[dev];
-        if (s.ws_bytes < L.total) {
-            if (s.ws) {
-                cudaDeviceSynchronize();
-                cudaFree(s.ws);
-                s.ws = nullptr;
-                s.ws_bytes = 0;
-            }
-            if (cudaMalloc(&s.ws, L.total) != cudaSuccess) return cuda_fail(cudaErrorMemoryAllocation);
-            s.ws_bytes = L.total;
-        }
-        ws = static_cast<uint8_t *>(s.ws);
+    unsigned long long *hmaxA, *hmaxB, *red, *rmaxA, *rmaxB;
+    int *cmax_row, *cmax_col, *ssA, *ssB, *ndev;
+    double *rsumA, *rsumB;
+    int32_t *mu, *nu;
+    __nv_bfloat16 *resA, *resB;
+    int8_t *W;
+    Operand<T> opA{}, opB{};
+    long planeA = 0, planeB = 0, w_plane = 0;
+
+    bool fast() const { return mode & OZ2_FAST; }
+    bool inject() const { return mu_in != nullptr; }
+    bool needs_scale_gemm() const { return !fast() && !inject(); }
+
+    void set(int m_, int n_, int k_, const T *A_, int lda_, const T *B_, int ldb_, T *C_, int ldc_, int N_, int mode_,
+             double target_, int nmax_) {
+        m = m_; n = n_; k = k_; A = A_; lda = lda_; B = B_; ldb = ldb_; C = C_; ldc = ldc_;
+        nmoduli = N_; mode = mode_; target = target_;
+        nmax = N_ ? N_ : (nmax_ ? nmax_ : (fp32 ? 14 : 20));
+        d = make_dims(m, n, k, nmax);
+        L = make_layout(d);
     }
-    auto at = [&](size_t off) { return ws + off; };
-    auto *hmaxA = reinterpret_cast<unsigned long long *>(at(L.hmaxA));
-    auto *hmaxB = reinterpret_cast<unsigned long long *>(at(L.hmaxB));
-    auto *cmax_row = reinterpret_cast<int *>(at(L.cmax_row));
-    auto *cmax_col = reinterpret_cast<int *>(at(L.cmax_col));
-    auto *red = reinterpret_cast<unsigned long long *>(at(L.red));
-    auto *ssA = reinterpret_cast<int *>(at(L.ssA));
-    auto *ssB = reinterpret_cast<int *>(at(L.ssB));
-    const bool fast = mode & OZ2_FAST;
-    auto *rmaxA = reinterpret_cast<unsigned long long *>(at(L.rmaxA));
-    auto *rmaxB = reinterpret_cast<unsigned long long *>(at(L.rmaxB));
-    auto *rsumA = reinterpret_cast<double *>(at(L.rsumA));
-    auto *rsumB = reinterpret_cast<double *>(at(L.rsumB));
-    auto *mu = reinterpret_cast<int32_t *>(at(L.mu));
-    auto *nu = reinterpret_cast<int32_t *>(at(L.nu));
-    auto *ndev = reinterpret_cast<int *>(at(L.ndev));
-    auto *resA = reinterpret_cast<__nv_bfloat16 *>(at(L.resA));
-    auto *resB = reinterpret_cast<__nv_bfloat16 *>(at(L.resB));
-    auto *W = reinterpret_cast<int8_t *>(at(L.W));
 
-    const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
-    // A's logical rows are the rows of A; B's are the columns of B.
-    const Operand<T> opA{A, long(lda), m, ta ? 0 : 1};
-    const Operand<T> opB{B, long(ldb), n, tb ? 1 : 0};
-    const long planeA = long(d.m_pad) * d.k_pad, planeB = long(d.n_pad) * d.k_pad;
+    void bind(uint8_t *w) {
+        ws = w;
+        auto at = [&](size_t off) { return ws + off; };
+        hmaxA = reinterpret_cast<unsigned long long *>(at(L.hmaxA));
+        hmaxB = reinterpret_cast<unsigned long long *>(at(L.hmaxB));
+        cmax_row = reinterpret_cast<int *>(at(L.cmax_row));
+        cmax_col = reinterpret_cast<int *>(at(L.cmax_col));
+        red = reinterpret_cast<unsigned long long *>(at(L.red));
+        ssA = reinterpret_cast<int *>(at(L.ssA));
+        ssB = reinterpret_cast<int *>(at(L.ssB));
+        rmaxA = reinterpret_cast<unsigned long long *>(at(L.rmaxA));
+        rmaxB = reinterpret_cast<unsigned long long *>(at(L.rmaxB));
+        rsumA = reinterpret_cast<double *>(at(L.rsumA));
+        rsumB = reinterpret_cast<double *>(at(L.rsumB));
+        mu = reinterpret_cast<int32_t *>(at(L.mu));
+        nu = reinterpret_cast<int32_t *>(at(L.nu));
+        ndev = reinterpret_cast<int *>(at(L.ndev));
+        resA = reinterpret_cast<__nv_bfloat16 *>(at(L.resA));
+        resB = reinterpret_cast<__nv_bfloat16 *>(at(L.resB));
+        W = reinterpret_cast<int8_t *>(at(L.W));
+        const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
+        // A's logical rows are the rows of A; B's are the columns of B.
+        opA = Operand<T>{A, long(lda), m, ta ? 0 : 1};
+        opB = Operand<T>{B, long(ldb), n, tb ? 1 : 0};
+        planeA = long(d.m_pad) * d.k_pad;
+        planeB = long(d.n_pad) * d.k_pad;
+        w_plane = long(d.m_pad) * d.n_pad;
+    }
 
-    static thread_local GemmGroup G;       // 24 KB: passed by value as the kernel parameter
-    std::memset(&G, 0, sizeof G);
-    G.count = 1;
-    GemmProblem &GP = G.p[0];
-    if ((rc = encode_bf16_2d(&GP.tmA, resA, uint64_t(nmax) * d.m_pad, uint64_t(d.k_pad), gemm::BM))) return rc;
-    if ((rc = encode_bf16_2d(&GP.tmB, resB, uint64_t(nmax) * d.n_pad, uint64_t(d.k_pad), gemm::BN))) return rc;
-    GP.m_pad = d.m_pad;
-    GP.n_pad = d.n_pad;
-    GP.kb_total = d.k_pad / gemm::BK;
-    GP.tiles_m = d.m_pad / gemm::BM;
-    GP.tiles_n = d.n_pad / gemm::BN;
-    const int sms = g_dev[dev].sms;
+    const int32_t *mu_use() const { return inject() ? mu_in : mu; }
+    const int32_t *nu_use() const { return inject() ? nu_in : nu; }
 
-    const bool inject = o && o->mu_in;
-    const int32_t *mu_use = inject ? o->mu_in : mu;
-    const int32_t *nu_use = inject ? o->nu_in : nu;
+    // the residue planes and their tensor maps (plane 0 holds Abar / Bbar first)
+    int describe(GemmProblem &P) const {
+        int rc = encode_bf16_2d(&P.tmA, resA, uint64_t(nmax) * d.m_pad, uint64_t(d.k_pad), gemm::BM);
+        if (rc) return rc;
+        if ((rc = encode_bf16_2d(&P.tmB, resB, uint64_t(nmax) * d.n_pad, uint64_t(d.k_pad), gemm::BN))) return rc;
+        P.m_pad = d.m_pad;
+        P.n_pad = d.n_pad;
+        P.kb_total = d.k_pad / gemm::BK;
+        P.tiles_m = d.m_pad / gemm::BM;
+        P.tiles_n = d.n_pad / gemm::BN;
+        return OZ2_OK;
+    }
+    void as_scale_gemm(GemmProblem &P) const {
+        P.planes = 1;
+        P.n_dev = nullptr;
+        P.W = nullptr;
+        P.row_max = cmax_row;
+        P.col_max = cmax_col;
+    }
+    void as_residue_gemm(GemmProblem &P) const {
+        P.planes = nmax;
+        P.n_dev = ndev;
+        P.W = W;
+        P.w_plane = w_plane;
+        P.row_max = P.col_max = nullptr;
+    }
 
-    auto mark = [&](int phase) -> int {
-        if (!o || !o->phase_events) return OZ2_OK;
-        return cuda_fail(cudaEventRecord(static_cast<cudaEvent_t>(o->phase_events[phase]), st));
-    };
-    if ((rc = mark(OZ2_PHASE_STATS))) return rc;
-    if ((rc = cuda_fail(cudaMemsetAsync(ws, 0, L.zero_end, st)))) return rc;
-    if (!inject) {
-        // Algorithm 2: mu', nu' (and the N-rule inputs)
+    // Algorithm 2 up to Cbar: mu', nu', the N-rule inputs, Abar, Bbar (fast
+    // mode: the majorant of Cbar instead of Abar, Bbar)
+    template <class Mark>
+    int phase_inputs(cudaStream_t st, Mark &&mark) {
+        int rc;
+        if ((rc = cuda_fail(cudaMemsetAsync(ws, 0, L.zero_end, st)))) return rc;
+        if (inject()) return OZ2_OK;
         if ((rc = launch_stats(opA, k, rmaxA, rsumA, hmaxA, st))) return rc;
         if ((rc = launch_stats(opB, k, rmaxB, rsumB, hmaxB, st))) return rc;
-        // Abar, Bbar
         if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
-        PlaneArgs qa{resA, planeA, d.m_pad, k, d.k_pad, rmaxA, nullptr, nullptr, fast ? ssA : nullptr, !fast};
-        PlaneArgs qb{resB, planeB, d.n_pad, k, d.k_pad, rmaxB, nullptr, nullptr, fast ? ssB : nullptr, !fast};
+        const bool f = fast();
+        PlaneArgs qa{resA, planeA, d.m_pad, k, d.k_pad, rmaxA, nullptr, nullptr, f ? ssA : nullptr, !f};
+        PlaneArgs qb{resB, planeB, d.n_pad, k, d.k_pad, rmaxB, nullptr, nullptr, f ? ssB : nullptr, !f};
         if ((rc = launch_quant(opA, qa, st))) return rc;
         if ((rc = launch_quant(opB, qb, st))) return rc;
-        if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
-        if (!fast) {
-            // Cbar = Abar Bbar: row and column maxima only
-            GP.planes = 1;
-            GP.n_dev = nullptr;
-            GP.row_max = cmax_row;
-            GP.col_max = cmax_col;
-            if ((rc = launch_gemm<EPI_MAX>(G, sms, st))) return rc;
-        } else {
-            // fast mode: Cauchy-Schwarz majorant of Cbar from the sums of squares
+        if (f) {
             int *mx = reinterpret_cast<int *>(red + 6);
             k_fast_max<<<std::min(148, (std::max(m, n) + 255) / 256), 256, 0, st>>>(ssA, m, ssB, n, mx);
             if ((rc = cuda_fail(cudaGetLastError()))) return rc;
@@ -367,60 +390,252 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
                                                                               cmax_col);
             if ((rc = cuda_fail(cudaGetLastError()))) return rc;
         }
-        // the N rule, then mu and nu
-        if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
-        if (nmoduli == 0) {
-            BoundArgs ba{m, n, k, rmaxA, rmaxB, hmaxA, hmaxB, rsumA, rsumB, cmax_row, cmax_col, red};
-            k_bound_reduce<<<148, 256, 0, st>>>(ba);
-            if ((rc = cuda_fail(cudaGetLastError()))) return rc;
-        }
-        k_choose_n<<<1, 32, 0, st>>>(red, k, nmoduli ? 0.0 : o->target, nmax, nmoduli, fp32 ? 1 : 0, ndev,
-                                     o ? o->n_out : nullptr);
-        if ((rc = cuda_fail(cudaGetLastError()))) return rc;
-        k_mu_nu<<<std::min(1184, (m + n + 255) / 256), 256, 0, st>>>(
-            m, n, rmaxA, rmaxB, cmax_row, cmax_col, ndev, fp32 ? 1 : 0, mu, nu, o ? o->mu_out : nullptr,
-            o ? o->nu_out : nullptr);
-        if ((rc = cuda_fail(cudaGetLastError()))) return rc;
-    } else {
-        for (int ph = OZ2_PHASE_QUANT; ph <= OZ2_PHASE_EXPONENTS; ph++)
-            if ((rc = mark(ph))) return rc;
-        k_choose_n<<<1, 32, 0, st>>>(red, k, 0.0, nmax, nmoduli, fp32 ? 1 : 0, ndev, o->n_out);
-        if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+        return OZ2_OK;
     }
-    // Algorithm 3: residues, N products, W_l
-    if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
-    PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, nullptr, mu_use, ndev};
-    PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, nullptr, nu_use, ndev};
-    if ((rc = launch_resid(opA, ra, st))) return rc;
-    if ((rc = launch_resid(opB, rb, st))) return rc;
-    const long w_plane = long(d.m_pad) * d.n_pad;
-    if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
-    GP.planes = nmax;
-    GP.n_dev = ndev;
-    GP.W = W;
-    GP.w_plane = w_plane;
-    GP.row_max = GP.col_max = nullptr;
-    if ((rc = launch_gemm<EPI_MOD>(G, sms, st))) return rc;
-    // CRT and inverse scaling
-    if ((rc = mark(OZ2_PHASE_CRT))) return rc;
-    {
+
+    // the N rule, mu and nu (Algorithm 2), then the residues (Algorithm 3)
+    int phase_exponents(cudaStream_t st) {
+        int rc;
+        if (!inject()) {
+            if (nmoduli == 0) {
+                BoundArgs ba{m, n, k, rmaxA, rmaxB, hmaxA, hmaxB, rsumA, rsumB, cmax_row, cmax_col, red};
+                k_bound_reduce<<<148, 256, 0, st>>>(ba);
+                if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+            }
+            k_choose_n<<<1, 32, 0, st>>>(red, k, nmoduli ? 0.0 : target, nmax, nmoduli, fp32 ? 1 : 0, ndev, n_out);
+            if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+            k_mu_nu<<<std::min(1184, (m + n + 255) / 256), 256, 0, st>>>(
+                m, n, rmaxA, rmaxB, cmax_row, cmax_col, ndev, fp32 ? 1 : 0, mu, nu, mu_out, nu_out);
+            return cuda_fail(cudaGetLastError());
+        }
+        k_choose_n<<<1, 32, 0, st>>>(red, k, 0.0, nmax, nmoduli, fp32 ? 1 : 0, ndev, n_out);
+        return cuda_fail(cudaGetLastError());
+    }
+    int phase_residues(cudaStream_t st) {
+        int rc;
+        PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, nullptr, mu_use(), ndev, nullptr, 1};
+        PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, nullptr, nu_use(), ndev, nullptr, 1};
+        if ((rc = launch_resid(opA, ra, st))) return rc;
+        return launch_resid(opB, rb, st);
+    }
+
+    // Algorithm 3 from W_l on and the inverse scaling of Algorithm 1
+    int phase_crt(cudaStream_t st) {
         dim3 grid((n + 1023) / 1024, grid_rows(m));
         if constexpr (fp32)
-            k_crt<T, 32><<<grid, 256, 0, st>>>(W, w_plane, d.n_pad, ndev, mu_use, nu_use, C, long(ldc), m, n);
+            k_crt<T, 32><<<grid, 256, 0, st>>>(W, w_plane, d.n_pad, ndev, mu_use(), nu_use(), C, long(ldc), m, n);
         else
-            k_crt<T, 64><<<grid, 256, 0, st>>>(W, w_plane, d.n_pad, ndev, mu_use, nu_use, C, long(ldc), m, n);
-        if ((rc = cuda_fail(cudaGetLastError()))) return rc;
+            k_crt<T, 64><<<grid, 256, 0, st>>>(W, w_plane, d.n_pad, ndev, mu_use(), nu_use(), C, long(ldc), m, n);
+        return cuda_fail(cudaGetLastError());
     }
+};
+
+// the library-managed workspace of the current device (grown with cudaMalloc)
+int managed_workspace(int dev, size_t bytes, uint8_t **out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState &s = g_dev[dev];
+    if (s.ws_bytes < bytes) {
+        if (s.ws) {
+            cudaDeviceSynchronize();
+            cudaFree(s.ws);
+            s.ws = nullptr;
+            s.ws_bytes = 0;
+        }
+        if (cudaMalloc(&s.ws, bytes) != cudaSuccess) return cuda_fail(cudaErrorMemoryAllocation);
+        s.ws_bytes = bytes;
+    }
+    *out = static_cast<uint8_t *>(s.ws);
+    return OZ2_OK;
+}
+
+template <typename T>
+int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, int nmoduli, int mode,
+        const oz2_opts *o) {
+    int rc = validate(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o);
+    if (rc) return rc;
+    Job<T> job;
+    job.set(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o ? o->target : 0.0, o ? o->nmax : 0);
+    if (o) {
+        job.n_out = o->n_out;
+        job.mu_out = o->mu_out;
+        job.nu_out = o->nu_out;
+        job.mu_in = o->mu_in;
+        job.nu_in = o->nu_in;
+    }
+    int dev = 0;
+    if ((rc = ensure_device(&dev))) return rc;
+    cudaStream_t st = o ? static_cast<cudaStream_t>(o->stream) : nullptr;
+    uint8_t *ws = nullptr;
+    if (o && o->workspace) {
+        if (o->workspace_bytes < job.L.total) return OZ2_ENOMEM;
+        if (reinterpret_cast<uintptr_t>(o->workspace) & 255u) return OZ2_EINVAL;
+        ws = static_cast<uint8_t *>(o->workspace);
+    } else if ((rc = managed_workspace(dev, job.L.total, &ws))) {
+        return rc;
+    }
+    job.bind(ws);
+
+    static thread_local GemmGroup G;       // 24 KB: passed by value as the kernel parameter
+    std::memset(&G, 0, sizeof G);
+    G.count = 1;
+    if ((rc = job.describe(G.p[0]))) return rc;
+    const int sms = g_dev[dev].sms;
+    auto mark = [&](int phase) -> int {
+        if (!o || !o->phase_events) return OZ2_OK;
+        return cuda_fail(cudaEventRecord(static_cast<cudaEvent_t>(o->phase_events[phase]), st));
+    };
+    if ((rc = mark(OZ2_PHASE_STATS))) return rc;
+    if ((rc = job.phase_inputs(st, mark))) return rc;
+    if (job.inject() && (rc = mark(OZ2_PHASE_QUANT))) return rc;
+    if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
+    if (job.needs_scale_gemm()) {
+        job.as_scale_gemm(G.p[0]);
+        if ((rc = launch_gemm<EPI_MAX>(G, sms, st))) return rc;
+    }
+    if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
+    if ((rc = job.phase_exponents(st))) return rc;
+    if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
+    if ((rc = job.phase_residues(st))) return rc;
+    if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
+    job.as_residue_gemm(G.p[0]);
+    if ((rc = launch_gemm<EPI_MOD>(G, sms, st))) return rc;
+    if ((rc = mark(OZ2_PHASE_CRT))) return rc;
+    if ((rc = job.phase_crt(st))) return rc;
     if ((rc = mark(OZ2_NPHASES))) return rc;
     if (o && o->w_out) {
         // export W_l (test aid): plane l, m x n row-major, from the padded layout
-        for (int l = 0; l < nmax; l++) {
-            rc = cuda_fail(cudaMemcpy2DAsync(o->w_out + size_t(l) * m * n, size_t(n), W + size_t(l) * w_plane,
-                                             size_t(d.n_pad), size_t(n), size_t(m), cudaMemcpyDeviceToDevice, st));
+        for (int l = 0; l < job.nmax; l++) {
+            rc = cuda_fail(cudaMemcpy2DAsync(o->w_out + size_t(l) * m * n, size_t(n), job.W + size_t(l) * job.w_plane,
+                                             size_t(job.d.n_pad), size_t(n), size_t(m), cudaMemcpyDeviceToDevice, st));
             if (rc) return rc;
         }
     }
     return OZ2_OK;
+}
+
+// ------------------------------------------------------------------ batches
+int validate_problem(const oz2_problem &q) {
+    oz2_opts o{};
+    o.target = q.target;
+    o.nmax = q.nmax;
+    return validate(q.m, q.n, q.k, q.A, q.lda, q.B, q.ldb, q.C, q.ldc, q.nmoduli, q.mode, &o);
+}
+
+// workspace offsets of each problem inside one batch workspace
+size_t batch_layout(int count, const oz2_problem *q, std::vector<Job<double>> &jobs, std::vector<size_t> &off) {
+    jobs.resize(size_t(count));
+    off.resize(size_t(count));
+    size_t total = 0;
+    for (int p = 0; p < count; p++) {
+        jobs[p].set(q[p].m, q[p].n, q[p].k, q[p].A, q[p].lda, q[p].B, q[p].ldb, q[p].C, q[p].ldc, q[p].nmoduli,
+                    q[p].mode, q[p].target, q[p].nmax);
+        jobs[p].n_out = q[p].n_out;
+        off[p] = total;
+        total = round_up(total + jobs[p].L.total, 256);
+    }
+    return total;
+}
+
+int run_batched(int count, const oz2_problem *q, const oz2_opts *o) {
+    if (count < 0 || (count > 0 && !q)) return OZ2_EINVAL;
+    if (count == 0) return OZ2_OK;
+    int rc;
+    for (int p = 0; p < count; p++)
+        if ((rc = validate_problem(q[p]))) return rc;
+    std::vector<Job<double>> jobs;
+    std::vector<size_t> off;
+    const size_t total = batch_layout(count, q, jobs, off);
+    int dev = 0;
+    if ((rc = ensure_device(&dev))) return rc;
+    cudaStream_t st = o ? static_cast<cudaStream_t>(o->stream) : nullptr;
+    uint8_t *ws = nullptr;
+    if (o && o->workspace) {
+        if (o->workspace_bytes < total) return OZ2_ENOMEM;
+        if (reinterpret_cast<uintptr_t>(o->workspace) & 255u) return OZ2_EINVAL;
+        ws = static_cast<uint8_t *>(o->workspace);
+    } else if ((rc = managed_workspace(dev, total, &ws))) {
+        return rc;
+    }
+    for (int p = 0; p < count; p++) jobs[p].bind(ws + off[p]);
+    DeviceState &ds = g_dev[dev];
+    const int sms = ds.sms;
+    std::lock_guard<std::mutex> lk(ds.batch_mu);
+    auto mark = [&](int phase) -> int {
+        if (!o || !o->phase_events) return OZ2_OK;
+        return cuda_fail(cudaEventRecord(static_cast<cudaEvent_t>(o->phase_events[phase]), st));
+    };
+    auto no_mark = [](int) { return OZ2_OK; };
+    // light phases of problem p run on pool stream p % kPool, forked from and
+    // joined back to the caller's stream around each grouped GEMM launch
+    const int used = std::min(count, kPool);
+    auto fork = [&]() -> int {
+        int r = cuda_fail(cudaEventRecord(ds.fork, st));
+        for (int i = 0; i < used && !r; i++) r = cuda_fail(cudaStreamWaitEvent(ds.pool[i], ds.fork, 0));
+        return r;
+    };
+    auto join = [&]() -> int {
+        int r = OZ2_OK;
+        for (int i = 0; i < used && !r; i++) {
+            r = cuda_fail(cudaEventRecord(ds.done[i], ds.pool[i]));
+            if (!r) r = cuda_fail(cudaStreamWaitEvent(st, ds.done[i], 0));
+        }
+        return r;
+    };
+    // grouped persistent GEMM launches, heaviest problems first (longest
+    // processing time first balances the static item assignment)
+    std::vector<int> order;
+    order.resize(size_t(count));
+    for (int p = 0; p < count; p++) order[p] = p;
+    auto cost = [&](int p) {
+        const auto &d = jobs[p].d;
+        return double(d.m_pad) * d.n_pad * d.k_pad * (jobs[p].nmax + 1);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    static thread_local GemmGroup G;
+    auto grouped = [&](bool scale) -> int {
+        int r = OZ2_OK;
+        std::memset(&G, 0, sizeof G);
+        for (int idx = 0; idx < count && !r; idx++) {
+            const int p = order[idx];
+            if (scale && !jobs[p].needs_scale_gemm()) continue;
+            GemmProblem &P = G.p[G.count];
+            if ((r = jobs[p].describe(P))) break;
+            if (scale) jobs[p].as_scale_gemm(P);
+            else jobs[p].as_residue_gemm(P);
+            if (++G.count == gemm::kMaxGroup) {
+                r = scale ? launch_gemm<EPI_MAX>(G, sms, st) : launch_gemm<EPI_MOD>(G, sms, st);
+                std::memset(&G, 0, sizeof G);
+            }
+        }
+        if (!r && G.count) r = scale ? launch_gemm<EPI_MAX>(G, sms, st) : launch_gemm<EPI_MOD>(G, sms, st);
+        return r;
+    };
+
+    if ((rc = mark(OZ2_PHASE_STATS))) return rc;
+    if ((rc = fork())) return rc;
+    for (int p = 0; p < count; p++)
+        if ((rc = jobs[p].phase_inputs(ds.pool[p % kPool], no_mark))) return rc;
+    if ((rc = join())) return rc;
+    if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
+    if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
+    if ((rc = grouped(true))) return rc;
+    if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
+    if ((rc = fork())) return rc;
+    for (int p = 0; p < count; p++) {
+        cudaStream_t s = ds.pool[p % kPool];
+        if ((rc = jobs[p].phase_exponents(s))) return rc;
+        if ((rc = jobs[p].phase_residues(s))) return rc;
+    }
+    if ((rc = join())) return rc;
+    if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
+    if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
+    if ((rc = grouped(false))) return rc;
+    if ((rc = mark(OZ2_PHASE_CRT))) return rc;
+    if ((rc = fork())) return rc;
+    for (int p = 0; p < count; p++)
+        if ((rc = jobs[p].phase_crt(ds.pool[p % kPool]))) return rc;
+    if ((rc = join())) return rc;
+    return mark(OZ2_NPHASES);
 }
 
 }  // namespace
@@ -448,6 +663,23 @@ int oz2_sgemm_ex(int m, int n, int k, const float *A, int lda, const float *B, i
 int oz2_sgemm(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
               int nmoduli, int mode) {
     return run<float>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, nullptr);
+}
+
+int oz2_gemm_batched(int count, const oz2_problem *problems, const oz2_opts *opts) {
+    return run_batched(count, problems, opts);
+}
+
+size_t oz2_batched_workspace_size(int count, const oz2_problem *problems) {
+    if (count < 0 || (count > 0 && !problems)) return 0;
+    for (int p = 0; p < count; p++) {
+        const oz2_problem &q = problems[p];
+        if (q.m < 1 || q.n < 1 || q.k < 1 || q.k > OZ2_K_MAX) return 0;
+        if (q.nmoduli != 0 && (q.nmoduli < OZ2_N_MIN || q.nmoduli > OZ2_N_MAX)) return 0;
+        if (q.nmax != 0 && (q.nmax < OZ2_N_MIN || q.nmax > OZ2_N_MAX)) return 0;
+    }
+    std::vector<Job<double>> jobs;
+    std::vector<size_t> off;
+    return batch_layout(count, problems, jobs, off);
 }
 
 size_t oz2_workspace_size(int m, int n, int k, int nmax, int mode, int fp32) {

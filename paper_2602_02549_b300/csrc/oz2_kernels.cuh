@@ -482,7 +482,7 @@ enum { EPI_MAX = 0, EPI_MOD = 1 };
 
 // One GEMM problem of a launch: X_l (rows l*m_pad ..) times Y_l^T for the planes
 // l < planes (and l < *n_dev when n_dev is set), 128 x 256 output tiles.
-struct alignas(64) GemmProblem {
+struct GemmProblem {
     CUtensorMap tmA, tmB;      // BF16, K-major, 128B-swizzled boxes of 64 x 128 / 64 x 256
     int m_pad, n_pad, kb_total;
     int tiles_m, tiles_n, planes;

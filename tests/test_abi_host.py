@@ -105,3 +105,24 @@ def test_tables_match_oracle(lib, N, fp32):
     bt = bound_terms(N, 32 if fp32 else 64)
     assert abs(t["t"] / bt["t"] - 1) < 1e-12
     assert abs(t["gN"] / bt["gN"] - 1) < 1e-10
+
+
+def test_batched_validation_and_workspace(lib):
+    P = B.oz2_problem
+    good = P(m=8, n=8, k=8, A=0x10000, lda=8, B=0x10000, ldb=8, C=0x10000, ldc=8, nmoduli=14, target=0.0,
+             nmax=0, mode=0, n_out=None)
+    bad = P(m=8, n=8, k=8, A=0x10000, lda=7, B=0x10000, ldb=8, C=0x10000, ldc=8, nmoduli=14, target=0.0,
+            nmax=0, mode=0, n_out=None)
+    lib.oz2_gemm_batched.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.oz2_gemm_batched.restype = ctypes.c_int
+    lib.oz2_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    lib.oz2_batched_workspace_size.restype = ctypes.c_size_t
+    arr = (P * 2)(good, bad)
+    assert lib.oz2_gemm_batched(2, ctypes.cast(arr, ctypes.c_void_p), None) == B.OZ2_EINVAL
+    assert lib.oz2_gemm_batched(-1, None, None) == B.OZ2_EINVAL
+    assert lib.oz2_gemm_batched(0, None, None) == 0
+    one = (P * 1)(good)
+    two = (P * 2)(good, good)
+    w1 = lib.oz2_batched_workspace_size(1, ctypes.cast(one, ctypes.c_void_p))
+    w2 = lib.oz2_batched_workspace_size(2, ctypes.cast(two, ctypes.c_void_p))
+    assert w1 >= B.workspace_size(8, 8, 8, 14) and w2 == 2 * w1

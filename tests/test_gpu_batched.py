@@ -1,0 +1,98 @@
+"""Batched emulated DGEMM: every problem of one oz2_gemm_batched call must be
+bit-identical to oz2_gemm_ex on the same problem (same exponents, same N), and
+the call must capture into a CUDA graph and replay correctly."""
+import numpy as np
+import pytest
+
+from paper_2602_02549_b300.inputs import paper_matrix
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2602_02549_b300.build import build
+    build()
+
+
+SPECS = [  # m, n, k, phi, nmoduli, target, fast, trans_a, trans_b
+    (128, 256, 64, 0.5, 14, 0.0, False, False, False),
+    (300, 200, 1500, 1.0, 0, 1e-14, False, False, False),
+    (33, 65, 17, 2.0, 8, 0.0, False, True, False),
+    (513, 129, 700, 4.0, 0, 1e-12, False, False, True),
+    (1, 1, 1, 1.0, 5, 0.0, False, False, False),
+    (777, 333, 2049, 1.0, 0, 1e-15, False, False, False),
+    (250, 260, 300, 1.0, 17, 0.0, True, False, False),
+    (64, 1000, 900, 2.0, 0, 1e-14, True, True, True),
+    (1200, 40, 80, 0.5, 20, 0.0, False, False, False),
+    (90, 91, 4100, 1.0, 0, 1e-15, False, False, False),
+]
+
+
+def make_problems(seed0=0):
+    import torch
+    probs = []
+    for i, (m, n, k, phi, N, tau, fast, ta, tb) in enumerate(SPECS):
+        A = paper_matrix(m, k, phi, seed0 + 2 * i)
+        Bm = paper_matrix(k, n, phi, seed0 + 2 * i + 1)
+        As = np.ascontiguousarray(A.T) if ta else A
+        Bs = np.ascontiguousarray(Bm.T) if tb else Bm
+        probs.append(dict(A=torch.tensor(As, device="cuda"), B=torch.tensor(Bs, device="cuda"),
+                          C=torch.full((m, n), float("nan"), dtype=torch.float64, device="cuda"),
+                          nmoduli=N, target=tau, nmax=30 if N == 0 else 0, fast=fast, trans_a=ta, trans_b=tb,
+                          n_out=torch.zeros(1, dtype=torch.int32, device="cuda")))
+    return probs
+
+
+def single_reference(q):
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    C = torch.empty_like(q["C"])
+    nout = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mode = (B.OZ2_FAST if q["fast"] else 0) | (B.OZ2_TRANS_A if q["trans_a"] else 0) | \
+        (B.OZ2_TRANS_B if q["trans_b"] else 0)
+    assert B.gemm_ex(q["A"], q["B"], C, q["nmoduli"], mode, target=q["target"], nmax=q["nmax"], n_out=nout) == 0
+    return C, nout
+
+
+def test_batched_equals_single_calls():
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    probs = make_problems()
+    assert B.gemm_batched(probs) == 0
+    torch.cuda.synchronize()
+    assert B.sync() == 0
+    for q in probs:
+        C, nout = single_reference(q)
+        torch.cuda.synchronize()
+        assert int(q["n_out"].item()) == int(nout.item())
+        assert torch.equal(q["C"], C)
+
+
+def test_batched_graph_capture_and_replay():
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    probs = make_problems()
+    ws = torch.empty(B.batched_workspace_size(probs), dtype=torch.uint8, device="cuda")
+    assert B.gemm_batched(probs, workspace=ws) == 0          # first call outside capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        assert B.gemm_batched(probs, workspace=ws, stream=s) == 0
+    for seed in (100, 200):
+        fresh = make_problems(seed)
+        for q, f in zip(probs, fresh):
+            q["A"].copy_(f["A"])
+            q["B"].copy_(f["B"])
+            q["C"].fill_(float("nan"))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        for q in probs:
+            C, nout = single_reference(q)
+            torch.cuda.synchronize()
+            assert torch.equal(q["C"], C) and int(q["n_out"].item()) == int(nout.item())
