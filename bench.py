@@ -45,6 +45,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--acc-samples", type=int, default=256)
+    p.add_argument("--workload", default="square", choices=["square", "batched", "autograd", "sgemm"],
+                   help="square: the headline DGEMM; batched: 64 uneven problems (one graph-captured call); "
+                        "autograd: loss ||AB - T||^2 forward + backward; sgemm: FP32 emulation")
+    p.add_argument("--mode", default="accurate", choices=["accurate", "fast"])
     return p.parse_args()
 
 
@@ -126,9 +130,9 @@ class ClockSampler:
 
 def workload_config(args, m, n, k, N, world=1):
     nmax = args.nmoduli or args.nmax
-    return {"workload": f"dgemm_square_{m}_phi{args.phi}_tau{args.target:g}_accurate",
+    return {"workload": f"dgemm_square_{m}_phi{args.phi}_tau{args.target:g}_{args.mode}",
             "m": m, "n": n, "k": k, "phi": args.phi, "target": args.target, "nmax": nmax,
-            "nmoduli": N, "mode": "accurate",
+            "nmoduli": N, "mode": args.mode,
             "l2": "inputs larger than L2 (A, B 2 GiB each; residues 1 GiB per modulus)",
             "parallelism": f"replicas{world}" if world > 1 else "single"}
 
@@ -185,10 +189,151 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- #
+def timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batched(args):
+    """64 uneven problems (m, n, k log-uniform in [128, 4096], phi ~ U(0.5, 4)),
+    per-problem bound-chosen N for tau = 1e-14, one oz2_gemm_batched call
+    captured in a CUDA graph, against 64 plain oz2_gemm_ex calls at the fixed N
+    that meets the target for every problem (the largest chosen N)."""
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.build import build
+    from paper_2602_02549_b300.inputs import batched_specs, paper_matrix_torch
+    build()
+    dev = torch.device("cuda", 0)
+    tau = 1e-14 if args.target == 1e-15 else args.target
+    specs = batched_specs(64, 0)
+    probs, flops = [], 0.0
+    for i, (m, n, k, phi) in enumerate(specs):
+        probs.append(dict(A=paper_matrix_torch(m, k, phi, 2 * i, dev), B=paper_matrix_torch(k, n, phi, 2 * i + 1, dev),
+                          C=torch.empty((m, n), dtype=torch.float64, device=dev), nmoduli=0, target=tau, nmax=30,
+                          fast=args.mode == "fast", n_out=torch.zeros(1, dtype=torch.int32, device=dev)))
+        flops += 2.0 * m * n * k
+    ws = torch.empty(B.batched_workspace_size(probs), dtype=torch.uint8, device=dev)
+    assert B.gemm_batched(probs, workspace=ws) == 0
+    torch.cuda.synchronize()
+    Ns = [int(q["n_out"].item()) for q in probs]
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        assert B.gemm_batched(probs, workspace=ws, stream=s) == 0
+    ms = timed(g.replay, args.steps, args.warmup, torch.cuda.current_stream())
+    assert B.sync() == 0
+    Nfix = max(Ns)
+    wmax = max(B.workspace_size(q["A"].size(0), q["B"].size(1), q["A"].size(1), Nfix) for q in probs)
+    ws1 = torch.empty(wmax, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        for q in probs:
+            rc = B.gemm_ex(q["A"], q["B"], q["C"], Nfix, B.OZ2_FAST if args.mode == "fast" else 0,
+                           workspace=ws1, stream=stream)
+            assert rc == 0
+    ms_plain = timed(plain, args.steps, args.warmup, stream)
+    peaks, kind = load_peaks()
+    mma = sum(2.0 * q["A"].size(0) * q["B"].size(1) * q["A"].size(1) * (n + 1) for q, n in zip(probs, Ns))
+    print(json.dumps({
+        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched_64_uneven_128_4096_tau%g_%s" % (tau, args.mode), "problems": 64,
+                   "total_2mnk": flops, "target": tau, "graph": "one oz2_gemm_batched call captured"},
+        "n_moduli": {"min": min(Ns), "max": max(Ns), "mean": sum(Ns) / len(Ns)},
+        "plain_fixed_N": {"N": Nfix, "ms": ms_plain, "tflops": flops / (ms_plain * 1e-3) / 1e12},
+        "mma_tflops_rate": mma / (ms * 1e-3) / 1e12,
+        "mma_frac_of_peak": mma / (ms * 1e-3) / 1e12 / float(peaks["bf16_tflops_sustained"])}))
+
+
+def run_autograd(args):
+    """loss = ||A B - T||_F^2 with A 4096 x 2048, B 2048 x 1024, phi = 1:
+    forward and hand-written backward (dA, dB) through the emulation."""
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.autograd import oz2_matmul
+    from paper_2602_02549_b300.build import build
+    from paper_2602_02549_b300.inputs import paper_matrix_torch
+    build()
+    dev = torch.device("cuda", 0)
+    m, k, n = 4096, 2048, 1024
+    A = paper_matrix_torch(m, k, 1.0, 0, dev).requires_grad_()
+    Bm = paper_matrix_torch(k, n, 1.0, 1, dev).requires_grad_()
+    T = paper_matrix_torch(m, n, 1.0, 2, dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        A.grad = None
+        Bm.grad = None
+        loss = ((oz2_matmul(A, Bm, args.nmoduli, args.target, args.nmax, args.mode == "fast") - T) ** 2).sum()
+        loss.backward()
+    ms = timed(step, args.steps, args.warmup, stream)
+    with torch.no_grad():
+        R = A @ Bm - T
+        dA, dB = 2 * R @ Bm.t(), 2 * A.t() @ R
+    err = max(((A.grad - dA).abs().max() / dA.abs().max()).item(), ((Bm.grad - dB).abs().max() / dB.abs().max()).item())
+    C = torch.empty((m, n), dtype=torch.float64, device=dev)
+    ms_fwd = timed(lambda: B.matmul(A.detach(), Bm.detach(), 20, out=C), args.steps, args.warmup, stream)
+    flops = 3 * 2.0 * m * n * k
+    print(json.dumps({
+        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "autograd_loss_4096x2048x1024_tau%g" % args.target, "target": args.target,
+                   "products_per_step": 3},
+        "grad_rel_err_vs_fp64": err,
+        "plain_fixed_N20_forward": {"ms": ms_fwd, "tflops": 2.0 * m * n * k / (ms_fwd * 1e-3) / 1e12}}))
+
+
+def run_sgemm(args):
+    """FP32 SGEMM emulation 8192^3, phi = 1, N from the bound rule for tau = 1e-7."""
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.build import build
+    from paper_2602_02549_b300.inputs import paper_matrix_torch
+    build()
+    dev = torch.device("cuda", 0)
+    s = 8192 if args.size == 16384 else args.size
+    tau = 1e-7 if args.target == 1e-15 else args.target
+    A = paper_matrix_torch(s, s, args.phi, 0, dev, torch.float32)
+    Bm = paper_matrix_torch(s, s, args.phi, 1, dev, torch.float32)
+    C = torch.empty((s, s), dtype=torch.float32, device=dev)
+    nout = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(B.workspace_size(s, s, s, 14, 0, True), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    fn = lambda: B.gemm_ex(A, Bm, C, args.nmoduli, B.OZ2_FAST if args.mode == "fast" else 0,
+                           target=tau if not args.nmoduli else 0.0, nmax=14 if not args.nmoduli else 0,
+                           workspace=ws, stream=stream, n_out=nout)
+    ms = timed(fn, args.steps, args.warmup, stream)
+    torch.matmul(A, Bm)
+    ms_native = timed(lambda: torch.matmul(A, Bm), 3, 1, stream)
+    print(json.dumps({
+        "metric": METRIC.replace("DGEMM", "SGEMM"), "value": 2.0 * s ** 3 / (ms * 1e-3) / 1e12, "unit": "TFLOPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "sgemm_square_%d_phi%g_tau%g_%s" % (s, args.phi, tau, args.mode)},
+        "n_moduli": int(nout.item()),
+        "native_fp32_tflops": 2.0 * s ** 3 / (ms_native * 1e-3) / 1e12}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "square":
+        {"batched": run_batched, "autograd": run_autograd, "sgemm": run_sgemm}[args.workload](args)
         return
     import torch
     from paper_2602_02549_b300 import binding as B
@@ -215,8 +360,10 @@ def main():
     tgt = args.target if not args.nmoduli else 0.0
     nmx = args.nmax if not args.nmoduli else 0
 
+    flags = B.OZ2_FAST if args.mode == "fast" else 0
+
     def step(events=None, a=A, b=Bm):
-        rc = B.gemm_ex(a, b, C, args.nmoduli, 0, target=tgt, nmax=nmx, workspace=ws, stream=stream,
+        rc = B.gemm_ex(a, b, C, args.nmoduli, flags, target=tgt, nmax=nmx, workspace=ws, stream=stream,
                        n_out=nout, phase_events=events)
         if rc:
             raise B.Oz2Error(rc, "oz2_gemm_ex")
@@ -333,7 +480,9 @@ def main():
         cpu = cpu_baseline(A[:s].cpu().numpy(), Bm[:, :s].cpu().numpy(), N_used, s, args.phi)
 
     if rank == 0:
-        launches_per_step = 12 if args.nmoduli == 0 else 11
+        # stats x2, quantise x2, scaling GEMM (fast: two majorant kernels instead),
+        # [bound reduction], choose N, mu/nu, residues x2, residue GEMM, CRT
+        launches_per_step = (12 if args.nmoduli == 0 else 11) + (1 if args.mode == "fast" else 0)
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

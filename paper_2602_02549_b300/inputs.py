@@ -58,3 +58,11 @@ def wide_exponent_matrix(rows: int, cols: int, emin: int, emax: int, seed: int,
     if zero_frac > 0:
         a[rng.random((rows, cols)) < zero_frac] = 0.0
     return a
+
+
+def batched_specs(count: int = 64, seed: int = 0, lo: int = 128, hi: int = 4096):
+    """Uneven batch: m, n, k = round(exp(U(ln lo, ln hi))) and phi ~ U(0.5, 4) per problem."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dims = np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), size=(count, 3)))).astype(int)
+    phis = rng.uniform(0.5, 4.0, size=count)
+    return [(int(m), int(n), int(k), float(p)) for (m, n, k), p in zip(dims, phis)]
