@@ -126,37 +126,6 @@ void oz2o_mod_i64(long count, const int64_t *X, int p, int8_t *out)
     }
 }
 
-/* Algorithm 3, accumulation and final reduction, per entry:                  */
-/*   C'(1) = fl(sum_l s_l1 W_l),  C'(2) = fl(sum_l s_l2 W_l)                   */
-/*   (both as fma chains in ascending l, starting from +0),                    */
-/*   Q = round(fl(P_inv * C'(1))),                                             */
-/*   C'' = fl(fma(-Q, P2, fma(-Q, P1, C'(1)) + C'(2))).                        */
-/* For b = 32 the rounding C'' = single(C'') is taken after the inverse        */
-/* scaling (oz2o_unscale), where it gives the same value whenever single(C'')  */
-/* is finite and C is normal, and does not overflow when P > 2^128.            */
-/* W holds N planes of `count` entries.                                        */
-void oz2o_crt(long count, int N, const int8_t *W, const double *s1, const double *s2,
-              double P1, double P2, double Pinv, int b,
-              double *C1out, double *C2out, double *Qout, double *Cpp)
-{
-#pragma omp parallel for schedule(static)
-    for (long e = 0; e < count; e++) {
-        double c1 = 0.0, c2 = 0.0;
-        for (int l = 0; l < N; l++) {
-            double w = (double)W[(long)l * count + e];
-            c1 = fma(s1[l], w, c1);
-            c2 = fma(s2[l], w, c2);
-        }
-        double q = nearbyint(Pinv * c1);        /* round to nearest (even) */
-        double c = fma(-q, P2, fma(-q, P1, c1) + c2);
-        (void)b;
-        if (C1out) C1out[e] = c1;
-        if (C2out) C2out[e] = c2;
-        if (Qout) Qout[e] = q;
-        Cpp[e] = c;
-    }
-}
-
 /* Algorithm 1, last line: C = fl(diag(2^-mu) C'' diag(2^-nu)), taken as one   */
 /* scaling by 2^-(mu_i + nu_j) (a single rounding, which only matters when    */
 /* the result is subnormal).  b = 32: C = single(2^-(mu_i+nu_j) C''), the     */
@@ -285,11 +254,56 @@ static double big_to_double(bigfix *x)
     uint64_t kept = 0;
     for (int pos = top; pos >= d; pos--) kept = (kept << 1) | (uint64_t)big_bit(x, pos);
     int roundbit = d - 1 >= 0 ? big_bit(x, d - 1) : 0;
-    int sticky = 0;
-    for (int pos = d - 2; pos >= 0 && !sticky; pos--) sticky |= big_bit(x, pos);
+    int sticky = 0;                             /* any bit below the round bit */
+    if (d - 2 >= 0) {
+        int top_limb = (d - 2) >> 6, nb = ((d - 2) & 63) + 1;
+        uint64_t mask = nb == 64 ? ~0ull : ((1ull << nb) - 1);
+        sticky = (x->l[top_limb] & mask) != 0;
+        for (int t = 0; t < top_limb && !sticky; t++) sticky = x->l[t] != 0;
+    }
     if (roundbit && (sticky || (kept & 1u))) kept++;
     double r = ldexp((double)kept, elsb);
     return neg ? -r : r;
+}
+
+/* Algorithm 3, accumulation and final reduction, per entry:                  */
+/*   C'(1) = fl(sum_l s_l1 W_l),  C'(2) = fl(sum_l s_l2 W_l),                   */
+/*   Q = round(fl(P_inv * C'(1))),                                             */
+/*   C'' = fl(fma(-Q, P2, fma(-Q, P1, C'(1)) + C'(2))).                        */
+/* Reading of fl(sum): each sum is taken exactly and rounded to the nearest   */
+/* double once.  The Section 4 analysis (proof of Lemma 2) bounds the error   */
+/* of any floating-point evaluation of these sums by N u_64 sum |s_l2 W_l|;   */
+/* the correctly rounded sum meets that bound and is the one evaluation whose */
+/* value does not depend on the order of the terms.  For b = 64, C'(1) is     */
+/* exact (Lemma 2), so only C'(2) is affected; for b = 32, s_l2 = 0 and       */
+/* C'(1) is the rounded sum.                                                  */
+/* For b = 32 the rounding C'' = single(C'') is taken after the inverse        */
+/* scaling (oz2o_unscale), where it gives the same value whenever single(C'')  */
+/* is finite and C is normal, and does not overflow when P > 2^128.            */
+/* W holds N planes of `count` entries.                                        */
+void oz2o_crt(long count, int N, const int8_t *W, const double *s1, const double *s2,
+              double P1, double P2, double Pinv, int b,
+              double *C1out, double *C2out, double *Qout, double *Cpp)
+{
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < count; e++) {
+        bigfix a1, a2;
+        memset(&a1, 0, sizeof a1);
+        memset(&a2, 0, sizeof a2);
+        for (int l = 0; l < N; l++) {
+            double w = (double)W[(long)l * count + e];
+            big_add_product(&a1, s1[l], w);
+            big_add_product(&a2, s2[l], w);
+        }
+        double c1 = big_to_double(&a1), c2 = big_to_double(&a2);
+        double q = nearbyint(Pinv * c1);        /* round to nearest (even) */
+        double c = fma(-q, P2, fma(-q, P1, c1) + c2);
+        (void)b;
+        if (C1out) C1out[e] = c1;
+        if (C2out) C2out[e] = c2;
+        if (Qout) Qout[e] = q;
+        Cpp[e] = c;
+    }
 }
 
 /* out_ij = RN( sum_h X[i,h] Y[h,j] - (Cm ? Cm[i,j] : 0) ), computed exactly   */

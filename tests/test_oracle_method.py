@@ -322,3 +322,47 @@ def test_fast_mode_sum_of_squares_by_hand(oracle):
     row, col = oracle.fast_cbar_maxima(Abar, Bbar)
     assert list(row) == [15, 25] and list(col) == [15, 25]
     assert oracle.ceil_sqrt(10) == 4 and oracle.ceil_sqrt(16) == 4 and oracle.ceil_sqrt(0) == 0
+
+
+@pytest.mark.parametrize("b", [64, 32])
+@pytest.mark.parametrize("N", [2, 6, 9, 17, 33, 49])
+def test_crt_sums_correctly_rounded(oracle, N, b):
+    # Algorithm 3: C'(1) and C'(2) are the exact sums sum_l s_l W_l rounded once
+    # to the nearest double; Python's int / int division is correctly rounded,
+    # so the reference values below come from exact rational arithmetic alone.
+    C = constants(N, b)
+    rng = np.random.default_rng(N + b)
+    lo = np.array([-(p // 2) for p in C.p])
+    hi = np.array([(p - 1) // 2 for p in C.p])
+    W = rng.integers(lo[:, None], hi[:, None] + 1, size=(N, 300)).astype(np.int8)
+    W[:, 0] = lo.astype(np.int8)                  # all at the negative extreme
+    W[:, 1] = hi.astype(np.int8)
+    W[:, 2] = 0
+    r = oracle.crt_from_W(W, N, b)
+
+    def rounded(svals, col):
+        num = sum(Fraction(s) * int(W[l, col]) for l, s in enumerate(svals))
+        return num.numerator / num.denominator
+
+    for e in range(W.shape[1]):
+        assert r["C1"][e] == rounded(C.s1, e)
+        assert r["C2"][e] == rounded(C.s2, e)
+    assert r["C1"][2] == 0.0 and r["C2"][2] == 0.0
+
+
+def test_crt_planted_fma_chain_differs(oracle):
+    # the correctly rounded C'(2) differs from an ascending fma chain on some
+    # entries (otherwise the test above would not pin the reading)
+    N, b = 17, 64
+    C = constants(N, b)
+    rng = np.random.default_rng(3)
+    W = np.stack([rng.integers(-(p // 2), (p - 1) // 2 + 1, size=1500) for p in C.p]).astype(np.int8)
+    r = oracle.crt_from_W(W, N, b)
+    diff = 0
+    for e in range(W.shape[1]):
+        acc = 0.0
+        for l in range(N):
+            t = Fraction(C.s2[l]) * int(W[l, e]) + Fraction(acc)     # fma: one rounding
+            acc = t.numerator / t.denominator
+        diff += acc != r["C2"][e]
+    assert diff > 0
