@@ -112,6 +112,17 @@ def tables(N: int, fp32: bool = False) -> dict:
                 Pprime=np.float32(pp.value))
 
 
+def sum_tables(N: int, fp32: bool = False) -> tuple:
+    """The CRT-sum constants as the device holds them: (list of k_l, esum) with
+    s_l2 (DGEMM) or s_l1 (SGEMM) = k_l 2^esum (host-only)."""
+    k = (ctypes.c_int * (2 * N))()
+    e = ctypes.c_int()
+    rc = lib().oz2_sum_tables(N, int(fp32), k, ctypes.byref(e))
+    if rc:
+        raise Oz2Error(rc, "oz2_sum_tables")
+    return [k[2 * l + 1] * (1 << 31) + k[2 * l] for l in range(N)], e.value
+
+
 # --------------------------------------------------------------------------- #
 # torch-facing calls
 # --------------------------------------------------------------------------- #

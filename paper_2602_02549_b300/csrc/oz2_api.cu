@@ -79,18 +79,19 @@ int ensure_device(int *dev_out) {
     }
     if (!st.tables) {
         const Tables &T = tables();
+        if (!T.sums_fit) return OZ2_ENOTSUP;
         DevN n64[kNMax + 1], n32[kNMax + 1];
         for (int N = 0; N <= kNMax; N++) {
             const NTable &a = T.n64[N], &b = T.n32[N];
-            n64[N] = DevN{a.P1, a.P2, a.Pinv, a.g, a.t, a.gN, a.Pprime, a.offset};
-            n32[N] = DevN{b.P1, b.P2, b.Pinv, b.g, b.t, b.gN, b.Pprime, b.offset};
+            n64[N] = DevN{a.P1, a.P2, a.Pinv, a.g, a.t, a.gN, a.Pprime, a.offset, a.eg, a.esum};
+            n32[N] = DevN{b.P1, b.P2, b.Pinv, b.g, b.t, b.gN, b.Pprime, b.offset, b.eg, b.esum};
         }
         cudaError_t e = cudaSuccess;
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_n64, n64, sizeof n64);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_n32, n32, sizeof n32);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_s1i, T.s1i, sizeof T.s1i);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_s2d, T.s2d, sizeof T.s2d);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_s1f, T.s1f, sizeof T.s1f);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_s1s, T.s1s, sizeof T.s1s);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ks64, T.ks64, sizeof T.ks64);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ks32, T.ks32, sizeof T.ks32);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_p, T.mod.p, sizeof T.mod.p);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_magic, T.mod.magic, sizeof T.mod.magic);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c16, T.mod.c16, sizeof T.mod.c16);
@@ -716,6 +717,20 @@ int oz2_tables(int N, int fp32, double *s1, double *s2, double *scal, float *ppr
     scal[4] = t.t;
     scal[5] = t.gN;
     *pprime = t.Pprime;
+    return OZ2_OK;
+}
+
+int oz2_sum_tables(int N, int fp32, int *k, int *esum) {
+    if (N < OZ2_N_MIN || N > OZ2_N_MAX || !k || !esum) return OZ2_EINVAL;
+    const Tables &T = tables();
+    if (!T.sums_fit) return OZ2_ENOTSUP;
+    const NTable &t = fp32 ? T.n32[N] : T.n64[N];
+    const int(*src)[2] = fp32 ? T.ks32 : T.ks64;
+    for (int l = 0; l < N; l++) {
+        k[2 * l] = src[t.offset + l][0];
+        k[2 * l + 1] = src[t.offset + l][1];
+    }
+    *esum = t.esum;
     return OZ2_OK;
 }
 

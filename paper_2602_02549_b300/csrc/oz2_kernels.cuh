@@ -29,13 +29,15 @@ struct DevN {
     double P1, P2, Pinv, g, t, gN;
     float Pprime;
     int offset;
+    int eg;       // b = 64: g = 2^eg
+    int esum;     // grid exponent of the rounded CRT sum
 };
 
 __constant__ DevN c_n64[kNMax + 1];
 __constant__ DevN c_n32[kNMax + 1];
-__constant__ long long c_s1i[kPackedLen];
-__constant__ double c_s2d[kPackedLen];
-__constant__ double c_s1f[kPackedLen];
+__constant__ int2 c_s1s[kPackedLen];      // b = 64: s_l1 / g = y 2^31 + x
+__constant__ int2 c_ks64[kPackedLen];     // b = 64: s_l2 / 2^esum = y 2^31 + x
+__constant__ int2 c_ks32[kPackedLen];     // b = 32: s_l1 / 2^esum = y 2^31 + x
 __constant__ int c_p[kNMax];
 __constant__ uint32_t c_magic[kNMax];
 __constant__ uint32_t c_c16[kNMax];
@@ -904,39 +906,72 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
     return y * __longlong_as_double((long long)(e2 + 1023) << 52);
 }
 
+// RN((hi 2^31 + lo) 2^e) as a double, from integer operations only (the FP64
+// pipe of this part is slow).  Requires |hi|, |lo| < 2^61 and a result in the
+// normal range (the tables check both for every N).  An exact zero gives +0.
+__device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
+    long long t = hi + (lo >> 31);                 // value = t 2^31 + r, 0 <= r < 2^31
+    unsigned long long r = (unsigned long long)(lo & 0x7FFFFFFFll);
+    const bool neg = t < 0;
+    unsigned long long T, R;                       // |value| = T 2^31 + R
+    if (!neg) { T = (unsigned long long)t; R = r; }
+    else if (r == 0) { T = (unsigned long long)(-t); R = 0; }
+    else { T = (unsigned long long)(-t - 1); R = (1ull << 31) - r; }
+    // X 2^s with the bits below 2^s folded into a sticky bit 0 of X
+    unsigned long long X;
+    int s = 0;
+    if (T < (1ull << 33)) {
+        X = (T << 31) | R;
+    } else {
+        s = (64 - __clzll((long long)T)) - 33;    // 1 .. 31: X gets 64 bits
+        X = (T << (31 - s)) | (R >> s) | ((R & ((1ull << s) - 1)) != 0 ? 1ull : 0ull);
+    }
+    if (X == 0) return 0.0;
+    const int bl = 64 - __clzll((long long)X);
+    int ex = bl - 1 + s + e;
+    unsigned long long mant;
+    if (bl <= 53) {
+        mant = X << (53 - bl);
+    } else {
+        const int sh = bl - 53;
+        mant = X >> sh;
+        const unsigned long long rem = X & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) mant++;
+        if (mant >> 53) { mant >>= 1; ex++; }
+    }
+    const unsigned long long bits = (neg ? (1ull << 63) : 0ull) | ((unsigned long long)(ex + 1023) << 52) |
+                                    (mant & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
+
 template <typename TO, int B>
 __global__ void __launch_bounds__(256) k_crt(const int8_t *W, long w_plane, int n_pad, const int *n_dev,
                                              const int32_t *mu, const int32_t *nu, TO *C, long ldc, int m, int n) {
-    // double(w) for every INT8 w, read from shared memory instead of converting
-    // on the (slow) FP64 pipe
-    __shared__ double wd[256];
-    wd[threadIdx.x] = double(int(int8_t(uint8_t(threadIdx.x))));
-    __syncthreads();
+    // C'(1) and C'(2) are sums of integer multiples of fixed grids: both are
+    // accumulated exactly in 64-bit integers (two 31-bit halves of each
+    // constant, |terms| < 2^38, N <= 49) and rounded once.
     const int N = *n_dev;
     const DevN d = B == 64 ? c_n64[N] : c_n32[N];
+    const int2 *ks = (B == 64 ? c_ks64 : c_ks32) + d.offset;
+    const int2 *s1s = c_s1s + d.offset;
     const int j0 = (blockIdx.x * 256 + threadIdx.x) * 4;
     if (j0 >= n) return;
     for (int i = blockIdx.y; i < m; i += gridDim.y) {
         const int8_t *wp = W + (long)i * n_pad + j0;
-        long long a1[4] = {0, 0, 0, 0};
-        double f1[4] = {0.0, 0.0, 0.0, 0.0}, f2[4] = {0.0, 0.0, 0.0, 0.0};
+        long long h1[4] = {0, 0, 0, 0}, l1[4] = {0, 0, 0, 0};
+        long long h2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0};
         for (int l = 0; l < N; l++) {
             const uint32_t w4 = *reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane);
-            if (B == 64) {
-                const long long s1 = c_s1i[d.offset + l];
-                const double s2 = c_s2d[d.offset + l];
+            const int2 k = ks[l];
+            const int2 s1 = B == 64 ? s1s[l] : make_int2(0, 0);
 #pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const uint32_t b = (w4 >> (8 * e)) & 255u;
-                    a1[e] += s1 * int(int8_t(b));
-                    f2[e] = fma(s2, wd[b], f2[e]);
-                }
-            } else {
-                const double s1 = c_s1f[d.offset + l];
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const uint32_t b = (w4 >> (8 * e)) & 255u;
-                    f1[e] = fma(s1, wd[b], f1[e]);
+            for (int e = 0; e < 4; e++) {
+                const int w = int(int8_t(uint8_t(w4 >> (8 * e))));
+                l2[e] += (long long)k.x * w;
+                h2[e] += (long long)k.y * w;
+                if (B == 64) {
+                    l1[e] += (long long)s1.x * w;
+                    h1[e] += (long long)s1.y * w;
                 }
             }
         }
@@ -945,10 +980,11 @@ __global__ void __launch_bounds__(256) k_crt(const int8_t *W, long w_plane, int 
         for (int e = 0; e < 4; e++) {
             const int j = j0 + e;
             if (j >= n) break;
-            const double c1 = B == 64 ? __ll2double_rn(a1[e]) * d.g : f1[e];
+            const double c1 = B == 64 ? rn_sum(h1[e], l1[e], d.eg) : rn_sum(h2[e], l2[e], d.esum);
             const double q = rint(d.Pinv * c1);
             // b = 32: P2 = 0 and C'(2) = +0, so fma(-q, 0, x + 0) = x + 0 as in the b = 64 form
-            const double cpp = B == 64 ? fma(-q, d.P2, fma(-q, d.P1, c1) + f2[e]) : fma(-q, d.P1, c1) + 0.0;
+            const double cpp = B == 64 ? fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum(h2[e], l2[e], d.esum))
+                                       : fma(-q, d.P1, c1) + 0.0;
             const double v = scale_pow2(cpp, -(mi + nu[j]));
             if (B == 64) C[(long)i * ldc + j] = TO(v);
             else C[(long)i * ldc + j] = TO(__double2float_rn(v));

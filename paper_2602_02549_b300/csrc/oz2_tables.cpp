@@ -14,6 +14,8 @@
 //   Theorem 2, Lemma 4:  t = 1/sqrt(2^5 (P-1)), the P-proportional part of R_b.
 #include "oz2_tables.h"
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -194,6 +196,32 @@ float f32_down(long double v) {
 
 int ceil_log2_u(uint64_t x) { return x <= 1 ? 0 : 64 - __builtin_clzll(x - 1); }
 
+// s_l = k_l 2^e for nonnegative doubles s_0..s_{N-1}: e is the exponent of the
+// least significant mantissa bit over all nonzero s_l, so every k_l is an
+// integer.  False if some k_l reaches 2^62 (the device sum would overflow) or
+// a result grid would leave the normal range.
+bool split_on_grid(const double *s, int N, int (*k)[2], int *e_out) {
+    int e = INT_MAX;
+    for (int l = 0; l < N; l++) {
+        if (s[l] == 0.0) continue;
+        if (!(s[l] > 0.0)) return false;
+        int ex;
+        std::frexp(s[l], &ex);
+        e = std::min(e, ex - 53);
+    }
+    if (e == INT_MAX) e = 0;
+    *e_out = e;
+    bool ok = e >= -1022 && e + 80 <= 1023;
+    for (int l = 0; l < N; l++) {
+        const double kd = std::ldexp(s[l], -e);
+        ok &= kd < 0x1p62;
+        const uint64_t v = ok ? uint64_t(kd) : 0;
+        k[l][0] = int(v & 0x7FFFFFFFu);
+        k[l][1] = int(v >> 31);
+    }
+    return ok;
+}
+
 void build(Tables &T) {
     std::memset(&T, 0, sizeof T);
     for (int l = 0; l < kNMax; l++) {
@@ -217,6 +245,7 @@ void build(Tables &T) {
     const long double u64 = 0x1p-53L, u32 = 0x1p-24L;
     T.c = f32_down(-0.5L / (1.0L - 4.0L * u32));
     int offset = 0;
+    T.sums_fit = true;
     for (int N = 1; N <= kNMax; N++) {
         Big P = Big::of(1);
         uint64_t rho = 0;
@@ -281,6 +310,15 @@ void build(Tables &T) {
             n.g = 1.0;
             n.offset = offset;
             for (int l = 0; l < N; l++) T.s1f[offset + l] = to_double(x[size_t(l)]);
+        }
+        T.n64[N].eg = std::ilogb(T.n64[N].g);
+        T.sums_fit &= split_on_grid(T.s2d + offset, N, T.ks64 + offset, &T.n64[N].esum);
+        T.sums_fit &= split_on_grid(T.s1f + offset, N, T.ks32 + offset, &T.n32[N].esum);
+        for (int l = 0; l < N; l++) {
+            const uint64_t v = uint64_t(T.s1i[offset + l]);
+            T.sums_fit &= v < (uint64_t(1) << 62);
+            T.s1s[offset + l][0] = int(v & 0x7FFFFFFFu);
+            T.s1s[offset + l][1] = int(v >> 31);
         }
         offset += N;
     }

@@ -30,6 +30,9 @@ struct NTable {
     double gN;               // P-proportional part of R_b (Lemma 4), rounded up
     float Pprime;            // single_down(log2(P-1)/2 - 0.5)
     int offset;              // start of this N's entries in the packed arrays
+    int eg;                  // b = 64: g = 2^eg
+    int esum;                // grid of the rounded CRT sum: s_l2 (b = 64) or s_l1
+                             // (b = 32) = (k[1] 2^31 + k[0]) 2^esum
 };
 
 struct Tables {
@@ -40,6 +43,12 @@ struct Tables {
     double s1d[kPackedLen];      // b = 64: s_l1
     double s2d[kPackedLen];      // b = 64: s_l2
     double s1f[kPackedLen];      // b = 32: s_l1 = double(P/p_l q_l)
+    // The constants of the two CRT sums as integers on a common grid, split
+    // into 31-bit halves (k = k[1] 2^31 + k[0], 0 <= k < 2^62):
+    int s1s[kPackedLen][2];      // b = 64: s_l1 / g
+    int ks64[kPackedLen][2];     // b = 64: s_l2 / 2^esum
+    int ks32[kPackedLen][2];     // b = 32: s_l1 / 2^esum
+    bool sums_fit;               // every k above is below 2^62 and every grid in range
     float c;                     // single_down(-0.5 / (1 - 4 u32))
 };
 

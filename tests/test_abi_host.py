@@ -107,6 +107,23 @@ def test_tables_match_oracle(lib, N, fp32):
     assert abs(t["gN"] / bt["gN"] - 1) < 1e-10
 
 
+@pytest.mark.parametrize("fp32", [False, True])
+def test_sum_tables_exact(lib, fp32):
+    # the integer form of the CRT-sum constants reproduces the oracle's doubles
+    # exactly, with every integer below 2^62 (the device sums cannot overflow)
+    from fractions import Fraction
+    for N in range(2, 50):
+        k, e = B.sum_tables(N, fp32)
+        C = constants(N, 32 if fp32 else 64)
+        target = C.s1 if fp32 else C.s2
+        for kl, sl in zip(k, target):
+            assert 0 <= kl < 1 << 62
+            assert Fraction(kl) * Fraction(2) ** e == Fraction(sl)
+        assert -1022 <= e and e + 80 <= 1023
+    with pytest.raises(B.Oz2Error):
+        B.sum_tables(1)
+
+
 def test_batched_validation_and_workspace(lib):
     P = B.oz2_problem
     good = P(m=8, n=8, k=8, A=0x10000, lda=8, B=0x10000, ldb=8, C=0x10000, ldc=8, nmoduli=14, target=0.0,
