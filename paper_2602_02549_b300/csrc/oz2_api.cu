@@ -97,6 +97,7 @@ int ensure_device(int *dev_out) {
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c16, T.mod.c16, sizeof T.mod.c16);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cneg, &T.c, sizeof T.c);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w12, T.mod.w12, sizeof T.mod.w12);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w13p, T.mod.w13p, sizeof T.mod.w13p);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_pf, T.mod.pf, sizeof T.mod.pf);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_invp, T.mod.invp, sizeof T.mod.invp);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_pow2, T.mod.pow2, sizeof T.mod.pow2);
@@ -223,7 +224,8 @@ int launch_quant(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
 template <typename T>
 int launch_resid(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
     if (X.kcontig) {
-        dim3 grid((a.k_pad / 2 + 255) / 256, grid_rows(a.R_pad));
+        const int gx = (a.k_pad / 8 + 255) / 256;
+        dim3 grid(gx, std::max(1, std::min(a.R_pad, 1184 / gx)));
         k_resid_kc<T><<<grid, 256, 0, st>>>(X, a);
     } else {
         dim3 grid(a.k_pad / 64, a.R_pad / 64);
@@ -414,8 +416,11 @@ struct Job {
     }
     int phase_residues(cudaStream_t st) {
         int rc;
-        PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, nullptr, mu_use(), ndev, nullptr, 1};
-        PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, nullptr, nu_use(), ndev, nullptr, 1};
+        // the row maxima bound |A'|, |B'| (fixed-position limbs); not computed
+        // when mu and nu are given
+        const unsigned long long *mxA = inject() ? nullptr : rmaxA, *mxB = inject() ? nullptr : rmaxB;
+        PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, mxA, mu_use(), ndev, nullptr, 1};
+        PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, mxB, nu_use(), ndev, nullptr, 1};
         if ((rc = launch_resid(opA, ra, st))) return rc;
         return launch_resid(opB, rb, st);
     }

@@ -43,6 +43,9 @@ __constant__ uint32_t c_magic[kNMax];
 __constant__ uint32_t c_c16[kNMax];
 __constant__ float c_cneg;                 // single_down(-0.5/(1-4 u32))
 __constant__ float c_w12[kNMax][kLimbs];   // balanced 2^(12 j) mod p_l
+// per modulus, each value duplicated into both FP32 lanes: balanced
+// 2^(13 j) mod p_l (j < 8), RN(1/p_l), -p_l
+__constant__ unsigned long long c_w13p[kNMax][kFixLimbs + 2];
 __device__ uint8_t g_pow2[kNMax][256];     // 2^E mod p_l
 __constant__ float c_pf[kNMax];            // p_l
 __constant__ float c_invp[kNMax];          // RN_f32(1/p_l)
@@ -391,15 +394,137 @@ __global__ void __launch_bounds__(256) k_planes_rc(Operand<T> X, PlaneArgs a) {
     }
 }
 
-// Residues of two neighbouring elements of row r for every modulus: one
-// 32-bit store (two BF16) per plane.
+// ------------------------------------------------------------------ residues
+// Two FP32 lanes in one 64-bit register (the paired FP32 instructions of
+// sm_100 and later).
+namespace f2 {
+__device__ __forceinline__ unsigned long long pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma(unsigned long long a, unsigned long long b,
+                                                  unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// BF16x2 of the two lanes (exact here: integers of magnitude <= 128)
+__device__ __forceinline__ uint32_t bf16x2(unsigned long long a) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+}  // namespace f2
+
+// Bit length of max_h |x'_rh| for x' = trunc(2^shift x), from the bits of
+// max_h |x_rh|: floor(log2 max) + shift + 1 (0 for a zero row).
+__device__ __forceinline__ int row_bits(unsigned long long max_bits, int shift) {
+    if (!max_bits) return 0;
+    const int b = floor_log2_bits(max_bits) + shift + 1;
+    return b < 0 ? 0 : b;
+}
+
+// Fixed-position limbs (rows whose |x'| < 2^(13 L), L <= 8): x' is cut into L
+// 13-bit limbs at bits 0, 13, 26, ..., each carrying the sign of x'.  For odd
+// p_l and balanced weights w_i = 2^(13 i) mod p_l:
+//   t = sum_i d_i w_i,  |t| <= 8 (2^13 - 1) 127 < 2^23: exact in FP32 (every
+//       product and partial sum is an integer below 2^24);
+//   q = RN(t RN(1/p) + 1.5 2^23) - 1.5 2^23 = round(t / p): the fma rounds the
+//       exact t RN(1/p), which lies strictly within |t| 2^-24 / p < 1/(2p) of
+//       t / p, to an integer, and t / p lies at least 1/(2p) from any
+//       half-integer (p odd);
+//   r = t - q p, the balanced residue of x'.
+// Two elements travel together through paired FP32 instructions.
 template <typename T>
-__device__ __forceinline__ void emit_resid2(uint32_t *dst, long pw, int N, T x0, T x1, int shift,
+__device__ __forceinline__ void fixed_limbs(T x, int shift, float *d, int L, int &r256) {
+    const Int v = trunc_scaled(x, shift);
+    const unsigned __int128 w = v.M == 0 ? (unsigned __int128)0 : ((unsigned __int128)v.M << v.E);
+#pragma unroll
+    for (int i = 0; i < kFixLimbs; i++) {
+        if (i < L) {
+            const float u = float(uint32_t(w >> (13 * i)) & 0x1FFFu);
+            d[i] = v.neg ? -u : u;
+        }
+    }
+    uint32_t b = uint32_t(w) & 255u;
+    if (v.neg) b = (256u - b) & 255u;
+    r256 = int(int8_t(b));
+}
+
+template <int L, typename T>
+__device__ __forceinline__ void emit_resid8_fixed(uint4 *dst, long pw16, int N, const T (&x)[8], int shift) {
+    unsigned long long dp[4][L];
+    uint32_t z[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        float d0[kFixLimbs], d1[kFixLimbs];
+        int r0, r1;
+        fixed_limbs(x[2 * j], shift, d0, L, r0);
+        fixed_limbs(x[2 * j + 1], shift, d1, L, r1);
+#pragma unroll
+        for (int i = 0; i < L; i++) dp[j][i] = f2::pack(d0[i], d1[i]);
+        z[j] = pack_bf16x2f(float(r0), float(r1));
+    }
+    dst[0] = make_uint4(z[0], z[1], z[2], z[3]);
+    const unsigned long long magic = f2::pack(12582912.0f, 12582912.0f);      // 1.5 2^23
+    const unsigned long long nmagic = f2::pack(-12582912.0f, -12582912.0f);
+    for (int l = 1; l < N; l++) {
+        const unsigned long long *cw = c_w13p[l];
+        unsigned long long w[L];
+#pragma unroll
+        for (int i = 1; i < L; i++) w[i] = cw[i];
+        const unsigned long long ip = cw[kFixLimbs], np = cw[kFixLimbs + 1];
+        uint32_t o[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            unsigned long long t = dp[j][0];                      // w_0 = 1
+#pragma unroll
+            for (int i = 1; i < L; i++) t = f2::fma(dp[j][i], w[i], t);
+            const unsigned long long q = f2::add(f2::fma(t, ip, magic), nmagic);
+            o[j] = f2::bf16x2(f2::fma(q, np, t));
+        }
+        dst[(long)l * pw16] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// Rows with |x'| >= 2^104: per element, limbs of the mantissa and a second
+// reduction by 2^E mod p (residue_odd).
+template <typename T>
+__device__ __forceinline__ void emit_resid8_general(uint4 *dst, long pw16, int N, const T (&x)[8], int shift,
+                                                    const uint8_t (*pow2)[256]) {
+    Limbs Lb[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) Lb[e] = limbs_of(x[e], shift);
+    dst[0] = make_uint4(pack_bf16x2f(float(Lb[0].r256), float(Lb[1].r256)),
+                        pack_bf16x2f(float(Lb[2].r256), float(Lb[3].r256)),
+                        pack_bf16x2f(float(Lb[4].r256), float(Lb[5].r256)),
+                        pack_bf16x2f(float(Lb[6].r256), float(Lb[7].r256)));
+    for (int l = 1; l < N; l++) {
+        uint32_t o[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            o[j] = pack_bf16x2f(residue_odd(Lb[2 * j], l, pow2), residue_odd(Lb[2 * j + 1], l, pow2));
+        dst[(long)l * pw16] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// Eight consecutive elements of one row; `need` = bit length of the largest
+// |x'| among the rows that the calling warp handles together (warp-uniform).
+template <typename T>
+__device__ __forceinline__ void emit_resid8(uint4 *dst, long pw16, int N, const T (&x)[8], int shift, int need,
                                             const uint8_t (*pow2)[256]) {
-    const Limbs a = limbs_of(x0, shift), b = limbs_of(x1, shift);
-    dst[0] = pack_bf16x2f(float(a.r256), float(b.r256));
-    for (int l = 1; l < N; l++)
-        dst[(long)l * pw] = pack_bf16x2f(residue_odd(a, l, pow2), residue_odd(b, l, pow2));
+    if (need <= 65) emit_resid8_fixed<5>(dst, pw16, N, x, shift);
+    else if (need <= 78) emit_resid8_fixed<6>(dst, pw16, N, x, shift);
+    else if (need <= 104) emit_resid8_fixed<8>(dst, pw16, N, x, shift);
+    else emit_resid8_general(dst, pw16, N, x, shift, pow2);
 }
 
 __device__ __forceinline__ void load_pow2(uint8_t (*s)[256], int N) {
@@ -408,37 +533,52 @@ __device__ __forceinline__ void load_pow2(uint8_t (*s)[256], int N) {
     for (int i = threadIdx.x; i < N * 64; i += blockDim.x) dst[i] = src[i];
 }
 
+__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
+
+// K-contiguous source: 8 consecutive h per thread (one 16-byte store per
+// plane), rows strided over blockIdx.y.
 template <typename T>
 __global__ void __launch_bounds__(256) k_resid_kc(Operand<T> X, PlaneArgs a) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     const int N = *a.n_dev;
     load_pow2(pow2, N);
     __syncthreads();
-    const long pw = a.plane / 2;
-    const int h0 = (blockIdx.x * 256 + threadIdx.x) * 2;
-    if (h0 >= a.k_pad) return;
+    const long pw16 = a.plane / 8;
+    const int h0 = (blockIdx.x * 256 + threadIdx.x) * 8;
+    const bool act = h0 < a.k_pad;
     for (int r = blockIdx.y; r < a.R_pad; r += gridDim.y) {
-        uint32_t *dst = reinterpret_cast<uint32_t *>(a.out + (long)r * a.k_pad + h0);
+        uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
         if (r >= X.R) {
-            for (int l = 0; l < N; l++) dst[(long)l * pw] = 0u;
+            if (act)
+                for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
             continue;
         }
+        const int shift = a.shift[r];
+        const int need = a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20;
+        if (!act) continue;
+        T x[8];
         const T *src = X.ptr + (long)r * X.ld + h0;
-        const T x0 = h0 < a.k ? src[0] : T(0);
-        const T x1 = h0 + 1 < a.k ? src[1] : T(0);
-        emit_resid2(dst, pw, N, x0, x1, a.shift[r], pow2);
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[e] = h0 + e < a.k ? src[e] : T(0);
+        emit_resid8(dst, pw16, N, x, shift, need, pow2);
     }
 }
 
 // R-contiguous source: a 64 (r) x 64 (h) tile transposed through shared
-// memory; each warp then writes 128 contiguous bytes of one row per plane.
+// memory.  Thread (row rr, group tc) then takes h = 8 tc .. 8 tc + 7 of row rr;
+// the 16-byte chunks of each group are stored XOR-swizzled by (tc >> 1) & 3 so
+// that those reads hit distinct banks.
+__device__ __forceinline__ int resid_swz(int hh) {
+    return (hh & ~7) | (((((hh >> 1) & 3) ^ ((hh >> 4) & 3))) << 1) | (hh & 1);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_resid_rc(Operand<T> X, PlaneArgs a) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
-    __shared__ T tile[64][65];               // [r][h]
+    __shared__ T tile[64][65];               // [r][swizzled h]
     const int N = *a.n_dev;
     load_pow2(pow2, N);
-    const long pw = a.plane / 2;
+    const long pw16 = a.plane / 8;
     const int h_base = blockIdx.x * 64, r_base = blockIdx.y * 64;
     {
         const int rr = threadIdx.x & 63;
@@ -447,23 +587,29 @@ __global__ void __launch_bounds__(256) k_resid_rc(Operand<T> X, PlaneArgs a) {
         for (int i = 0; i < 16; i++) {
             const int hh = (threadIdx.x >> 6) + 4 * i;
             const int h = h_base + hh;
-            tile[rr][hh] = (r < X.R && h < a.k) ? X.ptr[(long)h * X.ld + r] : T(0);
+            tile[rr][resid_swz(hh)] = (r < X.R && h < a.k) ? X.ptr[(long)h * X.ld + r] : T(0);
         }
     }
     __syncthreads();
-    const int pi = threadIdx.x & 31;
-    const int h0 = h_base + 2 * pi;
+    const int tc = threadIdx.x & 7;
+    const int h0 = h_base + 8 * tc;
 #pragma unroll 1
-    for (int i = 0; i < 8; i++) {
-        const int rr = (threadIdx.x >> 5) + 8 * i;
+    for (int i = 0; i < 2; i++) {
+        const int rr = (threadIdx.x >> 3) + 32 * i;
         const int r = r_base + rr;
-        if (r >= a.R_pad || h0 >= a.k_pad) continue;
-        uint32_t *dst = reinterpret_cast<uint32_t *>(a.out + (long)r * a.k_pad + h0);
-        if (r >= X.R) {
-            for (int l = 0; l < N; l++) dst[(long)l * pw] = 0u;
+        const bool live = r < X.R;
+        const int shift = live ? a.shift[r] : 0;
+        const int need = warp_max(live ? (a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20) : 0);
+        if (r >= a.R_pad) continue;
+        uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
+        if (!live) {
+            for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
             continue;
         }
-        emit_resid2(dst, pw, N, tile[rr][2 * pi], tile[rr][2 * pi + 1], a.shift[r], pow2);
+        T x[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[e] = tile[rr][resid_swz(8 * tc + e)];
+        emit_resid8(dst, pw16, N, x, shift, need, pow2);
     }
 }
 

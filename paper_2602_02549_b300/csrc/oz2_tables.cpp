@@ -241,6 +241,19 @@ void build(Tables &T) {
         }
         T.mod.pf[l] = float(p);
         T.mod.invp[l] = 1.0f / float(p);
+        auto dup = [](float f) {
+            uint32_t b;
+            std::memcpy(&b, &f, 4);
+            return (uint64_t(b) << 32) | b;
+        };
+        v = 1 % p;
+        for (int j = 0; j < kFixLimbs; j++) {
+            const int bal = 2 * v > p ? int(v) - int(p) : int(v);
+            T.mod.w13p[l][j] = dup(float(bal));
+            v = uint32_t((uint64_t(v) << 13) % p);
+        }
+        T.mod.w13p[l][kFixLimbs] = dup(T.mod.invp[l]);
+        T.mod.w13p[l][kFixLimbs + 1] = dup(-float(p));
     }
     const long double u64 = 0x1p-53L, u32 = 0x1p-24L;
     T.c = f32_down(-0.5L / (1.0L - 4.0L * u32));

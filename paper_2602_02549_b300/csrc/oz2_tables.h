@@ -7,6 +7,7 @@ namespace oz2 {
 
 constexpr int kNMax = 49;
 constexpr int kLimbs = 5;                               // 12-bit limbs of a 53-bit mantissa
+constexpr int kFixLimbs = 8;                            // 13-bit limbs of an integer below 2^104
 constexpr int kPackedLen = (kNMax * (kNMax + 1)) / 2;  // sum_{N=1}^{49} N entries
 
 // Per-modulus reduction constants (index l = 0..48).
@@ -18,6 +19,8 @@ struct ModTable {
     uint32_t c48[kNMax];     // 2^48 mod p
     uint8_t pow2[kNMax][256];// 2^E mod p, E = 0..255
     float w12[kNMax][kLimbs];     // balanced 2^(12 j) mod p, in [-(p-1)/2, (p-1)/2] (odd p)
+    // {w, w} pairs of FP32 bits: balanced 2^(13 j) mod p (j < kFixLimbs), RN(1/p), -p
+    unsigned long long w13p[kNMax][kFixLimbs + 2];
     float pf[kNMax];         // p as float
     float invp[kNMax];       // RN_f32(1/p)
 };

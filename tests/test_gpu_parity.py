@@ -74,7 +74,10 @@ def test_tall_problems(oracle, shape, N):
     check_against_oracle(oracle, A, Bm, g, bound=(m * n * k < 2e8))
 
 
-@pytest.mark.parametrize("N", [3, 5, 6, 8, 20, 33, 49])
+# the bit length of |A'| grows with N: N <= 14 stays below 2^65 here, N = 20
+# near 2^75, N = 24..28 between 2^78 and 2^104, N >= 33 above (every residue
+# path of the kernels)
+@pytest.mark.parametrize("N", [3, 5, 6, 8, 20, 24, 26, 28, 33, 49])
 def test_dgemm_parity_moduli(oracle, N):
     A, Bm = paper_pair(150, 170, 700, 1.0, seed=N)
     g = run_gpu(A, Bm, N)
