@@ -146,8 +146,8 @@ Dims make_dims(int m, int n, int k, int nmax) {
 
 struct Layout {
     // the block up to zero_end is cleared at the start of every call
-    size_t hmaxA, hmaxB, cmax_row, cmax_col, red, ssA, ssB, zero_end;
-    size_t rmaxA, rmaxB, rsumA, rsumB, mu, nu, ndev, resA, resB, W, total;
+    size_t hmaxA, hmaxB, cmax_row, cmax_col, red, ssA, ssB, rmaxA, rmaxB, l1A, l1B, zero_end;
+    size_t mu, nu, ndev, resA, resB, W, total;
 };
 
 Layout make_layout(const Dims &d) {
@@ -161,11 +161,11 @@ Layout make_layout(const Dims &d) {
     L.red = take(sizeof(unsigned long long) * 8);
     L.ssA = take(sizeof(int) * size_t(d.m_pad));
     L.ssB = take(sizeof(int) * size_t(d.n_pad));
-    L.zero_end = o;
     L.rmaxA = take(sizeof(unsigned long long) * size_t(d.m_pad));
     L.rmaxB = take(sizeof(unsigned long long) * size_t(d.n_pad));
-    L.rsumA = take(sizeof(double) * size_t(d.m_pad));
-    L.rsumB = take(sizeof(double) * size_t(d.n_pad));
+    L.l1A = take(2 * sizeof(unsigned long long) * size_t(d.m_pad));
+    L.l1B = take(2 * sizeof(unsigned long long) * size_t(d.n_pad));
+    L.zero_end = o;
     L.mu = take(sizeof(int32_t) * size_t(d.m_pad));
     L.nu = take(sizeof(int32_t) * size_t(d.n_pad));
     L.ndev = take(sizeof(int) * 4);
@@ -196,16 +196,21 @@ int encode_bf16_2d(CUtensorMap *tm, const void *base, uint64_t rows, uint64_t co
 int grid_rows(int rows) { return std::max(1, std::min(rows, 65535)); }
 
 // ------------------------------------------------------------------ launches
+// max |x| per logical row (row_max) and per k index (h_max) of one operand
 template <typename T>
-int launch_stats(const Operand<T> &X, int k, unsigned long long *row_max, double *row_sum,
-                 unsigned long long *h_max, cudaStream_t st) {
-    if (X.kcontig) {
-        const int blocks = (X.R + kStatsRows - 1) / kStatsRows;
-        k_stats_kc<T><<<blocks, 256, 0, st>>>(X, k, row_max, row_sum, h_max);
-    } else {
-        const int blocks = (X.R + 31) / 32;
-        k_stats_rc<T><<<blocks, 256, 0, st>>>(X, k, row_max, row_sum, h_max);
-    }
+int launch_stats(const Operand<T> &X, int k, unsigned long long *row_max, unsigned long long *h_max,
+                 cudaStream_t st) {
+    // lines x contiguous positions: A (K-contiguous) R x k, B (R-contiguous) k x R
+    const int S = X.kcontig ? X.R : k, C = X.kcontig ? k : X.R;
+    unsigned long long *smax = X.kcontig ? row_max : h_max, *cmax = X.kcontig ? h_max : row_max;
+    if (S == 0 || C == 0) return OZ2_OK;
+    const int gx = (C + 2047) / 2048;
+    const int gy = std::max(1, std::min(S, 2368 / gx));
+    const int spb = (S + gy - 1) / gy;
+    const bool vec = (reinterpret_cast<uintptr_t>(X.ptr) % 16 == 0) && ((X.ld * long(sizeof(T))) % 16 == 0);
+    dim3 grid(gx, (S + spb - 1) / spb);
+    if (vec) k_absmax<T, true><<<grid, 256, 0, st>>>(X.ptr, X.ld, S, C, spb, smax, cmax);
+    else k_absmax<T, false><<<grid, 256, 0, st>>>(X.ptr, X.ld, S, C, spb, smax, cmax);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -289,9 +294,8 @@ struct Job {
     Dims d{};
     Layout L{};
     uint8_t *ws = nullptr;
-    unsigned long long *hmaxA, *hmaxB, *red, *rmaxA, *rmaxB;
+    unsigned long long *hmaxA, *hmaxB, *red, *rmaxA, *rmaxB, *l1A, *l1B;
     int *cmax_row, *cmax_col, *ssA, *ssB, *ndev;
-    double *rsumA, *rsumB;
     int32_t *mu, *nu;
     __nv_bfloat16 *resA, *resB;
     int8_t *W;
@@ -323,8 +327,8 @@ struct Job {
         ssB = reinterpret_cast<int *>(at(L.ssB));
         rmaxA = reinterpret_cast<unsigned long long *>(at(L.rmaxA));
         rmaxB = reinterpret_cast<unsigned long long *>(at(L.rmaxB));
-        rsumA = reinterpret_cast<double *>(at(L.rsumA));
-        rsumB = reinterpret_cast<double *>(at(L.rsumB));
+        l1A = reinterpret_cast<unsigned long long *>(at(L.l1A));
+        l1B = reinterpret_cast<unsigned long long *>(at(L.l1B));
         mu = reinterpret_cast<int32_t *>(at(L.mu));
         nu = reinterpret_cast<int32_t *>(at(L.nu));
         ndev = reinterpret_cast<int *>(at(L.ndev));
@@ -377,12 +381,12 @@ struct Job {
         int rc;
         if ((rc = cuda_fail(cudaMemsetAsync(ws, 0, L.zero_end, st)))) return rc;
         if (inject()) return OZ2_OK;
-        if ((rc = launch_stats(opA, k, rmaxA, rsumA, hmaxA, st))) return rc;
-        if ((rc = launch_stats(opB, k, rmaxB, rsumB, hmaxB, st))) return rc;
+        if ((rc = launch_stats(opA, k, rmaxA, hmaxA, st))) return rc;
+        if ((rc = launch_stats(opB, k, rmaxB, hmaxB, st))) return rc;
         if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
         const bool f = fast();
-        PlaneArgs qa{resA, planeA, d.m_pad, k, d.k_pad, rmaxA, nullptr, nullptr, f ? ssA : nullptr, !f};
-        PlaneArgs qb{resB, planeB, d.n_pad, k, d.k_pad, rmaxB, nullptr, nullptr, f ? ssB : nullptr, !f};
+        PlaneArgs qa{resA, planeA, d.m_pad, k, d.k_pad, rmaxA, nullptr, nullptr, f ? ssA : nullptr, !f, l1A};
+        PlaneArgs qb{resB, planeB, d.n_pad, k, d.k_pad, rmaxB, nullptr, nullptr, f ? ssB : nullptr, !f, l1B};
         if ((rc = launch_quant(opA, qa, st))) return rc;
         if ((rc = launch_quant(opB, qb, st))) return rc;
         if (f) {
@@ -401,7 +405,7 @@ struct Job {
         int rc;
         if (!inject()) {
             if (nmoduli == 0) {
-                BoundArgs ba{m, n, k, rmaxA, rmaxB, hmaxA, hmaxB, rsumA, rsumB, cmax_row, cmax_col, red};
+                BoundArgs ba{m, n, k, rmaxA, rmaxB, hmaxA, hmaxB, l1A, l1B, cmax_row, cmax_col, red};
                 k_bound_reduce<<<148, 256, 0, st>>>(ba);
                 if ((rc = cuda_fail(cudaGetLastError()))) return rc;
             }
@@ -419,8 +423,8 @@ struct Job {
         // the row maxima bound |A'|, |B'| (fixed-position limbs); not computed
         // when mu and nu are given
         const unsigned long long *mxA = inject() ? nullptr : rmaxA, *mxB = inject() ? nullptr : rmaxB;
-        PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, mxA, mu_use(), ndev, nullptr, 1};
-        PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, mxB, nu_use(), ndev, nullptr, 1};
+        PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, mxA, mu_use(), ndev, nullptr, 1, nullptr};
+        PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, mxB, nu_use(), ndev, nullptr, 1, nullptr};
         if ((rc = launch_resid(opA, ra, st))) return rc;
         return launch_resid(opB, rb, st);
     }

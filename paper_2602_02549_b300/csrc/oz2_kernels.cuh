@@ -3,10 +3,11 @@
 // Included once, by oz2_api.cu, so that the __constant__ tables below live in a
 // single translation unit with every kernel that reads them.
 //
-//   k_stats_kc / k_stats_rc   Algorithm 2 inputs: max |x| per row of A (per
-//                             column of B) -> mu', nu'; |A| v, v^T |B| and
-//                             per-k maxima for the N rule (one HBM read)
-//   k_planes_kc / k_planes_rc Abar = ceil(2^mu' |A|), Bbar likewise, as BF16
+//   k_absmax                  Algorithm 2 inputs: max |x| per row of A (per
+//                             column of B) -> mu', nu', and the per-k maxima
+//                             of the N rule (one HBM read)
+//   k_planes_kc / k_planes_rc Abar = ceil(2^mu' |A|), Bbar likewise, as BF16;
+//                             also |A| v and v^T |B| for the N rule
 //   k_gemm<EPI_MAX>           Cbar = Abar Bbar on tcgen05, keeping only the row
 //                             and column maxima of Cbar
 //   k_bound_reduce, k_choose_n, k_mu_nu
@@ -196,95 +197,70 @@ struct Operand {
 };
 
 // ============================================================= stats
-// Per logical row r: bits of max |x| (row_max) and the FP64 sum of |x|
-// (row_sum, a fixed summation order); per h: atomicMax of |x| bits (h_max).
-constexpr int kStatsRows = 16;
-
+// Maxima of |x| (as the bits of double(|x|), which order like the values)
+// over a matrix stored as S lines of C contiguous elements, line s at
+// ptr + s ld: per line into smax[s] and per position into cmax[c], merged with
+// atomicMax (so the result does not depend on the order).  A, K-contiguous:
+// lines are rows i, positions h.  B, R-contiguous: lines are h, positions are
+// columns j.  Each thread takes 8 consecutive positions of s_per_block lines.
 template <typename T>
-__global__ void __launch_bounds__(256) k_stats_kc(Operand<T> X, int k, unsigned long long *row_max,
-                                                  double *row_sum, unsigned long long *h_max) {
-    const int r0 = blockIdx.x * kStatsRows;
-    double sum[kStatsRows];
-    unsigned long long mx[kStatsRows];
-#pragma unroll
-    for (int i = 0; i < kStatsRows; i++) { sum[i] = 0.0; mx[i] = 0ull; }
-    for (int h = threadIdx.x; h < k; h += 256) {
-        unsigned long long hm = 0;
-#pragma unroll
-        for (int i = 0; i < kStatsRows; i++) {
-            if (r0 + i < X.R) {
-                double v = absd(X.ptr[(long)(r0 + i) * X.ld + h]);
-                unsigned long long b = (unsigned long long)__double_as_longlong(v);
-                sum[i] += v;
-                mx[i] = b > mx[i] ? b : mx[i];
-                hm = b > hm ? b : hm;
-            }
-        }
-        if (hm) atomicMax(h_max + h, hm);
-    }
-    __shared__ double ssum[8][kStatsRows];
-    __shared__ unsigned long long smax[8][kStatsRows];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < kStatsRows; i++) {
-        double s = sum[i];
-        unsigned long long m = mx[i];
-        for (int o = 16; o; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            unsigned long long mo = __shfl_xor_sync(0xffffffffu, m, o);
-            m = mo > m ? mo : m;
-        }
-        if (lane == 0) { ssum[w][i] = s; smax[w][i] = m; }
-    }
-    __syncthreads();
-    if (threadIdx.x < kStatsRows && r0 + threadIdx.x < X.R) {
-        double s = 0.0;
-        unsigned long long m = 0;
-        for (int ww = 0; ww < 8; ww++) {
-            s += ssum[ww][threadIdx.x];
-            m = smax[ww][threadIdx.x] > m ? smax[ww][threadIdx.x] : m;
-        }
-        row_sum[r0 + threadIdx.x] = s;
-        row_max[r0 + threadIdx.x] = m;
-    }
+__device__ __forceinline__ unsigned long long abs_bits(T x) {
+    return (unsigned long long)__double_as_longlong(fabs(double(x)));
+}
+template <>
+__device__ __forceinline__ unsigned long long abs_bits<double>(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// R-contiguous storage: 32 logical rows per block, 8 phases over h.
-template <typename T>
-__global__ void __launch_bounds__(256) k_stats_rc(Operand<T> X, int k, unsigned long long *row_max,
-                                                  double *row_sum, unsigned long long *h_max) {
-    const int lane = threadIdx.x & 31, ph = threadIdx.x >> 5;
-    const int r = blockIdx.x * 32 + lane;
-    const bool live = r < X.R;
-    double s = 0.0;
-    unsigned long long m = 0;
-    for (int h = ph; h < k; h += 8) {
-        double v = live ? absd(X.ptr[(long)h * X.ld + r]) : 0.0;
-        unsigned long long b = (unsigned long long)__double_as_longlong(v);
-        s += v;
-        m = b > m ? b : m;
-        unsigned long long hm = b;
-        for (int o = 16; o; o >>= 1) {
-            unsigned long long t = __shfl_xor_sync(0xffffffffu, hm, o);
-            hm = t > hm ? t : hm;
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    const unsigned hi = __reduce_max_sync(0xffffffffu, unsigned(v >> 32));
+    const unsigned lo = __reduce_max_sync(0xffffffffu, unsigned(v >> 32) == hi ? unsigned(v) : 0u);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(256) k_absmax(const T *ptr, long ld, int S, int C, int s_per_block,
+                                               unsigned long long *smax, unsigned long long *cmax) {
+    const int c0 = (blockIdx.x * 256 + threadIdx.x) * 8;
+    const int s_begin = blockIdx.y * s_per_block;
+    const int s_end = min(S, s_begin + s_per_block);
+    const bool full = c0 + 8 <= C;
+    unsigned long long cm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int s = s_begin; s < s_end; s++) {
+        const T *src = ptr + (long)s * ld + c0;
+        T x[8];
+        if (VEC && full) {
+            if constexpr (sizeof(T) == 8) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const double2 v = reinterpret_cast<const double2 *>(src)[q];
+                    x[2 * q] = T(v.x);
+                    x[2 * q + 1] = T(v.y);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    const float4 v = reinterpret_cast<const float4 *>(src)[q];
+                    x[4 * q] = T(v.x); x[4 * q + 1] = T(v.y); x[4 * q + 2] = T(v.z); x[4 * q + 3] = T(v.w);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; e++) x[e] = c0 + e < C ? src[e] : T(0);
         }
-        if (lane == 0 && hm) atomicMax(h_max + h, hm);
-    }
-    __shared__ double ssum[8][32];
-    __shared__ unsigned long long smax[8][32];
-    ssum[ph][lane] = s;
-    smax[ph][lane] = m;
-    __syncthreads();
-    if (ph == 0 && live) {
-        double t = 0.0;
-        unsigned long long mm = 0;
-        for (int q = 0; q < 8; q++) {
-            t += ssum[q][lane];
-            mm = smax[q][lane] > mm ? smax[q][lane] : mm;
+        unsigned long long lm = 0;
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const unsigned long long b = abs_bits(x[e]);
+            cm[e] = b > cm[e] ? b : cm[e];
+            lm = b > lm ? b : lm;
         }
-        row_sum[r] = t;
-        row_max[r] = mm;
+        lm = warp_max_u64(lm);
+        if ((threadIdx.x & 31) == 0 && lm) atomicMax(smax + s, lm);
     }
+#pragma unroll
+    for (int e = 0; e < 8; e++)
+        if (cm[e] && c0 + e < C) atomicMax(cmax + c0 + e, cm[e]);
 }
 
 // ============================================================= planes
@@ -300,6 +276,8 @@ struct PlaneArgs {
     const int *n_dev;                     // residues: number of planes
     int *sumsq;                           // quantisation, fast mode: sum_h xbar^2 per row (atomicAdd)
     int write;                            // quantisation: store the BF16 plane (accurate mode)
+    unsigned long long *l1;               // quantisation: sum_h |x| 2^(mu'+57) per row, two 32-bit
+                                          // halves (l1[2r] high, l1[2r+1] low; atomicAdd)
 };
 
 __device__ __forceinline__ int quant_shift(const unsigned long long *row_max, int r) {
@@ -307,16 +285,51 @@ __device__ __forceinline__ int quant_shift(const unsigned long long *row_max, in
     return b ? 5 - floor_log2_bits(b) : 0;     // zero row: mu' = 0
 }
 
-// Stores 8 values of Abar (accurate mode) and returns their sum of squares
-// (fast mode's Cauchy-Schwarz majorant; exact: xbar <= 64, k <= 2^17).
+// Partial sums of one row: sum of xbar^2 (fast mode's Cauchy-Schwarz
+// majorant; exact: xbar <= 64, k <= 2^17) and sum of floor(|x| 2^(shift+57))
+// in two 32-bit halves: each term is an integer below 2^63 because
+// |x| 2^shift < 64, so the halves cannot overflow for k <= 2^17 and the sum
+// is exact (independent of the order); it is within k 2^-62 (relative) of
+// sum |x| 2^shift, the row's 1-norm for the N rule.
+struct RowAcc {
+    int ss;
+    unsigned long long hi, lo;
+};
+
 template <typename T>
-__device__ __forceinline__ int emit_quant8(const PlaneArgs &a, const T (&x)[8], int shift, int r, int h0) {
+__device__ __forceinline__ void add_scaled_abs(RowAcc &acc, T x, int shift) {
+    const Split sp = split_bits(x);
+    const int sh = sp.e + shift + 57;
+    const uint64_t v = sh >= 0 ? (sh > 10 ? 0ull : sp.M << sh) : (-sh >= 64 ? 0ull : sp.M >> -sh);
+    acc.hi += v >> 32;
+    acc.lo += v & 0xFFFFFFFFull;
+}
+
+// The row sums of a warp's lanes `mask`-reduced (xor distances < width) and
+// added into the row's counters by the lane with (lane & (width-1)) == 0.
+__device__ __forceinline__ void flush_row(const PlaneArgs &a, RowAcc acc, int r, int width, bool live) {
+    for (int o = 1; o < width; o <<= 1) {
+        acc.ss += __shfl_xor_sync(0xffffffffu, acc.ss, o);
+        acc.hi += __shfl_xor_sync(0xffffffffu, acc.hi, o);
+        acc.lo += __shfl_xor_sync(0xffffffffu, acc.lo, o);
+    }
+    if (live && (threadIdx.x & (width - 1)) == 0) {
+        if (a.sumsq && acc.ss) atomicAdd(a.sumsq + r, acc.ss);
+        if (acc.hi) atomicAdd(a.l1 + 2 * r, acc.hi);
+        if (acc.lo) atomicAdd(a.l1 + 2 * r + 1, acc.lo);
+    }
+}
+
+// Stores 8 values of Abar (accurate mode) and adds to the row sums.
+template <typename T>
+__device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8], int shift, int r, int h0,
+                                            RowAcc &acc) {
     uint32_t q[8];
-    int ss = 0;
 #pragma unroll
     for (int e = 0; e < 8; e++) {
         q[e] = ceil_scaled_abs(x[e], shift);
-        ss += int(q[e] * q[e]);
+        acc.ss += int(q[e] * q[e]);
+        add_scaled_abs(acc, x[e], shift);
     }
     if (a.write) {
         uint4 v;
@@ -326,7 +339,6 @@ __device__ __forceinline__ int emit_quant8(const PlaneArgs &a, const T (&x)[8], 
         v.w = pack_bf16x2(q[6], q[7]);
         *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = v;
     }
-    return ss;
 }
 
 // K-contiguous source: one row per blockIdx.y (grid-stride), 8 h per thread.
@@ -337,7 +349,7 @@ __global__ void __launch_bounds__(256) k_planes_kc(Operand<T> X, PlaneArgs a) {
     const int h0 = (blockIdx.x * 256 + threadIdx.x) * 8;
     const bool act = h0 < a.k_pad;
     for (int r = blockIdx.y; r < a.R_pad; r += gridDim.y) {
-        int ss = 0;
+        RowAcc acc{0, 0, 0};
         if (act) {
             if (r >= X.R) {
                 if (a.write) *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
@@ -347,13 +359,10 @@ __global__ void __launch_bounds__(256) k_planes_kc(Operand<T> X, PlaneArgs a) {
                 const T *src = X.ptr + (long)r * X.ld + h0;
 #pragma unroll
                 for (int e = 0; e < 8; e++) x[e] = (h0 + e < a.k) ? src[e] : T(0);
-                ss = emit_quant8(a, x, shift, r, h0);
+                emit_quant8(a, x, shift, r, h0, acc);
             }
         }
-        if (a.sumsq) {
-            for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-            if ((threadIdx.x & 31) == 0 && ss) atomicAdd(a.sumsq + r, ss);
-        }
+        flush_row(a, acc, r, 32, r < X.R);
     }
 }
 
@@ -377,7 +386,7 @@ __global__ void __launch_bounds__(256) k_planes_rc(Operand<T> X, PlaneArgs a) {
     const int r = r_base + rr;
     const bool live = r < X.R;
     const int shift = live ? quant_shift(a.row_max, r) : 0;
-    int ss = 0;
+    RowAcc acc{0, 0, 0};
 #pragma unroll
     for (int g = 0; g < 2; g++) {
         const int hh0 = hq * 16 + g * 8;
@@ -385,13 +394,9 @@ __global__ void __launch_bounds__(256) k_planes_rc(Operand<T> X, PlaneArgs a) {
         T x[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) x[e] = live ? tile[hh0 + e][rr] : T(0);
-        ss += emit_quant8(a, x, shift, r, h0);
+        emit_quant8(a, x, shift, r, h0, acc);
     }
-    if (a.sumsq) {   // the 4 threads of row rr are adjacent lanes
-        ss += __shfl_xor_sync(0xffffffffu, ss, 1);
-        ss += __shfl_xor_sync(0xffffffffu, ss, 2);
-        if (hq == 0 && live && ss) atomicAdd(a.sumsq + r, ss);
-    }
+    flush_row(a, acc, r, 4, live);   // the 4 threads of row rr are adjacent lanes
 }
 
 // ------------------------------------------------------------------ residues
@@ -903,7 +908,7 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
 struct BoundArgs {
     int m, n, k;
     const unsigned long long *rmaxA, *rmaxB, *hmaxA, *hmaxB;
-    const double *rsumA, *rsumB;
+    const unsigned long long *l1A, *l1B;     // fixed-point row sums (PlaneArgs::l1)
     const int *cmax_row, *cmax_col;
     unsigned long long *red;
 };
@@ -922,17 +927,23 @@ __device__ __forceinline__ void block_max_to(unsigned long long v, unsigned long
     if ((threadIdx.x & 31) == 0 && v) atomicMax(dst, v);
 }
 
+// sum_h |x_rh| from the fixed-point counters of the quantisation kernels
+__device__ __forceinline__ double row_l1(const unsigned long long *l1, const unsigned long long *rmax, int r) {
+    const double v = double(l1[2 * r]) * 4294967296.0 + double(l1[2 * r + 1]);
+    return ldexp(v, -(quant_shift(rmax, r) + 57));
+}
+
 __global__ void __launch_bounds__(256) k_bound_reduce(BoundArgs a) {
     unsigned long long mR = 0, mK = 0, m2a = 0, m2b = 0, mL = 0;
     const int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.m; i += stride) {
-        unsigned long long v = (unsigned long long)__double_as_longlong(a.rsumA[i]);
+        unsigned long long v = (unsigned long long)__double_as_longlong(row_l1(a.l1A, a.rmaxA, i));
         mR = v > mR ? v : mR;
         v = (unsigned long long)__double_as_longlong(pow2_prime(a.rmaxA[i], a.cmax_row[i]));
         m2a = v > m2a ? v : m2a;
     }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += stride) {
-        unsigned long long v = (unsigned long long)__double_as_longlong(a.rsumB[j]);
+        unsigned long long v = (unsigned long long)__double_as_longlong(row_l1(a.l1B, a.rmaxB, j));
         mK = v > mK ? v : mK;
         v = (unsigned long long)__double_as_longlong(pow2_prime(a.rmaxB[j], a.cmax_col[j]));
         m2b = v > m2b ? v : m2b;
