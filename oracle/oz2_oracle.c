@@ -277,25 +277,37 @@ static double big_to_double(bigfix *x)
 /* value does not depend on the order of the terms.  For b = 64, C'(1) is     */
 /* exact (Lemma 2), so only C'(2) is affected; for b = 32, s_l2 = 0 and       */
 /* C'(1) is the rounded sum.                                                  */
+/* fma_chain != 0 selects the other reading instead: both sums as fma chains  */
+/* in ascending l from +0 (an FP64 evaluation in one fixed order).            */
 /* For b = 32 the rounding C'' = single(C'') is taken after the inverse        */
 /* scaling (oz2o_unscale), where it gives the same value whenever single(C'')  */
 /* is finite and C is normal, and does not overflow when P > 2^128.            */
 /* W holds N planes of `count` entries.                                        */
 void oz2o_crt(long count, int N, const int8_t *W, const double *s1, const double *s2,
-              double P1, double P2, double Pinv, int b,
+              double P1, double P2, double Pinv, int b, int fma_chain,
               double *C1out, double *C2out, double *Qout, double *Cpp)
 {
 #pragma omp parallel for schedule(static)
     for (long e = 0; e < count; e++) {
-        bigfix a1, a2;
-        memset(&a1, 0, sizeof a1);
-        memset(&a2, 0, sizeof a2);
-        for (int l = 0; l < N; l++) {
-            double w = (double)W[(long)l * count + e];
-            big_add_product(&a1, s1[l], w);
-            big_add_product(&a2, s2[l], w);
+        double c1 = 0.0, c2 = 0.0;
+        if (fma_chain) {
+            for (int l = 0; l < N; l++) {
+                double w = (double)W[(long)l * count + e];
+                c1 = fma(s1[l], w, c1);
+                c2 = fma(s2[l], w, c2);
+            }
+        } else {
+            bigfix a1, a2;
+            memset(&a1, 0, sizeof a1);
+            memset(&a2, 0, sizeof a2);
+            for (int l = 0; l < N; l++) {
+                double w = (double)W[(long)l * count + e];
+                big_add_product(&a1, s1[l], w);
+                big_add_product(&a2, s2[l], w);
+            }
+            c1 = big_to_double(&a1);
+            c2 = big_to_double(&a2);
         }
-        double c1 = big_to_double(&a1), c2 = big_to_double(&a2);
         double q = nearbyint(Pinv * c1);        /* round to nearest (even) */
         double c = fma(-q, P2, fma(-q, P1, c1) + c2);
         (void)b;

@@ -51,7 +51,7 @@ def lib():
         _lib.oz2o_trunc_scaled.argtypes = [i32, i32, P, i64, i64, P, P]
         _lib.oz2o_residues.argtypes = [i64, P, i32, P]
         _lib.oz2o_mod_i64.argtypes = [i64, P, i32, P]
-        _lib.oz2o_crt.argtypes = [i64, i32, P, P, P, d, d, d, i32, P, P, P, P]
+        _lib.oz2o_crt.argtypes = [i64, i32, P, P, P, d, d, d, i32, i32, P, P, P, P]
         _lib.oz2o_unscale.argtypes = [i32, i32, P, P, P, i32, P]
         _lib.oz2o_log2f.argtypes = [i64, P, P]
         _lib.oz2o_exact_residual.argtypes = [i32, i32, i32, P, i64, i64, P, i64, i64, P, P]
@@ -229,7 +229,7 @@ def mod_i64(X: np.ndarray, p: int) -> np.ndarray:
 # Algorithm 3: CRT
 # --------------------------------------------------------------------------- #
 def crt(Ap: np.ndarray, Bp: np.ndarray, N: int, b: int = 64, keep_residues: bool = False,
-        consts=None) -> dict:
+        consts=None, fma_chain: bool = False) -> dict:
     C = consts if consts is not None else constants(N, b)
     m, k = Ap.shape
     n = Bp.shape[1]
@@ -242,13 +242,16 @@ def crt(Ap: np.ndarray, Bp: np.ndarray, N: int, b: int = 64, keep_residues: bool
         if keep_residues:
             Ares[l], Bres[l] = Al, Bl
         W[l] = mod_i64(gemm_i8(Al, Bl), pl)   # W_l = mod(A'_l B'_l, p_l)
-    out = crt_from_W(W, N, b, consts=C)
+    out = crt_from_W(W, N, b, consts=C, fma_chain=fma_chain)
     out.update(W=W, Ares=Ares, Bres=Bres)
     return out
 
 
-def crt_from_W(W: np.ndarray, N: int, b: int = 64, consts=None) -> dict:
-    """Algorithm 3 from W_l on; `consts` replaces the tables (tests plant mistakes with it)."""
+def crt_from_W(W: np.ndarray, N: int, b: int = 64, consts=None, fma_chain: bool = False) -> dict:
+    """Algorithm 3 from W_l on; `consts` replaces the tables (tests plant mistakes with it).
+
+    C'(1), C'(2) are the exactly rounded sums; fma_chain=True takes them as fma
+    chains in ascending l instead (the other reading of fl(sum))."""
     C = consts if consts is not None else constants(N, b)
     shape = W.shape[1:]
     count = int(np.prod(shape))
@@ -256,7 +259,7 @@ def crt_from_W(W: np.ndarray, N: int, b: int = 64, consts=None) -> dict:
     s1 = np.array(C.s1, dtype=np.float64)
     s2 = np.array(C.s2, dtype=np.float64)
     C1 = np.empty(count); C2 = np.empty(count); Q = np.empty(count); Cpp = np.empty(count)
-    lib().oz2o_crt(count, N, _p(W), _p(s1), _p(s2), C.P1, C.P2, C.Pinv, b,
+    lib().oz2o_crt(count, N, _p(W), _p(s1), _p(s2), C.P1, C.P2, C.Pinv, b, int(fma_chain),
                    _p(C1), _p(C2), _p(Q), _p(Cpp))
     return dict(C1=C1.reshape(shape), C2=C2.reshape(shape), Q=Q.reshape(shape),
                 Cpp=Cpp.reshape(shape))
@@ -275,7 +278,8 @@ def unscale(Cpp: np.ndarray, mu: np.ndarray, nu: np.ndarray, b: int = 64) -> np.
 # Algorithm 1: OS_II
 # --------------------------------------------------------------------------- #
 def os_ii(A: np.ndarray, B: np.ndarray, N: int, b: int = 64,
-          mu_in=None, nu_in=None, keep_residues: bool = False, consts=None, fast: bool = False) -> dict:
+          mu_in=None, nu_in=None, keep_residues: bool = False, consts=None, fast: bool = False,
+          fma_chain: bool = False) -> dict:
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
     if not (N_MIN <= N <= N_MAX):
@@ -283,7 +287,7 @@ def os_ii(A: np.ndarray, B: np.ndarray, N: int, b: int = 64,
     if A.shape[1] > K_MAX:
         raise ValueError("k > 2^17")
     s = scaling(A, B, N, b, mu_in, nu_in, fast=fast)
-    r = crt(s["Ap"], s["Bp"], N, b, keep_residues, consts)
+    r = crt(s["Ap"], s["Bp"], N, b, keep_residues, consts, fma_chain)
     s.update(r)
     s["C"] = unscale(r["Cpp"], s["mu"], s["nu"], b)
     s["N"], s["b"] = N, b

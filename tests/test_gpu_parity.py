@@ -228,3 +228,16 @@ def test_fast_mode_auto_N(oracle):
     assert info["ratios"][g["N"]] <= 1e-14 * (1 + 1e-9)
     assert info["ratios"][g["N"] - 1] > 1e-14 * (1 - 1e-9)
     check_against_oracle(oracle, A, Bm, g)
+
+
+@pytest.mark.parametrize("b,N", [(64, 8), (64, 17), (64, 20), (32, 9), (32, 14)])
+def test_vs_fma_chain_reading(oracle, b, N):
+    # the other reading of fl(sum) in Algorithm 3 (fma chains in ascending l):
+    # the GPU's correctly rounded sums stay within ULP_TOL of it
+    dt = np.float64 if b == 64 else np.float32
+    A, Bm = paper_pair(200, 300, 1500, 1.0, seed=N + 100, dtype=dt)
+    g = run_gpu(A, Bm, N, fp32=(b == 32))
+    A, Bm = A.astype(np.float64), Bm.astype(np.float64)
+    r = oracle.os_ii(A, Bm, N, b, mu_in=g["mu"], nu_in=g["nu"], fma_chain=True)
+    assert np.array_equal(g["W"], r["W"])
+    assert ulp_distance(g["C"], r["C"], fp32=(b == 32)).max() <= ULP_TOL

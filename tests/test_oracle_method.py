@@ -350,19 +350,26 @@ def test_crt_sums_correctly_rounded(oracle, N, b):
     assert r["C1"][2] == 0.0 and r["C2"][2] == 0.0
 
 
-def test_crt_planted_fma_chain_differs(oracle):
-    # the correctly rounded C'(2) differs from an ascending fma chain on some
-    # entries (otherwise the test above would not pin the reading)
+def test_crt_fma_chain_reading(oracle):
+    # the other reading of fl(sum): an fma chain in ascending l.  It is checked
+    # against fma steps emulated with exact rationals, and differs from the
+    # correctly rounded C'(2) on some entries (so the test above pins which
+    # reading the default takes), while C'' agrees to a few ulp.
     N, b = 17, 64
     C = constants(N, b)
     rng = np.random.default_rng(3)
     W = np.stack([rng.integers(-(p // 2), (p - 1) // 2 + 1, size=1500) for p in C.p]).astype(np.int8)
     r = oracle.crt_from_W(W, N, b)
+    rc = oracle.crt_from_W(W, N, b, fma_chain=True)
     diff = 0
     for e in range(W.shape[1]):
         acc = 0.0
         for l in range(N):
             t = Fraction(C.s2[l]) * int(W[l, e]) + Fraction(acc)     # fma: one rounding
             acc = t.numerator / t.denominator
+        assert rc["C2"][e] == acc
         diff += acc != r["C2"][e]
     assert diff > 0
+    assert np.array_equal(rc["C1"], r["C1"])                  # exact either way (Lemma 2)
+    d = np.abs(rc["Cpp"].view(np.int64) - r["Cpp"].view(np.int64))
+    assert d.max() <= 2
