@@ -300,7 +300,8 @@ template <typename T>
 __device__ __forceinline__ void add_scaled_abs(RowAcc &acc, T x, int shift) {
     const Split sp = split_bits(x);
     const int sh = sp.e + shift + 57;
-    const uint64_t v = sh >= 0 ? (sh > 10 ? 0ull : sp.M << sh) : (-sh >= 64 ? 0ull : sp.M >> -sh);
+    // M 2^(sh - 57) = |x| 2^shift < 64, so M << sh < 2^63 whenever sh >= 0
+    const uint64_t v = sh >= 0 ? (sh >= 64 ? 0ull : sp.M << sh) : (-sh >= 64 ? 0ull : sp.M >> -sh);
     acc.hi += v >> 32;
     acc.lo += v & 0xFFFFFFFFull;
 }

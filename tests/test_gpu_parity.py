@@ -188,6 +188,20 @@ def test_auto_N_rule(oracle):
         check_against_oracle(oracle, A, Bm, g)
 
 
+@pytest.mark.parametrize("phi,tau", [(1.0, 1e-7), (0.5, 1e-6), (2.0, 1e-5), (1.0, 1e-3)])
+def test_auto_N_rule_sgemm(oracle, phi, tau):
+    A, Bm = paper_pair(128, 160, 1024, phi, seed=int(phi * 7), dtype=np.float32)
+    g = run_gpu(A, Bm, 0, fp32=True, target=tau, nmax=20)
+    A, Bm = A.astype(np.float64), Bm.astype(np.float64)
+    s = oracle.scaling(A, Bm, 14, 32)
+    N, info = oracle.choose_N(A, Bm, s["alpha"], s["beta"], s["cmax_row"], s["cmax_col"], tau, 20, 32)
+    rat = info["ratios"]
+    assert rat[g["N"]] <= tau * (1 + 1e-9) or g["N"] == 20, (g["N"], N, rat)
+    if g["N"] > 2:
+        assert rat[g["N"] - 1] > tau * (1 - 1e-9), (g["N"], N, rat)
+    check_against_oracle(oracle, A, Bm, g, b=32)
+
+
 def test_deterministic():
     A, Bm = paper_pair(300, 200, 800, 1.0, seed=1)
     a = run_gpu(A, Bm, 0, target=1e-15)
