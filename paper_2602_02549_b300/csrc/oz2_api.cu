@@ -24,15 +24,10 @@ constexpr int kMaxDevices = 64;
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ------------------------------------------------------------------ per-device state
-constexpr int kPool = 8;   // streams that run the light phases of a batch concurrently
-
 struct DeviceState {
     bool tables = false;
     bool smem_attr = false;
     int sms = 0;
-    cudaStream_t pool[kPool] = {};
-    cudaEvent_t fork = nullptr, done[kPool] = {};
-    std::mutex batch_mu;
     void *ws = nullptr;
     size_t ws_bytes = 0;
 };
@@ -103,15 +98,6 @@ int ensure_device(int *dev_out) {
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_pow2, T.mod.pow2, sizeof T.mod.pow2);
         if (e != cudaSuccess) return cuda_fail(e);
         st.tables = true;
-    }
-    if (!st.pool[0]) {
-        cudaError_t e = cudaSuccess;
-        for (int i = 0; i < kPool && e == cudaSuccess; i++) {
-            e = cudaStreamCreateWithFlags(&st.pool[i], cudaStreamNonBlocking);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.done[i], cudaEventDisableTiming);
-        }
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.fork, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e);
     }
     if (!st.sms) {
         cudaError_t e = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, dev);
@@ -193,51 +179,8 @@ int encode_bf16_2d(CUtensorMap *tm, const void *base, uint64_t rows, uint64_t co
     return OZ2_OK;
 }
 
-int grid_rows(int rows) { return std::max(1, std::min(rows, 65535)); }
-
-// ------------------------------------------------------------------ launches
-// max |x| per logical row (row_max) and per k index (h_max) of one operand
-template <typename T>
-int launch_stats(const Operand<T> &X, int k, unsigned long long *row_max, unsigned long long *h_max,
-                 cudaStream_t st) {
-    // lines x contiguous positions: A (K-contiguous) R x k, B (R-contiguous) k x R
-    const int S = X.kcontig ? X.R : k, C = X.kcontig ? k : X.R;
-    unsigned long long *smax = X.kcontig ? row_max : h_max, *cmax = X.kcontig ? h_max : row_max;
-    if (S == 0 || C == 0) return OZ2_OK;
-    const int gx = (C + 2047) / 2048;
-    const int gy = std::max(1, std::min(S, 2368 / gx));
-    const int spb = (S + gy - 1) / gy;
-    const bool vec = (reinterpret_cast<uintptr_t>(X.ptr) % 16 == 0) && ((X.ld * long(sizeof(T))) % 16 == 0);
-    dim3 grid(gx, (S + spb - 1) / spb);
-    if (vec) k_absmax<T, true><<<grid, 256, 0, st>>>(X.ptr, X.ld, S, C, spb, smax, cmax);
-    else k_absmax<T, false><<<grid, 256, 0, st>>>(X.ptr, X.ld, S, C, spb, smax, cmax);
-    return cuda_fail(cudaGetLastError());
-}
-
-template <typename T>
-int launch_quant(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
-    if (X.kcontig) {
-        dim3 grid((a.k_pad / 8 + 255) / 256, grid_rows(a.R_pad));
-        k_planes_kc<T><<<grid, 256, 0, st>>>(X, a);
-    } else {
-        dim3 grid(a.k_pad / 64, a.R_pad / 64);
-        k_planes_rc<T><<<grid, 256, 0, st>>>(X, a);
-    }
-    return cuda_fail(cudaGetLastError());
-}
-
-template <typename T>
-int launch_resid(const Operand<T> &X, const PlaneArgs &a, cudaStream_t st) {
-    if (X.kcontig) {
-        const int gx = (a.k_pad / 8 + 255) / 256;
-        dim3 grid(gx, std::max(1, std::min(a.R_pad, 1184 / gx)));
-        k_resid_kc<T><<<grid, 256, 0, st>>>(X, a);
-    } else {
-        dim3 grid(a.k_pad / 64, a.R_pad / 64);
-        k_resid_rc<T><<<grid, 256, 0, st>>>(X, a);
-    }
-    return cuda_fail(cudaGetLastError());
-}
+// Resident blocks of 256 threads per SM for the looping light-phase launches.
+constexpr int kLightBlocksPerSM = 8;
 
 // One persistent launch over the problems of `G` (item counts filled in here):
 // one CTA per SM, or fewer when there are fewer work items.
@@ -374,69 +317,46 @@ struct Job {
         P.row_max = P.col_max = nullptr;
     }
 
-    // Algorithm 2 up to Cbar: mu', nu', the N-rule inputs, Abar, Bbar (fast
-    // mode: the majorant of Cbar instead of Abar, Bbar)
-    template <class Mark>
-    int phase_inputs(cudaStream_t st, Mark &&mark) {
-        int rc;
-        if ((rc = cuda_fail(cudaMemsetAsync(ws, 0, L.zero_end, st)))) return rc;
-        if (inject()) return OZ2_OK;
-        if ((rc = launch_stats(opA, k, rmaxA, hmaxA, st))) return rc;
-        if ((rc = launch_stats(opB, k, rmaxB, hmaxB, st))) return rc;
-        if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
-        const bool f = fast();
-        PlaneArgs qa{resA, planeA, d.m_pad, k, d.k_pad, rmaxA, nullptr, nullptr, f ? ssA : nullptr, !f, l1A};
-        PlaneArgs qb{resB, planeB, d.n_pad, k, d.k_pad, rmaxB, nullptr, nullptr, f ? ssB : nullptr, !f, l1B};
-        if ((rc = launch_quant(opA, qa, st))) return rc;
-        if ((rc = launch_quant(opB, qb, st))) return rc;
-        if (f) {
-            int *mx = reinterpret_cast<int *>(red + 6);
-            k_fast_max<<<std::min(148, (std::max(m, n) + 255) / 256), 256, 0, st>>>(ssA, m, ssB, n, mx);
-            if ((rc = cuda_fail(cudaGetLastError()))) return rc;
-            k_fast_cmax<<<std::min(1184, (m + n + 255) / 256), 256, 0, st>>>(ssA, m, ssB, n, mx, cmax_row,
-                                                                              cmax_col);
-            if ((rc = cuda_fail(cudaGetLastError()))) return rc;
-        }
-        return OZ2_OK;
-    }
-
-    // the N rule, mu and nu (Algorithm 2), then the residues (Algorithm 3)
-    int phase_exponents(cudaStream_t st) {
-        int rc;
-        if (!inject()) {
-            if (nmoduli == 0) {
-                BoundArgs ba{m, n, k, rmaxA, rmaxB, hmaxA, hmaxB, l1A, l1B, cmax_row, cmax_col, red};
-                k_bound_reduce<<<148, 256, 0, st>>>(ba);
-                if ((rc = cuda_fail(cudaGetLastError()))) return rc;
-            }
-            k_choose_n<<<1, 32, 0, st>>>(red, k, nmoduli ? 0.0 : target, nmax, nmoduli, fp32 ? 1 : 0, ndev, n_out);
-            if ((rc = cuda_fail(cudaGetLastError()))) return rc;
-            k_mu_nu<<<std::min(1184, (m + n + 255) / 256), 256, 0, st>>>(
-                m, n, rmaxA, rmaxB, cmax_row, cmax_col, ndev, fp32 ? 1 : 0, mu, nu, mu_out, nu_out);
-            return cuda_fail(cudaGetLastError());
-        }
-        k_choose_n<<<1, 32, 0, st>>>(red, k, 0.0, nmax, nmoduli, fp32 ? 1 : 0, ndev, n_out);
-        return cuda_fail(cudaGetLastError());
-    }
-    int phase_residues(cudaStream_t st) {
-        int rc;
-        // the row maxima bound |A'|, |B'| (fixed-position limbs); not computed
-        // when mu and nu are given
-        const unsigned long long *mxA = inject() ? nullptr : rmaxA, *mxB = inject() ? nullptr : rmaxB;
-        PlaneArgs ra{resA, planeA, d.m_pad, k, d.k_pad, mxA, mu_use(), ndev, nullptr, 1, nullptr};
-        PlaneArgs rb{resB, planeB, d.n_pad, k, d.k_pad, mxB, nu_use(), ndev, nullptr, 1, nullptr};
-        if ((rc = launch_resid(opA, ra, st))) return rc;
-        return launch_resid(opB, rb, st);
-    }
-
-    // Algorithm 3 from W_l on and the inverse scaling of Algorithm 1
-    int phase_crt(cudaStream_t st) {
-        dim3 grid((n + 1023) / 1024, grid_rows(m));
-        if constexpr (fp32)
-            k_crt<T, 32><<<grid, 256, 0, st>>>(W, w_plane, d.n_pad, ndev, mu_use(), nu_use(), C, long(ldc), m, n);
-        else
-            k_crt<T, 64><<<grid, 256, 0, st>>>(W, w_plane, d.n_pad, ndev, mu_use(), nu_use(), C, long(ldc), m, n);
-        return cuda_fail(cudaGetLastError());
+    // the device view of this problem for the grouped light-phase kernels
+    JobDesc<T> desc() const {
+        JobDesc<T> j{};
+        j.op[0] = opA;
+        j.op[1] = opB;
+        j.C = C;
+        j.ldc = ldc;
+        j.m = m; j.n = n; j.k = k;
+        j.k_pad = d.k_pad;
+        j.n_pad = d.n_pad;
+        j.R_pad[0] = d.m_pad;
+        j.R_pad[1] = d.n_pad;
+        j.nmoduli = nmoduli;
+        j.nmax = nmax;
+        j.fast = fast() ? 1 : 0;
+        j.inject = inject() ? 1 : 0;
+        auto aligned = [](const Operand<T> &op) {
+            return (reinterpret_cast<uintptr_t>(op.ptr) % 16 == 0 && (op.ld * long(sizeof(T))) % 16 == 0) ? 1 : 0;
+        };
+        j.vec[0] = aligned(opA);
+        j.vec[1] = aligned(opB);
+        j.target = nmoduli ? 0.0 : target;
+        j.hmax[0] = hmaxA; j.hmax[1] = hmaxB;
+        j.rmax[0] = rmaxA; j.rmax[1] = rmaxB;
+        j.l1[0] = l1A; j.l1[1] = l1B;
+        j.red = red;
+        j.cmax[0] = cmax_row; j.cmax[1] = cmax_col;
+        j.ss[0] = ssA; j.ss[1] = ssB;
+        j.ndev = ndev;
+        j.n_out = n_out;
+        j.expo[0] = mu; j.expo[1] = nu;
+        j.shift[0] = mu_use(); j.shift[1] = nu_use();
+        j.expo_out[0] = mu_out; j.expo_out[1] = nu_out;
+        j.res[0] = resA; j.res[1] = resB;
+        j.plane[0] = planeA; j.plane[1] = planeB;
+        j.W = W;
+        j.w_plane = w_plane;
+        j.zero = reinterpret_cast<uint4 *>(ws);
+        j.zero_vec = long(L.zero_end / 16);
+        return j;
     }
 };
 
@@ -456,6 +376,97 @@ int managed_workspace(int dev, size_t bytes, uint8_t **out) {
     }
     *out = static_cast<uint8_t *>(s.ws);
     return OZ2_OK;
+}
+
+// Every phase of Algorithms 1-3 for a group of at most kMaxJobs problems:
+// each light phase is one launch over the items of all problems, each GEMM one
+// persistent launch over the tiles of all problems (heaviest first).
+template <typename T, class Mark>
+int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&mark) {
+    static_assert(sizeof(JobGroup<T>) < 30000, "kernel parameter space");
+    static thread_local JobGroup<T> J;      // passed by value as the kernel parameter
+    static thread_local GemmGroup G;
+    std::memset(&J, 0, sizeof J);
+    J.count = count;
+    for (int p = 0; p < count; p++) J.j[p] = jobs[p]->desc();
+    // fills J.begin from the per-problem item counts; returns the grid size (0: nothing to do)
+    // (the kernels decode a problem's items with 32-bit arithmetic; a count of
+    // 2^32 would need terabytes of workspace, and is refused)
+    auto plan = [&](long long (*items)(const JobDesc<T> &), long long cap) -> int {
+        J.begin[0] = 0;
+        for (int p = 0; p < count; p++) {
+            const long long c = items(J.j[p]);
+            if (c >= (1ll << 32)) return -1;
+            J.begin[p + 1] = J.begin[p] + c;
+        }
+        return int(std::min<long long>(J.begin[count], cap));
+    };
+    // one item per block where a block has no setup to amortise; the residue
+    // kernels (which load a 12.5 KB table per block) stay resident and loop
+    const long long one_each = (1ll << 31) - 1, resident = (long long)sms * kLightBlocksPerSM;
+    int rc, g;
+    auto launched = [&]() { return cuda_fail(cudaGetLastError()); };
+#define OZ2_LAUNCH(kernel, items, cap)                              \
+    if ((g = plan(Items<T>::items, cap)) < 0) return OZ2_ENOTSUP;   \
+    if (g > 0) {                                                    \
+        kernel<T><<<g, 256, 0, st>>>(J);                            \
+        if ((rc = launched())) return rc;                           \
+    }
+    // heaviest problems first: the longest-processing-time order balances the
+    // static assignment of GEMM work items to CTAs
+    std::vector<int> order;
+    order.resize(size_t(count));
+    for (int p = 0; p < count; p++) order[p] = p;
+    auto cost = [&](int p) {
+        const auto &d = jobs[p]->d;
+        return double(d.m_pad) * d.n_pad * d.k_pad * (jobs[p]->nmax + 1);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    auto gemms = [&](bool scale) -> int {
+        std::memset(&G, 0, sizeof G);
+        for (int idx = 0; idx < count; idx++) {
+            const Job<T> &job = *jobs[order[idx]];
+            if (scale && !job.needs_scale_gemm()) continue;
+            GemmProblem &P = G.p[G.count++];
+            int r = job.describe(P);
+            if (r) return r;
+            if (scale) job.as_scale_gemm(P);
+            else job.as_residue_gemm(P);
+        }
+        if (!G.count) return OZ2_OK;
+        return scale ? launch_gemm<EPI_MAX>(G, sms, st) : launch_gemm<EPI_MOD>(G, sms, st);
+    };
+
+    if ((rc = mark(OZ2_PHASE_STATS))) return rc;
+    OZ2_LAUNCH(k_clear, clear, one_each)
+    OZ2_LAUNCH(k_absmax, absmax, one_each)
+    if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
+    OZ2_LAUNCH(k_quant_kc, quant_kc, one_each)
+    OZ2_LAUNCH(k_quant_rc, quant_rc, one_each)
+    OZ2_LAUNCH(k_fast_max, fast_max, one_each)
+    OZ2_LAUNCH(k_fast_cmax, fast_cmax, one_each)
+    if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
+    if ((rc = gemms(true))) return rc;
+    if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
+    OZ2_LAUNCH(k_bound, bound, one_each)
+    OZ2_LAUNCH(k_exponents, exponents, one_each)
+    if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
+    OZ2_LAUNCH(k_resid_kc, resid_kc, resident)
+    OZ2_LAUNCH(k_resid_rc, resid_rc, resident)
+    if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
+    if ((rc = gemms(false))) return rc;
+    if ((rc = mark(OZ2_PHASE_CRT))) return rc;
+    if (count == 1) {
+        const JobDesc<T> &j = J.j[0];
+        dim3 grid(unsigned(cdiv(j.n, 1024)), unsigned(std::min(j.m, 65535)));
+        k_crt_one<T><<<grid, 256, 0, st>>>(j.W, j.w_plane, long(j.n_pad), j.ndev, j.shift[0], j.shift[1], j.C,
+                                             j.ldc, j.m, j.n);
+        if ((rc = launched())) return rc;
+    } else {
+        OZ2_LAUNCH(k_crt, crt, one_each)
+    }
+#undef OZ2_LAUNCH
+    return mark(OZ2_NPHASES);
 }
 
 template <typename T>
@@ -484,34 +495,12 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
         return rc;
     }
     job.bind(ws);
-
-    static thread_local GemmGroup G;       // 24 KB: passed by value as the kernel parameter
-    std::memset(&G, 0, sizeof G);
-    G.count = 1;
-    if ((rc = job.describe(G.p[0]))) return rc;
-    const int sms = g_dev[dev].sms;
     auto mark = [&](int phase) -> int {
         if (!o || !o->phase_events) return OZ2_OK;
         return cuda_fail(cudaEventRecord(static_cast<cudaEvent_t>(o->phase_events[phase]), st));
     };
-    if ((rc = mark(OZ2_PHASE_STATS))) return rc;
-    if ((rc = job.phase_inputs(st, mark))) return rc;
-    if (job.inject() && (rc = mark(OZ2_PHASE_QUANT))) return rc;
-    if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
-    if (job.needs_scale_gemm()) {
-        job.as_scale_gemm(G.p[0]);
-        if ((rc = launch_gemm<EPI_MAX>(G, sms, st))) return rc;
-    }
-    if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
-    if ((rc = job.phase_exponents(st))) return rc;
-    if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
-    if ((rc = job.phase_residues(st))) return rc;
-    if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
-    job.as_residue_gemm(G.p[0]);
-    if ((rc = launch_gemm<EPI_MOD>(G, sms, st))) return rc;
-    if ((rc = mark(OZ2_PHASE_CRT))) return rc;
-    if ((rc = job.phase_crt(st))) return rc;
-    if ((rc = mark(OZ2_NPHASES))) return rc;
+    Job<T> *one = &job;
+    if ((rc = run_group(&one, 1, st, g_dev[dev].sms, mark))) return rc;
     if (o && o->w_out) {
         // export W_l (test aid): plane l, m x n row-major, from the padded layout
         for (int l = 0; l < job.nmax; l++) {
@@ -567,85 +556,22 @@ int run_batched(int count, const oz2_problem *q, const oz2_opts *o) {
         return rc;
     }
     for (int p = 0; p < count; p++) jobs[p].bind(ws + off[p]);
-    DeviceState &ds = g_dev[dev];
-    const int sms = ds.sms;
-    std::lock_guard<std::mutex> lk(ds.batch_mu);
+    std::vector<Job<double> *> ptrs;
+    ptrs.resize(size_t(count));
+    for (int p = 0; p < count; p++) ptrs[p] = &jobs[p];
     auto mark = [&](int phase) -> int {
         if (!o || !o->phase_events) return OZ2_OK;
         return cuda_fail(cudaEventRecord(static_cast<cudaEvent_t>(o->phase_events[phase]), st));
     };
     auto no_mark = [](int) { return OZ2_OK; };
-    // light phases of problem p run on pool stream p % kPool, forked from and
-    // joined back to the caller's stream around each grouped GEMM launch
-    const int used = std::min(count, kPool);
-    auto fork = [&]() -> int {
-        int r = cuda_fail(cudaEventRecord(ds.fork, st));
-        for (int i = 0; i < used && !r; i++) r = cuda_fail(cudaStreamWaitEvent(ds.pool[i], ds.fork, 0));
-        return r;
-    };
-    auto join = [&]() -> int {
-        int r = OZ2_OK;
-        for (int i = 0; i < used && !r; i++) {
-            r = cuda_fail(cudaEventRecord(ds.done[i], ds.pool[i]));
-            if (!r) r = cuda_fail(cudaStreamWaitEvent(st, ds.done[i], 0));
-        }
-        return r;
-    };
-    // grouped persistent GEMM launches, heaviest problems first (longest
-    // processing time first balances the static item assignment)
-    std::vector<int> order;
-    order.resize(size_t(count));
-    for (int p = 0; p < count; p++) order[p] = p;
-    auto cost = [&](int p) {
-        const auto &d = jobs[p].d;
-        return double(d.m_pad) * d.n_pad * d.k_pad * (jobs[p].nmax + 1);
-    };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-    static thread_local GemmGroup G;
-    auto grouped = [&](bool scale) -> int {
-        int r = OZ2_OK;
-        std::memset(&G, 0, sizeof G);
-        for (int idx = 0; idx < count && !r; idx++) {
-            const int p = order[idx];
-            if (scale && !jobs[p].needs_scale_gemm()) continue;
-            GemmProblem &P = G.p[G.count];
-            if ((r = jobs[p].describe(P))) break;
-            if (scale) jobs[p].as_scale_gemm(P);
-            else jobs[p].as_residue_gemm(P);
-            if (++G.count == gemm::kMaxGroup) {
-                r = scale ? launch_gemm<EPI_MAX>(G, sms, st) : launch_gemm<EPI_MOD>(G, sms, st);
-                std::memset(&G, 0, sizeof G);
-            }
-        }
-        if (!r && G.count) r = scale ? launch_gemm<EPI_MAX>(G, sms, st) : launch_gemm<EPI_MOD>(G, sms, st);
-        return r;
-    };
-
-    if ((rc = mark(OZ2_PHASE_STATS))) return rc;
-    if ((rc = fork())) return rc;
-    for (int p = 0; p < count; p++)
-        if ((rc = jobs[p].phase_inputs(ds.pool[p % kPool], no_mark))) return rc;
-    if ((rc = join())) return rc;
-    if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
-    if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
-    if ((rc = grouped(true))) return rc;
-    if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
-    if ((rc = fork())) return rc;
-    for (int p = 0; p < count; p++) {
-        cudaStream_t s = ds.pool[p % kPool];
-        if ((rc = jobs[p].phase_exponents(s))) return rc;
-        if ((rc = jobs[p].phase_residues(s))) return rc;
+    const int sms = g_dev[dev].sms;
+    // groups of kMaxJobs problems, one after another (phase events: first group)
+    for (int first = 0; first < count; first += kMaxJobs) {
+        const int c = std::min(kMaxJobs, count - first);
+        rc = first == 0 ? run_group(ptrs.data(), c, st, sms, mark) : run_group(ptrs.data() + first, c, st, sms, no_mark);
+        if (rc) return rc;
     }
-    if ((rc = join())) return rc;
-    if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
-    if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
-    if ((rc = grouped(false))) return rc;
-    if ((rc = mark(OZ2_PHASE_CRT))) return rc;
-    if ((rc = fork())) return rc;
-    for (int p = 0; p < count; p++)
-        if ((rc = jobs[p].phase_crt(ds.pool[p % kPool]))) return rc;
-    if ((rc = join())) return rc;
-    return mark(OZ2_NPHASES);
+    return OZ2_OK;
 }
 
 }  // namespace

@@ -6,12 +6,11 @@
 //   k_absmax                  Algorithm 2 inputs: max |x| per row of A (per
 //                             column of B) -> mu', nu', and the per-k maxima
 //                             of the N rule (one HBM read)
-//   k_planes_kc / k_planes_rc Abar = ceil(2^mu' |A|), Bbar likewise, as BF16;
+//   k_quant_kc / k_quant_rc   Abar = ceil(2^mu' |A|), Bbar likewise, as BF16;
 //                             also |A| v and v^T |B| for the N rule
 //   k_gemm<EPI_MAX>           Cbar = Abar Bbar on tcgen05, keeping only the row
 //                             and column maxima of Cbar
-//   k_bound_reduce, k_choose_n, k_mu_nu
-//                             Dbar, e, f, mu, nu (Algorithm 2) and the N rule
+//   k_bound, k_exponents      the N rule; Dbar, e, f, mu, nu (Algorithm 2)
 //   k_resid_kc / k_resid_rc   A'_l = mod(trunc(2^mu A), p_l) as BF16, N planes
 //   k_gemm<EPI_MOD>           C'_l = A'_l B'_l on tcgen05, W_l = mod(C'_l, p_l)
 //   k_crt                     C'(1), C'(2), Q, C'' (Algorithm 3) and the
@@ -196,13 +195,139 @@ struct Operand {
     int kcontig;
 };
 
+// ============================================================= grouped launches
+// Every phase outside the two GEMMs runs as one launch over the work items of
+// all problems of a group: one problem for oz2_gemm_ex, up to kMaxJobs for a
+// batch.  Blocks walk the items g = blockIdx.x, blockIdx.x + gridDim.x, ...;
+// problem p owns the items [begin[p], begin[p+1]).  The item counts below are
+// shared by the host (which fills begin[]) and the kernels (which decode).
+constexpr int kMaxJobs = 64;
+constexpr int kLineBlock = 64;     // lines per k_absmax item
+constexpr int kItemH = 2048;       // h per item of the K-contiguous kernels (256 threads x 8)
+
+template <typename T>
+struct JobDesc {
+    Operand<T> op[2];              // A (logical rows i) and B (logical rows j)
+    T *C;
+    long ldc;
+    int m, n, k, k_pad, n_pad;
+    int R_pad[2];                  // m_pad, n_pad
+    int nmoduli, nmax, fast, inject, vec[2];
+    double target;
+    unsigned long long *hmax[2];   // per-k maxima of |A|, |B|
+    unsigned long long *rmax[2];   // per logical row maxima (bits)
+    unsigned long long *l1[2];     // fixed-point 1-norms (PlaneArgs::l1)
+    unsigned long long *red;       // bound reductions
+    int *cmax[2];                  // Cbar row / column maxima
+    int *ss[2];                    // fast mode: sums of squares of Abar rows / Bbar columns
+    int *ndev, *n_out;
+    int32_t *expo[2];              // mu, nu computed by k_exponents
+    const int32_t *shift[2];       // mu, nu as used (computed or injected)
+    int32_t *expo_out[2];          // optional exports
+    __nv_bfloat16 *res[2];
+    long plane[2];
+    int8_t *W;
+    long w_plane;
+    uint4 *zero;                   // region cleared at the start of a call
+    long zero_vec;                 // its size in 16-byte units
+};
+
+template <typename T>
+struct JobGroup {
+    JobDesc<T> j[kMaxJobs];
+    int count;
+    long long begin[kMaxJobs + 1];
+};
+
+__host__ __device__ __forceinline__ long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+
+// k_absmax: operand X stored as S lines of C contiguous elements
+template <typename T>
+__host__ __device__ __forceinline__ void absmax_geom(const JobDesc<T> &j, int X, int &S, int &C) {
+    if (j.op[X].kcontig) { S = j.op[X].R; C = j.k; }
+    else { S = j.k; C = j.op[X].R; }
+}
+// threads per line: a multiple of 32 covering C / 8 positions, at most 256
+__host__ __device__ __forceinline__ int absmax_tpl(int C) {
+    int t = int(cdiv(cdiv(C, 8), 32) * 32);
+    return t < 32 ? 32 : (t > 256 ? 256 : t);
+}
+template <typename T>
+__host__ __device__ __forceinline__ long long items_absmax_x(const JobDesc<T> &j, int X) {
+    if (j.inject) return 0;
+    int S, C;
+    absmax_geom(j, X, S, C);
+    return cdiv(S, kLineBlock) * cdiv(C, absmax_tpl(C) * 8);
+}
+template <typename T>
+__host__ __device__ __forceinline__ long long items_kc_x(const JobDesc<T> &j, int X) {
+    return j.op[X].kcontig ? (long long)j.R_pad[X] * cdiv(j.k_pad, kItemH) : 0;
+}
+template <typename T>
+__host__ __device__ __forceinline__ long long items_rc_x(const JobDesc<T> &j, int X) {
+    return j.op[X].kcontig ? 0 : (long long)(j.k_pad / 64) * (j.R_pad[X] / 64);
+}
+template <typename T>
+__host__ __device__ __forceinline__ long long items_quant_kc_x(const JobDesc<T> &j, int X) {
+    return j.inject ? 0 : items_kc_x(j, X);
+}
+template <typename T>
+__host__ __device__ __forceinline__ long long items_quant_rc_x(const JobDesc<T> &j, int X) {
+    return j.inject ? 0 : items_rc_x(j, X);
+}
+
+template <typename T> struct Items {
+    __host__ __device__ static long long clear(const JobDesc<T> &j) { return cdiv(j.zero_vec, 256); }
+    __host__ __device__ static long long absmax(const JobDesc<T> &j) {
+        return items_absmax_x(j, 0) + items_absmax_x(j, 1);
+    }
+    __host__ __device__ static long long quant_kc(const JobDesc<T> &j) {
+        return items_quant_kc_x(j, 0) + items_quant_kc_x(j, 1);
+    }
+    __host__ __device__ static long long quant_rc(const JobDesc<T> &j) {
+        return items_quant_rc_x(j, 0) + items_quant_rc_x(j, 1);
+    }
+    __host__ __device__ static long long fast_max(const JobDesc<T> &j) {
+        return j.fast && !j.inject ? cdiv(j.m > j.n ? j.m : j.n, 2048) : 0;
+    }
+    __host__ __device__ static long long fast_cmax(const JobDesc<T> &j) {
+        return j.fast && !j.inject ? cdiv(j.m + j.n, 2048) : 0;
+    }
+    __host__ __device__ static long long bound(const JobDesc<T> &j) {
+        const int mx = j.m > j.n ? (j.m > j.k ? j.m : j.k) : (j.n > j.k ? j.n : j.k);
+        return !j.inject && j.nmoduli == 0 ? cdiv(mx, 2048) : 0;
+    }
+    __host__ __device__ static long long exponents(const JobDesc<T> &j) { return cdiv(j.m + j.n, 2048); }
+    __host__ __device__ static long long resid_kc(const JobDesc<T> &j) { return items_kc_x(j, 0) + items_kc_x(j, 1); }
+    __host__ __device__ static long long resid_rc(const JobDesc<T> &j) { return items_rc_x(j, 0) + items_rc_x(j, 1); }
+    __host__ __device__ static long long crt(const JobDesc<T> &j) { return (long long)j.m * cdiv(j.n, 1024); }
+};
+
+// Calls f(job, local item) for this block's items, in increasing order.
+template <typename T, class F>
+__device__ __forceinline__ void for_items(const JobGroup<T> &G, F &&f) {
+    const long long total = G.begin[G.count];
+    int p = 0;
+    for (long long g = blockIdx.x; g < total; g += gridDim.x) {
+        while (G.begin[p + 1] <= g) p++;
+        f(G.j[p], g - G.begin[p]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_clear(const __grid_constant__ JobGroup<T> G) {
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        const long long v = li * 256 + threadIdx.x;
+        if (v < j.zero_vec) j.zero[v] = make_uint4(0, 0, 0, 0);
+    });
+}
+
 // ============================================================= stats
 // Maxima of |x| (as the bits of double(|x|), which order like the values)
-// over a matrix stored as S lines of C contiguous elements, line s at
-// ptr + s ld: per line into smax[s] and per position into cmax[c], merged with
-// atomicMax (so the result does not depend on the order).  A, K-contiguous:
-// lines are rows i, positions h.  B, R-contiguous: lines are h, positions are
-// columns j.  Each thread takes 8 consecutive positions of s_per_block lines.
+// over an operand stored as S lines of C contiguous elements: per line and per
+// position, merged with atomicMax (so the result does not depend on the
+// order).  A, K-contiguous: lines are rows i, positions h.  B, R-contiguous:
+// lines are h, positions are columns j.
 template <typename T>
 __device__ __forceinline__ unsigned long long abs_bits(T x) {
     return (unsigned long long)__double_as_longlong(fabs(double(x)));
@@ -218,53 +343,70 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return ((unsigned long long)hi << 32) | lo;
 }
 
-template <typename T, bool VEC>
-__global__ void __launch_bounds__(256) k_absmax(const T *ptr, long ld, int S, int C, int s_per_block,
-                                               unsigned long long *smax, unsigned long long *cmax) {
-    const int c0 = (blockIdx.x * 256 + threadIdx.x) * 8;
-    const int s_begin = blockIdx.y * s_per_block;
-    const int s_end = min(S, s_begin + s_per_block);
-    const bool full = c0 + 8 <= C;
-    unsigned long long cm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int s = s_begin; s < s_end; s++) {
-        const T *src = ptr + (long)s * ld + c0;
-        T x[8];
-        if (VEC && full) {
-            if constexpr (sizeof(T) == 8) {
+// Item: kLineBlock lines x (threads per line x 8) positions of one operand.
+// Thread (line group ly, position group tx) takes 8 consecutive positions of
+// the lines ly, ly + lines-per-pass, ...; each warp lies in one line group.
+template <typename T>
+__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup<T> G) {
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        int X = 0;
+        const long long n0 = items_absmax_x(j, 0);
+        if (li >= n0) { X = 1; li -= n0; }
+        int S, C;
+        absmax_geom(j, X, S, C);
+        const int tpl = absmax_tpl(C), ppi = tpl * 8, lpp = 256 / tpl;
+        const unsigned ncb = unsigned(cdiv(C, ppi)), ui = unsigned(li);
+        const int lb = int(ui / ncb), cb = int(ui - unsigned(lb) * ncb);
+        const int ly = threadIdx.x / tpl, tx = threadIdx.x - ly * tpl;
+        const int c0 = cb * ppi + tx * 8;
+        const int s_end = min(S, (lb + 1) * kLineBlock);
+        const bool kc = j.op[X].kcontig != 0;
+        unsigned long long *smax = kc ? j.rmax[X] : j.hmax[X];
+        unsigned long long *cmax = kc ? j.hmax[X] : j.rmax[X];
+        const T *ptr = j.op[X].ptr;
+        const long ld = j.op[X].ld;
+        const bool full = c0 + 8 <= C, vec = full && j.vec[X];
+        unsigned long long cm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int s = lb * kLineBlock + ly; s < s_end; s += lpp) {
+            const T *src = ptr + (long)s * ld + c0;
+            T x[8];
+            if (vec) {
+                if constexpr (sizeof(T) == 8) {
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const double2 v = reinterpret_cast<const double2 *>(src)[q];
-                    x[2 * q] = T(v.x);
-                    x[2 * q + 1] = T(v.y);
+                    for (int q = 0; q < 4; q++) {
+                        const double2 v = reinterpret_cast<const double2 *>(src)[q];
+                        x[2 * q] = T(v.x);
+                        x[2 * q + 1] = T(v.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const float4 v = reinterpret_cast<const float4 *>(src)[q];
+                        x[4 * q] = T(v.x); x[4 * q + 1] = T(v.y); x[4 * q + 2] = T(v.z); x[4 * q + 3] = T(v.w);
+                    }
                 }
             } else {
 #pragma unroll
-                for (int q = 0; q < 2; q++) {
-                    const float4 v = reinterpret_cast<const float4 *>(src)[q];
-                    x[4 * q] = T(v.x); x[4 * q + 1] = T(v.y); x[4 * q + 2] = T(v.z); x[4 * q + 3] = T(v.w);
-                }
+                for (int e = 0; e < 8; e++) x[e] = c0 + e < C ? src[e] : T(0);
             }
-        } else {
+            unsigned long long lm = 0;
 #pragma unroll
-            for (int e = 0; e < 8; e++) x[e] = c0 + e < C ? src[e] : T(0);
+            for (int e = 0; e < 8; e++) {
+                const unsigned long long bits = abs_bits(x[e]);
+                cm[e] = bits > cm[e] ? bits : cm[e];
+                lm = bits > lm ? bits : lm;
+            }
+            lm = warp_max_u64(lm);
+            if ((threadIdx.x & 31) == 0 && lm) atomicMax(smax + s, lm);
         }
-        unsigned long long lm = 0;
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const unsigned long long b = abs_bits(x[e]);
-            cm[e] = b > cm[e] ? b : cm[e];
-            lm = b > lm ? b : lm;
-        }
-        lm = warp_max_u64(lm);
-        if ((threadIdx.x & 31) == 0 && lm) atomicMax(smax + s, lm);
-    }
-#pragma unroll
-    for (int e = 0; e < 8; e++)
-        if (cm[e] && c0 + e < C) atomicMax(cmax + c0 + e, cm[e]);
+        for (int e = 0; e < 8; e++)
+            if (cm[e] && c0 + e < C) atomicMax(cmax + c0 + e, cm[e]);
+    });
 }
 
 // ============================================================= planes
-// k_planes_*: Abar = BF16(ceil(2^mu' |x|)), plane 0, K-major, zeros in the padding.
+// k_quant_*: Abar = BF16(ceil(2^mu' |x|)), plane 0, K-major, zeros in the padding.
 // k_resid_*: planes l < N = BF16(mod(trunc(2^mu x), p_l)), K-major, zeros in padding.
 // Output element (l, r, h) at out[l*plane + r*k_pad + h].
 struct PlaneArgs {
@@ -342,62 +484,83 @@ __device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8],
     }
 }
 
-// K-contiguous source: one row per blockIdx.y (grid-stride), 8 h per thread.
-// Every lane stays to the end of each row (the fast-mode sum of squares is
-// reduced across the warp).
 template <typename T>
-__global__ void __launch_bounds__(256) k_planes_kc(Operand<T> X, PlaneArgs a) {
-    const int h0 = (blockIdx.x * 256 + threadIdx.x) * 8;
-    const bool act = h0 < a.k_pad;
-    for (int r = blockIdx.y; r < a.R_pad; r += gridDim.y) {
+__device__ __forceinline__ PlaneArgs quant_args(const JobDesc<T> &j, int X) {
+    return PlaneArgs{j.res[X], j.plane[X], j.R_pad[X], j.k, j.k_pad, j.rmax[X], nullptr, nullptr,
+                     j.fast ? j.ss[X] : nullptr, !j.fast, j.l1[X]};
+}
+
+// K-contiguous source.  Item: one row, kItemH h (8 per thread).  Every lane
+// stays to the end of the item (the row sums are reduced across the warp).
+template <typename T>
+__global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGroup<T> G) {
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        int X = 0;
+        const long long n0 = items_quant_kc_x(j, 0);
+        if (li >= n0) { X = 1; li -= n0; }
+        const PlaneArgs a = quant_args(j, X);
+        const Operand<T> &op = j.op[X];
+        const unsigned nhb = unsigned(cdiv(a.k_pad, kItemH)), ui = unsigned(li);
+        const int r = int(ui / nhb), h0 = int(ui - unsigned(r) * nhb) * kItemH + threadIdx.x * 8;
         RowAcc acc{0, 0, 0};
-        if (act) {
-            if (r >= X.R) {
+        if (h0 < a.k_pad) {
+            if (r >= op.R) {
                 if (a.write) *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
             } else {
                 const int shift = quant_shift(a.row_max, r);
                 T x[8];
-                const T *src = X.ptr + (long)r * X.ld + h0;
+                const T *src = op.ptr + (long)r * op.ld + h0;
 #pragma unroll
                 for (int e = 0; e < 8; e++) x[e] = (h0 + e < a.k) ? src[e] : T(0);
                 emit_quant8(a, x, shift, r, h0, acc);
             }
         }
-        flush_row(a, acc, r, 32, r < X.R);
-    }
+        flush_row(a, acc, r, 32, r < op.R);
+    });
 }
 
-// R-contiguous source: 64 (h) x 64 (r) tiles transposed through shared memory.
+// R-contiguous source.  Item: a 64 (h) x 64 (r) tile transposed through
+// shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256) k_planes_rc(Operand<T> X, PlaneArgs a) {
+__global__ void __launch_bounds__(256) k_quant_rc(const __grid_constant__ JobGroup<T> G) {
     __shared__ T tile[64][65];
-    const int h_base = blockIdx.x * 64, r_base = blockIdx.y * 64;
-    {
-        const int rr = threadIdx.x & 63;
-        const int r = r_base + rr;
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        int X = 0;
+        const long long n0 = items_quant_rc_x(j, 0);
+        if (li >= n0) { X = 1; li -= n0; }
+        const PlaneArgs a = quant_args(j, X);
+        const Operand<T> &op = j.op[X];
+        const unsigned nrb = unsigned(a.R_pad / 64), ui = unsigned(li);
+        const int hb = int(ui / nrb);
+        const int h_base = hb * 64, r_base = int(ui - unsigned(hb) * nrb) * 64;
+        __syncthreads();                     // the previous item's reads of the tile are done
+        {
+            const int rr = threadIdx.x & 63;
+            const int r = r_base + rr;
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
-            const int hh = (threadIdx.x >> 6) + 4 * i;
-            const int h = h_base + hh;
-            tile[hh][rr] = (r < X.R && h < a.k) ? X.ptr[(long)h * X.ld + r] : T(0);
+            for (int i = 0; i < 16; i++) {
+                const int hh = (threadIdx.x >> 6) + 4 * i;
+                const int h = h_base + hh;
+                tile[hh][rr] = (r < op.R && h < a.k) ? op.ptr[(long)h * op.ld + r] : T(0);
+            }
         }
-    }
-    __syncthreads();
-    const int rr = threadIdx.x >> 2, hq = threadIdx.x & 3;
-    const int r = r_base + rr;
-    const bool live = r < X.R;
-    const int shift = live ? quant_shift(a.row_max, r) : 0;
-    RowAcc acc{0, 0, 0};
+        __syncthreads();
+        const int rr = threadIdx.x >> 2, hq = threadIdx.x & 3;
+        const int r = r_base + rr;
+        const bool live = r < op.R;
+        const int shift = live ? quant_shift(a.row_max, r) : 0;
+        RowAcc acc{0, 0, 0};
 #pragma unroll
-    for (int g = 0; g < 2; g++) {
-        const int hh0 = hq * 16 + g * 8;
-        const int h0 = h_base + hh0;
-        T x[8];
+        for (int g = 0; g < 2; g++) {
+            const int hh0 = hq * 16 + g * 8;
+            const int h0 = h_base + hh0;
+            T x[8];
 #pragma unroll
-        for (int e = 0; e < 8; e++) x[e] = live ? tile[hh0 + e][rr] : T(0);
-        emit_quant8(a, x, shift, r, h0, acc);
-    }
-    flush_row(a, acc, r, 4, live);   // the 4 threads of row rr are adjacent lanes
+            for (int e = 0; e < 8; e++) x[e] = live ? tile[hh0 + e][rr] : T(0);
+            emit_quant8(a, x, shift, r, h0, acc);
+        }
+        flush_row(a, acc, r, 4, live);   // the 4 threads of row rr are adjacent lanes
+    });
 }
 
 // ------------------------------------------------------------------ residues
@@ -541,36 +704,48 @@ __device__ __forceinline__ void load_pow2(uint8_t (*s)[256], int N) {
 
 __device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
 
-// K-contiguous source: 8 consecutive h per thread (one 16-byte store per
-// plane), rows strided over blockIdx.y.
 template <typename T>
-__global__ void __launch_bounds__(256) k_resid_kc(Operand<T> X, PlaneArgs a) {
+__device__ __forceinline__ PlaneArgs resid_args(const JobDesc<T> &j, int X) {
+    // the row maxima bound |A'|, |B'| (fixed-position limbs); they are not
+    // computed when mu and nu are given
+    return PlaneArgs{j.res[X], j.plane[X], j.R_pad[X], j.k, j.k_pad, j.inject ? nullptr : j.rmax[X],
+                     j.shift[X], j.ndev, nullptr, 1, nullptr};
+}
+
+// K-contiguous source.  Item: one row, kItemH h: 8 consecutive h per thread
+// (one 16-byte store per plane).
+template <typename T>
+__global__ void __launch_bounds__(256) k_resid_kc(const __grid_constant__ JobGroup<T> G) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
-    const int N = *a.n_dev;
-    load_pow2(pow2, N);
+    load_pow2(pow2, kNMax);
     __syncthreads();
-    const long pw16 = a.plane / 8;
-    const int h0 = (blockIdx.x * 256 + threadIdx.x) * 8;
-    const bool act = h0 < a.k_pad;
-    for (int r = blockIdx.y; r < a.R_pad; r += gridDim.y) {
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        int X = 0;
+        const long long n0 = items_kc_x(j, 0);
+        if (li >= n0) { X = 1; li -= n0; }
+        const PlaneArgs a = resid_args(j, X);
+        const Operand<T> &op = j.op[X];
+        const int N = *a.n_dev;
+        const long pw16 = a.plane / 8;
+        const unsigned nhb = unsigned(cdiv(a.k_pad, kItemH)), ui = unsigned(li);
+        const int r = int(ui / nhb), h0 = int(ui - unsigned(r) * nhb) * kItemH + threadIdx.x * 8;
+        if (h0 >= a.k_pad) return;
         uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
-        if (r >= X.R) {
-            if (act)
-                for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
-            continue;
+        if (r >= op.R) {
+            for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
+            return;
         }
         const int shift = a.shift[r];
         const int need = a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20;
-        if (!act) continue;
         T x[8];
-        const T *src = X.ptr + (long)r * X.ld + h0;
+        const T *src = op.ptr + (long)r * op.ld + h0;
 #pragma unroll
         for (int e = 0; e < 8; e++) x[e] = h0 + e < a.k ? src[e] : T(0);
         emit_resid8(dst, pw16, N, x, shift, need, pow2);
-    }
+    });
 }
 
-// R-contiguous source: a 64 (r) x 64 (h) tile transposed through shared
+// R-contiguous source.  Item: a 64 (r) x 64 (h) tile transposed through shared
 // memory.  Thread (row rr, group tc) then takes h = 8 tc .. 8 tc + 7 of row rr;
 // the 16-byte chunks of each group are stored XOR-swizzled by (tc >> 1) & 3 so
 // that those reads hit distinct banks.
@@ -579,44 +754,53 @@ __device__ __forceinline__ int resid_swz(int hh) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_resid_rc(Operand<T> X, PlaneArgs a) {
+__global__ void __launch_bounds__(256) k_resid_rc(const __grid_constant__ JobGroup<T> G) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     __shared__ T tile[64][65];               // [r][swizzled h]
-    const int N = *a.n_dev;
-    load_pow2(pow2, N);
-    const long pw16 = a.plane / 8;
-    const int h_base = blockIdx.x * 64, r_base = blockIdx.y * 64;
-    {
-        const int rr = threadIdx.x & 63;
-        const int r = r_base + rr;
+    load_pow2(pow2, kNMax);
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        int X = 0;
+        const long long n0 = items_rc_x(j, 0);
+        if (li >= n0) { X = 1; li -= n0; }
+        const PlaneArgs a = resid_args(j, X);
+        const Operand<T> &op = j.op[X];
+        const int N = *a.n_dev;
+        const long pw16 = a.plane / 8;
+        const unsigned nrb = unsigned(a.R_pad / 64), ui = unsigned(li);
+        const int hb = int(ui / nrb);
+        const int h_base = hb * 64, r_base = int(ui - unsigned(hb) * nrb) * 64;
+        __syncthreads();                     // pow2 is loaded; the previous item's reads are done
+        {
+            const int rr = threadIdx.x & 63;
+            const int r = r_base + rr;
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
-            const int hh = (threadIdx.x >> 6) + 4 * i;
-            const int h = h_base + hh;
-            tile[rr][resid_swz(hh)] = (r < X.R && h < a.k) ? X.ptr[(long)h * X.ld + r] : T(0);
+            for (int i = 0; i < 16; i++) {
+                const int hh = (threadIdx.x >> 6) + 4 * i;
+                const int h = h_base + hh;
+                tile[rr][resid_swz(hh)] = (r < op.R && h < a.k) ? op.ptr[(long)h * op.ld + r] : T(0);
+            }
         }
-    }
-    __syncthreads();
-    const int tc = threadIdx.x & 7;
-    const int h0 = h_base + 8 * tc;
+        __syncthreads();
+        const int tc = threadIdx.x & 7;
+        const int h0 = h_base + 8 * tc;
 #pragma unroll 1
-    for (int i = 0; i < 2; i++) {
-        const int rr = (threadIdx.x >> 3) + 32 * i;
-        const int r = r_base + rr;
-        const bool live = r < X.R;
-        const int shift = live ? a.shift[r] : 0;
-        const int need = warp_max(live ? (a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20) : 0);
-        if (r >= a.R_pad) continue;
-        uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
-        if (!live) {
-            for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
-            continue;
-        }
-        T x[8];
+        for (int i = 0; i < 2; i++) {
+            const int rr = (threadIdx.x >> 3) + 32 * i;
+            const int r = r_base + rr;
+            const bool live = r < op.R;
+            const int shift = live ? a.shift[r] : 0;
+            const int need = warp_max(live ? (a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20) : 0);
+            uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
+            if (!live) {
+                for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
+                continue;
+            }
+            T x[8];
 #pragma unroll
-        for (int e = 0; e < 8; e++) x[e] = tile[rr][resid_swz(8 * tc + e)];
-        emit_resid8(dst, pw16, N, x, shift, need, pow2);
-    }
+            for (int e = 0; e < 8; e++) x[e] = tile[rr][resid_swz(8 * tc + e)];
+            emit_resid8(dst, pw16, N, x, shift, need, pow2);
+        }
+    });
 }
 
 // ============================================================= tcgen05 GEMM
@@ -905,14 +1089,8 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
 
 // ============================================================= exponents and N
 // red[] holds bits of nonnegative doubles (order-independent atomicMax):
-// 0 max_i |A|v, 1 max_j v^T|B|, 2 max_i 2^alpha'_i, 3 max_j 2^beta'_j, 4 L.
-struct BoundArgs {
-    int m, n, k;
-    const unsigned long long *rmaxA, *rmaxB, *hmaxA, *hmaxB;
-    const unsigned long long *l1A, *l1B;     // fixed-point row sums (PlaneArgs::l1)
-    const int *cmax_row, *cmax_col;
-    unsigned long long *red;
-};
+// 0 max_i |A|v, 1 max_j v^T|B|, 2 max_i 2^alpha'_i, 3 max_j 2^beta'_j, 4 L;
+// red[6] as two ints: fast mode's max_i ssA_i, max_j ssB_j.
 
 __device__ __forceinline__ double pow2_prime(unsigned long long rmax_bits, int cmax) {
     // 2^alpha' = 2^alpha sqrt(max cbar) (Theorem 2); 0 for an empty row
@@ -921,10 +1099,7 @@ __device__ __forceinline__ double pow2_prime(unsigned long long rmax_bits, int c
 }
 
 __device__ __forceinline__ void block_max_to(unsigned long long v, unsigned long long *dst) {
-    for (int o = 16; o; o >>= 1) {
-        unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
-        v = t > v ? t : v;
-    }
+    v = warp_max_u64(v);
     if ((threadIdx.x & 31) == 0 && v) atomicMax(dst, v);
 }
 
@@ -934,80 +1109,101 @@ __device__ __forceinline__ double row_l1(const unsigned long long *l1, const uns
     return ldexp(v, -(quant_shift(rmax, r) + 57));
 }
 
-__global__ void __launch_bounds__(256) k_bound_reduce(BoundArgs a) {
-    unsigned long long mR = 0, mK = 0, m2a = 0, m2b = 0, mL = 0;
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.m; i += stride) {
-        unsigned long long v = (unsigned long long)__double_as_longlong(row_l1(a.l1A, a.rmaxA, i));
-        mR = v > mR ? v : mR;
-        v = (unsigned long long)__double_as_longlong(pow2_prime(a.rmaxA[i], a.cmax_row[i]));
-        m2a = v > m2a ? v : m2a;
-    }
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += stride) {
-        unsigned long long v = (unsigned long long)__double_as_longlong(row_l1(a.l1B, a.rmaxB, j));
-        mK = v > mK ? v : mK;
-        v = (unsigned long long)__double_as_longlong(pow2_prime(a.rmaxB[j], a.cmax_col[j]));
-        m2b = v > m2b ? v : m2b;
-    }
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < a.k; h += stride) {
-        double v = __longlong_as_double((long long)a.hmaxA[h]) * __longlong_as_double((long long)a.hmaxB[h]);
-        unsigned long long b = (unsigned long long)__double_as_longlong(v);
-        mL = b > mL ? b : mL;
-    }
-    block_max_to(mR, a.red + 0);
-    block_max_to(mK, a.red + 1);
-    block_max_to(m2a, a.red + 2);
-    block_max_to(m2b, a.red + 3);
-    block_max_to(mL, a.red + 4);
+// The maxima that the N rule needs.  Item: 2048 consecutive indices of each
+// of the ranges i < m, j < n, h < k.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<T> G) {
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        unsigned long long mR = 0, mK = 0, m2a = 0, m2b = 0, mL = 0;
+        const int base = int(li) * 2048 + threadIdx.x;
+#pragma unroll 1
+        for (int e = 0; e < 8; e++) {
+            const int t = base + e * 256;
+            if (t < j.m) {
+                unsigned long long v = (unsigned long long)__double_as_longlong(row_l1(j.l1[0], j.rmax[0], t));
+                mR = v > mR ? v : mR;
+                v = (unsigned long long)__double_as_longlong(pow2_prime(j.rmax[0][t], j.cmax[0][t]));
+                m2a = v > m2a ? v : m2a;
+            }
+            if (t < j.n) {
+                unsigned long long v = (unsigned long long)__double_as_longlong(row_l1(j.l1[1], j.rmax[1], t));
+                mK = v > mK ? v : mK;
+                v = (unsigned long long)__double_as_longlong(pow2_prime(j.rmax[1][t], j.cmax[1][t]));
+                m2b = v > m2b ? v : m2b;
+            }
+            if (t < j.k) {
+                const double v = __longlong_as_double((long long)j.hmax[0][t]) *
+                                 __longlong_as_double((long long)j.hmax[1][t]);
+                const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+                mL = bits > mL ? bits : mL;
+            }
+        }
+        block_max_to(mR, j.red + 0);
+        block_max_to(mK, j.red + 1);
+        block_max_to(m2a, j.red + 2);
+        block_max_to(m2b, j.red + 3);
+        block_max_to(mL, j.red + 4);
+    });
 }
 
 // The N rule: smallest N in [2, nmax] with
 //   t_N (maxR max2b + max2a maxK) + (k + gN_N) t_N^2 max2a max2b <= tau * L,
-// else nmax.  fixed > 0 bypasses the rule.
-__global__ void k_choose_n(const unsigned long long *red, int k, double tau, int nmax, int fixed, int fp32,
-                           int *n_dev, int *n_out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int N = fixed;
-    if (N <= 0) {
-        const double maxR = __longlong_as_double((long long)red[0]);
-        const double maxK = __longlong_as_double((long long)red[1]);
-        const double m2a = __longlong_as_double((long long)red[2]);
-        const double m2b = __longlong_as_double((long long)red[3]);
-        const double L = __longlong_as_double((long long)red[4]);
-        N = nmax;
-        for (int c = 2; c <= nmax; c++) {
-            const DevN &d = fp32 ? c_n32[c] : c_n64[c];
-            const double T = d.t * (maxR * m2b + m2a * maxK) + (double(k) + d.gN) * d.t * d.t * m2a * m2b;
-            if (T <= tau * L) { N = c; break; }
-        }
+// else nmax.
+__device__ __forceinline__ int choose_n(const unsigned long long *red, int k, double tau, int nmax, int fp32) {
+    const double maxR = __longlong_as_double((long long)red[0]);
+    const double maxK = __longlong_as_double((long long)red[1]);
+    const double m2a = __longlong_as_double((long long)red[2]);
+    const double m2b = __longlong_as_double((long long)red[3]);
+    const double L = __longlong_as_double((long long)red[4]);
+    for (int c = 2; c <= nmax; c++) {
+        const DevN &d = fp32 ? c_n32[c] : c_n64[c];
+        const double T = d.t * (maxR * m2b + m2a * maxK) + (double(k) + d.gN) * d.t * d.t * m2a * m2b;
+        if (T <= tau * L) return c;
     }
-    *n_dev = N;
-    if (n_out) *n_out = N;
+    return nmax;
 }
 
-// Algorithm 2, mu/nu lines: d = single_up(max cbar) (1 for an empty row),
-// e = log2f(d) with CUDA's fast __log2f as in the paper,
-// mu = mu' + floor(fl_down(fma(c, e, P'))).
-__global__ void __launch_bounds__(256) k_mu_nu(int m, int n, const unsigned long long *rmaxA,
-                                               const unsigned long long *rmaxB, const int *cmax_row,
-                                               const int *cmax_col, const int *n_dev, int fp32, int32_t *mu,
-                                               int32_t *nu, int32_t *mu_out, int32_t *nu_out) {
-    const int N = *n_dev;
-    const float Pp = fp32 ? c_n32[N].Pprime : c_n64[N].Pprime;
-    const float c = c_cneg;
-    const int stride = gridDim.x * blockDim.x;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m + n; t += stride) {
-        const bool isrow = t < m;
-        const int i = isrow ? t : t - m;
-        const unsigned long long b = isrow ? rmaxA[i] : rmaxB[i];
-        const int mp = b ? 5 - floor_log2_bits(b) : 0;
-        const int cm = isrow ? cmax_row[i] : cmax_col[i];
-        const float d = cm > 0 ? __int2float_ru(cm) : 1.0f;
-        const float e = __log2f(d);
-        const int v = mp + int(floorf(__fmaf_rd(c, e, Pp)));
-        if (isrow) { mu[i] = v; if (mu_out) mu_out[i] = v; }
-        else { nu[i] = v; if (nu_out) nu_out[i] = v; }
-    }
+// N (fixed, or the rule), then Algorithm 2's mu/nu lines: d = single_up(max
+// cbar) (1 for an empty row), e = log2f(d) with CUDA's fast __log2f as in the
+// paper, mu = mu' + floor(fl_down(fma(c, e, P'))).  Item: 2048 of the m + n
+// rows and columns; every item of a problem derives the same N, and item 0
+// publishes it.
+template <typename T>
+__global__ void __launch_bounds__(256) k_exponents(const __grid_constant__ JobGroup<T> G) {
+    constexpr int fp32 = sizeof(T) == 4 ? 1 : 0;
+    __shared__ int sN;
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        __syncthreads();                     // the previous item has read sN
+        if (threadIdx.x == 0) {
+            const int N = j.nmoduli > 0 ? j.nmoduli : choose_n(j.red, j.k, j.target, j.nmax, fp32);
+            sN = N;
+            if (li == 0) {
+                *j.ndev = N;
+                if (j.n_out) *j.n_out = N;
+            }
+        }
+        __syncthreads();
+        if (j.inject) return;
+        const int N = sN;
+        const float Pp = fp32 ? c_n32[N].Pprime : c_n64[N].Pprime;
+        const float c = c_cneg;
+        const int base = int(li) * 2048 + threadIdx.x;
+#pragma unroll 1
+        for (int e = 0; e < 8; e++) {
+            const int t = base + e * 256;
+            if (t >= j.m + j.n) break;
+            const int X = t < j.m ? 0 : 1;
+            const int i = X ? t - j.m : t;
+            const unsigned long long bits = j.rmax[X][i];
+            const int mp = bits ? 5 - floor_log2_bits(bits) : 0;
+            const int cm = j.cmax[X][i];
+            const float d = cm > 0 ? __int2float_ru(cm) : 1.0f;
+            const float ex = __log2f(d);
+            const int v = mp + int(floorf(__fmaf_rd(c, ex, Pp)));
+            j.expo[X][i] = v;
+            if (j.expo_out[X]) j.expo_out[X][i] = v;
+        }
+    });
 }
 
 // Fast mode (a reading; the paper only names the mode): Cbar is replaced by
@@ -1015,17 +1211,24 @@ __global__ void __launch_bounds__(256) k_mu_nu(int m, int n, const unsigned long
 // row maxima are ceil(sqrt(ssA_i max_j ssB_j)) and column maxima
 // ceil(sqrt(max_i ssA_i ssB_j)).  Lemma 0 only needs Dbar >= Cbar and the
 // maxima <= 2^12 k, which the majorant satisfies.
-__global__ void __launch_bounds__(256) k_fast_max(const int *ssA, int m, const int *ssB, int n, int *mx) {
-    int a = 0, b = 0;
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) a = max(a, ssA[i]);
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) b = max(b, ssB[j]);
-    a = __reduce_max_sync(0xffffffffu, a);
-    b = __reduce_max_sync(0xffffffffu, b);
-    if ((threadIdx.x & 31) == 0) {
-        if (a) atomicMax(mx, a);
-        if (b) atomicMax(mx + 1, b);
-    }
+template <typename T>
+__global__ void __launch_bounds__(256) k_fast_max(const __grid_constant__ JobGroup<T> G) {
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        int a = 0, b = 0;
+        const int base = int(li) * 2048 + threadIdx.x;
+        for (int e = 0; e < 8; e++) {
+            const int t = base + e * 256;
+            if (t < j.m) a = max(a, j.ss[0][t]);
+            if (t < j.n) b = max(b, j.ss[1][t]);
+        }
+        a = __reduce_max_sync(0xffffffffu, a);
+        b = __reduce_max_sync(0xffffffffu, b);
+        int *mx = reinterpret_cast<int *>(j.red + 6);
+        if ((threadIdx.x & 31) == 0) {
+            if (a) atomicMax(mx, a);
+            if (b) atomicMax(mx + 1, b);
+        }
+    });
 }
 
 __device__ __forceinline__ int ceil_sqrt_u64(unsigned long long x) {
@@ -1035,38 +1238,48 @@ __device__ __forceinline__ int ceil_sqrt_u64(unsigned long long x) {
     return int(r * r == x ? r : r + 1);
 }
 
-__global__ void __launch_bounds__(256) k_fast_cmax(const int *ssA, int m, const int *ssB, int n, const int *mx,
-                                                   int *cmax_row, int *cmax_col) {
-    const unsigned long long mA = (unsigned long long)mx[0], mB = (unsigned long long)mx[1];
-    const int stride = gridDim.x * blockDim.x;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m + n; t += stride) {
-        if (t < m) cmax_row[t] = ceil_sqrt_u64((unsigned long long)ssA[t] * mB);
-        else cmax_col[t - m] = ceil_sqrt_u64(mA * (unsigned long long)ssB[t - m]);
-    }
+template <typename T>
+__global__ void __launch_bounds__(256) k_fast_cmax(const __grid_constant__ JobGroup<T> G) {
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        const int *mx = reinterpret_cast<const int *>(j.red + 6);
+        const unsigned long long mA = (unsigned long long)mx[0], mB = (unsigned long long)mx[1];
+        const int base = int(li) * 2048 + threadIdx.x;
+        for (int e = 0; e < 8; e++) {
+            const int t = base + e * 256;
+            if (t >= j.m + j.n) break;
+            if (t < j.m) j.cmax[0][t] = ceil_sqrt_u64((unsigned long long)j.ss[0][t] * mB);
+            else j.cmax[1][t - j.m] = ceil_sqrt_u64(mA * (unsigned long long)j.ss[1][t - j.m]);
+        }
+    });
 }
 
 // ============================================================= CRT
 // Algorithm 3 after the products, then Algorithm 1's inverse scaling:
-//   C'(1) = sum_l s_l1 W_l   (b = 64: exact, kept as the integer sum of
-//                             s_l1/g times W_l, then times g; b = 32: FP64 fma
-//                             chain in ascending l),
-//   C'(2) = fma chain of s_l2 W_l in ascending l (b = 64),
+//   C'(1) = sum_l s_l1 W_l, C'(2) = sum_l s_l2 W_l, each the exact sum rounded
+//           once to FP64 (b = 64: C'(1) is exact, Lemma 2; b = 32: s_l2 = 0),
 //   Q = rint(P_inv C'(1)),  C'' = fma(-Q, P2, fma(-Q, P1, C'(1)) + C'(2)),
 //   C = RN(2^-(mu_i + nu_j) C'')  (b = 32: rounded once to FP32).
+
+// ------------------------------------------------------------------ the epilogue's helpers
+
+// RN(x 2^e) for an integer-valued x with |x| < 2^400 (an exponent add, on the
+// integer units, whenever the result stays normal)
 __device__ __forceinline__ double scale_pow2(double x, int e) {
-    // RN(x * 2^e) for an integer-valued x with |x| < 2^400
     if (x == 0.0) return x;
-    if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+    const long long b = __double_as_longlong(x);
+    const int ex = int((b >> 52) & 0x7FF);
+    if (ex + e >= 1 && ex + e <= 2046) return __longlong_as_double(b + ((long long)e << 52));   // exact
     if (e > 1023) return x * 0x1p1023 * 0x1p1023;                 // overflows to +-inf as ldexp does
+    if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
     const double y = x * 0x1p-1022;                               // exact: |x| >= 1
     const int e2 = e + 1022;
     if (e2 < -1022) return copysign(0.0, x);
     return y * __longlong_as_double((long long)(e2 + 1023) << 52);
 }
 
-// RN((hi 2^31 + lo) 2^e) as a double, from integer operations only (the FP64
-// pipe of this part is slow).  Requires |hi|, |lo| < 2^61 and a result in the
-// normal range (the tables check both for every N).  An exact zero gives +0.
+// RN((hi 2^31 + lo) 2^e) as a double, from integer operations only.  Requires
+// |hi|, |lo| < 2^61 and a result in the normal range (the tables check both
+// for every N).  An exact zero gives +0.
 __device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
     long long t = hi + (lo >> 31);                 // value = t 2^31 + r, 0 <= r < 2^31
     unsigned long long r = (unsigned long long)(lo & 0x7FFFFFFFll);
@@ -1102,52 +1315,73 @@ __device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
     return __longlong_as_double((long long)bits);
 }
 
-template <typename TO, int B>
-__global__ void __launch_bounds__(256) k_crt(const int8_t *W, long w_plane, int n_pad, const int *n_dev,
-                                             const int32_t *mu, const int32_t *nu, TO *C, long ldc, int m, int n) {
-    // C'(1) and C'(2) are sums of integer multiples of fixed grids: both are
-    // accumulated exactly in 64-bit integers (two 31-bit halves of each
-    // constant, |terms| < 2^38, N <= 49) and rounded once.
-    const int N = *n_dev;
-    const DevN d = B == 64 ? c_n64[N] : c_n32[N];
+// One row i, columns j0 .. j0+3 of one thread.  C'(1) and C'(2) are sums of
+// integer multiples of fixed grids: both are accumulated exactly in 64-bit
+// integers (two 31-bit halves of each constant, |terms| < 2^38, N <= 49) and
+// rounded once.
+template <typename T>
+__device__ __forceinline__ void crt_row(const int8_t *W, long w_plane, long n_pad, int N, const DevN &d,
+                                        const int32_t *mu, const int32_t *nu, T *C, long ldc, int n, int i, int j0) {
+    constexpr int B = sizeof(T) == 8 ? 64 : 32;
     const int2 *ks = (B == 64 ? c_ks64 : c_ks32) + d.offset;
     const int2 *s1s = c_s1s + d.offset;
-    const int j0 = (blockIdx.x * 256 + threadIdx.x) * 4;
-    if (j0 >= n) return;
-    for (int i = blockIdx.y; i < m; i += gridDim.y) {
-        const int8_t *wp = W + (long)i * n_pad + j0;
-        long long h1[4] = {0, 0, 0, 0}, l1[4] = {0, 0, 0, 0};
-        long long h2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0};
-        for (int l = 0; l < N; l++) {
-            const uint32_t w4 = *reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane);
-            const int2 k = ks[l];
-            const int2 s1 = B == 64 ? s1s[l] : make_int2(0, 0);
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const int w = int(int8_t(uint8_t(w4 >> (8 * e))));
-                l2[e] += (long long)k.x * w;
-                h2[e] += (long long)k.y * w;
-                if (B == 64) {
-                    l1[e] += (long long)s1.x * w;
-                    h1[e] += (long long)s1.y * w;
-                }
-            }
-        }
-        const int mi = mu[i];
+    const int8_t *wp = W + (long)i * n_pad + j0;
+    long long h1[4] = {0, 0, 0, 0}, l1[4] = {0, 0, 0, 0};
+    long long h2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0};
+    for (int l = 0; l < N; l++) {
+        const uint32_t w4 = *reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane);
+        const int2 k = ks[l];
+        const int2 s1 = B == 64 ? s1s[l] : make_int2(0, 0);
 #pragma unroll
         for (int e = 0; e < 4; e++) {
-            const int j = j0 + e;
-            if (j >= n) break;
-            const double c1 = B == 64 ? rn_sum(h1[e], l1[e], d.eg) : rn_sum(h2[e], l2[e], d.esum);
-            const double q = rint(d.Pinv * c1);
-            // b = 32: P2 = 0 and C'(2) = +0, so fma(-q, 0, x + 0) = x + 0 as in the b = 64 form
-            const double cpp = B == 64 ? fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum(h2[e], l2[e], d.esum))
-                                       : fma(-q, d.P1, c1) + 0.0;
-            const double v = scale_pow2(cpp, -(mi + nu[j]));
-            if (B == 64) C[(long)i * ldc + j] = TO(v);
-            else C[(long)i * ldc + j] = TO(__double2float_rn(v));
+            const int w = int(int8_t(uint8_t(w4 >> (8 * e))));
+            l2[e] += (long long)k.x * w;
+            h2[e] += (long long)k.y * w;
+            if (B == 64) {
+                l1[e] += (long long)s1.x * w;
+                h1[e] += (long long)s1.y * w;
+            }
         }
     }
+    const int mi = mu[i];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const int j = j0 + e;
+        if (j >= n) break;
+        const double c1 = B == 64 ? rn_sum(h1[e], l1[e], d.eg) : rn_sum(h2[e], l2[e], d.esum);
+        const double q = rint(d.Pinv * c1);
+        // b = 32: P2 = 0 and C'(2) = +0, so fma(-q, 0, x + 0) = x + 0 as in the b = 64 form
+        const double cpp = B == 64 ? fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum(h2[e], l2[e], d.esum))
+                                   : fma(-q, d.P1, c1) + 0.0;
+        const double v = scale_pow2(cpp, -(mi + nu[j]));
+        if (B == 64) C[(long)i * ldc + j] = T(v);
+        else C[(long)i * ldc + j] = T(__double2float_rn(v));
+    }
+}
+
+// One problem: block (x, y) takes columns 1024 x .. of rows y, y + gridDim.y, ...
+template <typename T>
+__global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, long n_pad, const int *n_dev,
+                                                 const int32_t *mu, const int32_t *nu, T *C, long ldc, int m, int n) {
+    const int N = *n_dev;
+    const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
+    const int j0 = (blockIdx.x * 256 + threadIdx.x) * 4;
+    if (j0 >= n) return;
+    for (int i = blockIdx.y; i < m; i += gridDim.y) crt_row(W, w_plane, n_pad, N, d, mu, nu, C, ldc, n, i, j0);
+}
+
+// A group of problems.  Item: one row, 1024 columns (4 per thread).
+template <typename T>
+__global__ void __launch_bounds__(256) k_crt(const __grid_constant__ JobGroup<T> G) {
+    for_items(G, [&](const JobDesc<T> &jd, long long li) {
+        const unsigned ncb = unsigned(cdiv(jd.n, 1024)), ui = unsigned(li);
+        const int i = int(ui / ncb);
+        const int j0 = int(ui - unsigned(i) * ncb) * 1024 + threadIdx.x * 4;
+        if (j0 >= jd.n) return;
+        const int N = *jd.ndev;
+        const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
+        crt_row(jd.W, jd.w_plane, long(jd.n_pad), N, d, jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0);
+    });
 }
 
 // ============================================================= diagnostics

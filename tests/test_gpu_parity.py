@@ -246,12 +246,21 @@ def test_fast_mode_auto_N(oracle):
 
 @pytest.mark.parametrize("b,N", [(64, 8), (64, 17), (64, 20), (32, 9), (32, 14)])
 def test_vs_fma_chain_reading(oracle, b, N):
-    # the other reading of fl(sum) in Algorithm 3 (fma chains in ascending l):
-    # the GPU's correctly rounded sums stay within ULP_TOL of it
+    # the other reading of fl(sum) in Algorithm 3 (fma chains in ascending l).
+    # DGEMM: C'(1) is exact in both and C'(2) only feeds the last bits, so the
+    # results stay within ULP_TOL.  SGEMM: C'(1) itself differs by up to about
+    # N u_64 rho P (the first term of R_32, Lemma 4), which is many FP32 ulp on
+    # entries far below their row and column maxima; both results must then
+    # satisfy Theorem 2's bound.
     dt = np.float64 if b == 64 else np.float32
     A, Bm = paper_pair(200, 300, 1500, 1.0, seed=N + 100, dtype=dt)
     g = run_gpu(A, Bm, N, fp32=(b == 32))
     A, Bm = A.astype(np.float64), Bm.astype(np.float64)
     r = oracle.os_ii(A, Bm, N, b, mu_in=g["mu"], nu_in=g["nu"], fma_chain=True)
     assert np.array_equal(g["W"], r["W"])
-    assert ulp_distance(g["C"], r["C"], fp32=(b == 32)).max() <= ULP_TOL
+    if b == 64:
+        assert ulp_distance(g["C"], r["C"]).max() <= ULP_TOL
+    else:
+        eb = oracle.bound_from_exponents(A, Bm, g["mu"], g["nu"], r["Ap"], r["Bp"], N, b) + 2.0 ** -150
+        for C in (g["C"], np.asarray(r["C"], np.float64)):
+            assert (np.abs(oracle.exact_residual(A, Bm, C)) <= eb).all()
