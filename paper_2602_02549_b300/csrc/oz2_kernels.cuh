@@ -203,7 +203,6 @@ struct Operand {
 // shared by the host (which fills begin[]) and the kernels (which decode).
 constexpr int kMaxJobs = 64;
 constexpr int kLineBlock = 64;     // lines per k_absmax item
-constexpr int kItemH = 2048;       // h per item of the K-contiguous kernels (256 threads x 8)
 
 template <typename T>
 struct JobDesc {
@@ -259,9 +258,19 @@ __host__ __device__ __forceinline__ long long items_absmax_x(const JobDesc<T> &j
     absmax_geom(j, X, S, C);
     return cdiv(S, kLineBlock) * cdiv(C, absmax_tpl(C) * 8);
 }
+// K-contiguous kernels: threads per row (a multiple of 32 covering k_pad / 8
+// positions, at most 256) and rows per item (256 / threads per row)
+__host__ __device__ __forceinline__ int kc_tpr(int k_pad) { return absmax_tpl(k_pad); }
 template <typename T>
 __host__ __device__ __forceinline__ long long items_kc_x(const JobDesc<T> &j, int X) {
-    return j.op[X].kcontig ? (long long)j.R_pad[X] * cdiv(j.k_pad, kItemH) : 0;
+    if (!j.op[X].kcontig) return 0;
+    const int tpr = kc_tpr(j.k_pad);
+    return cdiv(j.R_pad[X], 256 / tpr) * cdiv(j.k_pad, tpr * 8);
+}
+// CRT: threads per row covering n / 4 columns
+__host__ __device__ __forceinline__ int crt_tpr(int n) {
+    int t = int(cdiv(cdiv(n, 4), 32) * 32);
+    return t < 32 ? 32 : (t > 256 ? 256 : t);
 }
 template <typename T>
 __host__ __device__ __forceinline__ long long items_rc_x(const JobDesc<T> &j, int X) {
@@ -300,7 +309,10 @@ template <typename T> struct Items {
     __host__ __device__ static long long exponents(const JobDesc<T> &j) { return cdiv(j.m + j.n, 2048); }
     __host__ __device__ static long long resid_kc(const JobDesc<T> &j) { return items_kc_x(j, 0) + items_kc_x(j, 1); }
     __host__ __device__ static long long resid_rc(const JobDesc<T> &j) { return items_rc_x(j, 0) + items_rc_x(j, 1); }
-    __host__ __device__ static long long crt(const JobDesc<T> &j) { return (long long)j.m * cdiv(j.n, 1024); }
+    __host__ __device__ static long long crt(const JobDesc<T> &j) {
+        const int tpr = crt_tpr(j.n);
+        return cdiv(j.m, 256 / tpr) * cdiv(j.n, tpr * 4);
+    }
 };
 
 // Calls f(job, local item) for this block's items, in increasing order.
@@ -358,6 +370,7 @@ __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup
         const unsigned ncb = unsigned(cdiv(C, ppi)), ui = unsigned(li);
         const int lb = int(ui / ncb), cb = int(ui - unsigned(lb) * ncb);
         const int ly = threadIdx.x / tpl, tx = threadIdx.x - ly * tpl;
+        if (ly >= lpp) return;                  // 256 % tpl threads left over (whole warps)
         const int c0 = cb * ppi + tx * 8;
         const int s_end = min(S, (lb + 1) * kLineBlock);
         const bool kc = j.op[X].kcontig != 0;
@@ -490,8 +503,9 @@ __device__ __forceinline__ PlaneArgs quant_args(const JobDesc<T> &j, int X) {
                      j.fast ? j.ss[X] : nullptr, !j.fast, j.l1[X]};
 }
 
-// K-contiguous source.  Item: one row, kItemH h (8 per thread).  Every lane
-// stays to the end of the item (the row sums are reduced across the warp).
+// K-contiguous source.  Item: 256 / tpr rows of tpr x 8 h (8 per thread, tpr
+// threads per row; each warp lies in one row).  Every lane stays to the end of
+// the item (the row sums are reduced across the warp).
 template <typename T>
 __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGroup<T> G) {
     for_items(G, [&](const JobDesc<T> &j, long long li) {
@@ -500,8 +514,11 @@ __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGro
         if (li >= n0) { X = 1; li -= n0; }
         const PlaneArgs a = quant_args(j, X);
         const Operand<T> &op = j.op[X];
-        const unsigned nhb = unsigned(cdiv(a.k_pad, kItemH)), ui = unsigned(li);
-        const int r = int(ui / nhb), h0 = int(ui - unsigned(r) * nhb) * kItemH + threadIdx.x * 8;
+        const int tpr = kc_tpr(a.k_pad), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
+        const unsigned nhb = unsigned(cdiv(a.k_pad, tpr * 8)), ui = unsigned(li);
+        const int rb = int(ui / nhb);
+        const int r = rb * (256 / tpr) + ly, h0 = int(ui - unsigned(rb) * nhb) * tpr * 8 + tx * 8;
+        if (ly >= 256 / tpr) return;            // 256 % tpr threads left over (whole warps)
         RowAcc acc{0, 0, 0};
         if (h0 < a.k_pad) {
             if (r >= op.R) {
@@ -712,8 +729,8 @@ __device__ __forceinline__ PlaneArgs resid_args(const JobDesc<T> &j, int X) {
                      j.shift[X], j.ndev, nullptr, 1, nullptr};
 }
 
-// K-contiguous source.  Item: one row, kItemH h: 8 consecutive h per thread
-// (one 16-byte store per plane).
+// K-contiguous source.  Item: 256 / tpr rows of tpr x 8 h: 8 consecutive h per
+// thread (one 16-byte store per plane), tpr threads per row, each warp in one row.
 template <typename T>
 __global__ void __launch_bounds__(256) k_resid_kc(const __grid_constant__ JobGroup<T> G) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
@@ -727,9 +744,11 @@ __global__ void __launch_bounds__(256) k_resid_kc(const __grid_constant__ JobGro
         const Operand<T> &op = j.op[X];
         const int N = *a.n_dev;
         const long pw16 = a.plane / 8;
-        const unsigned nhb = unsigned(cdiv(a.k_pad, kItemH)), ui = unsigned(li);
-        const int r = int(ui / nhb), h0 = int(ui - unsigned(r) * nhb) * kItemH + threadIdx.x * 8;
-        if (h0 >= a.k_pad) return;
+        const int tpr = kc_tpr(a.k_pad), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
+        const unsigned nhb = unsigned(cdiv(a.k_pad, tpr * 8)), ui = unsigned(li);
+        const int rb = int(ui / nhb);
+        const int r = rb * (256 / tpr) + ly, h0 = int(ui - unsigned(rb) * nhb) * tpr * 8 + tx * 8;
+        if (ly >= 256 / tpr || h0 >= a.k_pad) return;   // threads left over; past k_pad
         uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
         if (r >= op.R) {
             for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
@@ -1370,14 +1389,17 @@ __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, 
     for (int i = blockIdx.y; i < m; i += gridDim.y) crt_row(W, w_plane, n_pad, N, d, mu, nu, C, ldc, n, i, j0);
 }
 
-// A group of problems.  Item: one row, 1024 columns (4 per thread).
+// A group of problems.  Item: 256 / tpr rows of tpr x 4 columns (4 per thread,
+// tpr threads per row).
 template <typename T>
-__global__ void __launch_bounds__(256) k_crt(const __grid_constant__ JobGroup<T> G) {
+__global__ void __launch_bounds__(256, 5) k_crt(const __grid_constant__ JobGroup<T> G) {
     for_items(G, [&](const JobDesc<T> &jd, long long li) {
-        const unsigned ncb = unsigned(cdiv(jd.n, 1024)), ui = unsigned(li);
-        const int i = int(ui / ncb);
-        const int j0 = int(ui - unsigned(i) * ncb) * 1024 + threadIdx.x * 4;
-        if (j0 >= jd.n) return;
+        const int tpr = crt_tpr(jd.n), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
+        const unsigned ncb = unsigned(cdiv(jd.n, tpr * 4)), ui = unsigned(li);
+        const int rb = int(ui / ncb);
+        const int i = rb * (256 / tpr) + ly;
+        const int j0 = int(ui - unsigned(rb) * ncb) * tpr * 4 + tx * 4;
+        if (ly >= 256 / tpr || j0 >= jd.n || i >= jd.m) return;
         const int N = *jd.ndev;
         const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
         crt_row(jd.W, jd.w_plane, long(jd.n_pad), N, d, jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0);
