@@ -60,9 +60,13 @@ def load_peaks():
 
 
 def kernel_hash():
-    h = hashlib.sha256()
-    for f in ("oz2_kernels.cuh", "oz2_ptx.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2602_02549_b300", "csrc", f), "rb").read())
+    """Hash of the GEMM kernel's source (its section of oz2_kernels.cuh and the
+    inline-PTX header): the committed traffic figure is used only while it matches."""
+    src = open(os.path.join(ROOT, "paper_2602_02549_b300", "csrc", "oz2_kernels.cuh")).read()
+    i = src.index("// ============================================================= tcgen05 GEMM")
+    j = src.index("// ============================================================= exponents and N")
+    h = hashlib.sha256(src[i:j].encode())
+    h.update(open(os.path.join(ROOT, "paper_2602_02549_b300", "csrc", "oz2_ptx.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
 
