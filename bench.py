@@ -227,6 +227,8 @@ def run_batched(args):
                           fast=args.mode == "fast", n_out=torch.zeros(1, dtype=torch.int32, device=dev)))
         flops += 2.0 * m * n * k
     ws = torch.empty(B.batched_workspace_size(probs), dtype=torch.uint8, device=dev)
+    # tile widths per problem picked by the library's autotuner (outside the capture)
+    policy, policy_ms = B.batched_autotune(probs, workspace=ws)
     assert B.gemm_batched(probs, workspace=ws) == 0
     torch.cuda.synchronize()
     Ns = [int(q["n_out"].item()) for q in probs]
@@ -256,6 +258,9 @@ def run_batched(args):
         "config": {"workload": "batched_64_uneven_128_4096_tau%g_%s" % (tau, args.mode), "problems": 64,
                    "total_2mnk": flops, "target": tau, "graph": "one oz2_gemm_batched call captured"},
         "n_moduli": {"min": min(Ns), "max": max(Ns), "mean": sum(Ns) / len(Ns)},
+        "autotune": {"policy": policy, "ms_per_policy": policy_ms,
+                     "policies": ["all 128x256", "all 128x128", "128x128 where n mod 256 <= 128",
+                                  "per problem, measured alone"]},
         "plain_fixed_N": {"N": Nfix, "ms": ms_plain, "tflops": flops / (ms_plain * 1e-3) / 1e12},
         "mma_tflops_rate": mma / (ms * 1e-3) / 1e12,
         "mma_frac_of_peak": mma / (ms * 1e-3) / 1e12 / float(peaks["bf16_tflops_sustained"])}))

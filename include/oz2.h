@@ -139,6 +139,31 @@ typedef struct oz2_problem {
 
 OZ2_API int oz2_gemm_batched(int count, const oz2_problem *problems, const oz2_opts *opts);
 
+/*
+ * Tile autotuning for oz2_gemm_batched (the paper has no counterpart).  Each
+ * problem's residue GEMMs run with 128 x 256 or 128 x 128 output tiles; the
+ * results are identical either way (the products are exact), only the time
+ * differs.  oz2_batched_autotune runs this batch (the inputs as given, on
+ * opts->stream, with opts->workspace or the library's own) under each policy
+ *   0  every problem 128 x 256
+ *   1  every problem 128 x 128
+ *   2  128 x 128 where n mod 256 is in [1, 128] (less padding), else 128 x 256
+ *   3  per problem, the width that ran faster for that problem alone
+ * with one warm-up and three timed calls each, and keeps the fastest for later
+ * oz2_gemm_batched calls on problems with the same shapes and settings (C is
+ * overwritten by the runs).  It synchronises the stream and must not be
+ * captured into a graph.  *policy (optional): the policy kept; ms (optional,
+ * float[4]): milliseconds per batched call under each policy.  Without a kept
+ * policy a batch runs with policy 0.  Returns OZ2_OK, OZ2_EINVAL, OZ2_ENOMEM,
+ * OZ2_ECUDA or a status of the runs.
+ */
+OZ2_API int oz2_batched_autotune(int count, const oz2_problem *problems, const oz2_opts *opts, int *policy,
+                                 float *ms);
+
+/* Keep policy 0, 1 or 2 (above) for batches with these shapes and settings,
+ * without timing.  Returns OZ2_OK or OZ2_EINVAL. */
+OZ2_API int oz2_batched_set_policy(int count, const oz2_problem *problems, int policy);
+
 /* Workspace bytes of oz2_gemm_batched for these problems (0 if any is invalid). */
 OZ2_API size_t oz2_batched_workspace_size(int count, const oz2_problem *problems);
 

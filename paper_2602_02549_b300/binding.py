@@ -310,3 +310,42 @@ def gemm_batched(problems, *, workspace=None, stream=None, phase_events=None) ->
         o.phase_events = ctypes.cast(ev, ctypes.c_void_p)
     with torch.cuda.device(dev):
         return L.oz2_gemm_batched(len(problems), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(o))
+
+
+def batched_autotune(problems, *, workspace=None, stream=None):
+    """oz2_batched_autotune: times the tile policies on this batch and keeps the
+    fastest for later gemm_batched calls.  Returns (policy, [ms per policy])."""
+    import torch
+    L = lib()
+    L.oz2_batched_autotune.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(oz2_opts),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
+    L.oz2_batched_autotune.restype = ctypes.c_int
+    arr = _problem_array(problems)
+    o = oz2_opts()
+    dev = problems[0]["A"].device
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    o.stream = ctypes.c_void_p(s.cuda_stream)
+    if workspace is None:
+        workspace = torch.empty(max(batched_workspace_size(problems), 256), dtype=torch.uint8, device=dev)
+    o.workspace = ctypes.c_void_p(workspace.data_ptr())
+    o.workspace_bytes = workspace.numel()
+    pol = ctypes.c_int(-1)
+    ms = (ctypes.c_float * 4)()
+    with torch.cuda.device(dev):
+        rc = L.oz2_batched_autotune(len(problems), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(o),
+                                    ctypes.byref(pol), ctypes.cast(ms, ctypes.c_void_p))
+    if rc:
+        raise Oz2Error(rc, "oz2_batched_autotune")
+    return pol.value, [float(x) for x in ms]
+
+
+def batched_set_policy(problems, policy: int) -> int:
+    """oz2_batched_set_policy: keep tile policy 0, 1 or 2 for this batch's shapes."""
+    import torch
+    L = lib()
+    L.oz2_batched_set_policy.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    L.oz2_batched_set_policy.restype = ctypes.c_int
+    arr = _problem_array(problems)
+    with torch.cuda.device(problems[0]["A"].device):
+        return L.oz2_batched_set_policy(len(problems), ctypes.cast(arr, ctypes.c_void_p), int(policy))
+

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "oz2.h"
@@ -30,6 +31,9 @@ struct DeviceState {
     int sms = 0;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    // tile width per problem of a batch, chosen by oz2_batched_autotune (or set
+    // with oz2_batched_set_policy), keyed by the batch's shapes and settings
+    std::unordered_map<uint64_t, std::vector<uint8_t>> tiles;
 };
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
@@ -104,11 +108,14 @@ int ensure_device(int *dev_out) {
         if (e != cudaSuccess) return cuda_fail(e);
     }
     if (!st.smem_attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm<EPI_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(gemm::kSmemBytes));
+        const int s256 = int(gemm::Cfg<256>::kSmemBytes), s128 = int(gemm::Cfg<128>::kSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_gemm<EPI_MOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(gemm::kSmemBytes));
+            e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
         if (e != cudaSuccess) return cuda_fail(e);
         st.smem_attr = true;
     }
@@ -120,11 +127,12 @@ struct Dims {
     int m, n, k, m_pad, n_pad, k_pad, nmax;
 };
 
-Dims make_dims(int m, int n, int k, int nmax) {
+// bn: the GEMM tile width the problem runs with (256 or 128); n is padded to it
+Dims make_dims(int m, int n, int k, int nmax, int bn = gemm::kMaxBN) {
     Dims d;
     d.m = m; d.n = n; d.k = k;
     d.m_pad = int(round_up(size_t(m), gemm::BM));
-    d.n_pad = int(round_up(size_t(n), gemm::BN));
+    d.n_pad = int(round_up(size_t(n), size_t(bn)));
     d.k_pad = int(round_up(size_t(k), gemm::BK));
     d.nmax = nmax;
     return d;
@@ -184,7 +192,7 @@ constexpr int kLightBlocksPerSM = 8;
 
 // One persistent launch over the problems of `G` (item counts filled in here):
 // one CTA per SM, or fewer when there are fewer work items.
-template <int EPI>
+template <int EPI, int BN>
 int launch_gemm(GemmGroup &G, int sms, cudaStream_t st) {
     long long items = 0;
     for (int p = 0; p < G.count; p++) {
@@ -195,7 +203,7 @@ int launch_gemm(GemmGroup &G, int sms, cudaStream_t st) {
     G.total_items = items;
     if (items == 0) return OZ2_OK;
     const int grid = int(std::min<long long>(items, sms));
-    k_gemm<EPI><<<grid, gemm::kThreads, gemm::kSmemBytes, st>>>(G);
+    k_gemm<EPI, BN><<<grid, gemm::kThreads, gemm::Cfg<BN>::kSmemBytes, st>>>(G);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -227,6 +235,7 @@ struct Job {
     static constexpr bool fp32 = sizeof(T) == 4;
     // arguments
     int m = 0, n = 0, k = 0, lda = 0, ldb = 0, ldc = 0, nmoduli = 0, mode = 0, nmax = 0;
+    int bn = gemm::kMaxBN;         // GEMM tile width (n is padded to it)
     const T *A = nullptr, *B = nullptr;
     T *C = nullptr;
     double target = 0.0;
@@ -250,11 +259,12 @@ struct Job {
     bool needs_scale_gemm() const { return !fast() && !inject(); }
 
     void set(int m_, int n_, int k_, const T *A_, int lda_, const T *B_, int ldb_, T *C_, int ldc_, int N_, int mode_,
-             double target_, int nmax_) {
+             double target_, int nmax_, int bn_ = gemm::kMaxBN) {
         m = m_; n = n_; k = k_; A = A_; lda = lda_; B = B_; ldb = ldb_; C = C_; ldc = ldc_;
         nmoduli = N_; mode = mode_; target = target_;
         nmax = N_ ? N_ : (nmax_ ? nmax_ : (fp32 ? 14 : 20));
-        d = make_dims(m, n, k, nmax);
+        bn = bn_;
+        d = make_dims(m, n, k, nmax, bn);
         L = make_layout(d);
     }
 
@@ -294,12 +304,12 @@ struct Job {
     int describe(GemmProblem &P) const {
         int rc = encode_bf16_2d(&P.tmA, resA, uint64_t(nmax) * d.m_pad, uint64_t(d.k_pad), gemm::BM);
         if (rc) return rc;
-        if ((rc = encode_bf16_2d(&P.tmB, resB, uint64_t(nmax) * d.n_pad, uint64_t(d.k_pad), gemm::BN))) return rc;
+        if ((rc = encode_bf16_2d(&P.tmB, resB, uint64_t(nmax) * d.n_pad, uint64_t(d.k_pad), uint32_t(bn)))) return rc;
         P.m_pad = d.m_pad;
         P.n_pad = d.n_pad;
         P.kb_total = d.k_pad / gemm::BK;
         P.tiles_m = d.m_pad / gemm::BM;
-        P.tiles_n = d.n_pad / gemm::BN;
+        P.tiles_n = d.n_pad / bn;
         return OZ2_OK;
     }
     void as_scale_gemm(GemmProblem &P) const {
@@ -422,19 +432,26 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
         return double(d.m_pad) * d.n_pad * d.k_pad * (jobs[p]->nmax + 1);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    // one persistent launch per GEMM phase and tile width
     auto gemms = [&](bool scale) -> int {
-        std::memset(&G, 0, sizeof G);
-        for (int idx = 0; idx < count; idx++) {
-            const Job<T> &job = *jobs[order[idx]];
-            if (scale && !job.needs_scale_gemm()) continue;
-            GemmProblem &P = G.p[G.count++];
-            int r = job.describe(P);
+        for (int bn : {256, 128}) {
+            std::memset(&G, 0, sizeof G);
+            for (int idx = 0; idx < count; idx++) {
+                const Job<T> &job = *jobs[order[idx]];
+                if (job.bn != bn || (scale && !job.needs_scale_gemm())) continue;
+                GemmProblem &P = G.p[G.count++];
+                int r = job.describe(P);
+                if (r) return r;
+                if (scale) job.as_scale_gemm(P);
+                else job.as_residue_gemm(P);
+            }
+            if (!G.count) continue;
+            int r;
+            if (bn == 256) r = scale ? launch_gemm<EPI_MAX, 256>(G, sms, st) : launch_gemm<EPI_MOD, 256>(G, sms, st);
+            else r = scale ? launch_gemm<EPI_MAX, 128>(G, sms, st) : launch_gemm<EPI_MOD, 128>(G, sms, st);
             if (r) return r;
-            if (scale) job.as_scale_gemm(P);
-            else job.as_residue_gemm(P);
         }
-        if (!G.count) return OZ2_OK;
-        return scale ? launch_gemm<EPI_MAX>(G, sms, st) : launch_gemm<EPI_MOD>(G, sms, st);
+        return OZ2_OK;
     };
 
     if ((rc = mark(OZ2_PHASE_STATS))) return rc;
@@ -520,19 +537,52 @@ int validate_problem(const oz2_problem &q) {
     return validate(q.m, q.n, q.k, q.A, q.lda, q.B, q.ldb, q.C, q.ldc, q.nmoduli, q.mode, &o);
 }
 
-// workspace offsets of each problem inside one batch workspace
-size_t batch_layout(int count, const oz2_problem *q, std::vector<Job<double>> &jobs, std::vector<size_t> &off) {
+// workspace offsets of each problem inside one batch workspace (bn: tile width
+// per problem, or null for the widest, which gives the largest layout)
+size_t batch_layout(int count, const oz2_problem *q, std::vector<Job<double>> &jobs, std::vector<size_t> &off,
+                    const std::vector<uint8_t> *bn = nullptr) {
     jobs.resize(size_t(count));
     off.resize(size_t(count));
     size_t total = 0;
     for (int p = 0; p < count; p++) {
+        const int w = bn ? ((*bn)[size_t(p)] ? 128 : 256) : gemm::kMaxBN;
         jobs[p].set(q[p].m, q[p].n, q[p].k, q[p].A, q[p].lda, q[p].B, q[p].ldb, q[p].C, q[p].ldc, q[p].nmoduli,
-                    q[p].mode, q[p].target, q[p].nmax);
+                    q[p].mode, q[p].target, q[p].nmax, w);
         jobs[p].n_out = q[p].n_out;
         off[p] = total;
         total = round_up(total + jobs[p].L.total, 256);
     }
     return total;
+}
+
+// Identity of a batch for the tile cache: every shape and setting of every problem.
+uint64_t batch_key(int count, const oz2_problem *q) {
+    uint64_t h = 1469598103934665603ull;               // FNV-1a over 64-bit words
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; i++) { h ^= (v >> (8 * i)) & 255u; h *= 1099511628211ull; }
+    };
+    mix(uint64_t(count));
+    for (int p = 0; p < count; p++) {
+        uint64_t t;
+        std::memcpy(&t, &q[p].target, 8);
+        mix(uint64_t(uint32_t(q[p].m)) | (uint64_t(uint32_t(q[p].n)) << 32));
+        mix(uint64_t(uint32_t(q[p].k)) | (uint64_t(uint32_t(q[p].nmoduli)) << 32));
+        mix(uint64_t(uint32_t(q[p].nmax)) | (uint64_t(uint32_t(q[p].mode)) << 32));
+        mix(t);
+    }
+    return h;
+}
+
+// Tile-width policies (entry p: 1 = width 128, 0 = width 256).
+constexpr int kPolicies = 4;   // 0 all 256, 1 all 128, 2 narrow ones 128, 3 measured per problem
+std::vector<uint8_t> policy_tiles(int policy, int count, const oz2_problem *q) {
+    std::vector<uint8_t> t;
+    t.resize(size_t(count));
+    for (int p = 0; p < count; p++) {
+        const int r = q[p].n % 256;
+        t[size_t(p)] = policy == 1 ? 1 : (policy == 2 ? uint8_t(r > 0 && r <= 128) : 0);
+    }
+    return t;
 }
 
 int run_batched(int count, const oz2_problem *q, const oz2_opts *o) {
@@ -541,11 +591,17 @@ int run_batched(int count, const oz2_problem *q, const oz2_opts *o) {
     int rc;
     for (int p = 0; p < count; p++)
         if ((rc = validate_problem(q[p]))) return rc;
-    std::vector<Job<double>> jobs;
-    std::vector<size_t> off;
-    const size_t total = batch_layout(count, q, jobs, off);
     int dev = 0;
     if ((rc = ensure_device(&dev))) return rc;
+    std::vector<uint8_t> tiles;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_dev[dev].tiles.find(batch_key(count, q));
+        if (it != g_dev[dev].tiles.end() && int(it->second.size()) == count) tiles = it->second;
+    }
+    std::vector<Job<double>> jobs;
+    std::vector<size_t> off;
+    const size_t total = batch_layout(count, q, jobs, off, tiles.empty() ? nullptr : &tiles);
     cudaStream_t st = o ? static_cast<cudaStream_t>(o->stream) : nullptr;
     uint8_t *ws = nullptr;
     if (o && o->workspace) {
@@ -571,6 +627,103 @@ int run_batched(int count, const oz2_problem *q, const oz2_opts *o) {
         rc = first == 0 ? run_group(ptrs.data(), c, st, sms, mark) : run_group(ptrs.data() + first, c, st, sms, no_mark);
         if (rc) return rc;
     }
+    return OZ2_OK;
+}
+
+// Times each tile policy on this batch (inputs as given, on the caller's
+// stream, synchronising) and keeps the fastest for later oz2_gemm_batched
+// calls with the same shapes.  Policy 3 first times every problem alone with
+// both tile widths and keeps the faster width per problem.
+int autotune_batched(int count, const oz2_problem *q, const oz2_opts *o, int *policy_out, float *ms_out) {
+    if (count <= 0 || !q) return OZ2_EINVAL;
+    int rc;
+    for (int p = 0; p < count; p++)
+        if ((rc = validate_problem(q[p]))) return rc;
+    int dev = 0;
+    if ((rc = ensure_device(&dev))) return rc;
+    oz2_opts oo{};
+    if (o) oo = *o;
+    oo.phase_events = nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(oo.stream);
+    std::vector<Job<double>> jobs;
+    std::vector<size_t> off;
+    const size_t need = batch_layout(count, q, jobs, off);
+    if (!oo.workspace) {
+        uint8_t *ws = nullptr;
+        if ((rc = managed_workspace(dev, need, &ws))) return rc;
+        oo.workspace = ws;
+        oo.workspace_bytes = need;
+    } else if (oo.workspace_bytes < need) {
+        return OZ2_ENOMEM;
+    }
+    const uint64_t key = batch_key(count, q);
+    auto set_tiles = [&](const std::vector<uint8_t> &t) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_dev[dev].tiles[key] = t;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((rc = cuda_fail(cudaEventCreate(&e0))) || (rc = cuda_fail(cudaEventCreate(&e1)))) return rc;
+    // milliseconds per call of fn (one warm-up, then `reps` timed)
+    auto timed = [&](auto &&fn, int reps, float *ms) -> int {
+        int r = fn();
+        if (r) return r;
+        if ((r = cuda_fail(cudaEventRecord(e0, st)))) return r;
+        for (int i = 0; i < reps && !r; i++) r = fn();
+        if (r) return r;
+        if ((r = cuda_fail(cudaEventRecord(e1, st)))) return r;
+        if ((r = cuda_fail(cudaEventSynchronize(e1)))) return r;
+        float t = 0.0f;
+        if ((r = cuda_fail(cudaEventElapsedTime(&t, e0, e1)))) return r;
+        *ms = t / float(reps);
+        return OZ2_OK;
+    };
+    float ms[kPolicies] = {0, 0, 0, 0};
+    std::vector<uint8_t> best_tiles;
+    int best = -1;
+    for (int pol = 0; pol < kPolicies && !rc; pol++) {
+        std::vector<uint8_t> t;
+        if (pol < 3) {
+            t = policy_tiles(pol, count, q);
+        } else {
+            // each problem alone, with each width, in its own slice of the workspace
+            t.resize(size_t(count));
+            for (int p = 0; p < count && !rc; p++) {
+                float w[2] = {0, 0};
+                for (int wi = 0; wi < 2 && !rc; wi++) {
+                    Job<double> job;
+                    job.set(q[p].m, q[p].n, q[p].k, q[p].A, q[p].lda, q[p].B, q[p].ldb, q[p].C, q[p].ldc,
+                            q[p].nmoduli, q[p].mode, q[p].target, q[p].nmax, wi ? 128 : 256);
+                    job.n_out = q[p].n_out;
+                    job.bind(static_cast<uint8_t *>(oo.workspace) + off[size_t(p)]);
+                    Job<double> *one = &job;
+                    auto fn = [&]() { return run_group(&one, 1, st, g_dev[dev].sms, [](int) { return OZ2_OK; }); };
+                    rc = timed(fn, 2, &w[wi]);
+                }
+                t[size_t(p)] = w[1] < w[0] ? 1 : 0;
+            }
+            if (rc) break;
+        }
+        set_tiles(t);
+        auto fn = [&]() { return run_batched(count, q, &oo); };
+        if ((rc = timed(fn, 3, &ms[pol]))) break;
+        if (best < 0 || ms[pol] < ms[best]) { best = pol; best_tiles = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    set_tiles(best_tiles);
+    if (policy_out) *policy_out = best;
+    if (ms_out)
+        for (int i = 0; i < kPolicies; i++) ms_out[i] = ms[i];
+    return OZ2_OK;
+}
+
+int set_batched_policy(int count, const oz2_problem *q, int policy) {
+    if (count <= 0 || !q || policy < 0 || policy > 2) return OZ2_EINVAL;
+    int dev = 0, rc = ensure_device(&dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_dev[dev].tiles[batch_key(count, q)] = policy_tiles(policy, count, q);
     return OZ2_OK;
 }
 
@@ -603,6 +756,15 @@ int oz2_sgemm(int m, int n, int k, const float *A, int lda, const float *B, int 
 
 int oz2_gemm_batched(int count, const oz2_problem *problems, const oz2_opts *opts) {
     return run_batched(count, problems, opts);
+}
+
+int oz2_batched_autotune(int count, const oz2_problem *problems, const oz2_opts *opts, int *policy,
+                         float *ms) {
+    return autotune_batched(count, problems, opts, policy, ms);
+}
+
+int oz2_batched_set_policy(int count, const oz2_problem *problems, int policy) {
+    return set_batched_policy(count, problems, policy);
 }
 
 size_t oz2_batched_workspace_size(int count, const oz2_problem *problems) {

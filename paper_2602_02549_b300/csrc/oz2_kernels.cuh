@@ -824,23 +824,32 @@ __global__ void __launch_bounds__(256) k_resid_rc(const __grid_constant__ JobGro
 
 // ============================================================= tcgen05 GEMM
 namespace gemm {
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BK = 64;
 constexpr int SEG_KB = 16;                       // 1024 K per FP32-exact segment
 constexpr int GROUP_M = 8;                       // raster: 8 row tiles per column sweep
 constexpr int kThreads = 320;                    // w0 TMA, w1 MMA, w2..w9 epilogue
 constexpr int kMaxGroup = 64;                    // problems per launch (kernel parameter space)
-constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t kSmemBytes = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t IDESC = ptx::idesc_bf16_f32<BM, BN>();
+constexpr int kMaxBN = 256;                      // widest tile: the padding of n in the workspace
+constexpr uint32_t A_BYTES = BM * BK * 2;
+// Tile widths BN = 256 (4 stages) and 128 (6 stages) of the same kernel.
+template <int BN>
+struct Cfg {
+    static_assert(BN == 256 || BN == 128, "tile width");
+    static constexpr int STAGES = BN == 256 ? 4 : 6;
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+    static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t kSmemBytes = STAGES * STAGE_BYTES + 1024 + 256;
+    static constexpr uint32_t IDESC = ptx::idesc_bf16_f32<BM, BN>();
+    static constexpr int NC = BN / 2;            // columns per epilogue thread
+};
 }  // namespace gemm
 
 enum { EPI_MAX = 0, EPI_MOD = 1 };
 
 // One GEMM problem of a launch: X_l (rows l*m_pad ..) times Y_l^T for the planes
-// l < planes (and l < *n_dev when n_dev is set), 128 x 256 output tiles.
+// l < planes (and l < *n_dev when n_dev is set), 128 x BN output tiles.
 struct GemmProblem {
-    CUtensorMap tmA, tmB;      // BF16, K-major, 128B-swizzled boxes of 64 x 128 / 64 x 256
+    CUtensorMap tmA, tmB;      // BF16, K-major, 128B-swizzled boxes of 64 x 128 / 64 x BN
     int m_pad, n_pad, kb_total;
     int tiles_m, tiles_n, planes;
     long long item_begin;      // first work item of this problem in the launch
@@ -907,16 +916,16 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
     return __all_sync(0xffffffffu, ok) != 0;
 }
 
-// Epilogue of one output tile for one epilogue thread: 128 INT32 sums of row
-// `row`, columns col0 .. col0+127.
-template <int EPI>
+// Epilogue of one output tile for one epilogue thread: NC INT32 sums of row
+// `row`, columns col0 .. col0+NC-1.
+template <int EPI, int NC>
 __device__ __forceinline__ void tile_epilogue(const GemmProblem &P, int l, int row, int col0, int lane,
-                                              const int (&acc)[128]) {
+                                              const int (&acc)[NC]) {
     if (EPI == EPI_MOD) {
         int8_t *dst = P.W + (long long)l * P.w_plane + (long long)row * P.n_pad + col0;
         if (l == 0) {                            // p = 256: low byte
 #pragma unroll
-            for (int g = 0; g < 8; g++) {
+            for (int g = 0; g < NC / 16; g++) {
                 uint32_t w4[4];
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
@@ -930,7 +939,7 @@ __device__ __forceinline__ void tile_epilogue(const GemmProblem &P, int l, int r
             const uint32_t p = uint32_t(c_p[l]), mg = c_magic[l], c16 = c_c16[l];
             const int hp = int(p >> 1);
 #pragma unroll
-            for (int g = 0; g < 8; g++) {
+            for (int g = 0; g < NC / 16; g++) {
                 uint32_t w4[4];
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
@@ -952,30 +961,36 @@ __device__ __forceinline__ void tile_epilogue(const GemmProblem &P, int l, int r
     } else {
         int rm = 0;
 #pragma unroll
-        for (int i = 0; i < 128; i++) rm = max(rm, acc[i]);
+        for (int i = 0; i < NC; i++) rm = max(rm, acc[i]);
         atomicMax(P.row_max + row, rm);
-        int mine[4] = {0, 0, 0, 0};
+        int mine[NC / 32];
 #pragma unroll
-        for (int c = 0; c < 128; c++) {
+        for (int j = 0; j < NC / 32; j++) mine[j] = 0;
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
             const int v = __reduce_max_sync(0xffffffffu, acc[c]);
             if (lane == (c & 31)) mine[c >> 5] = v;
         }
 #pragma unroll
-        for (int j = 0; j < 4; j++) atomicMax(P.col_max + col0 + j * 32 + lane, mine[j]);
+        for (int j = 0; j < NC / 32; j++) atomicMax(P.col_max + col0 + j * 32 + lane, mine[j]);
     }
 }
 
 // Persistent CTA (one per SM) working through the items g = blockIdx.x,
-// blockIdx.x + gridDim.x, ... of one or more problems.  Each item is a 128 x 256
+// blockIdx.x + gridDim.x, ... of one or more problems.  Each item is a 128 x BN
 // tile of X_l Y_l^T (BF16, K-major, integer-valued).  K runs in segments of
 // <= 1024 elements: each segment starts a fresh FP32 accumulator in TMEM, so
 // every partial sum is an integer of magnitude <= 1024 * 2^14 = 2^24 and exact;
 // the epilogue warps turn each segment into INT32 and add it up.  The shared
 // memory stage ring and the two TMEM accumulators run on across items, so the
 // epilogue of one tile overlaps the MMAs of the next.
-template <int EPI>
+template <int EPI, int BN>
 __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constant__ GemmGroup G) {
     using namespace gemm;
+    using C = Cfg<BN>;
+    constexpr int STAGES = C::STAGES;
+    constexpr uint32_t STAGE_BYTES = C::STAGE_BYTES, IDESC = C::IDESC;
+    constexpr int NC = C::NC;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = ptx::smem_addr(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -999,7 +1014,7 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         ptx::fence_mbar_init();
     }
     if (warp == 1) {
-        ptx::tmem_alloc<512>(ptx::smem_addr(tmem_slot));
+        ptx::tmem_alloc<2 * BN>(ptx::smem_addr(tmem_slot));
         ptx::tmem_relinquish();
     }
     ptx::tc_fence_before();
@@ -1066,7 +1081,7 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         }
     } else {
         const int q = warp & 3;                 // TMEM lanes 32q..32q+31 (warp rank mod 4)
-        const int half = (warp - 2) >> 2;       // columns [128 half, 128 half + 128)
+        const int half = (warp - 2) >> 2;       // columns [NC half, NC half + NC)
         uint32_t segc = 0;
         bool ok = true;
         for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
@@ -1074,16 +1089,16 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
             if (w.skip) continue;
             const GemmProblem &P = G.p[w.p];
             const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
-            int acc[128];
+            int acc[NC];
 #pragma unroll
-            for (int i = 0; i < 128; i++) acc[i] = 0;
+            for (int i = 0; i < NC; i++) acc[i] = 0;
             for (int seg = 0; seg < nseg; seg++, segc++) {
                 const int buf = int(segc & 1u);
                 if (!warp_wait(bar_accf(buf), (segc >> 1) & 1u, abort_flag)) { ok = false; break; }
                 ptx::tc_fence_after();
-                const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + half * 128);
+                const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + half * NC);
 #pragma unroll
-                for (int c = 0; c < 4; c++) {
+                for (int c = 0; c < NC / 32; c++) {
                     uint32_t v[32];
                     ptx::tmem_ld_32x32b_x32(taddr + uint32_t(c * 32), v);
                     ptx::tmem_wait_ld();
@@ -1095,14 +1110,14 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
                 if (lane == 0) ptx::mbar_arrive(bar_acce(buf));
             }
             if (!ok) break;
-            tile_epilogue<EPI>(P, w.l, w.tile_m * BM + q * 32 + lane, w.tile_n * BN + half * 128, lane, acc);
+            tile_epilogue<EPI, NC>(P, w.l, w.tile_m * BM + q * 32 + lane, w.tile_n * BN + half * NC, lane, acc);
         }
     }
     ptx::tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc<512>(tmem);
+        ptx::tmem_dealloc<2 * BN>(tmem);
     }
 }
 

@@ -96,3 +96,41 @@ def test_batched_graph_capture_and_replay():
             C, nout = single_reference(q)
             torch.cuda.synchronize()
             assert torch.equal(q["C"], C) and int(q["n_out"].item()) == int(nout.item())
+
+
+@pytest.mark.parametrize("policy", [1, 2])
+def test_tile_policies_equal_single_calls(policy):
+    # 128 x 128 tiles (all problems, or the narrow ones) give bit-identical results
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    probs = make_problems(7)
+    assert B.batched_set_policy(probs, policy) == 0
+    assert B.gemm_batched(probs) == 0
+    torch.cuda.synchronize()
+    assert B.sync() == 0
+    for q in probs:
+        C, nout = single_reference(q)
+        torch.cuda.synchronize()
+        assert int(q["n_out"].item()) == int(nout.item())
+        assert torch.equal(q["C"], C)
+    assert B.batched_set_policy(probs, 0) == 0
+
+
+def test_autotune_keeps_a_policy_and_results():
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    probs = make_problems(11)
+    policy, ms = B.batched_autotune(probs)
+    assert policy in (0, 1, 2, 3)
+    assert len(ms) == 4 and all(t > 0 for t in ms)
+    assert ms[policy] == min(ms)
+    for q in probs:
+        q["C"].fill_(float("nan"))
+    assert B.gemm_batched(probs) == 0          # runs with the kept policy
+    torch.cuda.synchronize()
+    assert B.sync() == 0
+    for q in probs:
+        C, nout = single_reference(q)
+        torch.cuda.synchronize()
+        assert torch.equal(q["C"], C)
+    assert B.batched_set_policy(probs, 5) == B.OZ2_EINVAL
