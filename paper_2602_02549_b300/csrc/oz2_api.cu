@@ -187,8 +187,9 @@ int encode_bf16_2d(CUtensorMap *tm, const void *base, uint64_t rows, uint64_t co
     return OZ2_OK;
 }
 
-// Resident blocks of 256 threads per SM for the looping light-phase launches.
-constexpr int kLightBlocksPerSM = 8;
+// Resident blocks of 256 threads per SM of the looping residue kernels (their
+// __launch_bounds__ minimum).
+constexpr int kResidBlocksPerSM = 3;
 
 // One persistent launch over the problems of `G` (item counts filled in here):
 // one CTA per SM, or fewer when there are fewer work items.
@@ -412,8 +413,9 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
         return int(std::min<long long>(J.begin[count], cap));
     };
     // one item per block where a block has no setup to amortise; the residue
-    // kernels (which load a 12.5 KB table per block) stay resident and loop
-    const long long one_each = (1ll << 31) - 1, resident = (long long)sms * kLightBlocksPerSM;
+    // kernels (which load a 12.5 KB table per block) stay resident and loop,
+    // kResidBlocksPerSM blocks per SM (their launch bound)
+    const long long one_each = (1ll << 31) - 1, resident = (long long)sms * kResidBlocksPerSM;
     int rc, g;
     auto launched = [&]() { return cuda_fail(cudaGetLastError()); };
 #define OZ2_LAUNCH(kernel, items, cap)                              \

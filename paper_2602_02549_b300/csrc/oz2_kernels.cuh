@@ -732,7 +732,7 @@ __device__ __forceinline__ PlaneArgs resid_args(const JobDesc<T> &j, int X) {
 // K-contiguous source.  Item: 256 / tpr rows of tpr x 8 h: 8 consecutive h per
 // thread (one 16-byte store per plane), tpr threads per row, each warp in one row.
 template <typename T>
-__global__ void __launch_bounds__(256) k_resid_kc(const __grid_constant__ JobGroup<T> G) {
+__global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ JobGroup<T> G) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     load_pow2(pow2, kNMax);
     __syncthreads();
@@ -773,7 +773,7 @@ __device__ __forceinline__ int resid_swz(int hh) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_resid_rc(const __grid_constant__ JobGroup<T> G) {
+__global__ void __launch_bounds__(256, 3) k_resid_rc(const __grid_constant__ JobGroup<T> G) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     __shared__ T tile[64][65];               // [r][swizzled h]
     load_pow2(pow2, kNMax);
