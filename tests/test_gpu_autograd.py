@@ -28,7 +28,8 @@ def test_gradcheck_against_finite_differences():
                                     rtol=1e-6)
 
 
-@pytest.mark.parametrize("shape", [(130, 70, 90), (300, 257, 129)])
+# the last shape is the autograd benchmark's (A 4096 x 2048, B 2048 x 1024)
+@pytest.mark.parametrize("shape", [(130, 70, 90), (300, 257, 129), (4096, 2048, 1024)])
 def test_loss_gradient_matches_fp64(shape):
     # loss = ||A B - T||_F^2: dA = 2 (AB - T) B^T, dB = 2 A^T (AB - T)
     import torch

@@ -134,3 +134,53 @@ def test_autotune_keeps_a_policy_and_results():
         torch.cuda.synchronize()
         assert torch.equal(q["C"], C)
     assert B.batched_set_policy(probs, 5) == B.OZ2_EINVAL
+
+
+def test_batched_benchmark_set(oracle):
+    # the batched benchmark's 64 problems (m, n, k log-uniform in [128, 4096],
+    # phi ~ U(0.5, 4), tau = 1e-14): autotuned tiles, graph-captured call, each
+    # problem bit-identical to its single call; sampled entries of four
+    # problems against the oracle with the single call's exponents
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.inputs import batched_specs, paper_matrix_torch
+    dev = torch.device("cuda", 0)
+    probs = []
+    for i, (m, n, k, phi) in enumerate(batched_specs(64, 0)):
+        probs.append(dict(A=paper_matrix_torch(m, k, phi, 2 * i, dev), B=paper_matrix_torch(k, n, phi, 2 * i + 1, dev),
+                          C=torch.full((m, n), float("nan"), dtype=torch.float64, device=dev), nmoduli=0,
+                          target=1e-14, nmax=30, fast=False, trans_a=False, trans_b=False,
+                          n_out=torch.zeros(1, dtype=torch.int32, device=dev)))
+    ws = torch.empty(B.batched_workspace_size(probs), dtype=torch.uint8, device=dev)
+    B.batched_autotune(probs, workspace=ws)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        assert B.gemm_batched(probs, workspace=ws, stream=s) == 0
+    for q in probs:
+        q["C"].fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert B.sync() == 0
+    rng = np.random.default_rng(3)
+    checked = 0
+    for idx, q in enumerate(probs):
+        m, n = q["C"].shape
+        C = torch.empty_like(q["C"])
+        nout = torch.zeros(1, dtype=torch.int32, device=dev)
+        mu = torch.empty(m, dtype=torch.int32, device=dev)
+        nu = torch.empty(n, dtype=torch.int32, device=dev)
+        assert B.gemm_ex(q["A"], q["B"], C, 0, 0, target=1e-14, nmax=30, n_out=nout, mu_out=mu, nu_out=nu) == 0
+        torch.cuda.synchronize()
+        assert int(q["n_out"].item()) == int(nout.item())
+        assert torch.equal(q["C"], C)
+        if idx % 16 == 0:
+            ii = np.sort(rng.choice(m, size=min(m, 8), replace=False))
+            jj = np.sort(rng.choice(n, size=min(n, 8), replace=False))
+            A_rows = q["A"][ii].cpu().numpy()
+            B_cols = q["B"][:, jj].cpu().numpy()
+            ref = oracle.os_ii_block(A_rows, B_cols, mu.cpu().numpy()[ii], nu.cpu().numpy()[jj], int(nout.item()))
+            got = C.cpu().numpy()[np.ix_(ii, jj)]
+            assert np.abs(got.view(np.int64) - ref.view(np.int64)).max() <= 2
+            checked += 1
+    assert checked == 4

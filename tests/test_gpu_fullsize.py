@@ -118,3 +118,36 @@ def _abar_full(oracle, A, alpha):
 
 def _bbar_full(oracle, B, beta):
     return np.ascontiguousarray(_abar_full(oracle, np.ascontiguousarray(B.T), beta).T)
+
+
+def test_fullsize_sgemm_sampled_entries(oracle):
+    # the SGEMM benchmark's call: 8192^3 FP32, phi = 1, bound rule tau = 1e-7, nmax = 14
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.inputs import paper_matrix_torch
+    dev = torch.device("cuda", 0)
+    s = 8192
+    A = paper_matrix_torch(s, s, 1.0, 0, dev, torch.float32)
+    Bm = paper_matrix_torch(s, s, 1.0, 1, dev, torch.float32)
+    C = torch.empty((s, s), dtype=torch.float32, device=dev)
+    nout = torch.zeros(1, dtype=torch.int32, device=dev)
+    mu = torch.empty(s, dtype=torch.int32, device=dev)
+    nu = torch.empty(s, dtype=torch.int32, device=dev)
+    ws = torch.empty(B.workspace_size(s, s, s, 14, 0, True), dtype=torch.uint8, device=dev)
+    assert B.gemm_ex(A, Bm, C, 0, 0, target=1e-7, nmax=14, workspace=ws, n_out=nout, mu_out=mu, nu_out=nu) == 0
+    torch.cuda.synchronize()
+    assert B.sync() == 0
+    N = int(nout.item())
+    rng = np.random.default_rng(5)
+    ii = _sample(rng, s, 24)
+    jj = _sample(rng, s, 24)
+    A_rows = A[ii].double().cpu().numpy()
+    B_cols = Bm[:, jj].double().cpu().numpy()
+    mu_s, nu_s = mu.cpu().numpy()[ii], nu.cpu().numpy()[jj]
+    ref = oracle.os_ii_block(A_rows, B_cols, mu_s, nu_s, N, 32)
+    got = C.cpu().numpy()[np.ix_(ii, jj)].astype(np.float64)
+    assert ulp_distance(got, ref, fp32=True).max() <= ULP_TOL
+    Ap = oracle.trunc_scaled_rows(A_rows, mu_s)
+    Bp = np.ascontiguousarray(oracle.trunc_scaled_rows(B_cols.T, nu_s).T)
+    eb = oracle.bound_from_exponents(A_rows, B_cols, mu_s, nu_s, Ap, Bp, N, 32) + 2.0 ** -150
+    assert (np.abs(oracle.exact_residual(A_rows, B_cols, got)) <= eb).all()
