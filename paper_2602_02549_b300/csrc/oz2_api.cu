@@ -109,13 +109,15 @@ int ensure_device(int *dev_out) {
     }
     if (!st.smem_attr) {
         const int s256 = int(gemm::Cfg<256>::kSmemBytes), s128 = int(gemm::Cfg<128>::kSmemBytes);
-        cudaError_t e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 256, 1>, a, s256);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 256, 1>, a, s256);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 128, 1>, a, s128);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 128, 1>, a, s128);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 256, gemm::kMaxGroup>, a, s256);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 256, gemm::kMaxGroup>, a, s256);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 128, gemm::kMaxGroup>, a, s128);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 128, gemm::kMaxGroup>, a, s128);
         if (e != cudaSuccess) return cuda_fail(e);
         st.smem_attr = true;
     }
@@ -193,8 +195,8 @@ constexpr int kResidBlocksPerSM = 3;
 
 // One persistent launch over the problems of `G` (item counts filled in here):
 // one CTA per SM, or fewer when there are fewer work items.
-template <int EPI, int BN>
-int launch_gemm(GemmGroup &G, int sms, cudaStream_t st) {
+template <int EPI, int BN, int CAP>
+int launch_gemm(GemmGroup<CAP> &G, int sms, cudaStream_t st) {
     long long items = 0;
     for (int p = 0; p < G.count; p++) {
         GemmProblem &P = G.p[p];
@@ -204,7 +206,7 @@ int launch_gemm(GemmGroup &G, int sms, cudaStream_t st) {
     G.total_items = items;
     if (items == 0) return OZ2_OK;
     const int grid = int(std::min<long long>(items, sms));
-    k_gemm<EPI, BN><<<grid, gemm::kThreads, gemm::Cfg<BN>::kSmemBytes, st>>>(G);
+    k_gemm<EPI, BN, CAP><<<grid, gemm::kThreads, gemm::Cfg<BN>::kSmemBytes, st>>>(G);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -392,11 +394,11 @@ int managed_workspace(int dev, size_t bytes, uint8_t **out) {
 // Every phase of Algorithms 1-3 for a group of at most kMaxJobs problems:
 // each light phase is one launch over the items of all problems, each GEMM one
 // persistent launch over the tiles of all problems (heaviest first).
-template <typename T, class Mark>
+template <typename T, int CAP, class Mark>
 int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&mark) {
-    static_assert(sizeof(JobGroup<T>) < 30000, "kernel parameter space");
-    static thread_local JobGroup<T> J;      // passed by value as the kernel parameter
-    static thread_local GemmGroup G;
+    static_assert(sizeof(JobGroup<T, CAP>) < 30000 && sizeof(GemmGroup<CAP>) < 30000, "kernel parameter space");
+    static thread_local JobGroup<T, CAP> J;      // passed by value as the kernel parameter
+    static thread_local GemmGroup<CAP> G;
     std::memset(&J, 0, sizeof J);
     J.count = count;
     for (int p = 0; p < count; p++) J.j[p] = jobs[p]->desc();
@@ -421,7 +423,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
 #define OZ2_LAUNCH(kernel, items, cap)                              \
     if ((g = plan(Items<T>::items, cap)) < 0) return OZ2_ENOTSUP;   \
     if (g > 0) {                                                    \
-        kernel<T><<<g, 256, 0, st>>>(J);                            \
+        kernel<T, CAP><<<g, 256, 0, st>>>(J);                       \
         if ((rc = launched())) return rc;                           \
     }
     // heaviest problems first: the longest-processing-time order balances the
@@ -449,8 +451,10 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
             }
             if (!G.count) continue;
             int r;
-            if (bn == 256) r = scale ? launch_gemm<EPI_MAX, 256>(G, sms, st) : launch_gemm<EPI_MOD, 256>(G, sms, st);
-            else r = scale ? launch_gemm<EPI_MAX, 128>(G, sms, st) : launch_gemm<EPI_MOD, 128>(G, sms, st);
+            if (bn == 256)
+                r = scale ? launch_gemm<EPI_MAX, 256>(G, sms, st) : launch_gemm<EPI_MOD, 256>(G, sms, st);
+            else
+                r = scale ? launch_gemm<EPI_MAX, 128>(G, sms, st) : launch_gemm<EPI_MOD, 128>(G, sms, st);
             if (r) return r;
         }
         return OZ2_OK;
@@ -519,7 +523,7 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
         return cuda_fail(cudaEventRecord(static_cast<cudaEvent_t>(o->phase_events[phase]), st));
     };
     Job<T> *one = &job;
-    if ((rc = run_group(&one, 1, st, g_dev[dev].sms, mark))) return rc;
+    if ((rc = run_group<T, 1>(&one, 1, st, g_dev[dev].sms, mark))) return rc;
     if (o && o->w_out) {
         // export W_l (test aid): plane l, m x n row-major, from the padded layout
         for (int l = 0; l < job.nmax; l++) {
@@ -626,7 +630,8 @@ int run_batched(int count, const oz2_problem *q, const oz2_opts *o) {
     // groups of kMaxJobs problems, one after another (phase events: first group)
     for (int first = 0; first < count; first += kMaxJobs) {
         const int c = std::min(kMaxJobs, count - first);
-        rc = first == 0 ? run_group(ptrs.data(), c, st, sms, mark) : run_group(ptrs.data() + first, c, st, sms, no_mark);
+        rc = first == 0 ? run_group<double, kMaxJobs>(ptrs.data(), c, st, sms, mark)
+                        : run_group<double, kMaxJobs>(ptrs.data() + first, c, st, sms, no_mark);
         if (rc) return rc;
     }
     return OZ2_OK;
@@ -698,7 +703,9 @@ int autotune_batched(int count, const oz2_problem *q, const oz2_opts *o, int *po
                     job.n_out = q[p].n_out;
                     job.bind(static_cast<uint8_t *>(oo.workspace) + off[size_t(p)]);
                     Job<double> *one = &job;
-                    auto fn = [&]() { return run_group(&one, 1, st, g_dev[dev].sms, [](int) { return OZ2_OK; }); };
+                    auto fn = [&]() {
+                        return run_group<double, 1>(&one, 1, st, g_dev[dev].sms, [](int) { return OZ2_OK; });
+                    };
                     rc = timed(fn, 2, &w[wi]);
                 }
                 t[size_t(p)] = w[1] < w[0] ? 1 : 0;

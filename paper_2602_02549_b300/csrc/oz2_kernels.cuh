@@ -231,11 +231,13 @@ struct JobDesc {
     long zero_vec;                 // its size in 16-byte units
 };
 
-template <typename T>
+// CAP: problems the table holds (1 for a single call, so that each launch
+// passes a small parameter; kMaxJobs for a batch)
+template <typename T, int CAP = kMaxJobs>
 struct JobGroup {
-    JobDesc<T> j[kMaxJobs];
+    JobDesc<T> j[CAP];
     int count;
-    long long begin[kMaxJobs + 1];
+    long long begin[CAP + 1];
 };
 
 __host__ __device__ __forceinline__ long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
@@ -316,8 +318,8 @@ template <typename T> struct Items {
 };
 
 // Calls f(job, local item) for this block's items, in increasing order.
-template <typename T, class F>
-__device__ __forceinline__ void for_items(const JobGroup<T> &G, F &&f) {
+template <typename T, int CAP, class F>
+__device__ __forceinline__ void for_items(const JobGroup<T, CAP> &G, F &&f) {
     const long long total = G.begin[G.count];
     int p = 0;
     for (long long g = blockIdx.x; g < total; g += gridDim.x) {
@@ -326,8 +328,8 @@ __device__ __forceinline__ void for_items(const JobGroup<T> &G, F &&f) {
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_clear(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_clear(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         const long long v = li * 256 + threadIdx.x;
         if (v < j.zero_vec) j.zero[v] = make_uint4(0, 0, 0, 0);
@@ -358,8 +360,8 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 // Item: kLineBlock lines x (threads per line x 8) positions of one operand.
 // Thread (line group ly, position group tx) takes 8 consecutive positions of
 // the lines ly, ly + lines-per-pass, ...; each warp lies in one line group.
-template <typename T>
-__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         int X = 0;
         const long long n0 = items_absmax_x(j, 0);
@@ -506,8 +508,8 @@ __device__ __forceinline__ PlaneArgs quant_args(const JobDesc<T> &j, int X) {
 // K-contiguous source.  Item: 256 / tpr rows of tpr x 8 h (8 per thread, tpr
 // threads per row; each warp lies in one row).  Every lane stays to the end of
 // the item (the row sums are reduced across the warp).
-template <typename T>
-__global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         int X = 0;
         const long long n0 = items_quant_kc_x(j, 0);
@@ -538,8 +540,8 @@ __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGro
 
 // R-contiguous source.  Item: a 64 (h) x 64 (r) tile transposed through
 // shared memory.
-template <typename T>
-__global__ void __launch_bounds__(256) k_quant_rc(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_quant_rc(const __grid_constant__ JobGroup<T, CAP> G) {
     __shared__ T tile[64][65];
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         int X = 0;
@@ -731,8 +733,8 @@ __device__ __forceinline__ PlaneArgs resid_args(const JobDesc<T> &j, int X) {
 
 // K-contiguous source.  Item: 256 / tpr rows of tpr x 8 h: 8 consecutive h per
 // thread (one 16-byte store per plane), tpr threads per row, each warp in one row.
-template <typename T>
-__global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ JobGroup<T, CAP> G) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     load_pow2(pow2, kNMax);
     __syncthreads();
@@ -772,8 +774,8 @@ __device__ __forceinline__ int resid_swz(int hh) {
     return (hh & ~7) | (((((hh >> 1) & 3) ^ ((hh >> 4) & 3))) << 1) | (hh & 1);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 3) k_resid_rc(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256, 3) k_resid_rc(const __grid_constant__ JobGroup<T, CAP> G) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     __shared__ T tile[64][65];               // [r][swizzled h]
     load_pow2(pow2, kNMax);
@@ -859,8 +861,9 @@ struct GemmProblem {
     int *row_max, *col_max;    // EPI_MAX
 };
 
+template <int CAP = gemm::kMaxGroup>
 struct GemmGroup {
-    GemmProblem p[gemm::kMaxGroup];
+    GemmProblem p[CAP];
     int count;
     long long total_items;
 };
@@ -873,7 +876,8 @@ struct WorkItem {
 // Work item g -> (problem, plane, tile).  Planes run in order; inside a plane
 // the tiles go column by column through groups of GROUP_M row tiles, so the
 // CTAs working at the same time share few A and B panels (L2 reuse).
-__device__ __forceinline__ WorkItem decode_item(const GemmGroup &G, long long g) {
+template <int CAP>
+__device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long long g) {
     WorkItem w;
     int p = 0;
     while (p + 1 < G.count && G.p[p + 1].item_begin <= g) p++;
@@ -984,8 +988,8 @@ __device__ __forceinline__ void tile_epilogue(const GemmProblem &P, int l, int r
 // the epilogue warps turn each segment into INT32 and add it up.  The shared
 // memory stage ring and the two TMEM accumulators run on across items, so the
 // epilogue of one tile overlaps the MMAs of the next.
-template <int EPI, int BN>
-__global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constant__ GemmGroup G) {
+template <int EPI, int BN, int CAP>
+__global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constant__ GemmGroup<CAP> G) {
     using namespace gemm;
     using C = Cfg<BN>;
     constexpr int STAGES = C::STAGES;
@@ -1145,8 +1149,8 @@ __device__ __forceinline__ double row_l1(const unsigned long long *l1, const uns
 
 // The maxima that the N rule needs.  Item: 2048 consecutive indices of each
 // of the ranges i < m, j < n, h < k.
-template <typename T>
-__global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         unsigned long long mR = 0, mK = 0, m2a = 0, m2b = 0, mL = 0;
         const int base = int(li) * 2048 + threadIdx.x;
@@ -1202,8 +1206,8 @@ __device__ __forceinline__ int choose_n(const unsigned long long *red, int k, do
 // paper, mu = mu' + floor(fl_down(fma(c, e, P'))).  Item: 2048 of the m + n
 // rows and columns; every item of a problem derives the same N, and item 0
 // publishes it.
-template <typename T>
-__global__ void __launch_bounds__(256) k_exponents(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_exponents(const __grid_constant__ JobGroup<T, CAP> G) {
     constexpr int fp32 = sizeof(T) == 4 ? 1 : 0;
     __shared__ int sN;
     for_items(G, [&](const JobDesc<T> &j, long long li) {
@@ -1245,8 +1249,8 @@ __global__ void __launch_bounds__(256) k_exponents(const __grid_constant__ JobGr
 // row maxima are ceil(sqrt(ssA_i max_j ssB_j)) and column maxima
 // ceil(sqrt(max_i ssA_i ssB_j)).  Lemma 0 only needs Dbar >= Cbar and the
 // maxima <= 2^12 k, which the majorant satisfies.
-template <typename T>
-__global__ void __launch_bounds__(256) k_fast_max(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_fast_max(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         int a = 0, b = 0;
         const int base = int(li) * 2048 + threadIdx.x;
@@ -1272,8 +1276,8 @@ __device__ __forceinline__ int ceil_sqrt_u64(unsigned long long x) {
     return int(r * r == x ? r : r + 1);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_fast_cmax(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_fast_cmax(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         const int *mx = reinterpret_cast<const int *>(j.red + 6);
         const unsigned long long mA = (unsigned long long)mx[0], mB = (unsigned long long)mx[1];
@@ -1406,8 +1410,8 @@ __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, 
 
 // A group of problems.  Item: 256 / tpr rows of tpr x 4 columns (4 per thread,
 // tpr threads per row).
-template <typename T>
-__global__ void __launch_bounds__(256, 5) k_crt(const __grid_constant__ JobGroup<T> G) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256, 5) k_crt(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &jd, long long li) {
         const int tpr = crt_tpr(jd.n), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
         const unsigned ncb = unsigned(cdiv(jd.n, tpr * 4)), ui = unsigned(li);
