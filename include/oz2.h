@@ -201,6 +201,14 @@ OZ2_API int oz2_sum_tables(int N, int fp32, int *k, int *esum);
  * largest |__log2f(x) - log2 x| / (u32 log2 x) seen (a double). */
 OZ2_API int oz2_check_log2f(void *stream, unsigned long long *dev_out);
 
+/* Diagnostic for the device-side failure path: enqueues on `stream` one kernel
+ * whose thread waits, with the loop and status reporting of the GEMM's
+ * bounded waits, on an mbarrier that nothing arrives on, giving up after
+ * limit_us microseconds (1 .. 10^6).  The kernel then returns normally and the
+ * next oz2_sync on that stream reports OZ2_ETIMEOUT (and clears the status).
+ * Returns OZ2_OK, OZ2_EINVAL or OZ2_ECUDA.  No GPU fault is involved. */
+OZ2_API int oz2_wait_selftest(void *stream, unsigned int limit_us);
+
 /* Size of the fixed device scratch used by oz2_gemm_noalloc (32 MiB). */
 #define OZ2_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -112,6 +112,16 @@ def tables(N: int, fp32: bool = False) -> dict:
                 Pprime=np.float32(pp.value))
 
 
+def wait_selftest(limit_us: int = 20000, stream=None) -> int:
+    """oz2_wait_selftest: a bounded device wait that expires on purpose."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    L = lib()
+    L.oz2_wait_selftest.argtypes = [ctypes.c_void_p, ctypes.c_uint]
+    L.oz2_wait_selftest.restype = ctypes.c_int
+    return L.oz2_wait_selftest(ctypes.c_void_p(s.cuda_stream), int(limit_us))
+
+
 def sum_tables(N: int, fp32: bool = False) -> tuple:
     """The CRT-sum constants as the device holds them: (list of k_l, esum) with
     s_l2 (DGEMM) or s_l1 (SGEMM) = k_l 2^esum (host-only)."""

@@ -855,6 +855,14 @@ int oz2_check_log2f(void *stream, unsigned long long *dev_out) {
     return cuda_fail(cudaGetLastError());
 }
 
+int oz2_wait_selftest(void *stream, unsigned int limit_us) {
+    if (limit_us == 0 || limit_us > 1000000u) return OZ2_EINVAL;
+    int dev = 0, rc = ensure_device(&dev);
+    if (rc) return rc;
+    k_wait_selftest<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(uint64_t(limit_us) * 1000ull);
+    return cuda_fail(cudaGetLastError());
+}
+
 int oz2_last_error(int *line) {
     if (line) *line = g_last_cuda_line.load();
     return g_last_cuda_error.load();

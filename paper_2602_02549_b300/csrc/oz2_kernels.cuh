@@ -898,13 +898,14 @@ __device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long lo
     return w;
 }
 
-__device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                             uint64_t limit_ns = kWaitLimitNs) {
     if (ptx::mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = ptx::globaltimer();
     while (true) {
         if (ptx::mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (ptx::globaltimer() - t0 > kWaitLimitNs) {
+        if (ptx::globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(&g_status, 1);
             return false;
@@ -1426,6 +1427,21 @@ __global__ void __launch_bounds__(256, 5) k_crt(const __grid_constant__ JobGroup
 }
 
 // ============================================================= diagnostics
+// The failure path of the bounded waits, without a fault: one thread waits on
+// an mbarrier that nothing arrives on, with the GEMM's wait loop and a limit of
+// limit_ns; the wait gives up, sets the device status word (which oz2_sync
+// turns into OZ2_ETIMEOUT) and the kernel returns normally.
+__global__ void k_wait_selftest(uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    abort_flag = 0;
+    const uint32_t b = ptx::smem_addr(&bar);
+    ptx::mbar_init(b, 1);
+    ptx::fence_mbar_init();
+    bounded_wait(b, 0, &abort_flag, limit_ns);
+}
+
 // Assumption (1), Section 1.2: |log2f(x) - log2 x| <= 4 u32 log2 x, checked
 // for CUDA's __log2f on every FP32 value x that is an integer in [1, 2^29]
 // (the values Dbar can take).  out[0] += violations, out[1] = max ratio
