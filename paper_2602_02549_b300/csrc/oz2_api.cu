@@ -481,7 +481,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     if ((rc = mark(OZ2_PHASE_CRT))) return rc;
     if (count == 1) {
         const JobDesc<T> &j = J.j[0];
-        dim3 grid(unsigned(cdiv(j.n, 1024)), unsigned(std::min(j.m, 65535)));
+        dim3 grid(unsigned(cdiv(j.n, kCrtCols)), unsigned(std::min(j.m, 65535)));
         k_crt_one<T><<<grid, 256, 0, st>>>(j.W, j.w_plane, long(j.n_pad), j.ndev, j.shift[0], j.shift[1], j.C,
                                              j.ldc, j.m, j.n);
         if ((rc = launched())) return rc;

@@ -1316,6 +1316,12 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
     return y * __longlong_as_double((long long)(e2 + 1023) << 52);
 }
 
+// x 2^e for a double x that is 0 or stays normal (an exponent add).
+__device__ __forceinline__ double exp_add(double x, int e) {
+    const long long b = __double_as_longlong(x);
+    return (b << 1) == 0 ? x : __longlong_as_double(b + ((long long)e << 52));
+}
+
 // RN((hi 2^31 + lo) 2^e) as a double, from integer operations only.  Requires
 // |hi|, |lo| < 2^61 and a result in the normal range (the tables check both
 // for every N).  An exact zero gives +0.
@@ -1354,21 +1360,30 @@ __device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
     return __longlong_as_double((long long)bits);
 }
 
-// One row i, columns j0 .. j0+3 of one thread.  C'(1) and C'(2) are sums of
-// integer multiples of fixed grids: both are accumulated exactly in 64-bit
-// integers (two 31-bit halves of each constant, |terms| < 2^38, N <= 49) and
-// rounded once.
-template <typename T>
-__device__ __forceinline__ void crt_row(const int8_t *W, long w_plane, long n_pad, int N, const DevN &d,
-                                        const int32_t *mu, const int32_t *nu, T *C, long ldc, int n, int i, int j0) {
+// One row i, columns j0 .. j0+3 of one thread; load(l) gives the four W_l
+// bytes of those columns.  C'(1) and C'(2) are sums of integer multiples of
+// fixed grids: both are accumulated exactly in 64-bit integers (two 31-bit
+// halves of each constant, |terms| < 2^38, N <= 49) and rounded once.
+template <typename T, typename Load>
+__device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, const int32_t *mu,
+                                        const int32_t *nu, T *C, long ldc, int n, int i, int j0) {
     constexpr int B = sizeof(T) == 8 ? 64 : 32;
     const int2 *ks = (B == 64 ? c_ks64 : c_ks32) + d.offset;
     const int2 *s1s = c_s1s + d.offset;
-    const int8_t *wp = W + (long)i * n_pad + j0;
-    long long h1[4] = {0, 0, 0, 0}, l1[4] = {0, 0, 0, 0};
+    int h1[4] = {0, 0, 0, 0};                  // b = 64: |s1.y W| sums stay below 2^31 (tables)
+    long long l1[4] = {0, 0, 0, 0};
     long long h2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0};
+    // software pipeline: the loads of the next four planes are in flight while
+    // plane l is summed
+    uint32_t wq[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) wq[u] = u < N ? load(u) : 0u;
     for (int l = 0; l < N; l++) {
-        const uint32_t w4 = *reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane);
+        const uint32_t w4 = wq[0];
+        wq[0] = wq[1];
+        wq[1] = wq[2];
+        wq[2] = wq[3];
+        wq[3] = l + 4 < N ? load(l + 4) : 0u;
         const int2 k = ks[l];
         const int2 s1 = B == 64 ? s1s[l] : make_int2(0, 0);
 #pragma unroll
@@ -1378,7 +1393,7 @@ __device__ __forceinline__ void crt_row(const int8_t *W, long w_plane, long n_pa
             h2[e] += (long long)k.y * w;
             if (B == 64) {
                 l1[e] += (long long)s1.x * w;
-                h1[e] += (long long)s1.y * w;
+                h1[e] += s1.y * w;
             }
         }
     }
@@ -1387,7 +1402,10 @@ __device__ __forceinline__ void crt_row(const int8_t *W, long w_plane, long n_pa
     for (int e = 0; e < 4; e++) {
         const int j = j0 + e;
         if (j >= n) break;
-        const double c1 = B == 64 ? rn_sum(h1[e], l1[e], d.eg) : rn_sum(h2[e], l2[e], d.esum);
+        // b = 64: C'(1) = H g with H = s1.y-sum 2^31 + s1.x-sum an integer below
+        // 2^62 (tables): one RN conversion and an exponent add give RN(C'(1))
+        const double c1 = B == 64 ? exp_add(__ll2double_rn(((long long)h1[e] << 31) + l1[e]), d.eg)
+                                  : rn_sum(h2[e], l2[e], d.esum);
         const double q = rint(d.Pinv * c1);
         // b = 32: P2 = 0 and C'(2) = +0, so fma(-q, 0, x + 0) = x + 0 as in the b = 64 form
         const double cpp = B == 64 ? fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum(h2[e], l2[e], d.esum))
@@ -1398,21 +1416,28 @@ __device__ __forceinline__ void crt_row(const int8_t *W, long w_plane, long n_pa
     }
 }
 
-// One problem: block (x, y) takes columns 1024 x .. of rows y, y + gridDim.y, ...
+// One problem: block (x, y) takes columns 1024 x .. 1024 x + 1023 of rows y,
+// y + gridDim.y, ...
+constexpr int kCrtCols = 1024;
 template <typename T>
 __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, long n_pad, const int *n_dev,
                                                  const int32_t *mu, const int32_t *nu, T *C, long ldc, int m, int n) {
     const int N = *n_dev;
     const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
-    const int j0 = (blockIdx.x * 256 + threadIdx.x) * 4;
-    if (j0 >= n) return;
-    for (int i = blockIdx.y; i < m; i += gridDim.y) crt_row(W, w_plane, n_pad, N, d, mu, nu, C, ldc, n, i, j0);
+    const long col0 = (long)blockIdx.x * kCrtCols;
+    const int j0 = int(col0) + threadIdx.x * 4;
+    for (int i = blockIdx.y; i < m; i += gridDim.y) {
+        if (j0 >= n) continue;
+        const int8_t *wp = W + (long)i * n_pad + j0;
+        crt_row<T>([&](int l) { return __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane)); }, N, d,
+                   mu, nu, C, ldc, n, i, j0);
+    }
 }
 
 // A group of problems.  Item: 256 / tpr rows of tpr x 4 columns (4 per thread,
 // tpr threads per row).
 template <typename T, int CAP>
-__global__ void __launch_bounds__(256, 5) k_crt(const __grid_constant__ JobGroup<T, CAP> G) {
+__global__ void __launch_bounds__(256, 4) k_crt(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &jd, long long li) {
         const int tpr = crt_tpr(jd.n), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
         const unsigned ncb = unsigned(cdiv(jd.n, tpr * 4)), ui = unsigned(li);
@@ -1422,7 +1447,10 @@ __global__ void __launch_bounds__(256, 5) k_crt(const __grid_constant__ JobGroup
         if (ly >= 256 / tpr || j0 >= jd.n || i >= jd.m) return;
         const int N = *jd.ndev;
         const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
-        crt_row(jd.W, jd.w_plane, long(jd.n_pad), N, d, jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0);
+        const int8_t *wp = jd.W + (long)i * jd.n_pad + j0;
+        const long wpl = jd.w_plane;
+        crt_row<T>([&](int l) { return __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)); }, N, d,
+                   jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0);
     });
 }
 

@@ -333,6 +333,16 @@ void build(Tables &T) {
             T.s1s[offset + l][0] = int(v & 0x7FFFFFFFu);
             T.s1s[offset + l][1] = int(v >> 31);
         }
+        {   // the CRT kernel sums s1.y W_l in 32 bits and forms H = sum s_l1 W_l / g
+            // in 64: both bounds with |W_l| <= 128
+            long long hy = 0;
+            long double h = 0;
+            for (int l = 0; l < N; l++) {
+                hy += 128ll * T.s1s[offset + l][1];
+                h += 128.0L * (long double)T.s1i[offset + l];
+            }
+            T.sums_fit &= hy < (1ll << 31) && h < 0x1p62L && T.n64[N].eg + 62 < 1023 && T.n64[N].eg > -960;
+        }
         offset += N;
     }
 }

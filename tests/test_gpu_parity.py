@@ -154,6 +154,27 @@ def test_random_integer_residue_products(oracle):
     assert ulp_distance(g["C"], r["C"]).max() <= ULP_TOL
 
 
+@pytest.mark.parametrize("N,b,bits", [(2, 64, 20), (3, 64, 20), (5, 64, 20), (9, 64, 45), (12, 64, 50),
+                                       (2, 32, 20), (3, 32, 20), (5, 32, 20)])
+def test_q_near_half_integers(oracle, N, b, bits):
+    # injected mu = nu = 0 with |A'B'| far above P/2: C' wraps mod P, so
+    # P_inv C'(1) spreads evenly over whole intervals and about one entry in 128
+    # lies within 2^-8 of a half-integer, where the kernel forms Q from the FP64
+    # product instead of its FP32 estimate.  Every entry must still equal the
+    # oracle's (0 ulp: both take the same FP64 steps).
+    m, n, k = 96, 160, 300
+    A = integer_matrix(m, k, -(1 << bits), 1 << bits, seed=N)
+    Bm = integer_matrix(k, n, -(1 << bits), 1 << bits, seed=N + 100)
+    zm, zn = np.zeros(m, np.int32), np.zeros(n, np.int32)
+    g = run_gpu(A, Bm, N, fp32=(b == 32), mu_in=zm, nu_in=zn)
+    r = oracle.os_ii(A, Bm, N, b, mu_in=zm, nu_in=zn)
+    assert np.array_equal(g["W"], r["W"])
+    assert ulp_distance(g["C"], r["C"], fp32=(b == 32)).max() == 0
+    y = oracle.constants(N, b).Pinv * r["C1"]
+    near = np.abs(np.abs(y - np.rint(y)) - 0.5) < 2.0 ** -8
+    assert near.sum() >= 20, "the inputs no longer reach the FP64 branch"
+
+
 def test_wide_exponents_and_zeros(oracle):
     A = wide_exponent_matrix(70, 300, -1060, 400, seed=9, zero_frac=0.3)
     Bm = wide_exponent_matrix(300, 50, -900, 400, seed=10, zero_frac=0.3)
