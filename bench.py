@@ -45,9 +45,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--acc-samples", type=int, default=256)
-    p.add_argument("--workload", default="square", choices=["square", "batched", "autograd", "sgemm"],
+    p.add_argument("--workload", default="square", choices=["square", "batched", "autograd", "sgemm", "splitk"],
                    help="square: the headline DGEMM; batched: 64 uneven problems (one graph-captured call); "
-                        "autograd: loss ||AB - T||^2 forward + backward; sgemm: FP32 emulation")
+                        "autograd: loss ||AB - T||^2 forward + backward; sgemm: FP32 emulation; "
+                        "splitk: k beyond 2^17 (K ranges added in FP64)")
+    p.add_argument("--k", type=int, default=4 << 17, help="splitk: the contraction length")
     p.add_argument("--mode", default="accurate", choices=["accurate", "fast"])
     return p.parse_args()
 
@@ -336,13 +338,55 @@ def run_sgemm(args):
         "native_fp32_tflops": 2.0 * s ** 3 / (ms_native * 1e-3) / 1e12}))
 
 
+def run_splitk(args):
+    """Split-K beyond the paper's k <= 2^17: DGEMM 4096 x 4096 x 2^19 (four K
+    ranges of 2^17, each a full emulation at target / 4, added into C), phi = 1,
+    bound rule for tau = 1e-15."""
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.accuracy import sampled_errors
+    from paper_2602_02549_b300.build import build
+    from paper_2602_02549_b300.inputs import paper_matrix_torch
+    build()
+    dev = torch.device("cuda", 0)
+    m = n = 4096 if args.size == 16384 else args.size
+    k = args.k
+    A = paper_matrix_torch(m, k, args.phi, 0, dev)
+    Bm = paper_matrix_torch(k, n, args.phi, 1, dev)
+    C = torch.empty((m, n), dtype=torch.float64, device=dev)
+    S, kc = B.k_ranges(k)
+    nout = torch.zeros(S, dtype=torch.int32, device=dev)
+    nmax = args.nmoduli or args.nmax
+    ws = torch.empty(B.workspace_size(m, n, k, nmax, 0, False), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    mode = B.OZ2_FAST if args.mode == "fast" else 0
+    fn = lambda: B.gemm_ex(A, Bm, C, args.nmoduli, mode, target=args.target if not args.nmoduli else 0.0,
+                           nmax=args.nmax if not args.nmoduli else 0, workspace=ws, stream=stream, n_out=nout)
+    ms = timed(fn, args.steps, args.warmup, stream)
+    assert B.sync(stream) == 0
+    g = torch.Generator(device="cpu").manual_seed(1234)
+    ns = min(args.acc_samples, 64)
+    ii = torch.randint(0, m, (ns,), generator=g).to(dev)
+    jj = torch.randint(0, n, (ns,), generator=g).to(dev)
+    acc = sampled_errors(A[ii].cpu().numpy(), Bm[:, jj].t().contiguous().cpu().numpy(), C[ii, jj].cpu().numpy())
+    print(json.dumps({
+        "metric": METRIC, "value": 2.0 * m * n * k / (ms * 1e-3) / 1e12, "unit": "TFLOPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "dgemm_splitk_%dx%dx%d_phi%g_tau%g_%s" % (m, n, k, args.phi, args.target, args.mode),
+                   "l2": "inputs larger than L2 (A, B %d GiB each)" % (8 * m * k >> 30)},
+        "k_ranges": S, "range_length": kc, "n_moduli": [int(x) for x in nout.cpu().tolist()],
+        "accuracy": acc}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.workload != "square":
-        {"batched": run_batched, "autograd": run_autograd, "sgemm": run_sgemm}[args.workload](args)
+        {"batched": run_batched, "autograd": run_autograd, "sgemm": run_sgemm,
+         "splitk": run_splitk}[args.workload](args)
         return
     import torch
     from paper_2602_02549_b300 import binding as B

@@ -37,7 +37,8 @@ extern "C" {
 /* status codes */
 #define OZ2_OK          0
 #define OZ2_EINVAL     -1   /* bad dimension, leading dimension, N, mode or null pointer */
-#define OZ2_ERANGE     -2   /* k > 2^17 (Section 3: k <= 2^17 keeps INT32 sums exact)    */
+#define OZ2_ERANGE     -2   /* k > 2^17 in a batched problem (Section 3: k <= 2^17 keeps
+                                the INT32 sums exact; single calls split K instead)      */
 #define OZ2_ENOMEM     -3   /* workspace smaller than oz2_workspace_size()               */
 #define OZ2_ECUDA      -4   /* a CUDA runtime or driver call failed                      */
 #define OZ2_ETIMEOUT   -5   /* a bounded device-side wait gave up (see oz2_sync)         */
@@ -49,7 +50,8 @@ extern "C" {
 #define OZ2_TRANS_A     2
 #define OZ2_TRANS_B     4
 
-/* Limits stated by the paper (Section 3, Algorithm 1). */
+/* Limits stated by the paper (Section 3, Algorithm 1).  Single calls with a
+ * larger k split K into ranges of at most OZ2_K_MAX (oz2_k_ranges). */
 #define OZ2_K_MAX   131072  /* k <= 2^17 */
 #define OZ2_N_MIN   2
 #define OZ2_N_MAX   49      /* p_l <= 256 pairwise coprime, eq. (p_list) */
@@ -77,11 +79,15 @@ typedef struct oz2_opts {
     int32_t *nu_out;         /* optional device int32[n]: the exponents nu                  */
     const int32_t *mu_in;    /* optional device int32[m] and int32[n]: use these exponents  */
     const int32_t *nu_in;    /*   instead of Algorithm 2's (both or neither; needs N > 0)  */
+                             /* k > 2^17 (S K ranges, oz2_k_ranges): n_out int[S], and the
+                                four exponent vectors S of them back to back (range s at
+                                mu_out + s*m, nu_out + s*n, likewise mu_in, nu_in)         */
     int8_t *w_out;           /* optional device int8[N*m*n]: the residue products W_l of
                                 Algorithm 3, plane l at w_out + l*m*n, row-major m x n     */
     void  **phase_events;    /* optional cudaEvent_t[OZ2_NPHASES + 1], created by the
                                 caller: event i is recorded on the stream before phase i,
-                                event OZ2_NPHASES after the last one (for timing)          */
+                                event OZ2_NPHASES after the last one (for timing).
+                                w_out and phase_events: k <= 2^17 only (OZ2_ENOTSUP)       */
 } oz2_opts;
 
 /*
@@ -91,7 +97,14 @@ typedef struct oz2_opts {
  *            0 picks the smallest N in [2, opts->nmax] whose N-dependent part
  *            of the Theorem 2 bound (eq. thm:err-2) is <= opts->target times a
  *            lower bound of max_ij (|A||B|)_ij (requires opts with target > 0).
- *   k        must be <= 2^17 (OZ2_ERANGE otherwise).
+ *   k        up to 2^17 as in the paper (Section 3).  A larger k is split
+ *            into S consecutive K ranges of at most 2^17 (oz2_k_ranges); each
+ *            range is a full OS_II of A[:, range] B[range, :] with its own
+ *            exponents and its own N (the bound rule then targets target / S,
+ *            so the N-dependent parts of the ranges' Theorem 2 bounds add up
+ *            to at most target times the same lower bound of max (|A||B|)),
+ *            and the S results are added into C in range order, one rounding
+ *            in the output precision per addition.
  *   m, n, k  >= 1.
  * oz2_gemm uses the library-managed workspace and the legacy default stream.
  */
@@ -168,9 +181,17 @@ OZ2_API int oz2_batched_set_policy(int count, const oz2_problem *problems, int p
 OZ2_API size_t oz2_batched_workspace_size(int count, const oz2_problem *problems);
 
 /* Bytes of device workspace a call with these sizes needs; nmax is the largest
- * N the call may use (its nmoduli, or opts->nmax when nmoduli == 0).  Returns 0
- * for invalid sizes.  Host-only; touches no GPU. */
+ * N the call may use (its nmoduli, or opts->nmax when nmoduli == 0).  For
+ * k > 2^17 the ranges run one after another in the same workspace (sized for
+ * the longest range).  Returns 0 for invalid sizes.  Host-only; touches no GPU. */
 OZ2_API size_t oz2_workspace_size(int m, int n, int k, int nmax, int mode, int fp32);
+
+/* The split of K that oz2_gemm[_ex] and oz2_sgemm[_ex] use: *count ranges of
+ * *kc consecutive k each (the last one k - (*count - 1) *kc), where S =
+ * ceil(k / 2^17), *kc = 64 ceil(ceil(k / S) / 64) and *count = ceil(k / *kc)
+ * <= S; k <= 2^17 gives one range of k.  Returns OZ2_OK or OZ2_EINVAL (k < 1
+ * or a null pointer).  Host-only. */
+OZ2_API int oz2_k_ranges(int k, int *count, int *kc);
 
 /* Waits for `stream` and reports device-side status collected since the last
  * call: OZ2_ETIMEOUT if a kernel's bounded wait expired (the kernel then

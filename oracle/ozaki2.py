@@ -18,7 +18,10 @@ Readings where the paper is silent (each also listed in the design doc):
     rounding down never crosses the integer below; c*e + P' is exact in FP64.
   * A zero row of A (zero column of B) gets mu' = 0; a row whose Cbar row is
     all zero uses max dbar = 1 (e = 0).  The output there is exactly 0.
-  * C'(1) and C'(2) are fma chains in ascending l from +0.
+  * C'(1) and C'(2) are the exact sums rounded once (fma_chain=True: fma
+    chains in ascending l from +0, the other reading of fl(sum)).
+  * k > 2^17 (outside the paper's assumption, Section 3): split-K, one OS_II
+    per range of consecutive k, results added in range order (os_ii_splitk).
   * The final scaling is one ldexp by -(mu_i + nu_j).  For b = 32 the
     rounding single(C'') of Algorithm 3 is applied after that scaling, which
     changes nothing unless single(C'') would overflow (P > 2^128, N >= 17) or
@@ -292,6 +295,59 @@ def os_ii(A: np.ndarray, B: np.ndarray, N: int, b: int = 64,
     s["C"] = unscale(r["Cpp"], s["mu"], s["nu"], b)
     s["N"], s["b"] = N, b
     return s
+
+
+# --------------------------------------------------------------------------- #
+# Split-K beyond k = 2^17 (an extension; the paper assumes k <= 2^17)
+# --------------------------------------------------------------------------- #
+def splitk_ranges(k: int) -> list[tuple[int, int]]:
+    """Consecutive K ranges [k0, k1): S = ceil(k / 2^17) are wanted, each of
+    kc = 64 ceil(ceil(k / S) / 64) <= 2^17 values except a shorter last one."""
+    if k <= K_MAX:
+        return [(0, k)]
+    S = -(-k // K_MAX)
+    kc = 64 * -(-(-(-k // S)) // 64)
+    return [(k0, min(k, k0 + kc)) for k0 in range(0, k, kc)]
+
+
+def os_ii_splitk(A: np.ndarray, B: np.ndarray, N, b: int = 64, mu_in=None, nu_in=None,
+                 fast: bool = False) -> dict:
+    """C = sum over the K ranges of OS_II(A[:, range], B[range, :]), added in
+    range order in the output precision (FP64 for b = 64, FP32 for b = 32).
+
+    N: one int for every range or a list with one per range; mu_in / nu_in:
+    lists with one vector per range (or None).  Returns C, the per-range
+    results ("parts") and the running sums after each addition ("partial")."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    ranges = splitk_ranges(A.shape[1])
+    Ns = list(N) if isinstance(N, (list, tuple, np.ndarray)) else [int(N)] * len(ranges)
+    parts, partial, C = [], [], None
+    for s, (k0, k1) in enumerate(ranges):
+        r = os_ii(np.ascontiguousarray(A[:, k0:k1]), np.ascontiguousarray(B[k0:k1]), int(Ns[s]), b,
+                  mu_in=None if mu_in is None else mu_in[s], nu_in=None if nu_in is None else nu_in[s],
+                  fast=fast)
+        C = r["C"].copy() if C is None else C + r["C"]   # one rounding per addition
+        parts.append(r)
+        partial.append(C.copy())
+    return dict(C=C, parts=parts, partial=partial, ranges=ranges)
+
+
+def bound_splitk(A: np.ndarray, B: np.ndarray, res: dict, b: int = 64) -> np.ndarray:
+    """Upper bound of |AB - C| for os_ii_splitk's result: the sum of the ranges'
+    bounds (from their exponents) plus u |running sum| for every addition, and
+    half the smallest subnormal per range for underflow."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    u = 2.0 ** -53 if b == 64 else 2.0 ** -24
+    eta = 2.0 ** -1075 if b == 64 else 2.0 ** -150
+    total = np.zeros((A.shape[0], B.shape[1]))
+    for s, ((k0, k1), r) in enumerate(zip(res["ranges"], res["parts"])):
+        As, Bs = A[:, k0:k1], B[k0:k1]
+        total += bound_from_exponents(As, Bs, r["mu"], r["nu"], r["Ap"], r["Bp"], r["N"], b) + eta
+        if s > 0:
+            total += u * np.abs(res["partial"][s].astype(np.float64)) + eta
+    return total * _UP
 
 
 def os_ii_block(A_rows: np.ndarray, B_cols: np.ndarray, mu: np.ndarray, nu: np.ndarray,

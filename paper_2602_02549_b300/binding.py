@@ -69,6 +69,8 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).restype = i
         L.oz2_workspace_size.argtypes = [i, i, i, i, i, i]
         L.oz2_workspace_size.restype = sz
+        L.oz2_k_ranges.argtypes = [i, P, P]
+        L.oz2_k_ranges.restype = i
         L.oz2_sync.argtypes = [P]
         L.oz2_sync.restype = i
         L.oz2_tables.argtypes = [i, i, P, P, P, P]
@@ -96,6 +98,15 @@ def status_str(status: int) -> str:
 
 def workspace_size(m: int, n: int, k: int, nmax: int, mode: int = 0, fp32: bool = False) -> int:
     return int(lib().oz2_workspace_size(m, n, k, nmax, mode, int(fp32)))
+
+
+def k_ranges(k: int) -> tuple[int, int]:
+    """(count, kc): the K ranges a call with this k runs (oz2_k_ranges)."""
+    count, kc = ctypes.c_int(), ctypes.c_int()
+    rc = lib().oz2_k_ranges(int(k), ctypes.addressof(count), ctypes.addressof(kc))
+    if rc:
+        raise Oz2Error(rc, "oz2_k_ranges")
+    return count.value, kc.value
 
 
 def tables(N: int, fp32: bool = False) -> dict:

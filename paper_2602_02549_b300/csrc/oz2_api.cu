@@ -225,8 +225,21 @@ int validate(int m, int n, int k, const void *A, int lda, const void *B, int ldb
     }
     if (o && ((o->mu_in == nullptr) != (o->nu_in == nullptr))) return OZ2_EINVAL;
     if (o && o->mu_in && nmoduli == 0) return OZ2_EINVAL;
-    if (k > OZ2_K_MAX) return OZ2_ERANGE;
     return OZ2_OK;
+}
+
+// Split-K beyond the paper's k <= 2^17 (Section 3: the bound that keeps the INT32
+// sums of Algorithms 2 and 3 exact): S = ceil(k / 2^17) ranges are wanted; each
+// range holds kc = 64 ceil(ceil(k / S) / 64) <= 2^17 consecutive k (the last one
+// fewer), so there are count = ceil(k / kc) <= S of them.  k <= 2^17: one range.
+struct KSplit {
+    int count, kc;
+};
+inline KSplit k_split(int k) {
+    if (k <= OZ2_K_MAX) return KSplit{1, k};
+    const long long S = cdiv(k, OZ2_K_MAX);
+    const int kc = int(round_up(size_t(cdiv(k, S)), 64));
+    return KSplit{int(cdiv(k, kc)), kc};
 }
 
 // ------------------------------------------------------------------ the pipeline
@@ -245,6 +258,7 @@ struct Job {
     int *n_out = nullptr;
     int32_t *mu_out = nullptr, *nu_out = nullptr;
     const int32_t *mu_in = nullptr, *nu_in = nullptr;
+    bool accum = false;            // CRT adds to C (split-K ranges after the first)
     // workspace views
     Dims d{};
     Layout L{};
@@ -346,6 +360,7 @@ struct Job {
         j.nmax = nmax;
         j.fast = fast() ? 1 : 0;
         j.inject = inject() ? 1 : 0;
+        j.accum = accum ? 1 : 0;
         auto aligned = [](const Operand<T> &op) {
             return (reinterpret_cast<uintptr_t>(op.ptr) % 16 == 0 && (op.ld * long(sizeof(T))) % 16 == 0) ? 1 : 0;
         };
@@ -483,7 +498,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
         const JobDesc<T> &j = J.j[0];
         dim3 grid(unsigned(cdiv(j.n, kCrtCols)), unsigned(std::min(j.m, 65535)));
         k_crt_one<T><<<grid, 256, 0, st>>>(j.W, j.w_plane, long(j.n_pad), j.ndev, j.shift[0], j.shift[1], j.C,
-                                             j.ldc, j.m, j.n);
+                                             j.ldc, j.m, j.n, j.accum);
         if ((rc = launched())) return rc;
     } else {
         OZ2_LAUNCH(k_crt, crt, one_each)
@@ -497,15 +512,12 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
         const oz2_opts *o) {
     int rc = validate(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o);
     if (rc) return rc;
+    const KSplit ks = k_split(k);
+    if (ks.count > 1 && o && (o->w_out || o->phase_events)) return OZ2_ENOTSUP;
+    // the workspace is laid out for the longest K range and reused by each range
     Job<T> job;
-    job.set(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o ? o->target : 0.0, o ? o->nmax : 0);
-    if (o) {
-        job.n_out = o->n_out;
-        job.mu_out = o->mu_out;
-        job.nu_out = o->nu_out;
-        job.mu_in = o->mu_in;
-        job.nu_in = o->nu_in;
-    }
+    const double target = o ? o->target / ks.count : 0.0;
+    job.set(m, n, ks.kc, A, lda, B, ldb, C, ldc, nmoduli, mode, target, o ? o->nmax : 0);
     int dev = 0;
     if ((rc = ensure_device(&dev))) return rc;
     cudaStream_t st = o ? static_cast<cudaStream_t>(o->stream) : nullptr;
@@ -517,13 +529,30 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
     } else if ((rc = managed_workspace(dev, job.L.total, &ws))) {
         return rc;
     }
-    job.bind(ws);
     auto mark = [&](int phase) -> int {
         if (!o || !o->phase_events) return OZ2_OK;
         return cuda_fail(cudaEventRecord(static_cast<cudaEvent_t>(o->phase_events[phase]), st));
     };
-    Job<T> *one = &job;
-    if ((rc = run_group<T, 1>(&one, 1, st, g_dev[dev].sms, mark))) return rc;
+    // K range s: A[:, k0:k1] B[k0:k1, :] with its own exponents and N (target / S),
+    // added into C after the first range
+    const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
+    for (int s = 0; s < ks.count; s++) {
+        const int k0 = s * ks.kc, kl = std::min(k - k0, ks.kc);
+        const T *As = ta ? A + size_t(k0) * size_t(lda) : A + k0;
+        const T *Bs = tb ? B + k0 : B + size_t(k0) * size_t(ldb);
+        job.set(m, n, kl, As, lda, Bs, ldb, C, ldc, nmoduli, mode, target, o ? o->nmax : 0);
+        job.accum = s > 0;
+        if (o) {
+            job.n_out = o->n_out ? o->n_out + s : nullptr;
+            job.mu_out = o->mu_out ? o->mu_out + size_t(s) * m : nullptr;
+            job.nu_out = o->nu_out ? o->nu_out + size_t(s) * n : nullptr;
+            job.mu_in = o->mu_in ? o->mu_in + size_t(s) * m : nullptr;
+            job.nu_in = o->nu_in ? o->nu_in + size_t(s) * n : nullptr;
+        }
+        job.bind(ws);
+        Job<T> *one = &job;
+        if ((rc = run_group<T, 1>(&one, 1, st, g_dev[dev].sms, mark))) return rc;
+    }
     if (o && o->w_out) {
         // export W_l (test aid): plane l, m x n row-major, from the padded layout
         for (int l = 0; l < job.nmax; l++) {
@@ -540,7 +569,9 @@ int validate_problem(const oz2_problem &q) {
     oz2_opts o{};
     o.target = q.target;
     o.nmax = q.nmax;
-    return validate(q.m, q.n, q.k, q.A, q.lda, q.B, q.ldb, q.C, q.ldc, q.nmoduli, q.mode, &o);
+    const int rc = validate(q.m, q.n, q.k, q.A, q.lda, q.B, q.ldb, q.C, q.ldc, q.nmoduli, q.mode, &o);
+    if (rc) return rc;
+    return q.k > OZ2_K_MAX ? OZ2_ERANGE : OZ2_OK;   // no split-K inside a batch
 }
 
 // workspace offsets of each problem inside one batch workspace (bn: tile width
@@ -792,8 +823,16 @@ size_t oz2_batched_workspace_size(int count, const oz2_problem *problems) {
 size_t oz2_workspace_size(int m, int n, int k, int nmax, int mode, int fp32) {
     (void)mode;
     (void)fp32;
-    if (m < 1 || n < 1 || k < 1 || k > OZ2_K_MAX || nmax < OZ2_N_MIN || nmax > OZ2_N_MAX) return 0;
-    return make_layout(make_dims(m, n, k, nmax)).total;
+    if (m < 1 || n < 1 || k < 1 || nmax < OZ2_N_MIN || nmax > OZ2_N_MAX) return 0;
+    return make_layout(make_dims(m, n, k_split(k).kc, nmax)).total;
+}
+
+int oz2_k_ranges(int k, int *count, int *kc) {
+    if (k < 1 || !count || !kc) return OZ2_EINVAL;
+    const KSplit s = k_split(k);
+    *count = s.count;
+    *kc = s.kc;
+    return OZ2_OK;
 }
 
 int oz2_sync(void *stream) {
@@ -872,7 +911,7 @@ const char *oz2_status_str(int s) {
     switch (s) {
     case OZ2_OK: return "OZ2_OK";
     case OZ2_EINVAL: return "OZ2_EINVAL: invalid argument";
-    case OZ2_ERANGE: return "OZ2_ERANGE: k exceeds 2^17";
+    case OZ2_ERANGE: return "OZ2_ERANGE: k exceeds 2^17 in a batched problem";
     case OZ2_ENOMEM: return "OZ2_ENOMEM: workspace too small";
     case OZ2_ECUDA: return "OZ2_ECUDA: CUDA call failed";
     case OZ2_ETIMEOUT: return "OZ2_ETIMEOUT: a device-side wait gave up";

@@ -212,6 +212,7 @@ struct JobDesc {
     int m, n, k, k_pad, n_pad;
     int R_pad[2];                  // m_pad, n_pad
     int nmoduli, nmax, fast, inject, vec[2];
+    int accum;                     // CRT adds its result to C (the K ranges after the first)
     double target;
     unsigned long long *hmax[2];   // per-k maxima of |A|, |B|
     unsigned long long *rmax[2];   // per logical row maxima (bits)
@@ -1366,7 +1367,7 @@ __device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
 // halves of each constant, |terms| < 2^38, N <= 49) and rounded once.
 template <typename T, typename Load>
 __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, const int32_t *mu,
-                                        const int32_t *nu, T *C, long ldc, int n, int i, int j0) {
+                                        const int32_t *nu, T *C, long ldc, int n, int i, int j0, bool accum) {
     constexpr int B = sizeof(T) == 8 ? 64 : 32;
     const int2 *ks = (B == 64 ? c_ks64 : c_ks32) + d.offset;
     const int2 *s1s = c_s1s + d.offset;
@@ -1411,8 +1412,9 @@ __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, 
         const double cpp = B == 64 ? fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum(h2[e], l2[e], d.esum))
                                    : fma(-q, d.P1, c1) + 0.0;
         const double v = scale_pow2(cpp, -(mi + nu[j]));
-        if (B == 64) C[(long)i * ldc + j] = T(v);
-        else C[(long)i * ldc + j] = T(__double2float_rn(v));
+        const T c = B == 64 ? T(v) : T(__double2float_rn(v));
+        T *dst = C + (long)i * ldc + j;
+        *dst = accum ? *dst + c : c;            // one rounding per added K range
     }
 }
 
@@ -1421,7 +1423,8 @@ __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, 
 constexpr int kCrtCols = 1024;
 template <typename T>
 __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, long n_pad, const int *n_dev,
-                                                 const int32_t *mu, const int32_t *nu, T *C, long ldc, int m, int n) {
+                                                 const int32_t *mu, const int32_t *nu, T *C, long ldc, int m, int n,
+                                                 int accum) {
     const int N = *n_dev;
     const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
     const long col0 = (long)blockIdx.x * kCrtCols;
@@ -1430,7 +1433,7 @@ __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, 
         if (j0 >= n) continue;
         const int8_t *wp = W + (long)i * n_pad + j0;
         crt_row<T>([&](int l) { return __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane)); }, N, d,
-                   mu, nu, C, ldc, n, i, j0);
+                   mu, nu, C, ldc, n, i, j0, accum != 0);
     }
 }
 
@@ -1450,7 +1453,7 @@ __global__ void __launch_bounds__(256, 4) k_crt(const __grid_constant__ JobGroup
         const int8_t *wp = jd.W + (long)i * jd.n_pad + j0;
         const long wpl = jd.w_plane;
         crt_row<T>([&](int l) { return __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)); }, N, d,
-                   jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0);
+                   jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0, jd.accum != 0);
     });
 }
 

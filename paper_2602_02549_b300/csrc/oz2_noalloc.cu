@@ -52,7 +52,7 @@ extern "C" OZ2_API int oz2_gemm_noalloc(int m, int n, int k, const double *A, in
                                         void *stream) {
     const int nmax = nmoduli ? nmoduli : 20;
     const size_t need = oz2_workspace_size(m, n, k, nmax, mode, 0);
-    if (need == 0) return k > OZ2_K_MAX ? OZ2_ERANGE : OZ2_EINVAL;
+    if (need == 0) return OZ2_EINVAL;
     if (need > size_t(OZ2_NOALLOC_SCRATCH_BYTES)) return OZ2_ENOMEM;   // problem too large for the scratch
     void *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);

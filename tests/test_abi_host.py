@@ -46,7 +46,7 @@ def call(lib, m=8, n=8, k=8, lda=8, ldb=8, ldc=8, N=14, mode=0, opts=None, A=FAK
 
 @pytest.mark.parametrize("fp32", [False, True])
 def test_argument_validation(lib, fp32):
-    E, R = B.OZ2_EINVAL, B.OZ2_ERANGE
+    E = B.OZ2_EINVAL
     assert call(lib, m=0, fp32=fp32) == E
     assert call(lib, n=-1, fp32=fp32) == E
     assert call(lib, k=0, fp32=fp32) == E
@@ -58,7 +58,14 @@ def test_argument_validation(lib, fp32):
     assert call(lib, mode=8, fp32=fp32) == E
     assert call(lib, A=None, fp32=fp32) == E
     assert call(lib, C=None, fp32=fp32) == E
-    assert call(lib, k=(1 << 17) + 1, lda=(1 << 17) + 1, fp32=fp32) == R
+    # k > 2^17 runs as split-K, which exports no W_l and records no phase events
+    K1 = (1 << 17) + 1
+    o = B.oz2_opts()
+    o.w_out = FAKE
+    assert call(lib, k=K1, lda=K1, opts=o, fp32=fp32) == B.OZ2_ENOTSUP
+    o = B.oz2_opts()
+    o.phase_events = FAKE
+    assert call(lib, k=K1, lda=K1, opts=o, fp32=fp32) == B.OZ2_ENOTSUP
     # transposed leading dimensions: A^T is k x m, B^T is n x k
     assert call(lib, m=16, k=8, lda=8, mode=B.OZ2_TRANS_A, ldc=8, fp32=fp32) == E
     assert call(lib, n=16, k=8, ldb=4, ldc=16, mode=B.OZ2_TRANS_B, fp32=fp32) == E
@@ -80,7 +87,10 @@ def test_argument_validation(lib, fp32):
 
 def test_workspace_size(lib):
     assert B.workspace_size(0, 8, 8, 14) == 0
-    assert B.workspace_size(8, 8, (1 << 17) + 1, 14) == 0
+    # k > 2^17: the ranges share one workspace sized for the longest range
+    count, kc = B.k_ranges((1 << 17) + 1)
+    assert (count, kc) == (2, 65600)
+    assert B.workspace_size(8, 8, (1 << 17) + 1, 14) == B.workspace_size(8, 8, kc, 14) > 0
     assert B.workspace_size(8, 8, 8, 1) == 0
     a = B.workspace_size(100, 100, 100, 14)
     b = B.workspace_size(100, 100, 100, 20)
@@ -143,3 +153,18 @@ def test_batched_validation_and_workspace(lib):
     w1 = lib.oz2_batched_workspace_size(1, ctypes.cast(one, ctypes.c_void_p))
     w2 = lib.oz2_batched_workspace_size(2, ctypes.cast(two, ctypes.c_void_p))
     assert w1 >= B.workspace_size(8, 8, 8, 14) and w2 == 2 * w1
+
+
+def test_batched_keeps_the_k_limit(lib):
+    # split-K is for single calls; a batched problem with k > 2^17 is refused
+    P = B.oz2_problem
+    K1 = (1 << 17) + 1
+    big = P(m=8, n=8, k=K1, A=0x10000, lda=K1, B=0x10000, ldb=8, C=0x10000, ldc=8, nmoduli=14, target=0.0,
+            nmax=0, mode=0, n_out=None)
+    lib.oz2_gemm_batched.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.oz2_gemm_batched.restype = ctypes.c_int
+    lib.oz2_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    lib.oz2_batched_workspace_size.restype = ctypes.c_size_t
+    arr = (P * 1)(big)
+    assert lib.oz2_gemm_batched(1, ctypes.cast(arr, ctypes.c_void_p), None) == B.OZ2_ERANGE
+    assert lib.oz2_batched_workspace_size(1, ctypes.cast(arr, ctypes.c_void_p)) == 0
