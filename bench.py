@@ -45,10 +45,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--acc-samples", type=int, default=256)
-    p.add_argument("--workload", default="square", choices=["square", "batched", "autograd", "sgemm", "splitk"],
+    p.add_argument("--workload", default="square",
+                   choices=["square", "batched", "autograd", "sgemm", "splitk", "zgemm"],
                    help="square: the headline DGEMM; batched: 64 uneven problems (one graph-captured call); "
                         "autograd: loss ||AB - T||^2 forward + backward; sgemm: FP32 emulation; "
-                        "splitk: k beyond 2^17 (K ranges added in FP64)")
+                        "splitk: k beyond 2^17 (K ranges added in FP64); zgemm: complex FP64")
     p.add_argument("--k", type=int, default=4 << 17, help="splitk: the contraction length")
     p.add_argument("--mode", default="accurate", choices=["accurate", "fast"])
     return p.parse_args()
@@ -379,6 +380,52 @@ def run_splitk(args):
         "accuracy": acc}))
 
 
+def run_zgemm(args):
+    """Complex FP64 (ZGEMM) 8192^3, real and imaginary parts from Section 5's
+    generator (phi = 1), bound rule for tau = 1e-15 per part; flops 8 m n k."""
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.accuracy import sampled_errors
+    from paper_2602_02549_b300.build import build
+    from paper_2602_02549_b300.inputs import paper_matrix_torch
+    build()
+    dev = torch.device("cuda", 0)
+    s = 8192 if args.size == 16384 else args.size
+    A = torch.complex(paper_matrix_torch(s, s, args.phi, 0, dev), paper_matrix_torch(s, s, args.phi, 1, dev))
+    Bm = torch.complex(paper_matrix_torch(s, s, args.phi, 2, dev), paper_matrix_torch(s, s, args.phi, 3, dev))
+    C = torch.empty((s, s), dtype=torch.complex128, device=dev)
+    nmax = args.nmoduli or args.nmax
+    mode = B.OZ2_FAST if args.mode == "fast" else 0
+    ws = torch.empty(B.zworkspace_size(s, s, s, nmax, mode, False), dtype=torch.uint8, device=dev)
+    nout = torch.zeros(2 * B.k_ranges(2 * s)[0], dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    fn = lambda: B.zgemm_ex(A, Bm, C, args.nmoduli, mode, target=args.target if not args.nmoduli else 0.0,
+                            nmax=args.nmax if not args.nmoduli else 0, workspace=ws, stream=stream, n_out=nout)
+    ms = timed(fn, args.steps, args.warmup, stream)
+    assert B.sync(stream) == 0
+    # accuracy of each part on sampled entries, against the exact real and imaginary parts
+    g = torch.Generator(device="cpu").manual_seed(1234)
+    ns = min(args.acc_samples, 128)
+    ii = torch.randint(0, s, (ns,), generator=g).to(dev)
+    jj = torch.randint(0, s, (ns,), generator=g).to(dev)
+    Ar, Ai = A.real[ii].cpu().numpy(), A.imag[ii].cpu().numpy()
+    Br, Bi = Bm.real[:, jj].t().cpu().numpy(), Bm.imag[:, jj].t().cpu().numpy()
+    Cs = C[ii, jj].cpu().numpy()
+    import numpy as np
+    acc_re = sampled_errors(np.hstack([Ar, Ai]), np.hstack([Br, -Bi]), Cs.real)
+    acc_im = sampled_errors(np.hstack([Ar, Ai]), np.hstack([Bi, Br]), Cs.imag)
+    torch.matmul(A, Bm)
+    ms_native = timed(lambda: torch.matmul(A, Bm), 3, 1, stream)
+    print(json.dumps({
+        "metric": METRIC.replace("DGEMM", "ZGEMM"), "value": 8.0 * s ** 3 / (ms * 1e-3) / 1e12, "unit": "TFLOPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "zgemm_square_%d_phi%g_tau%g_%s" % (s, args.phi, args.target, args.mode),
+                   "flops": "8 m n k"},
+        "n_moduli": [int(x) for x in nout.cpu().tolist()], "accuracy": {"real": acc_re, "imag": acc_im},
+        "native_zgemm_tflops": 8.0 * s ** 3 / (ms_native * 1e-3) / 1e12}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -386,7 +433,7 @@ def main():
         return
     if args.workload != "square":
         {"batched": run_batched, "autograd": run_autograd, "sgemm": run_sgemm,
-         "splitk": run_splitk}[args.workload](args)
+         "splitk": run_splitk, "zgemm": run_zgemm}[args.workload](args)
         return
     import torch
     from paper_2602_02549_b300 import binding as B

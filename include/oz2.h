@@ -49,6 +49,8 @@ extern "C" {
 #define OZ2_FAST        1   /* Cbar replaced by a Cauchy-Schwarz majorant (no extra GEMM)    */
 #define OZ2_TRANS_A     2
 #define OZ2_TRANS_B     4
+#define OZ2_CONJ_A      8   /* complex calls only: op(A) conjugated (with OZ2_TRANS_A: A^H) */
+#define OZ2_CONJ_B     16   /* complex calls only: op(B) conjugated                        */
 
 /* Limits stated by the paper (Section 3, Algorithm 1).  Single calls with a
  * larger k split K into ranges of at most OZ2_K_MAX (oz2_k_ranges). */
@@ -121,6 +123,30 @@ OZ2_API int oz2_sgemm(int m, int n, int k, const float *A, int lda, const float 
                       float *C, int ldc, int nmoduli, int mode);
 OZ2_API int oz2_sgemm_ex(int m, int n, int k, const float *A, int lda, const float *B, int ldb,
                          float *C, int ldc, int nmoduli, int mode, const oz2_opts *opts);
+
+/*
+ * Complex products (ZGEMM: FP64 parts, CGEMM: FP32 parts), C = op(A) op(B) for
+ * interleaved complex matrices (real, imaginary; each pointer aligned to one
+ * complex element, lda/ldb/ldc counted in complex elements).  The paper treats
+ * real products only (complex emulation is left to other work); here a complex
+ * product is two real emulated products over 2k with the same Algorithms 1-3:
+ *   Re C = [Re op(A), Im op(A)] [Re op(B); -Im op(B)],
+ *   Im C = [Re op(A), Im op(A)] [Im op(B);  Re op(B)],
+ * so each part carries the Theorem 2 bound of its real product (k -> 2k, and
+ * 2k > 2^17 runs split-K).  mode: OZ2_FAST, OZ2_TRANS_A/B, OZ2_CONJ_A/B.
+ * opts as for the real calls, applied to both parts (the bound rule targets
+ * opts->target for each part); the exports are per part: n_out int[2S],
+ * mu_out int32[2Sm], nu_out int32[2Sn] (part 0 = Re, then part 1 = Im; S = the
+ * K ranges of 2k), likewise mu_in, nu_in; w_out and phase_events: OZ2_ENOTSUP.
+ * The workspace is oz2_zworkspace_size(...) bytes.  Returns as oz2_gemm_ex.
+ */
+OZ2_API int oz2_zgemm(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
+                      int ldc, int nmoduli, int mode, const oz2_opts *opts);
+OZ2_API int oz2_cgemm(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C,
+                      int ldc, int nmoduli, int mode, const oz2_opts *opts);
+/* Workspace bytes of oz2_zgemm (fp32 = 0) or oz2_cgemm (fp32 = 1); 0 for invalid
+ * sizes.  Host-only. */
+OZ2_API size_t oz2_zworkspace_size(int m, int n, int k, int nmax, int mode, int fp32);
 
 /*
  * Batched emulated DGEMM: many independent problems of uneven shapes, each

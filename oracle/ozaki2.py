@@ -350,6 +350,39 @@ def bound_splitk(A: np.ndarray, B: np.ndarray, res: dict, b: int = 64) -> np.nda
     return total * _UP
 
 
+# --------------------------------------------------------------------------- #
+# Complex products (an extension; the paper's analysis covers real GEMM)
+# --------------------------------------------------------------------------- #
+def complex_parts(A: np.ndarray, B: np.ndarray):
+    """The real operands of a complex product A B (A m x k, B k x n complex):
+    A_s = [Re A, Im A] (m x 2k), B_1 = [Re B; -Im B], B_2 = [Im B; Re B] (2k x n),
+    so that A_s B_1 = Re(A B) and A_s B_2 = Im(A B) exactly."""
+    A = np.asarray(A)
+    B = np.asarray(B)
+    As = np.hstack([A.real, A.imag]).astype(np.float64)
+    B1 = np.vstack([B.real, -B.imag]).astype(np.float64)
+    B2 = np.vstack([B.imag, B.real]).astype(np.float64)
+    return As, B1, B2
+
+
+def os_ii_complex(A: np.ndarray, B: np.ndarray, N, b: int = 64, mu_in=None, nu_in=None,
+                  fast: bool = False) -> dict:
+    """C = A B for complex A, B (already transposed / conjugated as wanted) as
+    two real emulated products over 2k (split-K when 2k > 2^17).  N: an int,
+    or a pair (one per part) of ints or per-range lists; mu_in / nu_in: a pair
+    of per-range lists or None."""
+    As, B1, B2 = complex_parts(A, B)
+    Ns = N if isinstance(N, (list, tuple)) else (N, N)
+    parts = []
+    for p, Bp in enumerate((B1, B2)):
+        parts.append(os_ii_splitk(As, Bp, Ns[p], b, mu_in=None if mu_in is None else mu_in[p],
+                                  nu_in=None if nu_in is None else nu_in[p], fast=fast))
+    dt = np.complex128 if b == 64 else np.complex64
+    C = np.empty(parts[0]["C"].shape, dtype=dt)
+    C.real, C.imag = parts[0]["C"], parts[1]["C"]
+    return dict(C=C, parts=parts, As=As, B1=B1, B2=B2)
+
+
 def os_ii_block(A_rows: np.ndarray, B_cols: np.ndarray, mu: np.ndarray, nu: np.ndarray,
                 N: int, b: int = 64) -> np.ndarray:
     """Entries C_ij for the given rows of A and columns of B with injected mu, nu.

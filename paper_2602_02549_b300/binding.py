@@ -16,6 +16,7 @@ from .build import LIB
 
 OZ2_OK, OZ2_EINVAL, OZ2_ERANGE, OZ2_ENOMEM, OZ2_ECUDA, OZ2_ETIMEOUT, OZ2_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 OZ2_ACCURATE, OZ2_FAST, OZ2_TRANS_A, OZ2_TRANS_B = 0, 1, 2, 4
+OZ2_CONJ_A, OZ2_CONJ_B = 8, 16
 K_MAX, N_MIN, N_MAX = 131072, 2, 49
 NPHASES = 7
 PHASE_NAMES = ("stats", "quant", "scale_gemm", "exponents", "residues", "gemm", "crt")
@@ -71,6 +72,11 @@ def lib() -> ctypes.CDLL:
         L.oz2_workspace_size.restype = sz
         L.oz2_k_ranges.argtypes = [i, P, P]
         L.oz2_k_ranges.restype = i
+        for name in ("oz2_zgemm", "oz2_cgemm"):
+            getattr(L, name).argtypes = gemm_args + [ctypes.POINTER(oz2_opts)]
+            getattr(L, name).restype = i
+        L.oz2_zworkspace_size.argtypes = [i, i, i, i, i, i]
+        L.oz2_zworkspace_size.restype = sz
         L.oz2_sync.argtypes = [P]
         L.oz2_sync.restype = i
         L.oz2_tables.argtypes = [i, i, P, P, P, P]
@@ -222,6 +228,65 @@ def matmul(A, B, nmoduli: int = 0, *, target: float = 1e-15, nmax: int = 0, tran
     rc = gemm_ex(A, B, C, nmoduli, mode, target=target if nmoduli == 0 else 0.0, nmax=nmax, **kw)
     if rc:
         raise Oz2Error(rc, "oz2 gemm")
+    return C
+
+
+def zworkspace_size(m: int, n: int, k: int, nmax: int, mode: int = 0, fp32: bool = False) -> int:
+    return int(lib().oz2_zworkspace_size(m, n, k, nmax, mode, int(fp32)))
+
+
+def zgemm_ex(A, B, C, nmoduli: int = 0, mode: int = 0, *, target: float = 0.0, nmax: int = 0,
+             workspace=None, stream=None, n_out=None, mu_out=None, nu_out=None, mu_in=None, nu_in=None) -> int:
+    """oz2_zgemm / oz2_cgemm on torch complex CUDA tensors (complex128 / complex64,
+    unit column stride); shapes as in gemm_ex.  Returns the status code."""
+    import torch
+    if A.dtype not in (torch.complex64, torch.complex128) or B.dtype != A.dtype or C.dtype != A.dtype:
+        raise TypeError("A, B, C must all be complex128 or all complex64")
+    fp32 = A.dtype == torch.complex64
+    for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+        if not t.is_cuda:
+            raise ValueError(f"{nm} must be a CUDA tensor (no CPU path)")
+    ta, tb = bool(mode & OZ2_TRANS_A), bool(mode & OZ2_TRANS_B)
+    m = A.size(1) if ta else A.size(0)
+    k = A.size(0) if ta else A.size(1)
+    n = B.size(0) if tb else B.size(1)
+    kb = B.size(1) if tb else B.size(0)
+    if kb != k or tuple(C.shape) != (m, n):
+        raise ValueError("shape mismatch")
+    o = oz2_opts()
+    s = stream if stream is not None else torch.cuda.current_stream(A.device)
+    o.stream = ctypes.c_void_p(s.cuda_stream)
+    n_eff = nmoduli if nmoduli else (nmax if nmax else (14 if fp32 else 20))
+    if workspace is None and n_eff >= 2:
+        size = zworkspace_size(m, n, k, n_eff, mode, fp32)
+        if size:
+            workspace = torch.empty(size, dtype=torch.uint8, device=A.device)
+    if workspace is not None:
+        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    o.target = float(target)
+    o.nmax = int(nmax)
+    o.n_out, o.mu_out, o.nu_out = _ptr(n_out), _ptr(mu_out), _ptr(nu_out)
+    o.mu_in, o.nu_in = _ptr(mu_in), _ptr(nu_in)
+    fn = lib().oz2_cgemm if fp32 else lib().oz2_zgemm
+    with torch.cuda.device(A.device):
+        return fn(m, n, k, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), _ptr(C), _ld(C, "C"),
+                  nmoduli, mode, ctypes.byref(o))
+
+
+def zmatmul(A, B, nmoduli: int = 0, *, target: float = 1e-15, nmax: int = 0, trans_a: bool = False,
+            trans_b: bool = False, conj_a: bool = False, conj_b: bool = False, fast: bool = False, out=None, **kw):
+    """C = op(A) @ op(B) for complex tensors through the emulation (raises on any
+    non-OK status); op = transpose and/or conjugate as requested."""
+    import torch
+    m = A.size(1) if trans_a else A.size(0)
+    n = B.size(0) if trans_b else B.size(1)
+    C = out if out is not None else torch.empty((m, n), dtype=A.dtype, device=A.device)
+    mode = ((OZ2_FAST if fast else 0) | (OZ2_TRANS_A if trans_a else 0) | (OZ2_TRANS_B if trans_b else 0) |
+            (OZ2_CONJ_A if conj_a else 0) | (OZ2_CONJ_B if conj_b else 0))
+    rc = zgemm_ex(A, B, C, nmoduli, mode, target=target if nmoduli == 0 else 0.0, nmax=nmax, **kw)
+    if rc:
+        raise Oz2Error(rc, "oz2 complex gemm")
     return C
 
 

@@ -564,6 +564,118 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
     return OZ2_OK;
 }
 
+// ------------------------------------------------------------------ complex
+// ZGEMM / CGEMM: op(A) op(B) for interleaved complex A, B, C as two real
+// emulations over 2k (k_zsplit): Re C = A_s B_1, Im C = A_s B_2 with
+// A_s = [Re op(A), Im op(A)], B_1 = [Re op(B); -Im op(B)], B_2 = [Im op(B); Re op(B)].
+// Transposed operands stay transposed: their real forms are built transposed
+// and handed to the real path with the same OZ2_TRANS_* flag.
+struct ZLayout {
+    size_t As, B1, B2, Cre, Cim, real, total;
+};
+
+template <typename T>
+ZLayout zlayout(int m, int n, int k, int nmax, int mode) {
+    ZLayout z{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = round_up(o + bytes, 256); return at; };
+    const size_t k2 = 2 * size_t(k);
+    z.As = take(sizeof(T) * size_t(m) * k2);
+    z.B1 = take(sizeof(T) * k2 * size_t(n));
+    z.B2 = take(sizeof(T) * k2 * size_t(n));
+    z.Cre = take(sizeof(T) * size_t(m) * size_t(n));
+    z.Cim = take(sizeof(T) * size_t(m) * size_t(n));
+    const size_t real = oz2_workspace_size(m, n, int(k2), nmax, mode, sizeof(T) == 4);
+    z.real = take(real);
+    z.total = real ? o : 0;
+    return z;
+}
+
+int zvalidate(int m, int n, int k, const void *A, int lda, const void *B, int ldb, const void *C, int ldc,
+              int nmoduli, int mode, const oz2_opts *o, size_t esize) {
+    if (m < 1 || n < 1 || k < 1 || k > (1 << 30)) return OZ2_EINVAL;
+    if (!A || !B || !C) return OZ2_EINVAL;
+    if (mode & ~(OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B | OZ2_CONJ_A | OZ2_CONJ_B)) return OZ2_EINVAL;
+    const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
+    if (lda < (ta ? m : k) || ldb < (tb ? k : n) || ldc < n) return OZ2_EINVAL;
+    const size_t al = 2 * esize;
+    if (reinterpret_cast<uintptr_t>(A) % al || reinterpret_cast<uintptr_t>(B) % al ||
+        reinterpret_cast<uintptr_t>(C) % al)
+        return OZ2_EINVAL;
+    if (nmoduli != 0 && (nmoduli < OZ2_N_MIN || nmoduli > OZ2_N_MAX)) return OZ2_EINVAL;
+    if (nmoduli == 0) {
+        if (!o || !(o->target > 0.0)) return OZ2_EINVAL;
+        if (o->nmax != 0 && (o->nmax < OZ2_N_MIN || o->nmax > OZ2_N_MAX)) return OZ2_EINVAL;
+    }
+    if (o && ((o->mu_in == nullptr) != (o->nu_in == nullptr))) return OZ2_EINVAL;
+    if (o && o->mu_in && nmoduli == 0) return OZ2_EINVAL;
+    if (o && (o->w_out || o->phase_events)) return OZ2_ENOTSUP;
+    return OZ2_OK;
+}
+
+template <typename T>
+int run_complex(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, int nmoduli,
+                int mode, const oz2_opts *o) {
+    int rc = zvalidate(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o, sizeof(T));
+    if (rc) return rc;
+    const bool fp32 = sizeof(T) == 4;
+    const int nmax = nmoduli ? nmoduli : (o && o->nmax ? o->nmax : (fp32 ? 14 : 20));
+    const int rmode = mode & (OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B);
+    const ZLayout z = zlayout<T>(m, n, k, nmax, rmode);
+    if (!z.total) return OZ2_EINVAL;
+    int dev = 0;
+    if ((rc = ensure_device(&dev))) return rc;
+    cudaStream_t st = o ? static_cast<cudaStream_t>(o->stream) : nullptr;
+    uint8_t *ws = nullptr;
+    if (o && o->workspace) {
+        if (o->workspace_bytes < z.total) return OZ2_ENOMEM;
+        if (reinterpret_cast<uintptr_t>(o->workspace) & 255u) return OZ2_EINVAL;
+        ws = static_cast<uint8_t *>(o->workspace);
+    } else if ((rc = managed_workspace(dev, z.total, &ws))) {
+        return rc;
+    }
+    const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
+    const int ca = (mode & OZ2_CONJ_A) ? 1 : 0, cb = (mode & OZ2_CONJ_B) ? 1 : 0;
+    T *As = reinterpret_cast<T *>(ws + z.As), *B1 = reinterpret_cast<T *>(ws + z.B1);
+    T *B2 = reinterpret_cast<T *>(ws + z.B2), *Cre = reinterpret_cast<T *>(ws + z.Cre);
+    T *Cim = reinterpret_cast<T *>(ws + z.Cim);
+    const int k2 = 2 * k;
+    auto split = [&](const T *X, int ldx, int R, int L, bool stacked, int im0, int neg0, int im1, int neg1, T *Y,
+                     int ldy) {
+        dim3 grid(unsigned(cdiv(L, 256)), unsigned(std::min(R, 65535)));
+        k_zsplit<T><<<grid, 256, 0, st>>>(X, ldx, R, L, stacked ? 1 : 0, im0, neg0, im1, neg1, Y, ldy);
+        return cuda_fail(cudaGetLastError());
+    };
+    // A_s: m x 2k side by side, or (transposed) 2k x m stacked
+    if ((rc = split(A, lda, ta ? k : m, ta ? m : k, ta, 0, 0, 1, ca, As, ta ? m : k2))) return rc;
+    // B_1 = [Re; -Im op(B)] and B_2 = [Im op(B); Re]: 2k x n stacked, or (transposed) n x 2k side by side
+    const int RB = tb ? n : k, LB = tb ? k : n, ldbs = tb ? k2 : n;
+    if ((rc = split(B, ldb, RB, LB, !tb, 0, 0, 1, cb ? 0 : 1, B1, ldbs))) return rc;
+    if ((rc = split(B, ldb, RB, LB, !tb, 1, cb, 0, 0, B2, ldbs))) return rc;
+    // the two real emulations, one after the other in the shared real workspace
+    const int S = k_split(k2).count;
+    for (int part = 0; part < 2; part++) {
+        oz2_opts r{};
+        r.stream = st;
+        r.workspace = ws + z.real;
+        r.workspace_bytes = z.total - z.real;
+        r.target = o ? o->target : 0.0;
+        r.nmax = o ? o->nmax : 0;
+        if (o) {
+            r.n_out = o->n_out ? o->n_out + size_t(part) * S : nullptr;
+            r.mu_out = o->mu_out ? o->mu_out + size_t(part) * S * m : nullptr;
+            r.nu_out = o->nu_out ? o->nu_out + size_t(part) * S * n : nullptr;
+            r.mu_in = o->mu_in ? o->mu_in + size_t(part) * S * m : nullptr;
+            r.nu_in = o->nu_in ? o->nu_in + size_t(part) * S * n : nullptr;
+        }
+        if ((rc = run<T>(m, n, k2, As, ta ? m : k2, part ? B2 : B1, ldbs, part ? Cim : Cre, n, nmoduli, rmode, &r)))
+            return rc;
+    }
+    dim3 grid(unsigned(cdiv(n, 256)), unsigned(std::min(m, 65535)));
+    k_zmerge<T><<<grid, 256, 0, st>>>(Cre, Cim, n, m, n, C, ldc);
+    return cuda_fail(cudaGetLastError());
+}
+
 // ------------------------------------------------------------------ batches
 int validate_problem(const oz2_problem &q) {
     oz2_opts o{};
@@ -792,6 +904,22 @@ int oz2_sgemm_ex(int m, int n, int k, const float *A, int lda, const float *B, i
 int oz2_sgemm(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
               int nmoduli, int mode) {
     return run<float>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, nullptr);
+}
+
+int oz2_zgemm(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+              int nmoduli, int mode, const oz2_opts *opts) {
+    return run_complex<double>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, opts);
+}
+
+int oz2_cgemm(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+              int nmoduli, int mode, const oz2_opts *opts) {
+    return run_complex<float>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, opts);
+}
+
+size_t oz2_zworkspace_size(int m, int n, int k, int nmax, int mode, int fp32) {
+    if (m < 1 || n < 1 || k < 1 || k > (1 << 30) || nmax < OZ2_N_MIN || nmax > OZ2_N_MAX) return 0;
+    const int rmode = mode & (OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B);
+    return fp32 ? zlayout<float>(m, n, k, nmax, rmode).total : zlayout<double>(m, n, k, nmax, rmode).total;
 }
 
 int oz2_gemm_batched(int count, const oz2_problem *problems, const oz2_opts *opts) {

@@ -1457,6 +1457,51 @@ __global__ void __launch_bounds__(256, 4) k_crt(const __grid_constant__ JobGroup
     });
 }
 
+// ============================================================= complex operands
+// A complex product as two real ones: with A_s = [Re op(A), Im op(A)] (m x 2k),
+//   Re C = A_s [Re op(B); -Im op(B)],   Im C = A_s [Im op(B); Re op(B)],
+// each one real emulated GEMM over 2k.  k_zsplit copies an interleaved complex
+// matrix X (R x L complex, row stride ldx complex) into a real one whose rows
+// hold two halves, each the real or the imaginary part of X with a sign:
+// side by side (row r = [half 0 of row r, half 1 of row r], R x 2L) or stacked
+// (rows r and R + r, 2R x L).  X is 2 sizeof(T)-aligned (checked on the host).
+template <typename T>
+struct Cplx;
+template <>
+struct Cplx<double> { using V = double2; };
+template <>
+struct Cplx<float> { using V = float2; };
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_zsplit(const T *X, long ldx, int R, int L, int stacked, int im0, int neg0,
+                                                int im1, int neg1, T *Y, long ldy) {
+    using V = typename Cplx<T>::V;
+    const int c = blockIdx.x * 256 + threadIdx.x;
+    if (c >= L) return;
+    for (int r = blockIdx.y; r < R; r += gridDim.y) {
+        const V x = reinterpret_cast<const V *>(X)[(long)r * ldx + c];
+        const T h0 = im0 ? x.y : x.x, h1 = im1 ? x.y : x.x;
+        T *row = Y + (long)r * ldy;
+        row[c] = neg0 ? -h0 : h0;
+        if (stacked) Y[(long)(R + r) * ldy + c] = neg1 ? -h1 : h1;
+        else row[L + c] = neg1 ? -h1 : h1;
+    }
+}
+
+// C (m x n complex, row stride ldc complex) = Re + i Im (both m x n real, ld).
+template <typename T>
+__global__ void __launch_bounds__(256) k_zmerge(const T *Re, const T *Im, long ld, int m, int n, T *C, long ldc) {
+    using V = typename Cplx<T>::V;
+    const int j = blockIdx.x * 256 + threadIdx.x;
+    if (j >= n) return;
+    for (int i = blockIdx.y; i < m; i += gridDim.y) {
+        V v;
+        v.x = Re[(long)i * ld + j];
+        v.y = Im[(long)i * ld + j];
+        reinterpret_cast<V *>(C)[(long)i * ldc + j] = v;
+    }
+}
+
 // ============================================================= diagnostics
 // The failure path of the bounded waits, without a fault: one thread waits on
 // an mbarrier that nothing arrives on, with the GEMM's wait loop and a limit of
