@@ -279,9 +279,13 @@ template <typename T>
 __host__ __device__ __forceinline__ long long items_rc_x(const JobDesc<T> &j, int X) {
     return j.op[X].kcontig ? 0 : (long long)(j.k_pad / 64) * (j.R_pad[X] / 64);
 }
+// quantisation of K-contiguous rows: kQuantGroups chunks of tpr x 8 h per item
+constexpr int kQuantGroups = 4;
 template <typename T>
 __host__ __device__ __forceinline__ long long items_quant_kc_x(const JobDesc<T> &j, int X) {
-    return j.inject ? 0 : items_kc_x(j, X);
+    if (j.inject || !j.op[X].kcontig) return 0;
+    const int tpr = kc_tpr(j.k_pad);
+    return cdiv(j.R_pad[X], 256 / tpr) * cdiv(j.k_pad, tpr * 8 * kQuantGroups);
 }
 template <typename T>
 __host__ __device__ __forceinline__ long long items_quant_rc_x(const JobDesc<T> &j, int X) {
@@ -479,6 +483,60 @@ __device__ __forceinline__ void flush_row(const PlaneArgs &a, RowAcc acc, int r,
     }
 }
 
+// One element of the quantisation from the bits of x: q = ceil(2^shift |x|)
+// and the 1-norm term floor(|x| 2^(shift+57)) as 32-bit halves (vhi, vlo).
+// A normal double takes 32-bit integer steps: |x| 2^shift = M 2^-r < 64 with
+// the 53-bit significand M >= 2^52 puts r >= 47, so the integer part of M 2^-r
+// lies in the significand's top word.  Zeros, subnormals and FP32 inputs take
+// the general path (ceil_scaled_abs, add_scaled_abs).
+template <typename T>
+__device__ __forceinline__ void quant_elem(T x, int shift, uint32_t &q, uint32_t &vhi, uint32_t &vlo) {
+    if constexpr (sizeof(T) == 8) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+        const uint32_t hi = uint32_t(b >> 32), lo = uint32_t(b);
+        const int ex = int((hi >> 20) & 0x7FFu);
+        const int r = 1075 - ex - shift;
+        if (ex != 0 && ex != 0x7FF && r >= 47) {
+            const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;   // M = mh 2^32 + lo
+            const int rr = r - 32;                              // >= 15
+            if (rr >= 32) {
+                q = 1u;
+            } else {
+                const uint32_t rest = (mh & ((1u << rr) - 1u)) | lo;
+                q = (mh >> rr) + (rest != 0u ? 1u : 0u);
+            }
+            if (r <= 57) {                                      // M << (57 - r), at most 10 bits
+                const int s = 57 - r;
+                vhi = __funnelshift_l(lo, mh, s);
+                vlo = lo << s;
+            } else {
+                const int t = r - 57;
+                if (t < 32) {
+                    vlo = __funnelshift_r(lo, mh, t);
+                    vhi = mh >> t;
+                } else {
+                    vlo = t < 64 ? mh >> (t - 32) : 0u;
+                    vhi = 0u;
+                }
+            }
+            return;
+        }
+    }
+    q = ceil_scaled_abs(x, shift);
+    RowAcc t{0, 0, 0};
+    add_scaled_abs(t, x, shift);
+    vhi = uint32_t(t.hi);
+    vlo = uint32_t(t.lo);
+}
+
+// BF16 of two integers in [0, 127] (exact): the FP32 value of 2^23 + q minus
+// 2^23 is q, and its top 16 bits are the BF16 encoding.
+__device__ __forceinline__ uint32_t pack_bf16x2_small(uint32_t a, uint32_t b) {
+    const float fa = __fsub_rn(__uint_as_float(0x4B000000u | a), 8388608.0f);
+    const float fb = __fsub_rn(__uint_as_float(0x4B000000u | b), 8388608.0f);
+    return __byte_perm(__float_as_uint(fa), __float_as_uint(fb), 0x7632);
+}
+
 // Stores 8 values of Abar (accurate mode) and adds to the row sums.
 template <typename T>
 __device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8], int shift, int r, int h0,
@@ -486,16 +544,18 @@ __device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8],
     uint32_t q[8];
 #pragma unroll
     for (int e = 0; e < 8; e++) {
-        q[e] = ceil_scaled_abs(x[e], shift);
+        uint32_t vh, vl;
+        quant_elem(x[e], shift, q[e], vh, vl);
         acc.ss += int(q[e] * q[e]);
-        add_scaled_abs(acc, x[e], shift);
+        acc.hi += vh;
+        acc.lo += vl;
     }
     if (a.write) {
         uint4 v;
-        v.x = pack_bf16x2(q[0], q[1]);
-        v.y = pack_bf16x2(q[2], q[3]);
-        v.z = pack_bf16x2(q[4], q[5]);
-        v.w = pack_bf16x2(q[6], q[7]);
+        v.x = pack_bf16x2_small(q[0], q[1]);
+        v.y = pack_bf16x2_small(q[2], q[3]);
+        v.z = pack_bf16x2_small(q[4], q[5]);
+        v.w = pack_bf16x2_small(q[6], q[7]);
         *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = v;
     }
 }
@@ -518,24 +578,29 @@ __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGro
         const PlaneArgs a = quant_args(j, X);
         const Operand<T> &op = j.op[X];
         const int tpr = kc_tpr(a.k_pad), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
-        const unsigned nhb = unsigned(cdiv(a.k_pad, tpr * 8)), ui = unsigned(li);
+        const unsigned nhb = unsigned(cdiv(a.k_pad, tpr * 8 * kQuantGroups)), ui = unsigned(li);
         const int rb = int(ui / nhb);
-        const int r = rb * (256 / tpr) + ly, h0 = int(ui - unsigned(rb) * nhb) * tpr * 8 + tx * 8;
+        const int r = rb * (256 / tpr) + ly;
+        const int hb = int(ui - unsigned(rb) * nhb) * tpr * 8 * kQuantGroups + tx * 8;
         if (ly >= 256 / tpr) return;            // 256 % tpr threads left over (whole warps)
         RowAcc acc{0, 0, 0};
-        if (h0 < a.k_pad) {
-            if (r >= op.R) {
+        const bool live = r < op.R;
+        const int shift = live ? quant_shift(a.row_max, r) : 0;
+#pragma unroll 2
+        for (int g = 0; g < kQuantGroups; g++) {
+            const int h0 = hb + g * tpr * 8;    // each chunk coalesced across the row's threads
+            if (h0 >= a.k_pad) break;
+            if (!live) {
                 if (a.write) *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
-            } else {
-                const int shift = quant_shift(a.row_max, r);
-                T x[8];
-                const T *src = op.ptr + (long)r * op.ld + h0;
-#pragma unroll
-                for (int e = 0; e < 8; e++) x[e] = (h0 + e < a.k) ? src[e] : T(0);
-                emit_quant8(a, x, shift, r, h0, acc);
+                continue;
             }
+            T x[8];
+            const T *src = op.ptr + (long)r * op.ld + h0;
+#pragma unroll
+            for (int e = 0; e < 8; e++) x[e] = (h0 + e < a.k) ? src[e] : T(0);
+            emit_quant8(a, x, shift, r, h0, acc);
         }
-        flush_row(a, acc, r, 32, r < op.R);
+        flush_row(a, acc, r, 32, live);
     });
 }
 
