@@ -161,6 +161,24 @@ def cpu_baseline(A_host, B_host, N: int, sample: int, phi: float):
             "sample": f"Algorithms 1-3 on A[:{s}, :] x B[:, :{s}] (k={k}, N={N}, phi={phi}), {dt:.1f} s"}
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time: every rank gets the MAX over the process group
+    (one tensor all-reduce on `device`, a CUDA device under NCCL, the CPU under
+    gloo).  Without an initialised group the local time is returned."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_tflops(world: int, flops_per_rank: float, ms: float) -> float:
+    """Whole-job throughput: the work of all replicas over the slowest rank's time."""
+    return world * flops_per_rank / (ms * 1e-3) / 1e12
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle on the host cores, a bounded sample per step."""
     from paper_2602_02549_b300.inputs import paper_matrix
@@ -494,16 +512,12 @@ def main():
         t_end.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = t_start.elapsed_time(t_end) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end) / args.steps, dev)
     assert B.sync(stream) == 0
     phase_ms = [statistics.mean(ev[s][p].elapsed_time(ev[s][p + 1]) for s in range(args.steps))
                 for p in range(B.NPHASES)]
     flops = 2.0 * m * n * k
-    value = world * flops / (ms * 1e-3) / 1e12
+    value = job_tflops(world, flops, ms)
 
     # dominant kernel: the N residue GEMMs (tcgen05, BF16 operands, FP32 accumulate)
     peaks, peak_kind = load_peaks()
@@ -573,14 +587,10 @@ def main():
         down.wait_event(done[1 - last])
         e1.record(down)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
         assert B.sync(stream) == 0
         same = bool(torch.equal(hC[last], C.cpu()))
-        e2e = {"value": world * flops / (e_ms * 1e-3) / 1e12, "unit": "TFLOPS", "ms_per_step": e_ms,
+        e2e = {"value": job_tflops(world, flops, e_ms), "unit": "TFLOPS", "ms_per_step": e_ms,
                "h2d_bytes_per_step": 8 * (m * k + k * n), "d2h_bytes_per_step": 8 * m * n,
                "pipelined": "double-buffered: step s+1 upload and s-1 download overlap step s",
                "result_matches_device_run": same}
