@@ -15,6 +15,8 @@ Using Ozaki-II Scheme"):
   * Algorithm 2, mu/nu lines: c = single_down(-0.5/(1-4*u32)).
   * Algorithm 3: P_inv = double(1/P).
   * Theorem 2 / Lemma 4: t = 1/sqrt(2^5 (P-1)), rho = sum floor(p_l/2).
+  * Proof of Lemma 0: the exhaustive evaluation behind the constant 2^-21
+    (lemma0_margin).
 
 Reading taken where the paper's Figure 1 is missing: "retains only the upper
 beta_l bits" is truncation toward zero onto the grid
@@ -159,3 +161,64 @@ def bound_terms(N: int, b: int = 64) -> dict:
         rb = gN + Fraction(1, 2) * U32 * P
     return {"t": C.t, "gN": float(gN * up), "h": float(h), "rb": float(rb * up),
             "P": P, "rho": rho}
+
+
+def lemma0_margin(N: int, cmax: int = 1 << 29, digits: int = 60) -> tuple:
+    """The exhaustive evaluation in the proof of Lemma 0, for P' of N moduli.
+
+    The proof states that, for every P' of eq. (p_list) and every
+    e' = log2(cbar) with cbar an integer in [1, 2^29] (cbar <= 2^12 k, k <= 2^17),
+        floor(P' - 0.5 (1 + u32) e') <= P' - 0.5 e' - 2^-21,
+    with 2^-21 found empirically.  Returns (margin, cbar): the smallest
+    P' - 0.5 e' - floor(P' - 0.5 (1 + u32) e') over all those cbar, and the
+    cbar where it occurs.
+
+    Over the cbar whose floor takes one value kf, the margin P' - 0.5 log2(cbar) - kf
+    falls as cbar grows, so each kf contributes only its largest cbar: the largest
+    integer with log2(cbar) <= 2 (P' - kf) / (1 + u32), clipped to cmax.  That
+    keeps the evaluation exhaustive at about 15 candidates per N.
+    """
+    Pp = Fraction(float(constants(N).Pprime))
+    one_u = 1 + U32
+    best = None
+    with localcontext() as ctx:
+        ctx.prec = digits
+        ln2 = Decimal(2).ln()
+
+        def log2d(c: int) -> Decimal:
+            return Decimal(c).ln() / ln2
+
+        def dec(fr: Fraction) -> Decimal:
+            return Decimal(fr.numerator) / Decimal(fr.denominator)
+
+        def floor_F(c: int) -> int:
+            # floor(P' - 0.5 (1 + u32) log2 c), exactly for powers of two
+            if c & (c - 1) == 0:
+                v = Pp - one_u * Fraction(c.bit_length() - 1, 2)
+                return math.floor(v)
+            v = dec(Pp) - dec(one_u) * log2d(c) / 2
+            f = math.floor(v)
+            assert abs(v - f) > Decimal(10) ** (10 - digits) and abs(v - f - 1) > Decimal(10) ** (10 - digits)
+            return f
+
+        def margin(c: int) -> Decimal:
+            return dec(Pp) - log2d(c) / 2 - floor_F(c)
+
+        k_lo = floor_F(cmax)
+        k_hi = math.floor(Pp)
+        for kf in range(k_lo, k_hi + 1):
+            X = dec(2 * (Pp - kf) / one_u)                       # log2(cbar) <= X
+            if X < 0:
+                continue
+            c = int((X * ln2).exp().to_integral_value(rounding="ROUND_FLOOR"))
+            c = min(max(c, 1), cmax)
+            while c < cmax and floor_F(c + 1) >= kf:              # guard against rounding in exp()
+                c += 1
+            while c > 1 and floor_F(c) < kf:
+                c -= 1
+            if floor_F(c) != kf:
+                continue                                          # no integer cbar has this floor
+            m = margin(c)
+            if best is None or m < best[0]:
+                best = (m, c)
+    return best

@@ -130,3 +130,42 @@ def test_paper_unit_roundoffs():
 def test_p256_is_first(N):
     # eq. (p_list): 256 first; INT8 wrap argument of Section 3.1
     assert constants(N).p[0] == 256
+
+
+# ---------------------------------------------------------------- Lemma 0's constant
+# The proof of Lemma 0 rests on an exhaustive evaluation: for every P' of
+# eq. (p_list) and every e' = log2(cbar), cbar an integer in [1, 2^29],
+#   floor(P' - 0.5 (1 + u32) e') <= P' - 0.5 e' - 2^-21,
+# with 2^-21 found empirically, i.e. the smallest margin lies in [2^-21, 2^-20).
+def test_lemma0_exhaustive_constant():
+    from decimal import Decimal
+    from oracle.constants import lemma0_margin
+    worst = min(lemma0_margin(N)[0] for N in range(2, 50))
+    assert Decimal(2) ** -21 <= worst < Decimal(2) ** -20
+
+
+@pytest.mark.parametrize("N", [2, 9, 17, 32, 49])
+def test_lemma0_margin_brute_force(N):
+    """The oracle's reduction to one candidate per floor value against every
+    cbar up to 2^16, evaluated directly (float64 log2, and mpmath at 50 digits
+    wherever float64 cannot decide the floor)."""
+    import mpmath
+    from oracle.constants import lemma0_margin
+    cmax = 1 << 16
+    Pp = float(constants(N).Pprime)
+    c = np.arange(1, cmax + 1, dtype=np.float64)
+    e = np.log2(c)
+    F = Pp - 0.5 * (1 + 2.0 ** -24) * e
+    fl = np.floor(F)
+    m = Pp - 0.5 * e - fl
+    close = (F - fl < 1e-9) | (fl + 1 - F < 1e-9)
+    mpmath.mp.dps = 50
+    for idx in np.nonzero(close)[0]:
+        cc = int(idx) + 1
+        ee = mpmath.log(cc, 2)
+        Fx = mpmath.mpf(Pp) - mpmath.mpf(1 + 2.0 ** -24) / 2 * ee
+        m[idx] = float(mpmath.mpf(Pp) - ee / 2 - mpmath.floor(Fx))
+    brute = m.min()
+    got, cg = lemma0_margin(N, cmax=cmax)
+    assert abs(float(got) - brute) < 1e-12
+    assert abs(m[cg - 1] - brute) < 1e-12
