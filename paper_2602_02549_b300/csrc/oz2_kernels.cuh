@@ -566,6 +566,39 @@ __device__ __forceinline__ PlaneArgs quant_args(const JobDesc<T> &j, int X) {
                      j.fast ? j.ss[X] : nullptr, !j.fast, j.l1[X]};
 }
 
+// Eight consecutive elements src[0 .. 7] of a row, zero from index `valid` on:
+// 16-byte vector loads when all eight are in range and src is 16-byte aligned.
+__device__ __forceinline__ void load8(const double *src, int valid, double (&x)[8]) {
+    if (valid >= 8 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const double2 *v = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const double2 t = __ldg(v + e);
+            x[2 * e] = t.x;
+            x[2 * e + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[e] = e < valid ? src[e] : 0.0;
+    }
+}
+__device__ __forceinline__ void load8(const float *src, int valid, float (&x)[8]) {
+    if (valid >= 8 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const float4 *v = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const float4 t = __ldg(v + e);
+            x[4 * e] = t.x;
+            x[4 * e + 1] = t.y;
+            x[4 * e + 2] = t.z;
+            x[4 * e + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[e] = e < valid ? src[e] : 0.0f;
+    }
+}
+
 // K-contiguous source.  Item: 256 / tpr rows of tpr x 8 h (8 per thread, tpr
 // threads per row; each warp lies in one row).  Every lane stays to the end of
 // the item (the row sums are reduced across the warp).
@@ -595,9 +628,7 @@ __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGro
                 continue;
             }
             T x[8];
-            const T *src = op.ptr + (long)r * op.ld + h0;
-#pragma unroll
-            for (int e = 0; e < 8; e++) x[e] = (h0 + e < a.k) ? src[e] : T(0);
+            load8(op.ptr + (long)r * op.ld + h0, a.k - h0, x);
             emit_quant8(a, x, shift, r, h0, acc);
         }
         flush_row(a, acc, r, 32, live);
