@@ -82,15 +82,14 @@ int ensure_device(int *dev_out) {
         DevN n64[kNMax + 1], n32[kNMax + 1];
         for (int N = 0; N <= kNMax; N++) {
             const NTable &a = T.n64[N], &b = T.n32[N];
-            n64[N] = DevN{a.P1, a.P2, a.Pinv, a.g, a.t, a.gN, a.Pprime, a.offset, a.eg, a.esum};
-            n32[N] = DevN{b.P1, b.P2, b.Pinv, b.g, b.t, b.gN, b.Pprime, b.offset, b.eg, b.esum};
+            n64[N] = DevN{a.P1, a.P2, a.Pinv, a.g, a.t, a.gN, a.Pprime, a.offset, a.eg, a.esum, a.poff};
+            n32[N] = DevN{b.P1, b.P2, b.Pinv, b.g, b.t, b.gN, b.Pprime, b.offset, b.eg, b.esum, b.poff};
         }
         cudaError_t e = cudaSuccess;
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_n64, n64, sizeof n64);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_n32, n32, sizeof n32);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_s1s, T.s1s, sizeof T.s1s);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ks64, T.ks64, sizeof T.ks64);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_ks32, T.ks32, sizeof T.ks32);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_dp64, T.dp64, sizeof T.dp64);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_dp32, T.dp32, sizeof T.dp32);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_p, T.mod.p, sizeof T.mod.p);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_magic, T.mod.magic, sizeof T.mod.magic);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c16, T.mod.c16, sizeof T.mod.c16);

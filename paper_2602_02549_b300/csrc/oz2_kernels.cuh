@@ -31,13 +31,14 @@ struct DevN {
     int offset;
     int eg;       // b = 64: g = 2^eg
     int esum;     // grid exponent of the rounded CRT sum
+    int poff;     // first plane pair of this N in c_dp64 / c_dp32
 };
 
 __constant__ DevN c_n64[kNMax + 1];
 __constant__ DevN c_n32[kNMax + 1];
-__constant__ int2 c_s1s[kPackedLen];      // b = 64: s_l1 / g = y 2^31 + x
-__constant__ int2 c_ks64[kPackedLen];     // b = 64: s_l2 / 2^esum = y 2^31 + x
-__constant__ int2 c_ks32[kPackedLen];     // b = 32: s_l1 / 2^esum = y 2^31 + x
+// CRT constants as 16-bit pieces, two planes per word (Tables::dp64 / dp32)
+__constant__ uint4 c_dp64[kPairsLen][2];  // b = 64: pieces 0-3 of s_l1 / g, then of s_l2 / 2^esum
+__constant__ uint4 c_dp32[kPairsLen];     // b = 32: pieces 0-3 of s_l1 / 2^esum
 __constant__ int c_p[kNMax];
 __constant__ uint32_t c_magic[kNMax];
 __constant__ uint32_t c_c16[kNMax];
@@ -1401,8 +1402,8 @@ __global__ void __launch_bounds__(256) k_fast_cmax(const __grid_constant__ JobGr
 // RN(x 2^e) for an integer-valued x with |x| < 2^400 (an exponent add, on the
 // integer units, whenever the result stays normal)
 __device__ __forceinline__ double scale_pow2(double x, int e) {
-    if (x == 0.0) return x;
     const long long b = __double_as_longlong(x);
+    if ((b << 1) == 0) return x;                                  // +-0, tested on the integer units
     const int ex = int((b >> 52) & 0x7FF);
     if (ex + e >= 1 && ex + e <= 2046) return __longlong_as_double(b + ((long long)e << 52));   // exact
     if (e > 1023) return x * 0x1p1023 * 0x1p1023;                 // overflows to +-inf as ldexp does
@@ -1419,25 +1420,26 @@ __device__ __forceinline__ double exp_add(double x, int e) {
     return (b << 1) == 0 ? x : __longlong_as_double(b + ((long long)e << 52));
 }
 
-// RN((hi 2^31 + lo) 2^e) as a double, from integer operations only.  Requires
-// |hi|, |lo| < 2^61 and a result in the normal range (the tables check both
-// for every N).  An exact zero gives +0.
+// RN((hi 2^S + lo) 2^e) as a double, from integer operations only (S = 31 or
+// 32).  Requires |hi|, |lo| < 2^61 and a result in the normal range (the tables
+// check both for every N).  An exact zero gives +0.
+template <int S>
 __device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
-    long long t = hi + (lo >> 31);                 // value = t 2^31 + r, 0 <= r < 2^31
-    unsigned long long r = (unsigned long long)(lo & 0x7FFFFFFFll);
+    long long t = hi + (lo >> S);                  // value = t 2^S + r, 0 <= r < 2^S
+    unsigned long long r = (unsigned long long)lo & ((1ull << S) - 1);
     const bool neg = t < 0;
-    unsigned long long T, R;                       // |value| = T 2^31 + R
+    unsigned long long T, R;                       // |value| = T 2^S + R
     if (!neg) { T = (unsigned long long)t; R = r; }
     else if (r == 0) { T = (unsigned long long)(-t); R = 0; }
-    else { T = (unsigned long long)(-t - 1); R = (1ull << 31) - r; }
+    else { T = (unsigned long long)(-t - 1); R = (1ull << S) - r; }
     // X 2^s with the bits below 2^s folded into a sticky bit 0 of X
     unsigned long long X;
     int s = 0;
-    if (T < (1ull << 33)) {
-        X = (T << 31) | R;
+    if (T < (1ull << (64 - S))) {
+        X = (T << S) | R;
     } else {
-        s = (64 - __clzll((long long)T)) - 33;    // 1 .. 31: X gets 64 bits
-        X = (T << (31 - s)) | (R >> s) | ((R & ((1ull << s) - 1)) != 0 ? 1ull : 0ull);
+        s = (64 - __clzll((long long)T)) - (64 - S);   // 1 .. S: X gets 64 bits
+        X = (T << (S - s)) | (R >> s) | ((R & ((1ull << s) - 1)) != 0 ? 1ull : 0ull);
     }
     if (X == 0) return 0.0;
     const int bl = 64 - __clzll((long long)X);
@@ -1457,40 +1459,86 @@ __device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
     return __longlong_as_double((long long)bits);
 }
 
+// H 2^e as a double for |H| < 2^53 (exact, on the integer units; the result is normal).
+__device__ __forceinline__ double exact_i53(long long H, int e) {
+    if (H == 0) return 0.0;
+    const unsigned long long a = H < 0 ? 0ull - (unsigned long long)H : (unsigned long long)H;
+    const int bl = 64 - __clzll((long long)a);                     // <= 53
+    const unsigned long long bits = ((unsigned long long)(bl + 1021 + e) << 52) + (a << (53 - bl));
+    return __longlong_as_double((long long)(bits | (H < 0 ? (1ull << 63) : 0ull)));
+}
+
+// rint(x) (round half to even, as FP64 rint) on the integer units: the
+// fraction bits are rounded off in place, a carry into the exponent field
+// giving the next power of two.
+__device__ __forceinline__ double rint_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = int((b >> 52) & 0x7FF);
+    if (e >= 1075) return x;                                      // |x| >= 2^52: an integer (or not finite)
+    const unsigned long long sign = b & (1ull << 63);
+    if (e < 1022) return __longlong_as_double((long long)sign);   // |x| < 1/2
+    if (e == 1022)                                                // 1/2 <= |x| < 1: 1/2 goes to the even 0
+        return __longlong_as_double((long long)((b << 12) == 0 ? sign : (sign | (1023ull << 52))));
+    const int f = 1075 - e;                                       // fraction bits, 1 .. 52
+    const unsigned long long t = b + ((1ull << (f - 1)) - 1) + ((b >> f) & 1ull);
+    return __longlong_as_double((long long)(t & ~((1ull << f) - 1)));
+}
+
+// c + a.lo16 b.byte0 + a.hi16 b.byte1 (dp2a.lo) or with b's bytes 2, 3
+// (dp2a.hi): unsigned 16-bit pieces of a, signed bytes of b.
+__device__ __forceinline__ int dp2a_lo(uint32_t a, uint32_t b, int c) {
+    int d;
+    asm("dp2a.lo.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ int dp2a_hi(uint32_t a, uint32_t b, int c) {
+    int d;
+    asm("dp2a.hi.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 // One row i, columns j0 .. j0+3 of one thread; load(l) gives the four W_l
-// bytes of those columns.  C'(1) and C'(2) are sums of integer multiples of
-// fixed grids: both are accumulated exactly in 64-bit integers (two 31-bit
-// halves of each constant, |terms| < 2^38, N <= 49) and rounded once.
+// bytes of those columns (zero for l >= N).  C'(1) and C'(2) are sums of
+// integer multiples of fixed grids, taken exactly: each constant is cut into
+// four 16-bit pieces, and one dp2a adds piece * W for two planes of one column
+// into a 32-bit sum (|sum| < 2^16 128 49 < 2^31).  The piece sums are then put
+// together in 64-bit integers and rounded once.
 template <typename T, typename Load>
 __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, const int32_t *mu,
                                         const int32_t *nu, T *C, long ldc, int n, int i, int j0, bool accum) {
     constexpr int B = sizeof(T) == 8 ? 64 : 32;
-    const int2 *ks = (B == 64 ? c_ks64 : c_ks32) + d.offset;
-    const int2 *s1s = c_s1s + d.offset;
-    int h1[4] = {0, 0, 0, 0};                  // b = 64: |s1.y W| sums stay below 2^31 (tables)
-    long long l1[4] = {0, 0, 0, 0};
-    long long h2[4] = {0, 0, 0, 0}, l2[4] = {0, 0, 0, 0};
-    // software pipeline: the loads of the next four planes are in flight while
-    // plane l is summed
-    uint32_t wq[4];
+    int s1[4][4], s2[4][4];                    // [column][piece]: C'(1) (b = 64 only), C'(2) / b = 32 C'(1)
 #pragma unroll
-    for (int u = 0; u < 4; u++) wq[u] = u < N ? load(u) : 0u;
-    for (int l = 0; l < N; l++) {
-        const uint32_t w4 = wq[0];
-        wq[0] = wq[1];
-        wq[1] = wq[2];
-        wq[2] = wq[3];
-        wq[3] = l + 4 < N ? load(l + 4) : 0u;
-        const int2 k = ks[l];
-        const int2 s1 = B == 64 ? s1s[l] : make_int2(0, 0);
+    for (int e = 0; e < 4; e++)
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int w = int(int8_t(uint8_t(w4 >> (8 * e))));
-            l2[e] += (long long)k.x * w;
-            h2[e] += (long long)k.y * w;
-            if (B == 64) {
-                l1[e] += (long long)s1.x * w;
-                h1[e] += s1.y * w;
+        for (int q = 0; q < 4; q++) s1[e][q] = s2[e][q] = 0;
+    const int pairs = (N + 1) / 2;
+    // software pipeline: the next pair's loads are in flight while a pair is summed
+    uint32_t w0 = load(0), w1 = load(1);
+    for (int pi = 0; pi < pairs; pi++) {
+        const uint32_t p0 = w0, p1 = w1;
+        w0 = load(2 * pi + 2);
+        w1 = load(2 * pi + 3);
+        // bytes of columns (0, 1) and (2, 3), planes 2 pi and 2 pi + 1 side by side
+        const uint32_t x01 = __byte_perm(p0, p1, 0x5140), x23 = __byte_perm(p0, p1, 0x7362);
+        const uint4 c2 = B == 64 ? c_dp64[d.poff + pi][1] : c_dp32[d.poff + pi];
+        const uint32_t cc2[4] = {c2.x, c2.y, c2.z, c2.w};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            s2[0][q] = dp2a_lo(cc2[q], x01, s2[0][q]);
+            s2[1][q] = dp2a_hi(cc2[q], x01, s2[1][q]);
+            s2[2][q] = dp2a_lo(cc2[q], x23, s2[2][q]);
+            s2[3][q] = dp2a_hi(cc2[q], x23, s2[3][q]);
+        }
+        if (B == 64) {
+            const uint4 c1 = c_dp64[d.poff + pi][0];
+            const uint32_t cc1[4] = {c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                s1[0][q] = dp2a_lo(cc1[q], x01, s1[0][q]);
+                s1[1][q] = dp2a_hi(cc1[q], x01, s1[1][q]);
+                s1[2][q] = dp2a_lo(cc1[q], x23, s1[2][q]);
+                s1[3][q] = dp2a_hi(cc1[q], x23, s1[3][q]);
             }
         }
     }
@@ -1499,14 +1547,26 @@ __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, 
     for (int e = 0; e < 4; e++) {
         const int j = j0 + e;
         if (j >= n) break;
-        // b = 64: C'(1) = H g with H = s1.y-sum 2^31 + s1.x-sum an integer below
-        // 2^62 (tables): one RN conversion and an exponent add give RN(C'(1))
-        const double c1 = B == 64 ? exp_add(__ll2double_rn(((long long)h1[e] << 31) + l1[e]), d.eg)
-                                  : rn_sum(h2[e], l2[e], d.esum);
-        const double q = rint(d.Pinv * c1);
-        // b = 32: P2 = 0 and C'(2) = +0, so fma(-q, 0, x + 0) = x + 0 as in the b = 64 form
-        const double cpp = B == 64 ? fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum(h2[e], l2[e], d.esum))
-                                   : fma(-q, d.P1, c1) + 0.0;
+        // the second sum as hi 2^32 + lo: pieces 0, 1 and 2, 3
+        const long long lo2 = (long long)s2[e][0] + ((long long)s2[e][1] << 16);
+        const long long hi2 = (long long)s2[e][2] + ((long long)s2[e][3] << 16);
+        double cpp;
+        if (B == 64) {
+            // C'(1) = H g exactly, |H| < 2^53 (Lemma 2): the four piece sums added
+            // modulo 2^64, which is exact because H fits
+            const unsigned long long Hu = (unsigned long long)(long long)s1[e][0] +
+                                          ((unsigned long long)(long long)s1[e][1] << 16) +
+                                          ((unsigned long long)(long long)s1[e][2] << 32) +
+                                          ((unsigned long long)(long long)s1[e][3] << 48);
+            const double c1 = exact_i53((long long)Hu, d.eg);
+            const double q = rint_bits(d.Pinv * c1);
+            cpp = fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum<32>(hi2, lo2, d.esum));
+        } else {
+            const double c1 = rn_sum<32>(hi2, lo2, d.esum);
+            const double q = rint_bits(d.Pinv * c1);
+            // P2 = 0 and C'(2) = +0, so fma(-q, 0, x + 0) = x + 0 as in the b = 64 form
+            cpp = fma(-q, d.P1, c1) + 0.0;
+        }
         const double v = scale_pow2(cpp, -(mi + nu[j]));
         const T c = B == 64 ? T(v) : T(__double2float_rn(v));
         T *dst = C + (long)i * ldc + j;
@@ -1528,8 +1588,8 @@ __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, 
     for (int i = blockIdx.y; i < m; i += gridDim.y) {
         if (j0 >= n) continue;
         const int8_t *wp = W + (long)i * n_pad + j0;
-        crt_row<T>([&](int l) { return __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane)); }, N, d,
-                   mu, nu, C, ldc, n, i, j0, accum != 0);
+        crt_row<T>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane)) : 0u; },
+                   N, d, mu, nu, C, ldc, n, i, j0, accum != 0);
     }
 }
 
@@ -1548,8 +1608,8 @@ __global__ void __launch_bounds__(256, 4) k_crt(const __grid_constant__ JobGroup
         const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
         const int8_t *wp = jd.W + (long)i * jd.n_pad + j0;
         const long wpl = jd.w_plane;
-        crt_row<T>([&](int l) { return __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)); }, N, d,
-                   jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0, jd.accum != 0);
+        crt_row<T>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)) : 0u; },
+                   N, d, jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0, jd.accum != 0);
     });
 }
 

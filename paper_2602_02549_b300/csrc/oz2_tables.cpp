@@ -257,7 +257,7 @@ void build(Tables &T) {
     }
     const long double u64 = 0x1p-53L, u32 = 0x1p-24L;
     T.c = f32_down(-0.5L / (1.0L - 4.0L * u32));
-    int offset = 0;
+    int offset = 0, poff = 0;
     T.sums_fit = true;
     for (int N = 1; N <= kNMax; N++) {
         Big P = Big::of(1);
@@ -342,6 +342,29 @@ void build(Tables &T) {
                 h += 128.0L * (long double)T.s1i[offset + l];
             }
             T.sums_fit &= hy < (1ll << 31) && h < 0x1p62L && T.n64[N].eg + 62 < 1023 && T.n64[N].eg > -960;
+            // the dp2a form rebuilds H from four 16-bit piece sums modulo 2^64, which is
+            // exact while |H| < 2^63; each piece sum stays below 2^16 128 49 < 2^31
+            T.sums_fit &= h < 0x1p62L;
+        }
+        {   // 16-bit pieces of the constants, two planes per word (the last pair of
+            // an odd N pairs its plane with a zero)
+            if (poff + (N + 1) / 2 > kPairsLen) { T.sums_fit = false; break; }
+            T.n64[N].poff = T.n32[N].poff = poff;
+            auto whole = [](const int (*k)[2], int l) { return (uint64_t(uint32_t(k[l][1])) << 31) | uint32_t(k[l][0]); };
+            for (int i = 0; 2 * i < N; i++) {
+                for (int h = 0; h < 2; h++) {
+                    const int l = 2 * i + h;
+                    const uint64_t c1 = l < N ? uint64_t(T.s1i[offset + l]) : 0;
+                    const uint64_t c2 = l < N ? whole(T.ks64 + offset, l) : 0;
+                    const uint64_t c3 = l < N ? whole(T.ks32 + offset, l) : 0;
+                    for (int j = 0; j < 4; j++) {
+                        T.dp64[poff + i][j] |= uint32_t((c1 >> (16 * j)) & 0xFFFFu) << (16 * h);
+                        T.dp64[poff + i][4 + j] |= uint32_t((c2 >> (16 * j)) & 0xFFFFu) << (16 * h);
+                        T.dp32[poff + i][j] |= uint32_t((c3 >> (16 * j)) & 0xFFFFu) << (16 * h);
+                    }
+                }
+            }
+            poff += (N + 1) / 2;
         }
         offset += N;
     }

@@ -9,6 +9,7 @@ constexpr int kNMax = 49;
 constexpr int kLimbs = 5;                               // 12-bit limbs of a 53-bit mantissa
 constexpr int kFixLimbs = 8;                            // 13-bit limbs of an integer below 2^104
 constexpr int kPackedLen = (kNMax * (kNMax + 1)) / 2;  // sum_{N=1}^{49} N entries
+constexpr int kPairsLen = 625;                          // sum_{N=1}^{49} ceil(N / 2) plane pairs
 
 // Per-modulus reduction constants (index l = 0..48).
 struct ModTable {
@@ -36,6 +37,7 @@ struct NTable {
     int eg;                  // b = 64: g = 2^eg
     int esum;                // grid of the rounded CRT sum: s_l2 (b = 64) or s_l1
                              // (b = 32) = (k[1] 2^31 + k[0]) 2^esum
+    int poff;                // start of this N's plane pairs in dp64 / dp32
 };
 
 struct Tables {
@@ -51,6 +53,12 @@ struct Tables {
     int s1s[kPackedLen][2];      // b = 64: s_l1 / g
     int ks64[kPackedLen][2];     // b = 64: s_l2 / 2^esum
     int ks32[kPackedLen][2];     // b = 32: s_l1 / 2^esum
+    // The same constants as 16-bit pieces for the CRT kernel's dp2a sums: for the
+    // plane pair (l, l + 1) = (2 i, 2 i + 1) of N, word j holds piece j (bits
+    // 16 j .. 16 j + 15) of the constant of plane l in its low half and of plane
+    // l + 1 (0 when l + 1 = N) in its high half.
+    uint32_t dp64[kPairsLen][8]; // b = 64: words 0-3 pieces of s_l1 / g, 4-7 of s_l2 / 2^esum
+    uint32_t dp32[kPairsLen][4]; // b = 32: pieces of s_l1 / 2^esum
     bool sums_fit;               // every k above is below 2^62 and every grid in range
     float c;                     // single_down(-0.5 / (1 - 4 u32))
 };
