@@ -312,9 +312,9 @@ template <typename T> struct Items {
     }
     __host__ __device__ static long long bound(const JobDesc<T> &j) {
         const int mx = j.m > j.n ? (j.m > j.k ? j.m : j.k) : (j.n > j.k ? j.n : j.k);
-        return !j.inject && j.nmoduli == 0 ? cdiv(mx, 2048) : 0;
+        return !j.inject && j.nmoduli == 0 ? cdiv(mx, 256) : 0;
     }
-    __host__ __device__ static long long exponents(const JobDesc<T> &j) { return cdiv(j.m + j.n, 2048); }
+    __host__ __device__ static long long exponents(const JobDesc<T> &j) { return cdiv(j.m + j.n, 256); }
     __host__ __device__ static long long resid_kc(const JobDesc<T> &j) { return items_kc_x(j, 0) + items_kc_x(j, 1); }
     __host__ __device__ static long long resid_rc(const JobDesc<T> &j) { return items_rc_x(j, 0) + items_rc_x(j, 1); }
     __host__ __device__ static long long crt(const JobDesc<T> &j) {
@@ -1246,16 +1246,15 @@ __device__ __forceinline__ double row_l1(const unsigned long long *l1, const uns
     return ldexp(v, -(quant_shift(rmax, r) + 57));
 }
 
-// The maxima that the N rule needs.  Item: 2048 consecutive indices of each
-// of the ranges i < m, j < n, h < k.
+// The maxima that the N rule needs.  Item: 256 consecutive indices (one per
+// thread) of each of the ranges i < m, j < n, h < k, so that these short,
+// latency-bound reductions spread over many SMs.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         unsigned long long mR = 0, mK = 0, m2a = 0, m2b = 0, mL = 0;
-        const int base = int(li) * 2048 + threadIdx.x;
-#pragma unroll 1
-        for (int e = 0; e < 8; e++) {
-            const int t = base + e * 256;
+        {
+            const int t = int(li) * 256 + threadIdx.x;
             if (t < j.m) {
                 unsigned long long v = (unsigned long long)__double_as_longlong(row_l1(j.l1[0], j.rmax[0], t));
                 mR = v > mR ? v : mR;
@@ -1302,9 +1301,9 @@ __device__ __forceinline__ int choose_n(const unsigned long long *red, int k, do
 
 // N (fixed, or the rule), then Algorithm 2's mu/nu lines: d = single_up(max
 // cbar) (1 for an empty row), e = log2f(d) with CUDA's fast __log2f as in the
-// paper, mu = mu' + floor(fl_down(fma(c, e, P'))).  Item: 2048 of the m + n
-// rows and columns; every item of a problem derives the same N, and item 0
-// publishes it.
+// paper, mu = mu' + floor(fl_down(fma(c, e, P'))).  Item: 256 of the m + n
+// rows and columns (one per thread); every item of a problem derives the same
+// N, and item 0 publishes it.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_exponents(const __grid_constant__ JobGroup<T, CAP> G) {
     constexpr int fp32 = sizeof(T) == 4 ? 1 : 0;
@@ -1324,11 +1323,9 @@ __global__ void __launch_bounds__(256) k_exponents(const __grid_constant__ JobGr
         const int N = sN;
         const float Pp = fp32 ? c_n32[N].Pprime : c_n64[N].Pprime;
         const float c = c_cneg;
-        const int base = int(li) * 2048 + threadIdx.x;
-#pragma unroll 1
-        for (int e = 0; e < 8; e++) {
-            const int t = base + e * 256;
-            if (t >= j.m + j.n) break;
+        {
+            const int t = int(li) * 256 + threadIdx.x;
+            if (t >= j.m + j.n) return;
             const int X = t < j.m ? 0 : 1;
             const int i = X ? t - j.m : t;
             const unsigned long long bits = j.rmax[X][i];
