@@ -309,6 +309,22 @@ def run_autograd(args):
         loss = ((oz2_matmul(A, Bm, args.nmoduli, args.target, args.nmax, args.mode == "fast") - T) ** 2).sum()
         loss.backward()
     ms = timed(step, args.steps, args.warmup, stream)
+    # the same step captured once in a CUDA graph and replayed: the eager step's
+    # host side (PyTorch autograd and elementwise launches) is about as long as
+    # its GPU work, the replay shows the GPU-bound rate
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    A.grad = None
+    Bm.grad = None
+    with torch.cuda.graph(graph):
+        loss_g = ((oz2_matmul(A, Bm, args.nmoduli, args.target, args.nmax, args.mode == "fast") - T) ** 2).sum()
+        loss_g.backward()
+    ms_graph = timed(graph.replay, args.steps, args.warmup, stream)
     with torch.no_grad():
         R = A @ Bm - T
         dA, dB = 2 * R @ Bm.t(), 2 * A.t() @ R
@@ -323,6 +339,8 @@ def run_autograd(args):
         "config": {"workload": "autograd_loss_4096x2048x1024_tau%g" % args.target, "target": args.target,
                    "products_per_step": 3},
         "grad_rel_err_vs_fp64": err,
+        "graph_replay": {"ms_per_step": ms_graph, "tflops": flops / (ms_graph * 1e-3) / 1e12,
+                         "note": "the whole forward + backward step captured in one CUDA graph"},
         "plain_fixed_N20_forward": {"ms": ms_fwd, "tflops": 2.0 * m * n * k / (ms_fwd * 1e-3) / 1e12}}))
 
 
