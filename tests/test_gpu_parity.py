@@ -113,7 +113,7 @@ def test_transposes(tr):
     assert np.array_equal(g["mu"], ref["mu"]) and np.array_equal(g["nu"], ref["nu"])
 
 
-@pytest.mark.parametrize("N", [2, 8, 14, 20])
+@pytest.mark.parametrize("N", [2, 8, 14, 20, 33, 49])
 def test_sgemm_parity(oracle, N):
     A, Bm = paper_pair(100, 140, 900, 1.0, seed=N, dtype=np.float32)
     g = run_gpu(A, Bm, N, fp32=True)
@@ -159,9 +159,9 @@ def test_random_integer_residue_products(oracle):
 def test_q_near_half_integers(oracle, N, b, bits):
     # injected mu = nu = 0 with |A'B'| far above P/2: C' wraps mod P, so
     # P_inv C'(1) spreads evenly over whole intervals and about one entry in 128
-    # lies within 2^-8 of a half-integer, where the kernel forms Q from the FP64
-    # product instead of its FP32 estimate.  Every entry must still equal the
-    # oracle's (0 ulp: both take the same FP64 steps).
+    # lies within 2^-8 of a half-integer, where the rounding of the FP64 product
+    # and the round-half-even of Q (taken on the integer units) decide Q.  Every
+    # entry must still equal the oracle's (0 ulp: both take the same FP64 steps).
     m, n, k = 96, 160, 300
     A = integer_matrix(m, k, -(1 << bits), 1 << bits, seed=N)
     Bm = integer_matrix(k, n, -(1 << bits), 1 << bits, seed=N + 100)
@@ -172,7 +172,7 @@ def test_q_near_half_integers(oracle, N, b, bits):
     assert ulp_distance(g["C"], r["C"], fp32=(b == 32)).max() == 0
     y = oracle.constants(N, b).Pinv * r["C1"]
     near = np.abs(np.abs(y - np.rint(y)) - 0.5) < 2.0 ** -8
-    assert near.sum() >= 20, "the inputs no longer reach the FP64 branch"
+    assert near.sum() >= 20, "the inputs no longer come near half-integers"
 
 
 def test_wide_exponents_and_zeros(oracle):
