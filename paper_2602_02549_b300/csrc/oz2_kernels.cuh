@@ -729,20 +729,27 @@ __device__ __forceinline__ int row_bits(unsigned long long max_bits, int shift) 
 //       half-integer (p odd);
 //   r = t - q p, the balanced residue of x'.
 // Two elements travel together through paired FP32 instructions.
-template <typename T>
-__device__ __forceinline__ void fixed_limbs(T x, int shift, float *d, int L, int &r256) {
-    const Int v = trunc_scaled(x, shift);
-    const unsigned __int128 w = v.M == 0 ? (unsigned __int128)0 : ((unsigned __int128)v.M << v.E);
+//
+// fixed_limbs2: the limbs of two elements as FP32 pairs, the residues mod 256 as BF16x2.
+// Limb u (13 bits) becomes the float 2^23 + u by setting the exponent bits,
+// and one paired fma s (2^23 + u) - s 2^23 = s u (exact) applies the sign s.
+template <int L, typename T>
+__device__ __forceinline__ uint32_t fixed_limbs2(T x0, T x1, int shift, unsigned long long (&dp)[L]) {
+    const Int v0 = trunc_scaled(x0, shift), v1 = trunc_scaled(x1, shift);
+    const unsigned __int128 w0 = v0.M == 0 ? (unsigned __int128)0 : ((unsigned __int128)v0.M << v0.E);
+    const unsigned __int128 w1 = v1.M == 0 ? (unsigned __int128)0 : ((unsigned __int128)v1.M << v1.E);
+    const unsigned long long sg = f2::pack(v0.neg ? -1.0f : 1.0f, v1.neg ? -1.0f : 1.0f);
+    const unsigned long long off = f2::pack(v0.neg ? 8388608.0f : -8388608.0f, v1.neg ? 8388608.0f : -8388608.0f);
 #pragma unroll
-    for (int i = 0; i < kFixLimbs; i++) {
-        if (i < L) {
-            const float u = float(uint32_t(w >> (13 * i)) & 0x1FFFu);
-            d[i] = v.neg ? -u : u;
-        }
+    for (int i = 0; i < L; i++) {
+        const uint32_t a0 = (uint32_t(w0 >> (13 * i)) & 0x1FFFu) | 0x4B000000u;
+        const uint32_t a1 = (uint32_t(w1 >> (13 * i)) & 0x1FFFu) | 0x4B000000u;
+        dp[i] = f2::fma((unsigned long long)a0 | ((unsigned long long)a1 << 32), sg, off);
     }
-    uint32_t b = uint32_t(w) & 255u;
-    if (v.neg) b = (256u - b) & 255u;
-    r256 = int(int8_t(b));
+    uint32_t b0 = uint32_t(w0) & 255u, b1 = uint32_t(w1) & 255u;
+    if (v0.neg) b0 = (256u - b0) & 255u;
+    if (v1.neg) b1 = (256u - b1) & 255u;
+    return pack_bf16x2f(float(int(int8_t(b0))), float(int(int8_t(b1))));
 }
 
 template <int L, typename T>
@@ -750,15 +757,7 @@ __device__ __forceinline__ void emit_resid8_fixed(uint4 *dst, long pw16, int N, 
     unsigned long long dp[4][L];
     uint32_t z[4];
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-        float d0[kFixLimbs], d1[kFixLimbs];
-        int r0, r1;
-        fixed_limbs(x[2 * j], shift, d0, L, r0);
-        fixed_limbs(x[2 * j + 1], shift, d1, L, r1);
-#pragma unroll
-        for (int i = 0; i < L; i++) dp[j][i] = f2::pack(d0[i], d1[i]);
-        z[j] = pack_bf16x2f(float(r0), float(r1));
-    }
+    for (int j = 0; j < 4; j++) z[j] = fixed_limbs2<L>(x[2 * j], x[2 * j + 1], shift, dp[j]);
     dst[0] = make_uint4(z[0], z[1], z[2], z[3]);
     const unsigned long long magic = f2::pack(12582912.0f, 12582912.0f);      // 1.5 2^23
     const unsigned long long nmagic = f2::pack(-12582912.0f, -12582912.0f);
