@@ -329,8 +329,27 @@ def run_autograd(args):
         R = A @ Bm - T
         dA, dB = 2 * R @ Bm.t(), 2 * A.t() @ R
     err = max(((A.grad - dA).abs().max() / dA.abs().max()).item(), ((Bm.grad - dB).abs().max() / dB.abs().max()).item())
-    C = torch.empty((m, n), dtype=torch.float64, device=dev)
-    ms_fwd = timed(lambda: B.matmul(A.detach(), Bm.detach(), 20, out=C), args.steps, args.warmup, stream)
+    # the plain fixed-N form at the same accuracy: every product at the largest N
+    # that the bound rule chose for the three products of a step
+    Ad, Bd = A.detach(), Bm.detach()
+    with torch.no_grad():
+        dC = 2 * (Ad @ Bd - T)
+    nsel = []
+    for X, Y, mode, shp in ((Ad, Bd, 0, (m, n)), (dC, Bd, B.OZ2_TRANS_B, (m, k)), (Ad, dC, B.OZ2_TRANS_A, (k, n))):
+        out = torch.empty(shp, dtype=torch.float64, device=dev)
+        nout = torch.zeros(1, dtype=torch.int32, device=dev)
+        rc = B.gemm_ex(X, Y, out, 0, mode, target=args.target, nmax=args.nmax, n_out=nout)
+        if rc:
+            raise B.Oz2Error(rc, "oz2_gemm_ex")
+        nsel.append(int(nout.item()))
+    n_fix = max(nsel)
+
+    def step_fixed():
+        A.grad = None
+        Bm.grad = None
+        loss = ((oz2_matmul(A, Bm, n_fix, 0.0, 0, args.mode == "fast") - T) ** 2).sum()
+        loss.backward()
+    ms_fixed = timed(step_fixed, args.steps, args.warmup, stream)
     flops = 3 * 2.0 * m * n * k
     print(json.dumps({
         "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOPS", "n_gpus": 1,
@@ -341,7 +360,8 @@ def run_autograd(args):
         "grad_rel_err_vs_fp64": err,
         "graph_replay": {"ms_per_step": ms_graph, "tflops": flops / (ms_graph * 1e-3) / 1e12,
                          "note": "the whole forward + backward step captured in one CUDA graph"},
-        "plain_fixed_N20_forward": {"ms": ms_fwd, "tflops": 2.0 * m * n * k / (ms_fwd * 1e-3) / 1e12}}))
+        "n_moduli": {"forward": nsel[0], "dA": nsel[1], "dB": nsel[2]},
+        "plain_fixed_N": {"N": n_fix, "ms_per_step": ms_fixed, "tflops": flops / (ms_fixed * 1e-3) / 1e12}}))
 
 
 def run_sgemm(args):
@@ -364,6 +384,13 @@ def run_sgemm(args):
                            target=tau if not args.nmoduli else 0.0, nmax=14 if not args.nmoduli else 0,
                            workspace=ws, stream=stream, n_out=nout)
     ms = timed(fn, args.steps, args.warmup, stream)
+    n_used = int(nout.item())
+    plain = None
+    if not args.nmoduli:
+        fixed = lambda: B.gemm_ex(A, Bm, C, n_used, B.OZ2_FAST if args.mode == "fast" else 0, workspace=ws,
+                                  stream=stream)
+        p_ms = timed(fixed, args.steps, args.warmup, stream)
+        plain = {"N": n_used, "ms_per_step": p_ms, "tflops": 2.0 * s ** 3 / (p_ms * 1e-3) / 1e12}
     torch.matmul(A, Bm)
     ms_native = timed(lambda: torch.matmul(A, Bm), 3, 1, stream)
     print(json.dumps({
@@ -371,7 +398,8 @@ def run_sgemm(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "sgemm_square_%d_phi%g_tau%g_%s" % (s, args.phi, tau, args.mode)},
-        "n_moduli": int(nout.item()),
+        "n_moduli": n_used,
+        "plain_fixed_N": plain,
         "native_fp32_tflops": 2.0 * s ** 3 / (ms_native * 1e-3) / 1e12}))
 
 
@@ -614,6 +642,17 @@ def main():
                "result_matches_device_run": same}
         del hA, hB, hC, dA, dB, dC
 
+    # the plain fixed-N form at the N the bound rule chose (the same accuracy): the
+    # same call without the rule's two reduction kernels
+    plain = None
+    if args.nmoduli == 0:
+        def step_fixed():
+            rc = B.gemm_ex(A, Bm, C, N_used, flags, workspace=ws, stream=stream)
+            if rc:
+                raise B.Oz2Error(rc, "oz2_gemm_ex")
+        p_ms = max_over_ranks(timed(step_fixed, args.steps, args.warmup, stream), dev)
+        plain = {"N": N_used, "ms_per_step": p_ms, "tflops": job_tflops(world, flops, p_ms)}
+
     # accuracy against the exact product on sampled entries
     from paper_2602_02549_b300.accuracy import sampled_errors
     g = torch.Generator(device="cpu").manual_seed(1234)
@@ -657,6 +696,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "plain_fixed_N": plain,
             "gpu_launches": launches_per_step * args.steps,
             "native_fp64_tflops": {"value": native_tflops, "size": ns, "note": "torch.matmul float64, context"},
             "clocks": clk.summary(),
