@@ -28,7 +28,6 @@ namespace oz2 {
 struct DevN {
     double P1, P2, Pinv, g, t, gN;
     float Pprime;
-    int offset;
     int eg;       // b = 64: g = 2^eg
     int esum;     // grid exponent of the rounded CRT sum
     int poff;     // first plane pair of this N in c_dp64 / c_dp32
