@@ -346,6 +346,7 @@ struct Job {
     // the device view of this problem for the grouped light-phase kernels
     JobDesc<T> desc() const {
         JobDesc<T> j{};
+        j.absmax_lb = kLineBlock;
         j.op[0] = opA;
         j.op[1] = opB;
         j.C = C;
@@ -416,6 +417,21 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     std::memset(&J, 0, sizeof J);
     J.count = count;
     for (int p = 0; p < count; p++) J.j[p] = jobs[p]->desc();
+    // k_absmax: fewer lines per item while the whole launch would give fewer than
+    // two blocks per SM (each item ends in one atomicMax per position, so large
+    // launches keep the full kLineBlock)
+    for (int lb = kLineBlock; lb > 8; lb /= 2) {
+        long long total = 0;
+        for (int p = 0; p < count; p++) {
+            J.j[p].absmax_lb = lb;
+            total += Items<T>::absmax(J.j[p]);
+        }
+        if (total >= 2ll * sms) break;
+        if (lb / 2 <= 8) {
+            for (int p = 0; p < count; p++) J.j[p].absmax_lb = lb / 2;
+            break;
+        }
+    }
     // fills J.begin from the per-problem item counts; returns the grid size (0: nothing to do)
     // (the kernels decode a problem's items with 32-bit arithmetic; a count of
     // 2^32 would need terabytes of workspace, and is refused)

@@ -202,7 +202,7 @@ struct Operand {
 // problem p owns the items [begin[p], begin[p+1]).  The item counts below are
 // shared by the host (which fills begin[]) and the kernels (which decode).
 constexpr int kMaxJobs = 64;
-constexpr int kLineBlock = 64;     // lines per k_absmax item
+constexpr int kLineBlock = 64;     // lines per k_absmax item, unless the launch has few items
 
 template <typename T>
 struct JobDesc {
@@ -212,6 +212,7 @@ struct JobDesc {
     int m, n, k, k_pad, n_pad;
     int R_pad[2];                  // m_pad, n_pad
     int nmoduli, nmax, fast, inject, vec[2];
+    int absmax_lb;                 // lines per k_absmax item (kLineBlock or fewer, per launch)
     int accum;                     // CRT adds its result to C (the K ranges after the first)
     double target;
     unsigned long long *hmax[2];   // per-k maxima of |A|, |B|
@@ -259,7 +260,7 @@ __host__ __device__ __forceinline__ long long items_absmax_x(const JobDesc<T> &j
     if (j.inject) return 0;
     int S, C;
     absmax_geom(j, X, S, C);
-    return cdiv(S, kLineBlock) * cdiv(C, absmax_tpl(C) * 8);
+    return cdiv(S, j.absmax_lb) * cdiv(C, absmax_tpl(C) * 8);
 }
 // K-contiguous kernels: threads per row (a multiple of 32 covering k_pad / 8
 // positions, at most 256) and rows per item (256 / threads per row)
@@ -362,7 +363,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return ((unsigned long long)hi << 32) | lo;
 }
 
-// Item: kLineBlock lines x (threads per line x 8) positions of one operand.
+// Item: j.absmax_lb lines x (threads per line x 8) positions of one operand.
 // Thread (line group ly, position group tx) takes 8 consecutive positions of
 // the lines ly, ly + lines-per-pass, ...; each warp lies in one line group.
 template <typename T, int CAP>
@@ -379,7 +380,8 @@ __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup
         const int ly = threadIdx.x / tpl, tx = threadIdx.x - ly * tpl;
         if (ly >= lpp) return;                  // 256 % tpl threads left over (whole warps)
         const int c0 = cb * ppi + tx * 8;
-        const int s_end = min(S, (lb + 1) * kLineBlock);
+        const int LB = j.absmax_lb;
+        const int s_end = min(S, (lb + 1) * LB);
         const bool kc = j.op[X].kcontig != 0;
         unsigned long long *smax = kc ? j.rmax[X] : j.hmax[X];
         unsigned long long *cmax = kc ? j.hmax[X] : j.rmax[X];
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup
         const long ld = j.op[X].ld;
         const bool full = c0 + 8 <= C, vec = full && j.vec[X];
         unsigned long long cm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int s = lb * kLineBlock + ly; s < s_end; s += lpp) {
+        for (int s = lb * LB + ly; s < s_end; s += lpp) {
             const T *src = ptr + (long)s * ld + c0;
             T x[8];
             if (vec) {
