@@ -1400,9 +1400,10 @@ __global__ void __launch_bounds__(256) k_fast_cmax(const __grid_constant__ JobGr
 // integer units, whenever the result stays normal)
 __device__ __forceinline__ double scale_pow2(double x, int e) {
     const long long b = __double_as_longlong(x);
-    if ((b << 1) == 0) return x;                                  // +-0, tested on the integer units
+    const bool zero = (b << 1) == 0;                              // +-0, tested on the integer units
     const int ex = int((b >> 52) & 0x7FF);
-    if (ex + e >= 1 && ex + e <= 2046) return __longlong_as_double(b + ((long long)e << 52));   // exact
+    if (zero || (ex + e >= 1 && ex + e <= 2046))
+        return zero ? x : __longlong_as_double(b + ((long long)e << 52));   // exact
     if (e > 1023) return x * 0x1p1023 * 0x1p1023;                 // overflows to +-inf as ldexp does
     if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
     const double y = x * 0x1p-1022;                               // exact: |x| >= 1
@@ -1422,47 +1423,36 @@ __device__ __forceinline__ double exp_add(double x, int e) {
 // check both for every N).  An exact zero gives +0.
 template <int S>
 __device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
-    long long t = hi + (lo >> S);                  // value = t 2^S + r, 0 <= r < 2^S
-    unsigned long long r = (unsigned long long)lo & ((1ull << S) - 1);
+    // written without branches (selects only); every shift amount stays in [0, 63]
+    const long long t = hi + (lo >> S);            // value = t 2^S + r, 0 <= r < 2^S
+    const unsigned long long r = (unsigned long long)lo & ((1ull << S) - 1);
     const bool neg = t < 0;
-    unsigned long long T, R;                       // |value| = T 2^S + R
-    if (!neg) { T = (unsigned long long)t; R = r; }
-    else if (r == 0) { T = (unsigned long long)(-t); R = 0; }
-    else { T = (unsigned long long)(-t - 1); R = (1ull << S) - r; }
-    // X 2^s with the bits below 2^s folded into a sticky bit 0 of X
-    unsigned long long X;
-    int s = 0;
-    if (T < (1ull << (64 - S))) {
-        X = (T << S) | R;
-    } else {
-        s = (64 - __clzll((long long)T)) - (64 - S);   // 1 .. S: X gets 64 bits
-        X = (T << (S - s)) | (R >> s) | ((R & ((1ull << s) - 1)) != 0 ? 1ull : 0ull);
-    }
-    if (X == 0) return 0.0;
+    // |value| = T 2^S + R
+    const unsigned long long T = neg ? ~(unsigned long long)t + (r == 0 ? 1ull : 0ull) : (unsigned long long)t;
+    const unsigned long long R = neg ? ((1ull << S) - r) & ((1ull << S) - 1) : r;
+    // X 2^s with the bits below 2^s folded into a sticky bit 0 of X (T < 2^63, so s < S)
+    const int bt = 64 - __clzll((long long)T);
+    const int s = max(bt - (64 - S), 0);
+    const unsigned long long X = (T << (S - s)) | (R >> s) | ((R & ((1ull << s) - 1)) != 0 ? 1ull : 0ull);
     const int bl = 64 - __clzll((long long)X);
-    int ex = bl - 1 + s + e;
-    unsigned long long mant;
-    if (bl <= 53) {
-        mant = X << (53 - bl);
-    } else {
-        const int sh = bl - 53;
-        mant = X >> sh;
-        const unsigned long long rem = X & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1ull))) mant++;
-        if (mant >> 53) { mant >>= 1; ex++; }
-    }
+    const int sh = max(bl - 53, 0);
+    unsigned long long mant = bl <= 53 ? X << min(53 - bl, 63) : X >> sh;
+    const unsigned long long rem = X & ((1ull << sh) - 1), half = (1ull << sh) >> 1;
+    mant += (sh > 0 && (rem > half || (rem == half && (mant & 1ull)))) ? 1ull : 0ull;
+    const int carry = int(mant >> 53);
+    mant >>= carry;
+    const int ex = bl - 1 + s + e + carry;
     const unsigned long long bits = (neg ? (1ull << 63) : 0ull) | ((unsigned long long)(ex + 1023) << 52) |
                                     (mant & ((1ull << 52) - 1));
-    return __longlong_as_double((long long)bits);
+    return X == 0 ? 0.0 : __longlong_as_double((long long)bits);
 }
 
 // H 2^e as a double for |H| < 2^53 (exact, on the integer units; the result is normal).
 __device__ __forceinline__ double exact_i53(long long H, int e) {
-    if (H == 0) return 0.0;
     const unsigned long long a = H < 0 ? 0ull - (unsigned long long)H : (unsigned long long)H;
-    const int bl = 64 - __clzll((long long)a);                     // <= 53
+    const int bl = 64 - __clzll((long long)a);                     // <= 53 (0 for H = 0)
     const unsigned long long bits = ((unsigned long long)(bl + 1021 + e) << 52) + (a << (53 - bl));
-    return __longlong_as_double((long long)(bits | (H < 0 ? (1ull << 63) : 0ull)));
+    return H == 0 ? 0.0 : __longlong_as_double((long long)(bits | (H < 0 ? (1ull << 63) : 0ull)));
 }
 
 // rint(x) (round half to even, as FP64 rint) on the integer units: the
@@ -1471,14 +1461,12 @@ __device__ __forceinline__ double exact_i53(long long H, int e) {
 __device__ __forceinline__ double rint_bits(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = int((b >> 52) & 0x7FF);
-    if (e >= 1075) return x;                                      // |x| >= 2^52: an integer (or not finite)
     const unsigned long long sign = b & (1ull << 63);
-    if (e < 1022) return __longlong_as_double((long long)sign);   // |x| < 1/2
-    if (e == 1022)                                                // 1/2 <= |x| < 1: 1/2 goes to the even 0
-        return __longlong_as_double((long long)((b << 12) == 0 ? sign : (sign | (1023ull << 52))));
-    const int f = 1075 - e;                                       // fraction bits, 1 .. 52
-    const unsigned long long t = b + ((1ull << (f - 1)) - 1) + ((b >> f) & 1ull);
-    return __longlong_as_double((long long)(t & ~((1ull << f) - 1)));
+    const int f = min(max(1075 - e, 1), 52);                     // fraction bits where 1 <= |x| < 2^52
+    const unsigned long long t = (b + ((1ull << (f - 1)) - 1) + ((b >> f) & 1ull)) & ~((1ull << f) - 1);
+    // |x| < 1: 0, or 1 above 1/2 (1/2 itself goes to the even 0)
+    const unsigned long long small = sign | ((b & ~(1ull << 63)) > 0x3FE0000000000000ull ? 0x3FF0000000000000ull : 0ull);
+    return __longlong_as_double((long long)(e >= 1075 ? b : (e < 1023 ? small : t)));   // |x| >= 2^52: x
 }
 
 // c + a.lo16 b.byte0 + a.hi16 b.byte1 (dp2a.lo) or with b's bytes 2, 3
