@@ -233,9 +233,11 @@ OZ2_API int oz2_sync(void *stream);
  * Returns OZ2_OK or OZ2_EINVAL.  Touches no GPU. */
 OZ2_API int oz2_tables(int N, int fp32, double *s1, double *s2, double *scal, float *pprime);
 
-/* The constants of the two CRT sums of Algorithm 3 as the device uses them:
- * s_l2 (fp32 == 0) or s_l1 (fp32 != 0) = (k[2l+1] 2^31 + k[2l]) 2^(*esum),
- * with 0 <= k[2l], k[2l+1] < 2^31, for l = 0..N-1 (k: host int[2N]).
+/* The constants of the two CRT sums of Algorithm 3 as integers on the grid
+ * the device sums them on: s_l2 (fp32 == 0) or s_l1 (fp32 != 0) =
+ * (k[2l+1] 2^31 + k[2l]) 2^(*esum), with 0 <= k[2l], k[2l+1] < 2^31, for
+ * l = 0..N-1 (k: host int[2N]); the device holds the same integers as four
+ * 16-bit pieces each.
  * Returns OZ2_OK, OZ2_EINVAL (N out of range or a null pointer) or
  * OZ2_ENOTSUP (some constant does not fit that form).  Touches no GPU. */
 OZ2_API int oz2_sum_tables(int N, int fp32, int *k, int *esum);
