@@ -1400,22 +1400,16 @@ __global__ void __launch_bounds__(256) k_fast_cmax(const __grid_constant__ JobGr
 // integer units, whenever the result stays normal)
 __device__ __forceinline__ double scale_pow2(double x, int e) {
     const long long b = __double_as_longlong(x);
-    const bool zero = (b << 1) == 0;                              // +-0, tested on the integer units
+    const bool zero = ((unsigned long long)b << 1) == 0;          // +-0, tested on the integer units
     const int ex = int((b >> 52) & 0x7FF);
     if (zero || (ex + e >= 1 && ex + e <= 2046))
-        return zero ? x : __longlong_as_double(b + ((long long)e << 52));   // exact
+        return zero ? x : __longlong_as_double((long long)((unsigned long long)b + ((unsigned long long)(long long)e << 52)));   // exact
     if (e > 1023) return x * 0x1p1023 * 0x1p1023;                 // overflows to +-inf as ldexp does
     if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
     const double y = x * 0x1p-1022;                               // exact: |x| >= 1
     const int e2 = e + 1022;
     if (e2 < -1022) return copysign(0.0, x);
     return y * __longlong_as_double((long long)(e2 + 1023) << 52);
-}
-
-// x 2^e for a double x that is 0 or stays normal (an exponent add).
-__device__ __forceinline__ double exp_add(double x, int e) {
-    const long long b = __double_as_longlong(x);
-    return (b << 1) == 0 ? x : __longlong_as_double(b + ((long long)e << 52));
 }
 
 // RN((hi 2^S + lo) 2^e) as a double, from integer operations only (S = 31 or
@@ -1532,9 +1526,12 @@ __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, 
     for (int e = 0; e < 4; e++) {
         const int j = j0 + e;
         if (j >= n) break;
-        // the second sum as hi 2^32 + lo: pieces 0, 1 and 2, 3
-        const long long lo2 = (long long)s2[e][0] + ((long long)s2[e][1] << 16);
-        const long long hi2 = (long long)s2[e][2] + ((long long)s2[e][3] << 16);
+        // the second sum as hi 2^32 + lo: pieces 0, 1 and 2, 3 (shifted as unsigned:
+        // the sums may be negative)
+        const long long lo2 = (long long)((unsigned long long)(long long)s2[e][0] +
+                                          ((unsigned long long)(long long)s2[e][1] << 16));
+        const long long hi2 = (long long)((unsigned long long)(long long)s2[e][2] +
+                                          ((unsigned long long)(long long)s2[e][3] << 16));
         double cpp;
         if (B == 64) {
             // C'(1) = H g exactly, |H| < 2^53 (Lemma 2): the four piece sums added
