@@ -682,9 +682,11 @@ def main():
         cpu = cpu_baseline(A[:s].cpu().numpy(), Bm[:, :s].cpu().numpy(), N_used, s, args.phi)
 
     if rank == 0:
-        # stats x2, quantise x2, scaling GEMM (fast: two majorant kernels instead),
-        # [bound reduction], choose N, mu/nu, residues x2, residue GEMM, CRT
-        launches_per_step = (12 if args.nmoduli == 0 else 11) + (1 if args.mode == "fast" else 0)
+        # clear, stats (A and B in one launch), quantise x2, scaling GEMM (fast: the
+        # two majorant kernels instead), [bound reduction], N + mu/nu, residues x2,
+        # residue GEMM, CRT: 11 per bound-chosen accurate call (as the ncu launch
+        # list shows), one fewer with a fixed N, one more in fast mode
+        launches_per_step = (11 if args.nmoduli == 0 else 10) + (1 if args.mode == "fast" else 0)
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
