@@ -280,12 +280,21 @@ template <typename T>
 __host__ __device__ __forceinline__ long long items_rc_x(const JobDesc<T> &j, int X) {
     return j.op[X].kcontig ? 0 : (long long)(j.k_pad / 64) * (j.R_pad[X] / 64);
 }
-// quantisation of K-contiguous rows: kQuantGroups chunks of tpr x 8 h per item
+// quantisation of K-contiguous rows: kQuantGroups chunks of tpr x 8 h per item;
+// tpr is a power of two in [8, 256] with tpr x 8 x kQuantGroups >= k_pad where
+// possible, so that short rows share a block (and a warp) instead of leaving
+// threads idle
 constexpr int kQuantGroups = 4;
+__host__ __device__ __forceinline__ int quant_tpr(int k_pad) {
+    const long long need = cdiv(k_pad, 8 * kQuantGroups);
+    int t = 8;
+    while (t < 256 && t < need) t <<= 1;
+    return t;
+}
 template <typename T>
 __host__ __device__ __forceinline__ long long items_quant_kc_x(const JobDesc<T> &j, int X) {
     if (j.inject || !j.op[X].kcontig) return 0;
-    const int tpr = kc_tpr(j.k_pad);
+    const int tpr = quant_tpr(j.k_pad);
     return cdiv(j.R_pad[X], 256 / tpr) * cdiv(j.k_pad, tpr * 8 * kQuantGroups);
 }
 template <typename T>
@@ -612,7 +621,7 @@ __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGro
         if (li >= n0) { X = 1; li -= n0; }
         const PlaneArgs a = quant_args(j, X);
         const Operand<T> &op = j.op[X];
-        const int tpr = kc_tpr(a.k_pad), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
+        const int tpr = quant_tpr(a.k_pad), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
         const unsigned nhb = unsigned(cdiv(a.k_pad, tpr * 8 * kQuantGroups)), ui = unsigned(li);
         const int rb = int(ui / nhb);
         const int r = rb * (256 / tpr) + ly;
@@ -633,7 +642,7 @@ __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGro
             load8(op.ptr + (long)r * op.ld + h0, a.k - h0, x);
             emit_quant8(a, x, shift, r, h0, acc);
         }
-        flush_row(a, acc, r, 32, live);
+        flush_row(a, acc, r, tpr < 32 ? tpr : 32, live);   // a row's lanes: tpr of them, or whole warps
     });
 }
 
