@@ -262,14 +262,13 @@ __host__ __device__ __forceinline__ long long items_absmax_x(const JobDesc<T> &j
     absmax_geom(j, X, S, C);
     return cdiv(S, j.absmax_lb) * cdiv(C, absmax_tpl(C) * 8);
 }
-// K-contiguous kernels: threads per row (a multiple of 32 covering k_pad / 8
-// positions, at most 256) and rows per item (256 / threads per row)
-__host__ __device__ __forceinline__ int kc_tpr(int k_pad) { return absmax_tpl(k_pad); }
+// Residues of K-contiguous rows: 256 consecutive groups of 8 positions per
+// item, in the row-major order of the R_pad x k_pad plane (R_pad x k_pad / 8
+// groups in all, a multiple of 256: R_pad is a multiple of 128, k_pad of 64)
 template <typename T>
 __host__ __device__ __forceinline__ long long items_kc_x(const JobDesc<T> &j, int X) {
     if (!j.op[X].kcontig) return 0;
-    const int tpr = kc_tpr(j.k_pad);
-    return cdiv(j.R_pad[X], 256 / tpr) * cdiv(j.k_pad, tpr * 8);
+    return cdiv((long long)j.R_pad[X] * (j.k_pad / 8), 256);
 }
 // CRT: threads per row covering n / 4 columns
 __host__ __device__ __forceinline__ int crt_tpr(int n) {
@@ -838,8 +837,9 @@ __device__ __forceinline__ PlaneArgs resid_args(const JobDesc<T> &j, int X) {
                      j.shift[X], j.ndev, nullptr, 1, nullptr};
 }
 
-// K-contiguous source.  Item: 256 / tpr rows of tpr x 8 h: 8 consecutive h per
-// thread (one 16-byte store per plane), tpr threads per row, each warp in one row.
+// K-contiguous source.  Item: 256 consecutive groups of 8 h in row-major order
+// (rows shorter than 2048 share an item, so no thread idles); 8 consecutive h
+// per thread, one 16-byte store per plane.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ JobGroup<T, CAP> G) {
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
@@ -853,11 +853,11 @@ __global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ Job
         const Operand<T> &op = j.op[X];
         const int N = *a.n_dev;
         const long pw16 = a.plane / 8;
-        const int tpr = kc_tpr(a.k_pad), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
-        const unsigned nhb = unsigned(cdiv(a.k_pad, tpr * 8)), ui = unsigned(li);
-        const int rb = int(ui / nhb);
-        const int r = rb * (256 / tpr) + ly, h0 = int(ui - unsigned(rb) * nhb) * tpr * 8 + tx * 8;
-        if (ly >= 256 / tpr || h0 >= a.k_pad) return;   // threads left over; past k_pad
+        const unsigned k8 = unsigned(a.k_pad / 8);
+        const unsigned long long g = (unsigned long long)li * 256u + threadIdx.x;
+        const unsigned long long rq = (g >> 32) == 0 ? unsigned(g) / k8 : g / k8;
+        if (rq >= (unsigned long long)a.R_pad) return;   // the last item's tail (none while 256 | R_pad k_pad / 8)
+        const int r = int(rq), h0 = int(g - rq * k8) * 8;
         uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
         if (r >= op.R) {
             for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
@@ -866,9 +866,7 @@ __global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ Job
         const int shift = a.shift[r];
         const int need = a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20;
         T x[8];
-        const T *src = op.ptr + (long)r * op.ld + h0;
-#pragma unroll
-        for (int e = 0; e < 8; e++) x[e] = h0 + e < a.k ? src[e] : T(0);
+        load8(op.ptr + (long)r * op.ld + h0, a.k - h0, x);
         emit_resid8(dst, pw16, N, x, shift, need, pow2);
     });
 }
