@@ -810,8 +810,8 @@ __device__ __forceinline__ void emit_resid8_general(uint4 *dst, long pw16, int N
     }
 }
 
-// Eight consecutive elements of one row; `need` = bit length of the largest
-// |x'| among the rows that the calling warp handles together (warp-uniform).
+// Eight consecutive elements of one row; `need` >= the bit length of every |x'|
+// of the row (a larger bound only takes more limbs, never a wrong residue).
 template <typename T>
 __device__ __forceinline__ void emit_resid8(uint4 *dst, long pw16, int N, const T (&x)[8], int shift, int need,
                                             const uint8_t (*pow2)[256]) {
@@ -864,6 +864,10 @@ __global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ Job
             return;
         }
         const int shift = a.shift[r];
+        // this row's own bound: where a warp spans several short rows, lanes on
+        // both sides of a limb-count limit diverge (rare: the scaling gives
+        // neighbouring rows nearly the same bit length; a warp-wide maximum
+        // measured slower)
         const int need = a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20;
         T x[8];
         load8(op.ptr + (long)r * op.ld + h0, a.k - h0, x);
