@@ -69,8 +69,6 @@ __device__ __forceinline__ int floor_log2_bits(uint64_t b) {
     return -1074 + (63 - __clzll((long long)m));
 }
 
-template <typename T> __device__ __forceinline__ double absd(T x) { return fabs(double(x)); }
-
 // x = (-1)^neg * M * 2^e with M an integer (< 2^53), from the bits of x.
 struct Split {
     uint64_t M;
@@ -176,11 +174,6 @@ __device__ __forceinline__ float residue_odd(const Limbs &L, int l, const uint8_
 
 __device__ __forceinline__ uint32_t pack_bf16x2f(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(int a, int b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(float(a), float(b));
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
