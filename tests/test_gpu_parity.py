@@ -301,3 +301,28 @@ def test_short_rows_limb_thresholds(oracle, N, phi):
     As, Bs = np.ascontiguousarray(A.T), np.ascontiguousarray(Bm.T)
     gt = run_gpu(As, Bs, N, trans_a=True, trans_b=True)
     assert np.array_equal(gt["C"], g["C"]) and np.array_equal(gt["W"], g["W"])
+
+
+@pytest.mark.parametrize("phi", [0.5, 1.0, 2.0, 4.0])
+def test_paper_shape_error_vs_bounds(oracle, phi):
+    # the paper's shape for its error-versus-bound comparison (m = n = 128,
+    # k = 8192): per N, the measured error of the GPU's C against the exact
+    # product, divided by the bound of eq. thm:err-1 and eq. thm:err-2 (the
+    # oracle's own scaling) and by the Lemma 1 + Lemma 4 bound from the GPU's
+    # exponents; the mu / nu mismatch count against the oracle's own exponents
+    A, Bm = paper_pair(128, 128, 8192, phi, seed=int(phi * 10))
+    for N in (8, 14, 20):
+        g = run_gpu(A, Bm, N)
+        check_against_oracle(oracle, A, Bm, g)
+        own = oracle.os_ii(A, Bm, N)
+        mism = int((g["mu"] != own["mu"]).sum() + (g["nu"] != own["nu"]).sum())
+        assert mism <= 2
+        err = np.abs(oracle.exact_residual(A, Bm, g["C"]))
+        e1, e2 = oracle.bounds(A, Bm, own)
+        eb = oracle.bound_from_exponents(A, Bm, g["mu"], g["nu"], own["Ap"], own["Bp"], N) \
+            if mism == 0 else None
+        r1, r2 = float((err / e1).max()), float((err / e2).max())
+        if mism == 0:
+            assert r1 <= 1.0 and r2 <= 1.0
+        print(f"phi={phi} N={N} mu/nu mismatches={mism} max err/err1={r1:.3e} max err/err2={r2:.3e}"
+              + (f" max err/bound(exponents)={float((err / eb).max()):.3e}" if eb is not None else ""))
