@@ -86,6 +86,12 @@ def traffic_for(kernel: str, alg_bytes: float):
     return e["dram_bytes"] / e["alg_bytes"] * alg_bytes
 
 
+def cublas_emulation_env():
+    """The cuBLAS environment settings that switch on its own floating-point
+    emulation, as set for this process (an empty dict: native FP64 / FP32)."""
+    return {k: v for k, v in os.environ.items() if k.startswith("CUBLAS_") and "EMULAT" in k}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -400,7 +406,9 @@ def run_sgemm(args):
         "config": {"workload": "sgemm_square_%d_phi%g_tau%g_%s" % (s, args.phi, tau, args.mode)},
         "n_moduli": n_used,
         "plain_fixed_N": plain,
-        "native_fp32_tflops": 2.0 * s ** 3 / (ms_native * 1e-3) / 1e12}))
+        "native_fp32_tflops": 2.0 * s ** 3 / (ms_native * 1e-3) / 1e12,
+        "cublas_emulation_env": cublas_emulation_env(),
+        "native_fp32_tf32": bool(torch.backends.cuda.matmul.allow_tf32)}))
 
 
 def run_splitk(args):
@@ -700,7 +708,8 @@ def main():
             "e2e": e2e,
             "plain_fixed_N": plain,
             "gpu_launches": launches_per_step * args.steps,
-            "native_fp64_tflops": {"value": native_tflops, "size": ns, "note": "torch.matmul float64, context"},
+            "native_fp64_tflops": {"value": native_tflops, "size": ns, "note": "torch.matmul float64, context",
+                                   "cublas_emulation_env": cublas_emulation_env()},
             "clocks": clk.summary(),
         }))
     if world > 1:
