@@ -13,7 +13,7 @@ The steps below follow the paper's order and notation:
       W_l = mod(C'_l, p_l), C'(1), C'(2), Q, C''.
   Algorithm 1:  C = diag(2^-mu) C'' diag(2^-nu).
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
   * floor(fl_down(fma(c, e, P'))) equals floor(c*e + P') taken exactly, because
     rounding down never crosses the integer below; c*e + P' is exact in FP64.
   * A zero row of A (zero column of B) gets mu' = 0; a row whose Cbar row is
@@ -490,7 +490,9 @@ def mu_band(mu_p: np.ndarray, cmax: np.ndarray, N: int, b: int = 64) -> tuple[np
 
 
 # --------------------------------------------------------------------------- #
-# Bound-chosen N (reading of the paper's motivation)
+# Bound-chosen N (a reading: the paper motivates choosing N from the bound
+# for a target accuracy but gives no rule; this takes the smallest N whose
+# N-dependent part of eq. thm:err-2 meets the target)
 # --------------------------------------------------------------------------- #
 def choose_N(A: np.ndarray, B: np.ndarray, alpha, beta, cmax_row, cmax_col,
              tau: float, nmax: int, b: int = 64) -> tuple[int, dict]:
