@@ -6,7 +6,10 @@ hand-written backward that computes both gradients through the same path.
 
 Each of the three products picks its own mu, nu and (with nmoduli = 0) its own
 N from the bound rule, so every product meets the stated target.  No transposed
-copies are made; only a non-row-major gradient is made contiguous first.
+copies are made; only a non-row-major gradient is made contiguous first.  In
+FP64, when both gradients are wanted, the two backward products go out as one
+two-problem oz2_gemm_batched call (one launch per phase for both; each result is
+bit-identical to its own oz2_gemm_ex call).
 """
 from __future__ import annotations
 
@@ -29,6 +32,18 @@ class Oz2Matmul(torch.autograd.Function):
         if dC.stride(-1) != 1:
             dC = dC.contiguous()
         dA = dB = None
+        m, k, n = A.size(0), A.size(1), B.size(1)
+        if (ctx.needs_input_grad[0] and ctx.needs_input_grad[1] and A.dtype == torch.float64
+                and min(m, n, k) > 0 and max(m, n) <= binding.K_MAX):
+            dA = torch.empty((m, k), dtype=A.dtype, device=A.device)
+            dB = torch.empty((k, n), dtype=A.dtype, device=A.device)
+            cfg = dict(nmoduli=ctx.nmoduli, target=ctx.cfg["target"] if ctx.nmoduli == 0 else 0.0,
+                       nmax=ctx.cfg["nmax"], fast=ctx.cfg["fast"])
+            rc = binding.gemm_batched([dict(A=dC, B=B, C=dA, trans_b=True, **cfg),
+                                       dict(A=A, B=dC, C=dB, trans_a=True, **cfg)])
+            if rc:
+                raise binding.Oz2Error(rc, "oz2_gemm_batched")
+            return dA, dB, None, None, None, None
         if ctx.needs_input_grad[0]:
             dA = binding.matmul(dC, B, ctx.nmoduli, trans_b=True, **ctx.cfg)
         if ctx.needs_input_grad[1]:

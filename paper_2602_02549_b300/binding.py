@@ -384,7 +384,10 @@ def gemm_batched(problems, *, workspace=None, stream=None, phase_events=None) ->
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     o.stream = ctypes.c_void_p(s.cuda_stream)
     if workspace is None:
-        workspace = torch.empty(max(batched_workspace_size(problems), 256), dtype=torch.uint8, device=dev)
+        L.oz2_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p]
+        L.oz2_batched_workspace_size.restype = ctypes.c_size_t
+        size = int(L.oz2_batched_workspace_size(len(problems), ctypes.cast(arr, ctypes.c_void_p)))
+        workspace = torch.empty(max(size, 256), dtype=torch.uint8, device=dev)
     o.workspace = ctypes.c_void_p(workspace.data_ptr())
     o.workspace_bytes = workspace.numel()
     ev = None

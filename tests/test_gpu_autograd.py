@@ -53,19 +53,27 @@ def test_loss_gradient_matches_fp64(shape):
         assert err <= 1e-13 * scale, (err, scale)
 
 
-def test_backward_uses_transposed_operands_exactly():
-    # the backward products equal direct emulated calls on materialised transposes
+@pytest.mark.parametrize("nmoduli", [14, 0])
+@pytest.mark.parametrize("both", [True, False])
+def test_backward_uses_transposed_operands_exactly(nmoduli, both):
+    # the backward products (one batched call when both gradients are wanted,
+    # single calls otherwise) equal direct emulated calls on materialised
+    # transposes, bit for bit; nmoduli = 0: each product's own bound-chosen N
     import torch
     from paper_2602_02549_b300 import binding as Bd
     from paper_2602_02549_b300.autograd import oz2_matmul
     A = torch.tensor(paper_matrix(64, 48, 1.0, 4), device="cuda", requires_grad=True)
-    B = torch.tensor(paper_matrix(48, 80, 1.0, 5), device="cuda", requires_grad=True)
-    dC = torch.tensor(paper_matrix(64, 80, 1.0, 6), device="cuda")
-    oz2_matmul(A, B, 14).backward(dC)
+    B = torch.tensor(paper_matrix(48, 80, 4.0, 5), device="cuda", requires_grad=both)
+    dC = torch.tensor(paper_matrix(64, 80, 2.0, 6), device="cuda")
+    oz2_matmul(A, B, nmoduli, 1e-15).backward(dC)
     with torch.no_grad():
-        dA = Bd.matmul(dC, B.t().contiguous(), 14)
-        dB = Bd.matmul(A.t().contiguous(), dC, 14)
-    assert torch.equal(A.grad, dA) and torch.equal(B.grad, dB)
+        dA = Bd.matmul(dC, B.t().contiguous(), nmoduli, target=1e-15)
+        dB = Bd.matmul(A.t().contiguous(), dC, nmoduli, target=1e-15)
+    assert torch.equal(A.grad, dA)
+    if both:
+        assert torch.equal(B.grad, dB)
+    else:
+        assert B.grad is None
 
 
 def test_call_from_another_host_thread():
