@@ -10,6 +10,14 @@ A step is one full call of the emulated GEMM (all kernels).  Inputs are
 resident in HBM for `value`; `e2e` adds the host->device copy of A and B from
 pinned memory and the device->host copy of C to every step.
 
+The same line carries one sub-record per other form, each timed in a region of
+its own (CUDA events around every call, L2 flushed before it) and each beside
+the plain fixed-N form at the same accuracy: `fast` (16384^3, fast scaling),
+`small` (1024^3 and 4096^3, also replayed from a CUDA graph), `sgemm` (FP32,
+8192^3, target 1e-7), `autograd` (loss ||AB - T||^2, A 4096 x 2048, B 2048 x
+1024) and `batched` (64 uneven problems, target 1e-14, one graph-captured
+call).  `--workload` runs one of them alone; `--no-forms` skips them.
+
 Prints one JSON line on rank 0.
 """
 from __future__ import annotations
@@ -52,6 +60,8 @@ def parse():
                         "splitk: k beyond 2^17 (K ranges added in FP64); zgemm: complex FP64")
     p.add_argument("--k", type=int, default=4 << 17, help="splitk: the contraction length")
     p.add_argument("--mode", default="accurate", choices=["accurate", "fast"])
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the other forms' sub-records (fast mode, small sizes, SGEMM, autograd, batched)")
     return p.parse_args()
 
 
@@ -234,181 +244,316 @@ def timed(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def run_batched(args):
-    """64 uneven problems (m, n, k log-uniform in [128, 4096], phi ~ U(0.5, 4)),
-    per-problem bound-chosen N for tau = 1e-14, one oz2_gemm_batched call
-    captured in a CUDA graph, against 64 plain oz2_gemm_ex calls at the fixed N
-    that meets the target for every problem (the largest chosen N)."""
+L2_FLUSH_BYTES = 256 << 20      # twice the B300's 126 MB L2
+
+
+def timed_each(fn, steps, warmup, stream, flush):
+    """Mean device time of one call of fn: each timed call between its own two
+    CUDA events on `stream`, after a write of `flush` (a buffer larger than L2,
+    outside the events) so that no call finds its inputs in L2."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+
+
+def sampled_accuracy(A, Bm, C, samples, seed=1234, fp32=False):
+    """Errors of C against the exact product on sampled entries (A, Bm, C device tensors)."""
+    import torch
+    from paper_2602_02549_b300.accuracy import sampled_errors
+    m, n = C.shape
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    ii = torch.randint(0, m, (samples,), generator=g).to(C.device)
+    jj = torch.randint(0, n, (samples,), generator=g).to(C.device)
+    rows = A[ii].double().cpu().numpy()
+    cols = Bm[:, jj].t().contiguous().double().cpu().numpy()
+    vals = C[ii, jj].double().cpu().numpy()
+    return sampled_errors(rows, cols, vals)
+
+
+def emulated_frac(tflops, N, fast, peak):
+    """Emulated TFLOPS over the rate the N (+1 for the scaling GEMM in accurate
+    mode) BF16 products would reach at `peak` with nothing else taking time."""
+    return tflops / (peak / (N + (0 if fast else 1)))
+
+
+def form_square(dev, size, phi, target, nmax, fast, steps, warmup, peak, flush, samples,
+                graph=False, A=None, Bm=None, ws=None):
+    """Square DGEMM m = n = k = size (Section 5's generator, seeds 0 and 1), N
+    from the bound rule for `target`: one call per step, against the same call
+    at the chosen N (the plain fixed-N form); graph=True also times the call
+    replayed from a CUDA graph (small sizes, where the host's launch work shows)."""
     import torch
     from paper_2602_02549_b300 import binding as B
-    from paper_2602_02549_b300.build import build
-    from paper_2602_02549_b300.inputs import batched_specs, paper_matrix_torch
-    build()
-    dev = torch.device("cuda", 0)
-    tau = 1e-14 if args.target == 1e-15 else args.target
-    specs = batched_specs(64, 0)
-    probs, flops = [], 0.0
-    for i, (m, n, k, phi) in enumerate(specs):
-        probs.append(dict(A=paper_matrix_torch(m, k, phi, 2 * i, dev), B=paper_matrix_torch(k, n, phi, 2 * i + 1, dev),
-                          C=torch.empty((m, n), dtype=torch.float64, device=dev), nmoduli=0, target=tau, nmax=30,
-                          fast=args.mode == "fast", n_out=torch.zeros(1, dtype=torch.int32, device=dev)))
-        flops += 2.0 * m * n * k
-    ws = torch.empty(B.batched_workspace_size(probs), dtype=torch.uint8, device=dev)
-    # tile widths per problem picked by the library's autotuner (outside the capture)
-    policy, policy_ms = B.batched_autotune(probs, workspace=ws)
-    assert B.gemm_batched(probs, workspace=ws) == 0
+    from paper_2602_02549_b300.inputs import paper_matrix_torch
+    m = n = k = size
+    if A is None:
+        A = paper_matrix_torch(m, k, phi, 0, dev)
+        Bm = paper_matrix_torch(k, n, phi, 1, dev)
+    if ws is None:
+        ws = torch.empty(B.workspace_size(m, n, k, nmax), dtype=torch.uint8, device=dev)
+    C = torch.empty((m, n), dtype=torch.float64, device=dev)
+    nout = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flags = B.OZ2_FAST if fast else 0
+
+    def call(N=0):
+        rc = B.gemm_ex(A, Bm, C, N, flags, target=target if N == 0 else 0.0, nmax=nmax if N == 0 else 0,
+                       workspace=ws, stream=stream, n_out=nout if N == 0 else None)
+        if rc:
+            raise B.Oz2Error(rc, "oz2_gemm_ex")
+    ms = timed_each(call, steps, warmup, stream, flush)
+    assert B.sync(stream) == 0
+    N = int(nout.item())
+    flops = 2.0 * m * n * k
+    tf = flops / (ms * 1e-3) / 1e12
+    ms_fix = timed_each(lambda: call(N), steps, warmup, stream, flush)
+    tf_fix = flops / (ms_fix * 1e-3) / 1e12
+    rec = {"workload": "dgemm_square_%d_phi%g_tau%g_%s" % (size, phi, target, "fast" if fast else "accurate"),
+           "ms_per_step": ms, "tflops": tf, "n_moduli": N,
+           "emulated_frac": emulated_frac(tf, N, fast, peak),
+           "plain_fixed_N": {"N": N, "ms_per_step": ms_fix, "tflops": tf_fix,
+                             "emulated_frac": emulated_frac(tf_fix, N, fast, peak)}}
+    if graph:
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            call()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                rc = B.gemm_ex(A, Bm, C, 0, flags, target=target, nmax=nmax, workspace=ws, stream=s, n_out=nout)
+                assert rc == 0
+        ms_g = timed_each(g.replay, steps, warmup, stream, flush)
+        tf_g = flops / (ms_g * 1e-3) / 1e12
+        rec["graph_replay"] = {"ms_per_step": ms_g, "tflops": tf_g, "emulated_frac": emulated_frac(tf_g, N, fast, peak)}
+    call()
     torch.cuda.synchronize()
-    Ns = [int(q["n_out"].item()) for q in probs]
-    s = torch.cuda.Stream()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=s):
-        assert B.gemm_batched(probs, workspace=ws, stream=s) == 0
-    ms = timed(g.replay, args.steps, args.warmup, torch.cuda.current_stream())
-    assert B.sync() == 0
-    Nfix = max(Ns)
-    wmax = max(B.workspace_size(q["A"].size(0), q["B"].size(1), q["A"].size(1), Nfix) for q in probs)
-    ws1 = torch.empty(wmax, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-
-    def plain():
-        for q in probs:
-            rc = B.gemm_ex(q["A"], q["B"], q["C"], Nfix, B.OZ2_FAST if args.mode == "fast" else 0,
-                           workspace=ws1, stream=stream)
-            assert rc == 0
-    ms_plain = timed(plain, args.steps, args.warmup, stream)
-    peaks, kind = load_peaks()
-    mma = sum(2.0 * q["A"].size(0) * q["B"].size(1) * q["A"].size(1) * (n + 1) for q, n in zip(probs, Ns))
-    print(json.dumps({
-        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOPS", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batched_64_uneven_128_4096_tau%g_%s" % (tau, args.mode), "problems": 64,
-                   "total_2mnk": flops, "target": tau, "graph": "one oz2_gemm_batched call captured"},
-        "n_moduli": {"min": min(Ns), "max": max(Ns), "mean": sum(Ns) / len(Ns)},
-        "autotune": {"policy": policy, "ms_per_policy": policy_ms,
-                     "policies": ["all 128x256", "all 128x128", "128x128 where n mod 256 <= 128",
-                                  "per problem, measured alone"]},
-        "plain_fixed_N": {"N": Nfix, "ms": ms_plain, "tflops": flops / (ms_plain * 1e-3) / 1e12},
-        "mma_tflops_rate": mma / (ms * 1e-3) / 1e12,
-        "mma_frac_of_peak": mma / (ms * 1e-3) / 1e12 / float(peaks["bf16_tflops_sustained"])}))
+    rec["accuracy"] = sampled_accuracy(A, Bm, C, samples)
+    rec["l2"] = "flushed (256 MiB write) before every timed call"
+    return rec
 
 
-def run_autograd(args):
-    """loss = ||A B - T||_F^2 with A 4096 x 2048, B 2048 x 1024, phi = 1:
-    forward and hand-written backward (dA, dB) through the emulation."""
+def form_sgemm(dev, size, phi, target, fast, steps, warmup, peak, flush, samples):
+    """FP32 SGEMM emulation size^3, phi, N from the bound rule for `target` (nmax 14)."""
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.inputs import paper_matrix_torch
+    s = size
+    A = paper_matrix_torch(s, s, phi, 0, dev, torch.float32)
+    Bm = paper_matrix_torch(s, s, phi, 1, dev, torch.float32)
+    C = torch.empty((s, s), dtype=torch.float32, device=dev)
+    nout = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(B.workspace_size(s, s, s, 14, 0, True), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flags = B.OZ2_FAST if fast else 0
+
+    def call(N=0):
+        rc = B.gemm_ex(A, Bm, C, N, flags, target=target if N == 0 else 0.0, nmax=14 if N == 0 else 0,
+                       workspace=ws, stream=stream, n_out=nout if N == 0 else None)
+        if rc:
+            raise B.Oz2Error(rc, "oz2_sgemm_ex")
+    ms = timed_each(call, steps, warmup, stream, flush)
+    assert B.sync(stream) == 0
+    N = int(nout.item())
+    flops = 2.0 * s ** 3
+    tf = flops / (ms * 1e-3) / 1e12
+    ms_fix = timed_each(lambda: call(N), steps, warmup, stream, flush)
+    tf_fix = flops / (ms_fix * 1e-3) / 1e12
+    call()
+    torch.cuda.synchronize()
+    acc = sampled_accuracy(A, Bm, C, samples)
+    torch.matmul(A, Bm)
+    ms_native = timed(lambda: torch.matmul(A, Bm), 3, 1, stream)
+    return {"workload": "sgemm_square_%d_phi%g_tau%g_%s" % (s, phi, target, "fast" if fast else "accurate"),
+            "ms_per_step": ms, "tflops": tf, "n_moduli": N, "emulated_frac": emulated_frac(tf, N, fast, peak),
+            "plain_fixed_N": {"N": N, "ms_per_step": ms_fix, "tflops": tf_fix,
+                              "emulated_frac": emulated_frac(tf_fix, N, fast, peak)},
+            "accuracy": acc, "native_fp32_tflops": flops / (ms_native * 1e-3) / 1e12,
+            "native_fp32_tf32": bool(torch.backends.cuda.matmul.allow_tf32),
+            "l2": "flushed (256 MiB write) before every timed call"}
+
+
+def form_autograd(dev, target, nmax, fast, steps, warmup, peak, flush):
+    """loss = ||A B - T||_F^2 with A 4096 x 2048, B 2048 x 1024, phi = 1: forward
+    and hand-written backward (dA, dB) through the emulation, eager and replayed
+    from one CUDA graph, against every product at the largest N the bound rule
+    chose for the three (the plain fixed-N form)."""
     import torch
     from paper_2602_02549_b300 import binding as B
     from paper_2602_02549_b300.autograd import oz2_matmul
-    from paper_2602_02549_b300.build import build
     from paper_2602_02549_b300.inputs import paper_matrix_torch
-    build()
-    dev = torch.device("cuda", 0)
     m, k, n = 4096, 2048, 1024
     A = paper_matrix_torch(m, k, 1.0, 0, dev).requires_grad_()
     Bm = paper_matrix_torch(k, n, 1.0, 1, dev).requires_grad_()
     T = paper_matrix_torch(m, n, 1.0, 2, dev)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.current_stream(dev)
 
-    def step():
-        A.grad = None
-        Bm.grad = None
-        loss = ((oz2_matmul(A, Bm, args.nmoduli, args.target, args.nmax, args.mode == "fast") - T) ** 2).sum()
-        loss.backward()
-    ms = timed(step, args.steps, args.warmup, stream)
-    # the same step captured once in a CUDA graph and replayed: the eager step's
-    # host side (PyTorch autograd and elementwise launches) is about as long as
-    # its GPU work, the replay shows the GPU-bound rate
-    side = torch.cuda.Stream()
+    def make_step(N):
+        def step():
+            A.grad = None
+            Bm.grad = None
+            loss = ((oz2_matmul(A, Bm, N, target if N == 0 else 0.0, nmax if N == 0 else 0, fast) - T) ** 2).sum()
+            loss.backward()
+        return step
+    ms = timed_each(make_step(0), steps, warmup, stream, flush)
+    # the same step captured in one CUDA graph (the eager step's host side,
+    # PyTorch's autograd and elementwise launches, is about as long as its GPU work)
+    side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
     with torch.cuda.stream(side):
         for _ in range(3):
-            step()
+            make_step(0)()
     stream.wait_stream(side)
     graph = torch.cuda.CUDAGraph()
     A.grad = None
     Bm.grad = None
     with torch.cuda.graph(graph):
-        loss_g = ((oz2_matmul(A, Bm, args.nmoduli, args.target, args.nmax, args.mode == "fast") - T) ** 2).sum()
+        loss_g = ((oz2_matmul(A, Bm, 0, target, nmax, fast) - T) ** 2).sum()
         loss_g.backward()
-    ms_graph = timed(graph.replay, args.steps, args.warmup, stream)
+    ms_graph = timed_each(graph.replay, steps, warmup, stream, flush)
     with torch.no_grad():
         R = A @ Bm - T
         dA, dB = 2 * R @ Bm.t(), 2 * A.t() @ R
-    err = max(((A.grad - dA).abs().max() / dA.abs().max()).item(), ((Bm.grad - dB).abs().max() / dB.abs().max()).item())
-    # the plain fixed-N form at the same accuracy: every product at the largest N
-    # that the bound rule chose for the three products of a step
+    err = max(((A.grad - dA).abs().max() / dA.abs().max()).item(),
+              ((Bm.grad - dB).abs().max() / dB.abs().max()).item())
     Ad, Bd = A.detach(), Bm.detach()
     with torch.no_grad():
         dC = 2 * (Ad @ Bd - T)
-    nsel = []
-    for X, Y, mode, shp in ((Ad, Bd, 0, (m, n)), (dC, Bd, B.OZ2_TRANS_B, (m, k)), (Ad, dC, B.OZ2_TRANS_A, (k, n))):
+    nsel, mma = [], 0.0
+    for X, Y, mode, shp, kk in ((Ad, Bd, 0, (m, n), k), (dC, Bd, B.OZ2_TRANS_B, (m, k), n),
+                                (Ad, dC, B.OZ2_TRANS_A, (k, n), m)):
         out = torch.empty(shp, dtype=torch.float64, device=dev)
         nout = torch.zeros(1, dtype=torch.int32, device=dev)
-        rc = B.gemm_ex(X, Y, out, 0, mode, target=args.target, nmax=args.nmax, n_out=nout)
+        rc = B.gemm_ex(X, Y, out, 0, mode | (B.OZ2_FAST if fast else 0), target=target, nmax=nmax, n_out=nout)
         if rc:
             raise B.Oz2Error(rc, "oz2_gemm_ex")
         nsel.append(int(nout.item()))
+        mma += 2.0 * shp[0] * shp[1] * kk * (nsel[-1] + (0 if fast else 1))
     n_fix = max(nsel)
-
-    def step_fixed():
-        A.grad = None
-        Bm.grad = None
-        loss = ((oz2_matmul(A, Bm, n_fix, 0.0, 0, args.mode == "fast") - T) ** 2).sum()
-        loss.backward()
-    ms_fixed = timed(step_fixed, args.steps, args.warmup, stream)
+    ms_fixed = timed_each(make_step(n_fix), steps, warmup, stream, flush)
     flops = 3 * 2.0 * m * n * k
-    print(json.dumps({
-        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOPS", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "autograd_loss_4096x2048x1024_tau%g" % args.target, "target": args.target,
-                   "products_per_step": 3},
-        "grad_rel_err_vs_fp64": err,
-        "graph_replay": {"ms_per_step": ms_graph, "tflops": flops / (ms_graph * 1e-3) / 1e12,
-                         "note": "the whole forward + backward step captured in one CUDA graph"},
-        "n_moduli": {"forward": nsel[0], "dA": nsel[1], "dB": nsel[2]},
-        "plain_fixed_N": {"N": n_fix, "ms_per_step": ms_fixed, "tflops": flops / (ms_fixed * 1e-3) / 1e12}}))
+    tf = lambda t: flops / (t * 1e-3) / 1e12   # noqa: E731
+    frac = lambda t: mma / (t * 1e-3) / 1e12 / peak   # noqa: E731
+    return {"workload": "autograd_loss_4096x2048x1024_tau%g_%s" % (target, "fast" if fast else "accurate"),
+            "products_per_step": 3, "ms_per_step": ms, "tflops": tf(ms), "emulated_frac": frac(ms),
+            "graph_replay": {"ms_per_step": ms_graph, "tflops": tf(ms_graph), "emulated_frac": frac(ms_graph)},
+            "n_moduli": {"forward": nsel[0], "dA": nsel[1], "dB": nsel[2]},
+            "plain_fixed_N": {"N": n_fix, "ms_per_step": ms_fixed, "tflops": tf(ms_fixed)},
+            "grad_rel_err_vs_fp64": err, "l2": "flushed (256 MiB write) before every timed step"}
 
 
-def run_sgemm(args):
-    """FP32 SGEMM emulation 8192^3, phi = 1, N from the bound rule for tau = 1e-7."""
+def form_batched(dev, target, fast, steps, warmup, peak, flush, samples_per_problem=4):
+    """64 uneven problems (m, n, k log-uniform in [128, 4096], phi ~ U(0.5, 4)),
+    per-problem bound-chosen N for `target`, one oz2_gemm_batched call replayed
+    from a CUDA graph, against 64 plain oz2_gemm_ex calls at the fixed N that
+    meets the target for every problem (the largest chosen N)."""
     import torch
     from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.accuracy import sampled_errors
+    from paper_2602_02549_b300.inputs import batched_specs, paper_matrix_torch
+    specs = batched_specs(64, 0)
+    probs, flops = [], 0.0
+    for i, (m, n, k, phi) in enumerate(specs):
+        probs.append(dict(A=paper_matrix_torch(m, k, phi, 2 * i, dev), B=paper_matrix_torch(k, n, phi, 2 * i + 1, dev),
+                          C=torch.empty((m, n), dtype=torch.float64, device=dev), nmoduli=0, target=target, nmax=30,
+                          fast=fast, n_out=torch.zeros(1, dtype=torch.int32, device=dev)))
+        flops += 2.0 * m * n * k
+    ws = torch.empty(B.batched_workspace_size(probs), dtype=torch.uint8, device=dev)
+    policy, policy_ms = B.batched_autotune(probs, workspace=ws)     # outside the capture
+    assert B.gemm_batched(probs, workspace=ws) == 0
+    torch.cuda.synchronize()
+    Ns = [int(q["n_out"].item()) for q in probs]
+    stream = torch.cuda.current_stream(dev)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        assert B.gemm_batched(probs, workspace=ws, stream=s) == 0
+    ms = timed_each(g.replay, steps, warmup, stream, flush)
+    assert B.sync() == 0
+    Nfix = max(Ns)
+    wmax = max(B.workspace_size(q["A"].size(0), q["B"].size(1), q["A"].size(1), Nfix) for q in probs)
+    ws1 = torch.empty(wmax, dtype=torch.uint8, device=dev)
+
+    def plain():
+        for q in probs:
+            rc = B.gemm_ex(q["A"], q["B"], q["C"], Nfix, B.OZ2_FAST if fast else 0, workspace=ws1, stream=stream)
+            assert rc == 0
+    ms_plain = timed_each(plain, steps, warmup, stream, flush)
+    g.replay()
+    torch.cuda.synchronize()
+    # errors per problem on sampled entries; the largest of each measure over the batch
+    worst = {"literal": 0.0, "componentwise": 0.0, "normwise": 0.0}
+    gen = torch.Generator(device="cpu").manual_seed(99)
+    for q in probs:
+        m, n = q["C"].shape
+        ii = torch.randint(0, m, (samples_per_problem,), generator=gen).to(dev)
+        jj = torch.randint(0, n, (samples_per_problem,), generator=gen).to(dev)
+        e = sampled_errors(q["A"][ii].cpu().numpy(), q["B"][:, jj].t().contiguous().cpu().numpy(),
+                           q["C"][ii, jj].cpu().numpy())
+        for key in worst:
+            worst[key] = max(worst[key], e[key])
+    mma = sum(2.0 * q["A"].size(0) * q["B"].size(1) * q["A"].size(1) * (N + (0 if fast else 1))
+              for q, N in zip(probs, Ns))
+    tf = lambda t: flops / (t * 1e-3) / 1e12   # noqa: E731
+    return {"workload": "batched_64_uneven_128_4096_tau%g_%s" % (target, "fast" if fast else "accurate"),
+            "problems": 64, "total_2mnk": flops, "ms_per_step": ms, "tflops": tf(ms),
+            "emulated_frac": mma / (ms * 1e-3) / 1e12 / peak,
+            "graph": "one oz2_gemm_batched call captured and replayed",
+            "n_moduli": {"min": min(Ns), "max": max(Ns), "mean": sum(Ns) / len(Ns)},
+            "autotune": {"policy": policy, "ms_per_policy": policy_ms,
+                         "policies": ["all 128x256", "all 128x128", "128x128 where n mod 256 <= 128",
+                                      "per problem, measured alone"]},
+            "plain_fixed_N": {"N": Nfix, "ms_per_step": ms_plain, "tflops": tf(ms_plain),
+                              "emulated_frac": sum(2.0 * q["A"].size(0) * q["B"].size(1) * q["A"].size(1)
+                                                   * (Nfix + (0 if fast else 1)) for q in probs)
+                              / (ms_plain * 1e-3) / 1e12 / peak},
+            "accuracy": dict(worst, samples=samples_per_problem * 64),
+            "l2": "flushed (256 MiB write) before every timed call"}
+
+
+def run_workload(args):
+    """--workload other than the square headline: one JSON line for that form."""
+    import torch
     from paper_2602_02549_b300.build import build
-    from paper_2602_02549_b300.inputs import paper_matrix_torch
     build()
     dev = torch.device("cuda", 0)
-    s = 8192 if args.size == 16384 else args.size
-    tau = 1e-7 if args.target == 1e-15 else args.target
-    A = paper_matrix_torch(s, s, args.phi, 0, dev, torch.float32)
-    Bm = paper_matrix_torch(s, s, args.phi, 1, dev, torch.float32)
-    C = torch.empty((s, s), dtype=torch.float32, device=dev)
-    nout = torch.zeros(1, dtype=torch.int32, device=dev)
-    ws = torch.empty(B.workspace_size(s, s, s, 14, 0, True), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-    fn = lambda: B.gemm_ex(A, Bm, C, args.nmoduli, B.OZ2_FAST if args.mode == "fast" else 0,
-                           target=tau if not args.nmoduli else 0.0, nmax=14 if not args.nmoduli else 0,
-                           workspace=ws, stream=stream, n_out=nout)
-    ms = timed(fn, args.steps, args.warmup, stream)
-    n_used = int(nout.item())
-    plain = None
-    if not args.nmoduli:
-        fixed = lambda: B.gemm_ex(A, Bm, C, n_used, B.OZ2_FAST if args.mode == "fast" else 0, workspace=ws,
-                                  stream=stream)
-        p_ms = timed(fixed, args.steps, args.warmup, stream)
-        plain = {"N": n_used, "ms_per_step": p_ms, "tflops": 2.0 * s ** 3 / (p_ms * 1e-3) / 1e12}
-    torch.matmul(A, Bm)
-    ms_native = timed(lambda: torch.matmul(A, Bm), 3, 1, stream)
-    print(json.dumps({
-        "metric": METRIC.replace("DGEMM", "SGEMM"), "value": 2.0 * s ** 3 / (ms * 1e-3) / 1e12, "unit": "TFLOPS",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "sgemm_square_%d_phi%g_tau%g_%s" % (s, args.phi, tau, args.mode)},
-        "n_moduli": n_used,
-        "plain_fixed_N": plain,
-        "native_fp32_tflops": 2.0 * s ** 3 / (ms_native * 1e-3) / 1e12,
-        "cublas_emulation_env": cublas_emulation_env(),
-        "native_fp32_tf32": bool(torch.backends.cuda.matmul.allow_tf32)}))
+    torch.cuda.set_device(dev)
+    peaks, kind = load_peaks()
+    peak = float(peaks["bf16_tflops_sustained"])
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    fast = args.mode == "fast"
+    if args.workload == "batched":
+        rec = form_batched(dev, 1e-14 if args.target == 1e-15 else args.target, fast, args.steps, args.warmup,
+                           peak, flush)
+        metric = METRIC
+    elif args.workload == "autograd":
+        rec = form_autograd(dev, args.target, args.nmax, fast, args.steps, args.warmup, peak, flush)
+        metric = METRIC
+    elif args.workload == "sgemm":
+        rec = form_sgemm(dev, 8192 if args.size == 16384 else args.size, args.phi,
+                         1e-7 if args.target == 1e-15 else args.target, fast, args.steps, args.warmup, peak, flush,
+                         min(args.acc_samples, 256))
+        metric = METRIC.replace("DGEMM", "SGEMM")
+    else:
+        {"splitk": run_splitk, "zgemm": run_zgemm}[args.workload](args)
+        return
+    line = {"metric": metric, "value": rec["tflops"], "unit": "TFLOPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.workload == "sgemm" else "f64",
+            "data": "synthetic", "config": {"workload": rec["workload"]}, "peak_source": f"bf16_tflops_sustained ({kind})"}
+    line.update({k: v for k, v in rec.items() if k not in ("workload", "ms_per_step", "tflops")})
+    print(json.dumps(line))
 
 
 def run_splitk(args):
@@ -504,8 +649,7 @@ def main():
         run_reference(args)
         return
     if args.workload != "square":
-        {"batched": run_batched, "autograd": run_autograd, "sgemm": run_sgemm,
-         "splitk": run_splitk, "zgemm": run_zgemm}[args.workload](args)
+        run_workload(args)
         return
     import torch
     from paper_2602_02549_b300 import binding as B
@@ -689,6 +833,24 @@ def main():
         s = args.cpu_sample
         cpu = cpu_baseline(A[:s].cpu().numpy(), Bm[:, :s].cpu().numpy(), N_used, s, args.phi)
 
+    # the other forms, each against the plain fixed-N form at the same accuracy,
+    # in timed regions of their own (one GPU, rank 0 of a single-rank run)
+    forms = {}
+    if rank == 0 and world == 1 and not args.no_forms:
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        FS, FW = 5, 3
+        forms["fast"] = form_square(dev, m, args.phi, args.target, nmax, True, FS, FW, peak, flush, 128,
+                                    A=A, Bm=Bm, ws=ws)
+        del A, Bm, C, ws
+        torch.cuda.empty_cache()
+        forms["small"] = [form_square(dev, sz, 1.0, args.target, args.nmax, args.mode == "fast", 10, FW, peak, flush,
+                                      128, graph=True) for sz in (1024, 4096)]
+        forms["sgemm"] = form_sgemm(dev, 8192, 1.0, 1e-7, args.mode == "fast", FS, FW, peak, flush, 128)
+        forms["autograd"] = form_autograd(dev, args.target, args.nmax, args.mode == "fast", 10, FW, peak, flush)
+        forms["batched"] = form_batched(dev, 1e-14, args.mode == "fast", 10, FW, peak, flush)
+        torch.cuda.synchronize()
+        assert B.sync() == 0
+
     if rank == 0:
         # clear, stats (A and B in one launch), quantise x2, scaling GEMM (fast: the
         # two majorant kernels instead), [bound reduction], N + mu/nu, residues x2,
@@ -711,6 +873,7 @@ def main():
             "native_fp64_tflops": {"value": native_tflops, "size": ns, "note": "torch.matmul float64, context",
                                    "cublas_emulation_env": cublas_emulation_env()},
             "clocks": clk.summary(),
+            **forms,
         }))
     if world > 1:
         torch.distributed.destroy_process_group()

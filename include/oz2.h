@@ -71,8 +71,12 @@ extern "C" {
 typedef struct oz2_opts {
     void   *stream;          /* cudaStream_t; NULL = legacy default stream                 */
     void   *workspace;       /* device scratch of >= oz2_workspace_size(...) bytes,
-                                256-byte aligned.  NULL: the library uses a per-device
-                                cached buffer it grows with cudaMalloc.                    */
+                                256-byte aligned.  NULL: the library uses one cached
+                                buffer per device, shared by every call without a
+                                workspace and grown with cudaMalloc (a buffer it replaces
+                                stays allocated until exit); such calls must not overlap
+                                on the GPU (serialise them per device: calls on two
+                                streams or from two host threads race on that buffer).   */
     size_t  workspace_bytes;
     double  target;          /* nmoduli == 0: target normwise relative error tau           */
     int     nmax;            /* nmoduli == 0: largest N tried (0 = 20 DGEMM, 14 SGEMM)     */
@@ -108,7 +112,9 @@ typedef struct oz2_opts {
  *            and the S results are added into C in range order, one rounding
  *            in the output precision per addition.
  *   m, n, k  >= 1.
- * oz2_gemm uses the library-managed workspace and the legacy default stream.
+ * oz2_gemm uses the library-managed workspace (see oz2_opts.workspace: calls
+ * without a workspace share one buffer per device and must be serialised per
+ * device) and the legacy default stream.
  */
 OZ2_API int oz2_gemm(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
                      double *C, int ldc, int nmoduli, int mode);
@@ -153,11 +159,11 @@ OZ2_API size_t oz2_zworkspace_size(int m, int n, int k, int nmax, int mode, int 
  * with its own exponents and its own N (fixed, or the bound rule for its own
  * target).  The scaling GEMMs of all problems run as one persistent tcgen05
  * launch and the N residue GEMMs of all problems as another (64 problems per
- * launch; heaviest first); the light phases of the problems run concurrently
- * on library-owned streams forked from and joined back to opts->stream.  With
- * a caller workspace the call allocates nothing and enqueues only stream work
- * and event records/waits, so it can be captured into a CUDA graph and
- * replayed as one launch.  Each result is bit-identical to oz2_gemm_ex on the
+ * launch; heaviest first), and every other phase is one launch over the work
+ * of all problems, each on opts->stream (there are no library-owned streams).
+ * With a caller workspace the call allocates nothing and enqueues only kernel
+ * launches (and, with phase_events, event records) on that stream, so it can be
+ * captured into a CUDA graph and replayed as one launch.  Each result is bit-identical to oz2_gemm_ex on the
  * same problem.  opts: stream, workspace, phase_events are used; the other
  * fields are ignored (per-problem settings live in oz2_problem).
  */

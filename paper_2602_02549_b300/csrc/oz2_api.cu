@@ -31,6 +31,10 @@ struct DeviceState {
     int sms = 0;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    // buffers replaced by a larger one: kept (not freed) until the process
+    // exits, because a call on another stream or host thread may have been
+    // handed one of them and not yet enqueued its kernels
+    std::vector<void *> retired;
     // tile width per problem of a batch, chosen by oz2_batched_autotune (or set
     // with oz2_batched_set_policy), keyed by the batch's shapes and settings
     std::unordered_map<uint64_t, std::vector<uint8_t>> tiles;
@@ -388,19 +392,26 @@ struct Job {
     }
 };
 
-// the library-managed workspace of the current device (grown with cudaMalloc)
+// The library-managed workspace of the current device, for calls without a
+// workspace of their own: one buffer per device, shared by every such call (so
+// those calls must not overlap on the GPU).  It grows with cudaMalloc, by at
+// least a quarter each time so that the superseded buffers, which stay
+// allocated until the process exits, add up to a bounded multiple of the
+// largest size.  Nothing synchronises the device or frees memory here.
 int managed_workspace(int dev, size_t bytes, uint8_t **out) {
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceState &s = g_dev[dev];
     if (s.ws_bytes < bytes) {
-        if (s.ws) {
-            cudaDeviceSynchronize();
-            cudaFree(s.ws);
-            s.ws = nullptr;
-            s.ws_bytes = 0;
+        size_t size = std::max(bytes, s.ws_bytes + s.ws_bytes / 4);
+        void *p = nullptr;
+        if (cudaMalloc(&p, size) != cudaSuccess) {
+            (void)cudaGetLastError();
+            size = bytes;                    // the larger step did not fit: exactly what is needed
+            if (cudaMalloc(&p, size) != cudaSuccess) return cuda_fail(cudaErrorMemoryAllocation);
         }
-        if (cudaMalloc(&s.ws, bytes) != cudaSuccess) return cuda_fail(cudaErrorMemoryAllocation);
-        s.ws_bytes = bytes;
+        if (s.ws) s.retired.push_back(s.ws);
+        s.ws = p;
+        s.ws_bytes = size;
     }
     *out = static_cast<uint8_t *>(s.ws);
     return OZ2_OK;

@@ -26,9 +26,12 @@ void *g_scratch_ptr[kMaxDevices] = {};
 // Device address of the scratch array on the current device, looked up once per
 // device.  In host code `g_noalloc_scratch` only names a host-side stand-in, so
 // the address must come from cudaGetSymbolAddress with the device current.
+// cudaSetDevice first binds the device's primary context, the one the library's
+// kernels run in, so the address is that context's even when the caller had
+// another context current.
 int scratch_for_current_device(void **out) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices || cudaSetDevice(dev) != cudaSuccess) {
         (void)cudaGetLastError();
         return OZ2_ECUDA;
     }

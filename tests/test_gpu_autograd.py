@@ -95,3 +95,25 @@ def test_call_from_another_host_thread():
     t.start()
     t.join()
     assert torch.equal(out["C"], ref)
+
+
+def test_backward_single_calls_beyond_k_max():
+    # dB = A^T dC has the inner dimension m; with m just above 2^17 the
+    # two-problem batched backward (k <= 2^17 per problem) cannot take it, so
+    # both gradients come from single calls, dB through split-K.  Each equals a
+    # direct emulated call on the materialised transpose, bit for bit.
+    import torch
+    from paper_2602_02549_b300 import binding as Bd
+    from paper_2602_02549_b300.autograd import oz2_matmul
+    m, k, n = Bd.K_MAX + 3, 8, 3
+    A = torch.tensor(paper_matrix(m, k, 1.0, 11), device="cuda", requires_grad=True)
+    B = torch.tensor(paper_matrix(k, n, 1.0, 12), device="cuda", requires_grad=True)
+    dC = torch.tensor(paper_matrix(m, n, 1.0, 13), device="cuda")
+    oz2_matmul(A, B, 0, 1e-15).backward(dC)
+    with torch.no_grad():
+        dA = Bd.matmul(dC, B.t().contiguous(), 0, target=1e-15)
+        dB = Bd.matmul(A.t().contiguous(), dC, 0, target=1e-15)
+        ref = A.detach().t() @ dC
+    assert torch.equal(A.grad, dA)
+    assert torch.equal(B.grad, dB)
+    assert ((B.grad - ref).abs().max() <= 1e-13 * ref.abs().max()).item()
