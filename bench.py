@@ -280,6 +280,23 @@ def sampled_accuracy(A, Bm, C, samples, seed=1234, fp32=False):
     return sampled_errors(rows, cols, vals)
 
 
+def phase_split(run, stream, reps=5):
+    """Mean milliseconds per phase of a call (the library's phase events), from
+    `reps` extra calls outside any timed region; run(events) makes one call."""
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(B.NPHASES + 1)] for _ in range(reps)]
+    for evs in ev:
+        for e in evs:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for evs in ev:
+        run(evs)
+    torch.cuda.synchronize()
+    return dict(zip(B.PHASE_NAMES, [statistics.mean(evs[p].elapsed_time(evs[p + 1]) for evs in ev)
+                                    for p in range(B.NPHASES)]))
+
+
 def emulated_frac(tflops, N, fast, peak):
     """Emulated TFLOPS over the rate the N (+1 for the scaling GEMM in accurate
     mode) BF16 products would reach at `peak` with nothing else taking time."""
@@ -336,6 +353,8 @@ def form_square(dev, size, phi, target, nmax, fast, steps, warmup, peak, flush, 
         ms_g = timed_each(g.replay, steps, warmup, stream, flush)
         tf_g = flops / (ms_g * 1e-3) / 1e12
         rec["graph_replay"] = {"ms_per_step": ms_g, "tflops": tf_g, "emulated_frac": emulated_frac(tf_g, N, fast, peak)}
+    rec["phase_ms"] = phase_split(lambda ev: B.gemm_ex(A, Bm, C, 0, flags, target=target, nmax=nmax, workspace=ws,
+                                                       stream=stream, phase_events=ev), stream)
     call()
     torch.cuda.synchronize()
     rec["accuracy"] = sampled_accuracy(A, Bm, C, samples)
@@ -490,6 +509,7 @@ def form_batched(dev, target, fast, steps, warmup, peak, flush, samples_per_prob
             rc = B.gemm_ex(q["A"], q["B"], q["C"], Nfix, B.OZ2_FAST if fast else 0, workspace=ws1, stream=stream)
             assert rc == 0
     ms_plain = timed_each(plain, steps, warmup, stream, flush)
+    phases = phase_split(lambda ev: B.gemm_batched(probs, workspace=ws, stream=stream, phase_events=ev), stream)
     g.replay()
     torch.cuda.synchronize()
     # errors per problem on sampled entries; the largest of each measure over the batch
@@ -509,7 +529,7 @@ def form_batched(dev, target, fast, steps, warmup, peak, flush, samples_per_prob
     return {"workload": "batched_64_uneven_128_4096_tau%g_%s" % (target, "fast" if fast else "accurate"),
             "problems": 64, "total_2mnk": flops, "ms_per_step": ms, "tflops": tf(ms),
             "emulated_frac": mma / (ms * 1e-3) / 1e12 / peak,
-            "graph": "one oz2_gemm_batched call captured and replayed",
+            "graph": "one oz2_gemm_batched call captured and replayed", "phase_ms": phases,
             "n_moduli": {"min": min(Ns), "max": max(Ns), "mean": sum(Ns) / len(Ns)},
             "autotune": {"policy": policy, "ms_per_policy": policy_ms,
                          "policies": ["all 128x256", "all 128x128", "128x128 where n mod 256 <= 128",
