@@ -515,8 +515,14 @@ def choose_N(A: np.ndarray, B: np.ndarray, alpha, beta, cmax_row, cmax_col,
     a2 = pow2_prime(np.asarray(alpha), np.asarray(cmax_row))
     b2 = pow2_prime(np.asarray(beta), np.asarray(cmax_col))
     L = float(np.max(np.abs(A).max(axis=0) * np.abs(B).max(axis=1))) if m and n and k else 0.0
-    maxR, maxK = float(R.max(initial=0)), float(K.max(initial=0))
-    ma2, mb2 = float(a2.max(initial=0)), float(b2.max(initial=0))
+    return choose_N_from_maxima(float(R.max(initial=0)), float(K.max(initial=0)), float(a2.max(initial=0)),
+                                float(b2.max(initial=0)), L, k, tau, nmax, b)
+
+
+def choose_N_from_maxima(maxR: float, maxK: float, ma2: float, mb2: float, L: float, k: int,
+                         tau: float, nmax: int, b: int = 64) -> tuple[int, dict]:
+    """The N rule of choose_N from its five maxima (max_i R_i, max_j K_j,
+    max_i 2^alpha'_i, max_j 2^beta'_j, L) and k."""
     chosen, ratios = nmax, {}
     for N in range(N_MIN, nmax + 1):
         bt = bound_terms(N, b)
