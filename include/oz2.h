@@ -264,6 +264,21 @@ OZ2_API int oz2_check_log2f(void *stream, unsigned long long *dev_out);
  * Returns OZ2_OK, OZ2_EINVAL or OZ2_ECUDA.  No GPU fault is involved. */
 OZ2_API int oz2_wait_selftest(void *stream, unsigned int limit_us);
 
+/* Diagnostic for the failure path of the residue GEMM (the paper has no
+ * counterpart): the same call as oz2_gemm_ex (mode 0, 64 < k <= 2^17),
+ * except that in the residue GEMM every CTA arms the mbarrier of the operand
+ * stage of k-block 1 of its first tile but issues no copy for it.  The MMA
+ * warp's wait on that stage gives up after limit_us microseconds (1 .. 10^6;
+ * every wait of that launch uses this limit), the CTA stops its loops, waits
+ * (again at most limit_us) for the copies and MMAs it had already issued, frees
+ * its TMEM and returns.  The next oz2_sync on that stream reports OZ2_ETIMEOUT
+ * and clears the status; C is invalid.  No GPU fault is involved, and later
+ * calls run normally.  Returns as oz2_gemm_ex, or OZ2_EINVAL for a limit or k
+ * out of range. */
+OZ2_API int oz2_gemm_timeout_selftest(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                                      double *C, int ldc, int nmoduli, unsigned int limit_us,
+                                      const oz2_opts *opts);
+
 /* Size of the fixed device scratch used by oz2_gemm_noalloc (32 MiB). */
 #define OZ2_NOALLOC_SCRATCH_BYTES (32u << 20)
 

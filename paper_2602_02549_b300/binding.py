@@ -139,6 +139,29 @@ def wait_selftest(limit_us: int = 20000, stream=None) -> int:
     return L.oz2_wait_selftest(ctypes.c_void_p(s.cuda_stream), int(limit_us))
 
 
+def gemm_timeout_selftest(A, B, C, nmoduli: int, limit_us: int = 5000, *, workspace=None, stream=None) -> int:
+    """oz2_gemm_timeout_selftest on float64 CUDA tensors: the emulated GEMM with
+    the residue GEMM's loads of one stage left out, so that its bounded waits
+    give up after limit_us (the next sync reports OZ2_ETIMEOUT).  Returns the status."""
+    import torch
+    m, k = A.shape
+    n = B.size(1)
+    o = oz2_opts()
+    s = stream if stream is not None else torch.cuda.current_stream(A.device)
+    o.stream = ctypes.c_void_p(s.cuda_stream)
+    if workspace is None:
+        workspace = torch.empty(workspace_size(m, n, k, nmoduli), dtype=torch.uint8, device=A.device)
+    o.workspace = ctypes.c_void_p(workspace.data_ptr())
+    o.workspace_bytes = workspace.numel()
+    L = lib()
+    L.oz2_gemm_timeout_selftest.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int] * 3 + \
+        [ctypes.c_int, ctypes.c_uint, ctypes.POINTER(oz2_opts)]
+    L.oz2_gemm_timeout_selftest.restype = ctypes.c_int
+    with torch.cuda.device(A.device):
+        return L.oz2_gemm_timeout_selftest(m, n, k, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), _ptr(C),
+                                           _ld(C, "C"), int(nmoduli), int(limit_us), ctypes.byref(o))
+
+
 def sum_tables(N: int, fp32: bool = False) -> tuple:
     """The CRT-sum constants as the device holds them: (list of k_l, esum) with
     s_l2 (DGEMM) or s_l1 (SGEMM) = k_l 2^esum (host-only)."""

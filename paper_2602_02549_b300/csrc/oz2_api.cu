@@ -196,6 +196,15 @@ int encode_bf16_2d(CUtensorMap *tm, const void *base, uint64_t rows, uint64_t co
 // __launch_bounds__ minimum).
 constexpr int kResidBlocksPerSM = 3;
 
+// The residue GEMM's failure-path test hook (oz2_gemm_timeout_selftest sets it
+// for the duration of one call on its host thread): the k-block whose loads
+// each CTA skips on its first item (-1: none) and the limit of every wait.
+struct GemmHook {
+    int kb = -1;
+    unsigned long long limit_ns = kWaitLimitNs;
+};
+thread_local GemmHook g_hook;
+
 // One persistent launch over the problems of `G` (item counts filled in here):
 // one CTA per SM, or fewer when there are fewer work items.
 template <int EPI, int BN, int CAP>
@@ -207,6 +216,8 @@ int launch_gemm(GemmGroup<CAP> &G, int sms, cudaStream_t st) {
         items += (long long)P.tiles_m * P.tiles_n * P.planes;
     }
     G.total_items = items;
+    G.wait_limit_ns = EPI == EPI_MOD ? g_hook.limit_ns : kWaitLimitNs;
+    G.hook_kb = EPI == EPI_MOD ? g_hook.kb : -1;
     if (items == 0) return OZ2_OK;
     const int grid = int(std::min<long long>(items, sms));
     k_gemm<EPI, BN, CAP><<<grid, gemm::kThreads, gemm::Cfg<BN>::kSmemBytes, st>>>(G);
@@ -1054,6 +1065,16 @@ int oz2_wait_selftest(void *stream, unsigned int limit_us) {
     if (rc) return rc;
     k_wait_selftest<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(uint64_t(limit_us) * 1000ull);
     return cuda_fail(cudaGetLastError());
+}
+
+int oz2_gemm_timeout_selftest(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
+                              int ldc, int nmoduli, unsigned int limit_us, const oz2_opts *opts) {
+    if (limit_us == 0 || limit_us > 1000000u || k <= gemm::BK || k > OZ2_K_MAX) return OZ2_EINVAL;
+    g_hook.kb = 1;
+    g_hook.limit_ns = (unsigned long long)limit_us * 1000ull;
+    const int rc = run<double>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, 0, opts);
+    g_hook = GemmHook{};
+    return rc;
 }
 
 int oz2_last_error(int *line) {

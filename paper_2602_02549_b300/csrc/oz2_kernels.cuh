@@ -968,6 +968,10 @@ struct GemmGroup {
     GemmProblem p[CAP];
     int count;
     long long total_items;
+    unsigned long long wait_limit_ns;   // limit of every bounded wait (kWaitLimitNs)
+    int hook_kb;                        // test hook, -1 normally: at this k-block of its
+                                        // first item each CTA's producer arms the stage
+                                        // but loads nothing, so the MMA warp's wait expires
 };
 
 struct WorkItem {
@@ -1018,9 +1022,25 @@ __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, vola
 // Every lane waits (each gets the barrier's acquire); the warp proceeds only if
 // all lanes saw the phase complete, so .sync.aligned tcgen05 instructions that
 // follow are always executed by the whole warp.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-    const bool ok = bounded_wait(bar, parity, abort_flag);
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          uint64_t limit_ns) {
+    const bool ok = bounded_wait(bar, parity, abort_flag, limit_ns);
     return __all_sync(0xffffffffu, ok) != 0;
+}
+
+// Teardown after an abort: waits, up to limit_ns and whatever the abort flag
+// says, for the phase `parity` of `bar` (the completion of copies or MMAs that
+// were already issued), so that the CTA releases its shared memory and TMEM
+// only once nothing in flight writes to them.  Gives up with bit 1 of the
+// status word set.
+__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    const uint64_t t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(bar, parity)) {
+        if (ptx::globaltimer() - t0 > limit_ns) {
+            atomicOr(&g_status, 2);
+            return;
+        }
+    }
 }
 
 // Epilogue of one output tile for one epilogue thread: NC INT32 sums of row
@@ -1091,6 +1111,11 @@ __device__ __forceinline__ void tile_epilogue(const GemmProblem &P, int l, int r
 // the epilogue warps turn each segment into INT32 and add it up.  The shared
 // memory stage ring and the two TMEM accumulators run on across items, so the
 // epilogue of one tile overlaps the MMAs of the next.
+//
+// Failure path: every wait gives up after G.wait_limit_ns, sets the CTA's abort
+// flag (which stops the other roles' loops) and the device status word.  Before
+// the CTA frees its TMEM and exits, the producer waits for the loads it issued
+// and the MMA warp for the MMAs it issued (drain_wait, bounded again).
 template <int EPI, int BN, int CAP>
 __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constant__ GemmGroup<CAP> G) {
     using namespace gemm;
@@ -1104,12 +1129,14 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
     uint8_t *smem = smem_raw + pad;
     const uint32_t sbase = raw + pad;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     auto bar_full = [&](int s) { return ptx::smem_addr(bars + s); };
     auto bar_empty = [&](int s) { return ptx::smem_addr(bars + STAGES + s); };
     auto bar_accf = [&](int b) { return ptx::smem_addr(bars + 2 * STAGES + b); };
     auto bar_acce = [&](int b) { return ptx::smem_addr(bars + 2 * STAGES + 2 + b); };
+    const uint32_t bar_drain = ptx::smem_addr(bars + 2 * STAGES + 4);   // MMA teardown after an abort
+    const uint64_t limit = G.wait_limit_ns;
     auto sA = [&](int s) { return sbase + uint32_t(s) * STAGE_BYTES; };
     auto sB = [&](int s) { return sbase + uint32_t(s) * STAGE_BYTES + A_BYTES; };
 
@@ -1117,6 +1144,7 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) { ptx::mbar_init(bar_full(s), 1); ptx::mbar_init(bar_empty(s), 1); }
         for (int b = 0; b < 2; b++) { ptx::mbar_init(bar_accf(b), 1); ptx::mbar_init(bar_acce(b), 8); }
+        ptx::mbar_init(bar_drain, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -1129,11 +1157,12 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const long long total = G.total_items;
+    uint32_t issued = 0;                         // producer: stages armed (lane 0 of warp 0)
 
     if (warp == 0) {
         if (lane == 0) {
             uint32_t kbc = 0;                    // stage ring position, across items
-            bool ok = true;
+            bool ok = true, first = true;
             for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
                 const WorkItem w = decode_item(G, g);
                 if (w.skip) continue;
@@ -1143,12 +1172,15 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
                 for (int kb = 0; kb < P.kb_total; kb++, kbc++) {
                     const int s = int(kbc % STAGES);
                     const uint32_t ph = (kbc / STAGES) & 1u;
-                    if (kbc >= STAGES && !bounded_wait(bar_empty(s), ph ^ 1u, abort_flag)) { ok = false; break; }
+                    if (kbc >= STAGES && !bounded_wait(bar_empty(s), ph ^ 1u, abort_flag, limit)) { ok = false; break; }
                     ptx::mbar_arrive_expect_tx(bar_full(s), STAGE_BYTES);
+                    if (first && kb == G.hook_kb) continue;      // test hook: armed, never loaded
                     ptx::tma_load_2d(sA(s), &P.tmA, kb * BK, row_a, bar_full(s));
                     ptx::tma_load_2d(sB(s), &P.tmB, kb * BK, row_b, bar_full(s));
                 }
+                first = false;
             }
+            issued = kbc;
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -1161,7 +1193,7 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
                 const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
                 for (int seg = 0; seg < nseg && ok; seg++, segc++) {
                     const int buf = int(segc & 1u);
-                    if (segc >= 2 && !bounded_wait(bar_acce(buf), ((segc >> 1) - 1) & 1u, abort_flag)) {
+                    if (segc >= 2 && !bounded_wait(bar_acce(buf), ((segc >> 1) - 1) & 1u, abort_flag, limit)) {
                         ok = false;
                         break;
                     }
@@ -1172,7 +1204,7 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
                     for (int kb = kb0; kb < kb1; kb++, kbc++) {
                         const int s = int(kbc % STAGES);
                         const uint32_t ph = (kbc / STAGES) & 1u;
-                        if (!bounded_wait(bar_full(s), ph, abort_flag)) { ok = false; break; }
+                        if (!bounded_wait(bar_full(s), ph, abort_flag, limit)) { ok = false; break; }
                         ptx::tc_fence_after();
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; kk++) {
@@ -1201,7 +1233,7 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
             for (int i = 0; i < NC; i++) acc[i] = 0;
             for (int seg = 0; seg < nseg; seg++, segc++) {
                 const int buf = int(segc & 1u);
-                if (!warp_wait(bar_accf(buf), (segc >> 1) & 1u, abort_flag)) { ok = false; break; }
+                if (!warp_wait(bar_accf(buf), (segc >> 1) & 1u, abort_flag, limit)) { ok = false; break; }
                 ptx::tc_fence_after();
                 const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + half * NC);
 #pragma unroll
@@ -1218,6 +1250,20 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
             }
             if (!ok) break;
             tile_epilogue<EPI, NC>(P, w.l, w.tile_m * BM + q * 32 + lane, w.tile_n * BN + half * NC, lane, acc);
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    // every role has left its loop; the abort flag no longer changes
+    if (*abort_flag && lane == 0) {
+        if (warp == 0) {
+            // the last STAGES stages armed: their loads (if issued) must land
+            for (uint32_t j = issued > uint32_t(STAGES) ? issued - STAGES : 0u; j < issued; j++)
+                drain_wait(bar_full(int(j % STAGES)), (j / STAGES) & 1u, limit);
+        } else if (warp == 1) {
+            // arrives once every MMA this thread issued has completed
+            ptx::mma_commit(bar_drain);
+            drain_wait(bar_drain, 0, limit);
         }
     }
     ptx::tc_fence_before();
