@@ -15,8 +15,10 @@ its own (CUDA events around every call, L2 flushed before it) and each beside
 the plain fixed-N form at the same accuracy: `fast` (16384^3, fast scaling),
 `small` (1024^3 and 4096^3, also replayed from a CUDA graph), `sgemm` (FP32,
 8192^3, target 1e-7), `autograd` (loss ||AB - T||^2, A 4096 x 2048, B 2048 x
-1024) and `batched` (64 uneven problems, target 1e-14, one graph-captured
-call).  `--workload` runs one of them alone; `--no-forms` skips them.
+1024), `batched` (64 uneven problems, target 1e-14, one graph-captured
+call) and `componentwise` (the componentwise N rule beside the normwise one
+at 4096^3, phi = 0.5 .. 4).  `--workload` runs one of them alone; `--no-forms`
+skips them.
 
 Prints one JSON line on rank 0.
 """
@@ -542,6 +544,44 @@ def form_batched(dev, target, fast, steps, warmup, peak, flush, samples_per_prob
             "l2": "flushed (256 MiB write) before every timed call"}
 
 
+def form_componentwise(dev, size, target, steps, warmup, peak, flush, samples):
+    """The componentwise N rule (OZ2_COMPONENTWISE) beside the normwise rule at
+    size^3 for phi = 0.5, 1, 2, 4: the N each picks, the time of the
+    componentwise call (its second integer product included) and the
+    componentwise error max |C - AB| / (|A||B|) of each on sampled entries."""
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    from paper_2602_02549_b300.inputs import paper_matrix_torch
+    out = []
+    m = n = k = size
+    ws = torch.empty(B.workspace_size(m, n, k, 49), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for phi in (0.5, 1.0, 2.0, 4.0):
+        A = paper_matrix_torch(m, k, phi, 0, dev)
+        Bm = paper_matrix_torch(k, n, phi, 1, dev)
+        C = torch.empty((m, n), dtype=torch.float64, device=dev)
+        rec = {"phi": phi}
+        for name, mode in (("normwise", 0), ("componentwise", B.OZ2_COMPONENTWISE)):
+            nout = torch.zeros(1, dtype=torch.int32, device=dev)
+
+            def call():
+                rc = B.gemm_ex(A, Bm, C, 0, mode, target=target, nmax=49, workspace=ws, stream=stream, n_out=nout)
+                if rc:
+                    raise B.Oz2Error(rc, "oz2_gemm_ex")
+            ms = timed_each(call, steps, warmup, stream, flush)
+            N = int(nout.item())
+            call()
+            torch.cuda.synchronize()
+            acc = sampled_accuracy(A, Bm, C, samples)
+            tf = 2.0 * m * n * k / (ms * 1e-3) / 1e12
+            rec[name] = {"n_moduli": N, "ms_per_step": ms, "tflops": tf,
+                         "componentwise_err": acc["componentwise"], "normwise_err": acc["normwise"]}
+        out.append(rec)
+        del A, Bm, C
+    return {"workload": "dgemm_square_%d_tau%g_normwise_vs_componentwise_rule" % (size, target), "nmax": 49,
+            "by_phi": out, "l2": "flushed (256 MiB write) before every timed call"}
+
+
 def run_workload(args):
     """--workload other than the square headline: one JSON line for that form."""
     import torch
@@ -868,6 +908,7 @@ def main():
         forms["sgemm"] = form_sgemm(dev, 8192, 1.0, 1e-7, args.mode == "fast", FS, FW, peak, flush, 128)
         forms["autograd"] = form_autograd(dev, args.target, args.nmax, args.mode == "fast", 10, FW, peak, flush)
         forms["batched"] = form_batched(dev, 1e-14, args.mode == "fast", 10, FW, peak, flush)
+        forms["componentwise"] = form_componentwise(dev, 4096, args.target, FS, FW, peak, flush, 128)
         torch.cuda.synchronize()
         assert B.sync() == 0
 

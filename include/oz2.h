@@ -51,6 +51,7 @@ extern "C" {
 #define OZ2_TRANS_B     4
 #define OZ2_CONJ_A      8   /* complex calls only: op(A) conjugated (with OZ2_TRANS_A: A^H) */
 #define OZ2_CONJ_B     16   /* complex calls only: op(B) conjugated                        */
+#define OZ2_COMPONENTWISE 32 /* bound rule (nmoduli == 0) per entry: see below              */
 
 /* Limits stated by the paper (Section 3, Algorithm 1).  Single calls with a
  * larger k split K into ranges of at most OZ2_K_MAX (oz2_k_ranges). */
@@ -103,6 +104,11 @@ typedef struct oz2_opts {
  *            0 picks the smallest N in [2, opts->nmax] whose N-dependent part
  *            of the Theorem 2 bound (eq. thm:err-2) is <= opts->target times a
  *            lower bound of max_ij (|A||B|)_ij (requires opts with target > 0).
+ *            With mode | OZ2_COMPONENTWISE (nmoduli == 0 only) the N-dependent
+ *            part must be <= target * L_ij on every entry, L_ij =
+ *            2^-(mu'_i + nu'_j) (floor(2^mu' |A|) floor(|B| 2^nu'))_ij <=
+ *            (|A||B|)_ij, one more integer product on the tensor cores; an
+ *            entry whose L_ij is 0 while its bound terms are not gets nmax.
  *   k        up to 2^17 as in the paper (Section 3).  A larger k is split
  *            into S consecutive K ranges of at most 2^17 (oz2_k_ranges); each
  *            range is a full OS_II of A[:, range] B[range, :] with its own
@@ -178,7 +184,7 @@ typedef struct oz2_problem {
     int nmoduli;       /* N in [2, 49], or 0 for the bound rule with `target`  */
     double target;     /* nmoduli == 0: target normwise relative error         */
     int nmax;          /* nmoduli == 0: largest N tried (0 = 20)               */
-    int mode;          /* OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B                 */
+    int mode;          /* OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B | OZ2_COMPONENTWISE */
     int *n_out;        /* optional device int: the N used                      */
 } oz2_problem;
 

@@ -537,6 +537,73 @@ def choose_N_from_maxima(maxR: float, maxK: float, ma2: float, mb2: float, L: fl
 
 
 # --------------------------------------------------------------------------- #
+# Componentwise N rule (a reading: Theorem 2 bounds every entry; this rule
+# asks the N-dependent part of eq. thm:err-1 to meet the target relative to
+# (|A||B|)_ij on every entry instead of relative to max (|A||B|))
+# --------------------------------------------------------------------------- #
+def floor_scaled_abs(X: np.ndarray, shift: np.ndarray, axis: int) -> np.ndarray:
+    """floor(2^shift |x|) with the shift of each row (axis = 1) or column
+    (axis = 0): nonnegative integers <= 63 for shift = 5 - floor(log2 max)."""
+    X = np.abs(np.asarray(X, np.float64))
+    sh = np.asarray(shift, np.int64)
+    sc = np.ldexp(X, sh[:, None] if axis == 1 else sh[None, :])     # exact (or 0 on underflow)
+    return np.floor(sc).astype(np.int8)
+
+
+def componentwise_lower(A: np.ndarray, B: np.ndarray, mu_p: np.ndarray, nu_p: np.ndarray) -> np.ndarray:
+    """L_ij = 2^-(mu'_i + nu'_j) (Ahat Bhat)_ij <= (|A||B|)_ij, Ahat = floor(2^mu' |A|),
+    Bhat = floor(|B| 2^nu'): every term of Ahat Bhat is at most the scaled |a_ih||b_hj|."""
+    Ch = gemm_i8(floor_scaled_abs(A, mu_p, 1), floor_scaled_abs(B, nu_p, 0)).astype(np.float64)
+    return np.ldexp(Ch, -(np.asarray(mu_p, np.int64)[:, None] + np.asarray(nu_p, np.int64)[None, :]))
+
+
+def componentwise_maxima(A: np.ndarray, B: np.ndarray, alpha, beta, cmax_row, cmax_col):
+    """max_ij X_ij / L_ij and max_ij Y_ij / L_ij (upper bounds), where
+    X_ij = R_i 2^beta'_j + 2^alpha'_i K_j and Y_ij = 2^alpha'_i 2^beta'_j multiply
+    t and t^2 in the N-dependent part of eq. thm:err-1 (R = |A|v, K = v^T|B|),
+    and L_ij is componentwise_lower.  An entry with L_ij = 0 gives +inf."""
+    A = np.asarray(A, np.float64)
+    B = np.asarray(B, np.float64)
+    alpha = np.asarray(alpha)
+    beta = np.asarray(beta)
+    mu_p = np.where(alpha == INT32_MIN, 0, 5 - alpha.astype(np.int64))
+    nu_p = np.where(beta == INT32_MIN, 0, 5 - beta.astype(np.int64))
+    R = abs_sums(A, 1) * _UP
+    K = abs_sums(B, 0) * _UP
+    a2 = pow2_prime(alpha, np.asarray(cmax_row))
+    b2 = pow2_prime(beta, np.asarray(cmax_col))
+    L = componentwise_lower(A, B, mu_p, nu_p)
+    X = (np.outer(R, b2) + np.outer(a2, K)) * _UP
+    Y = np.outer(a2, b2) * _UP
+    # entries with X = Y = 0 (a zero row of A or column of B) need no protection
+    live = (X > 0) | (Y > 0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        x = np.where(live, np.where(L > 0, X / L, np.inf), 0.0) * _UP
+        y = np.where(live, np.where(L > 0, Y / L, np.inf), 0.0) * _UP
+    return float(x.max(initial=0.0)), float(y.max(initial=0.0))
+
+
+def choose_N_componentwise(A: np.ndarray, B: np.ndarray, alpha, beta, cmax_row, cmax_col,
+                           tau: float, nmax: int, b: int = 64) -> tuple[int, dict]:
+    """Smallest N in [2, nmax] with t_N xmax + (k + g_N) t_N^2 ymax <= tau
+    (componentwise_maxima), i.e. the N-dependent part of eq. thm:err-1 is at most
+    tau (|A||B|)_ij on every entry; nmax when no N qualifies."""
+    k = np.asarray(A).shape[1]
+    xmax, ymax = componentwise_maxima(A, B, alpha, beta, cmax_row, cmax_col)
+    chosen, ratios = nmax, {}
+    for N in range(N_MIN, nmax + 1):
+        bt = bound_terms(N, b)
+        t = bt["t"]
+        ratios[N] = t * xmax + (k + bt["gN"]) * t * t * ymax if np.isfinite(xmax) and np.isfinite(ymax) \
+            else np.inf
+    for N in range(N_MIN, nmax + 1):
+        if ratios[N] <= tau:
+            chosen = N
+            break
+    return chosen, dict(ratios=ratios, xmax=xmax, ymax=ymax)
+
+
+# --------------------------------------------------------------------------- #
 # Exact integer checks (Lemmas 0, 2, 3; Theorem 1)
 # --------------------------------------------------------------------------- #
 def crt_exact(W: np.ndarray, N: int) -> tuple[list, list]:

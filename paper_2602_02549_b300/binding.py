@@ -17,6 +17,7 @@ from .build import LIB
 OZ2_OK, OZ2_EINVAL, OZ2_ERANGE, OZ2_ENOMEM, OZ2_ECUDA, OZ2_ETIMEOUT, OZ2_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 OZ2_ACCURATE, OZ2_FAST, OZ2_TRANS_A, OZ2_TRANS_B = 0, 1, 2, 4
 OZ2_CONJ_A, OZ2_CONJ_B = 8, 16
+OZ2_COMPONENTWISE = 32
 K_MAX, N_MIN, N_MAX = 131072, 2, 49
 NPHASES = 7
 PHASE_NAMES = ("stats", "quant", "scale_gemm", "exponents", "residues", "gemm", "crt")
@@ -241,13 +242,14 @@ def gemm_ex(A, B, C, nmoduli: int = 0, mode: int = 0, *, target: float = 0.0, nm
 
 
 def matmul(A, B, nmoduli: int = 0, *, target: float = 1e-15, nmax: int = 0, trans_a: bool = False,
-           trans_b: bool = False, fast: bool = False, out=None, **kw):
+           trans_b: bool = False, fast: bool = False, componentwise: bool = False, out=None, **kw):
     """C = A @ B through the Ozaki-II emulation (raises on any non-OK status)."""
     import torch
     m = A.size(1) if trans_a else A.size(0)
     n = B.size(0) if trans_b else B.size(1)
     C = out if out is not None else torch.empty((m, n), dtype=A.dtype, device=A.device)
-    mode = (OZ2_FAST if fast else 0) | (OZ2_TRANS_A if trans_a else 0) | (OZ2_TRANS_B if trans_b else 0)
+    mode = (OZ2_FAST if fast else 0) | (OZ2_TRANS_A if trans_a else 0) | (OZ2_TRANS_B if trans_b else 0) | \
+        (OZ2_COMPONENTWISE if componentwise else 0)
     rc = gemm_ex(A, B, C, nmoduli, mode, target=target if nmoduli == 0 else 0.0, nmax=nmax, **kw)
     if rc:
         raise Oz2Error(rc, "oz2 gemm")
@@ -370,7 +372,7 @@ def _problem_array(problems):
             if t.dtype.itemsize != 8 or not t.is_cuda:
                 raise TypeError("batched problems are float64 CUDA tensors")
         mode = (OZ2_FAST if d.get("fast") else 0) | (OZ2_TRANS_A if d.get("trans_a") else 0) | \
-            (OZ2_TRANS_B if d.get("trans_b") else 0)
+            (OZ2_TRANS_B if d.get("trans_b") else 0) | (OZ2_COMPONENTWISE if d.get("componentwise") else 0)
         q.m = A.size(1) if d.get("trans_a") else A.size(0)
         q.k = A.size(0) if d.get("trans_a") else A.size(1)
         q.n = Bm.size(0) if d.get("trans_b") else Bm.size(1)

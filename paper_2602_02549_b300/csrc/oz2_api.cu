@@ -94,9 +94,6 @@ int ensure_device(int *dev_out) {
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_n32, n32, sizeof n32);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_dp64, T.dp64, sizeof T.dp64);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_dp32, T.dp32, sizeof T.dp32);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_p, T.mod.p, sizeof T.mod.p);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_magic, T.mod.magic, sizeof T.mod.magic);
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_c16, T.mod.c16, sizeof T.mod.c16);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_cneg, &T.c, sizeof T.c);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w12, T.mod.w12, sizeof T.mod.w12);
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w13p, T.mod.w13p, sizeof T.mod.w13p);
@@ -121,6 +118,10 @@ int ensure_device(int *dev_out) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 256, gemm::kMaxGroup>, a, s256);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 128, gemm::kMaxGroup>, a, s128);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 128, gemm::kMaxGroup>, a, s128);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 256, 1>, a, s256);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 128, 1>, a, s128);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 256, gemm::kMaxGroup>, a, s256);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 128, gemm::kMaxGroup>, a, s128);
         if (e != cudaSuccess) return cuda_fail(e);
         st.smem_attr = true;
     }
@@ -145,7 +146,7 @@ Dims make_dims(int m, int n, int k, int nmax, int bn = gemm::kMaxBN) {
 
 struct Layout {
     // the block up to zero_end is cleared at the start of every call
-    size_t hmaxA, hmaxB, cmax_row, cmax_col, red, ssA, ssB, rmaxA, rmaxB, l1A, l1B, zero_end;
+    size_t hmaxA, hmaxB, cmax_row, cmax_col, red, ssA, ssB, rmaxA, rmaxB, l1A, l1B, cwA, cwB, zero_end;
     size_t mu, nu, ndev, resA, resB, W, total;
 };
 
@@ -164,6 +165,8 @@ Layout make_layout(const Dims &d) {
     L.rmaxB = take(sizeof(unsigned long long) * size_t(d.n_pad));
     L.l1A = take(2 * sizeof(unsigned long long) * size_t(d.m_pad));
     L.l1B = take(2 * sizeof(unsigned long long) * size_t(d.n_pad));
+    L.cwA = take(2 * sizeof(float) * size_t(d.m_pad));
+    L.cwB = take(2 * sizeof(float) * size_t(d.n_pad));
     L.zero_end = o;
     L.mu = take(sizeof(int32_t) * size_t(d.m_pad));
     L.nu = take(sizeof(int32_t) * size_t(d.n_pad));
@@ -229,10 +232,11 @@ int validate(int m, int n, int k, const void *A, int lda, const void *B, int ldb
              int nmoduli, int mode, const oz2_opts *o) {
     if (m < 1 || n < 1 || k < 1) return OZ2_EINVAL;
     if (!A || !B || !C) return OZ2_EINVAL;
-    if (mode & ~(OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B)) return OZ2_EINVAL;
+    if (mode & ~(OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B | OZ2_COMPONENTWISE)) return OZ2_EINVAL;
     const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
     if (lda < (ta ? m : k) || ldb < (tb ? k : n) || ldc < n) return OZ2_EINVAL;
     if (nmoduli != 0 && (nmoduli < OZ2_N_MIN || nmoduli > OZ2_N_MAX)) return OZ2_EINVAL;
+    if (nmoduli != 0 && (mode & OZ2_COMPONENTWISE)) return OZ2_EINVAL;   // a rule for choosing N
     if (nmoduli == 0) {
         if (!o || !(o->target > 0.0)) return OZ2_EINVAL;
         if (o->nmax != 0 && (o->nmax < OZ2_N_MIN || o->nmax > OZ2_N_MAX)) return OZ2_EINVAL;
@@ -278,6 +282,7 @@ struct Job {
     Layout L{};
     uint8_t *ws = nullptr;
     unsigned long long *hmaxA, *hmaxB, *red, *rmaxA, *rmaxB, *l1A, *l1B;
+    float *cwA, *cwB;
     int *cmax_row, *cmax_col, *ssA, *ssB, *ndev;
     int32_t *mu, *nu;
     __nv_bfloat16 *resA, *resB;
@@ -286,6 +291,7 @@ struct Job {
     long planeA = 0, planeB = 0, w_plane = 0;
 
     bool fast() const { return mode & OZ2_FAST; }
+    bool cw() const { return mode & OZ2_COMPONENTWISE; }
     bool inject() const { return mu_in != nullptr; }
     bool needs_scale_gemm() const { return !fast() && !inject(); }
 
@@ -313,6 +319,8 @@ struct Job {
         rmaxB = reinterpret_cast<unsigned long long *>(at(L.rmaxB));
         l1A = reinterpret_cast<unsigned long long *>(at(L.l1A));
         l1B = reinterpret_cast<unsigned long long *>(at(L.l1B));
+        cwA = reinterpret_cast<float *>(at(L.cwA));
+        cwB = reinterpret_cast<float *>(at(L.cwB));
         mu = reinterpret_cast<int32_t *>(at(L.mu));
         nu = reinterpret_cast<int32_t *>(at(L.nu));
         ndev = reinterpret_cast<int *>(at(L.ndev));
@@ -341,6 +349,9 @@ struct Job {
         P.kb_total = d.k_pad / gemm::BK;
         P.tiles_m = d.m_pad / gemm::BM;
         P.tiles_n = d.n_pad / bn;
+        P.plane0 = 0;
+        P.cw_row = P.cw_col = nullptr;
+        P.cw_red = nullptr;
         return OZ2_OK;
     }
     void as_scale_gemm(GemmProblem &P) const {
@@ -356,6 +367,17 @@ struct Job {
         P.W = W;
         P.w_plane = w_plane;
         P.row_max = P.col_max = nullptr;
+    }
+    // componentwise rule: floor(2^mu' |A|) floor(|B| 2^nu') from plane 1
+    void as_cw_gemm(GemmProblem &P) const {
+        P.planes = 1;
+        P.plane0 = 1;
+        P.n_dev = nullptr;
+        P.W = nullptr;
+        P.row_max = P.col_max = nullptr;
+        P.cw_row = cwA;
+        P.cw_col = cwB;
+        P.cw_red = red + 5;
     }
 
     // the device view of this problem for the grouped light-phase kernels
@@ -374,6 +396,9 @@ struct Job {
         j.nmoduli = nmoduli;
         j.nmax = nmax;
         j.fast = fast() ? 1 : 0;
+        j.cw = cw() ? 1 : 0;
+        j.cwv[0] = cwA;
+        j.cwv[1] = cwB;
         j.inject = inject() ? 1 : 0;
         j.accum = accum ? 1 : 0;
         auto aligned = [](const Operand<T> &op) {
@@ -488,25 +513,32 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
         return double(d.m_pad) * d.n_pad * d.k_pad * (jobs[p]->nmax + 1);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-    // one persistent launch per GEMM phase and tile width
-    auto gemms = [&](bool scale) -> int {
+    // one persistent launch per GEMM phase and tile width: EPI_MAX the scaling
+    // GEMM, EPI_CW the componentwise rule's second product, EPI_MOD the residues
+    auto gemms = [&](int epi) -> int {
         for (int bn : {256, 128}) {
             std::memset(&G, 0, sizeof G);
             for (int idx = 0; idx < count; idx++) {
                 const Job<T> &job = *jobs[order[idx]];
-                if (job.bn != bn || (scale && !job.needs_scale_gemm())) continue;
+                if (job.bn != bn) continue;
+                if ((epi == EPI_MAX && !job.needs_scale_gemm()) || (epi == EPI_CW && !job.cw())) continue;
                 GemmProblem &P = G.p[G.count++];
                 int r = job.describe(P);
                 if (r) return r;
-                if (scale) job.as_scale_gemm(P);
+                if (epi == EPI_MAX) job.as_scale_gemm(P);
+                else if (epi == EPI_CW) job.as_cw_gemm(P);
                 else job.as_residue_gemm(P);
             }
             if (!G.count) continue;
             int r;
             if (bn == 256)
-                r = scale ? launch_gemm<EPI_MAX, 256>(G, sms, st) : launch_gemm<EPI_MOD, 256>(G, sms, st);
+                r = epi == EPI_MAX ? launch_gemm<EPI_MAX, 256>(G, sms, st)
+                                   : (epi == EPI_CW ? launch_gemm<EPI_CW, 256>(G, sms, st)
+                                                    : launch_gemm<EPI_MOD, 256>(G, sms, st));
             else
-                r = scale ? launch_gemm<EPI_MAX, 128>(G, sms, st) : launch_gemm<EPI_MOD, 128>(G, sms, st);
+                r = epi == EPI_MAX ? launch_gemm<EPI_MAX, 128>(G, sms, st)
+                                   : (epi == EPI_CW ? launch_gemm<EPI_CW, 128>(G, sms, st)
+                                                    : launch_gemm<EPI_MOD, 128>(G, sms, st));
             if (r) return r;
         }
         return OZ2_OK;
@@ -521,15 +553,16 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     OZ2_LAUNCH(k_fast_max, fast_max, one_each)
     OZ2_LAUNCH(k_fast_cmax, fast_cmax, one_each)
     if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
-    if ((rc = gemms(true))) return rc;
+    if ((rc = gemms(EPI_MAX))) return rc;
     if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
     OZ2_LAUNCH(k_bound, bound, one_each)
+    if ((rc = gemms(EPI_CW))) return rc;
     OZ2_LAUNCH(k_exponents, exponents, one_each)
     if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
     OZ2_LAUNCH(k_resid_kc, resid_kc, resident)
     OZ2_LAUNCH(k_resid_rc, resid_rc, resident)
     if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
-    if ((rc = gemms(false))) return rc;
+    if ((rc = gemms(EPI_MOD))) return rc;
     if ((rc = mark(OZ2_PHASE_CRT))) return rc;
     if (count == 1) {
         const JobDesc<T> &j = J.j[0];
@@ -632,7 +665,7 @@ int zvalidate(int m, int n, int k, const void *A, int lda, const void *B, int ld
               int nmoduli, int mode, const oz2_opts *o, size_t esize) {
     if (m < 1 || n < 1 || k < 1 || k > (1 << 30)) return OZ2_EINVAL;
     if (!A || !B || !C) return OZ2_EINVAL;
-    if (mode & ~(OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B | OZ2_CONJ_A | OZ2_CONJ_B)) return OZ2_EINVAL;
+    if (mode & ~(OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B | OZ2_CONJ_A | OZ2_CONJ_B | OZ2_COMPONENTWISE)) return OZ2_EINVAL;
     const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
     if (lda < (ta ? m : k) || ldb < (tb ? k : n) || ldc < n) return OZ2_EINVAL;
     const size_t al = 2 * esize;
@@ -657,7 +690,7 @@ int run_complex(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T
     if (rc) return rc;
     const bool fp32 = sizeof(T) == 4;
     const int nmax = nmoduli ? nmoduli : (o && o->nmax ? o->nmax : (fp32 ? 14 : 20));
-    const int rmode = mode & (OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B);
+    const int rmode = mode & (OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B | OZ2_COMPONENTWISE);
     const ZLayout z = zlayout<T>(m, n, k, nmax, rmode);
     if (!z.total) return OZ2_EINVAL;
     int dev = 0;
@@ -955,7 +988,7 @@ int oz2_cgemm(int m, int n, int k, const float *A, int lda, const float *B, int 
 
 size_t oz2_zworkspace_size(int m, int n, int k, int nmax, int mode, int fp32) {
     if (m < 1 || n < 1 || k < 1 || k > (1 << 30) || nmax < OZ2_N_MIN || nmax > OZ2_N_MAX) return 0;
-    const int rmode = mode & (OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B);
+    const int rmode = mode & (OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B | OZ2_COMPONENTWISE);
     return fp32 ? zlayout<float>(m, n, k, nmax, rmode).total : zlayout<double>(m, n, k, nmax, rmode).total;
 }
 

@@ -38,9 +38,6 @@ __constant__ DevN c_n32[kNMax + 1];
 // CRT constants as 16-bit pieces, two planes per word (Tables::dp64 / dp32)
 __constant__ uint4 c_dp64[kPairsLen][2];  // b = 64: pieces 0-3 of s_l1 / g, then of s_l2 / 2^esum
 __constant__ uint4 c_dp32[kPairsLen];     // b = 32: pieces 0-3 of s_l1 / 2^esum
-__constant__ int c_p[kNMax];
-__constant__ uint32_t c_magic[kNMax];
-__constant__ uint32_t c_c16[kNMax];
 __constant__ float c_cneg;                 // single_down(-0.5/(1-4 u32))
 __constant__ float c_w12[kNMax][kLimbs];   // balanced 2^(12 j) mod p_l
 // per modulus, each value duplicated into both FP32 lanes: balanced
@@ -56,11 +53,6 @@ __device__ int g_status;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
 
 // ============================================================= small helpers
-__device__ __forceinline__ uint32_t mod_small(uint32_t t, uint32_t p, uint32_t magic) {
-    // t < 2^24, p <= 256: floor(t/p) = umulhi(t, ceil(2^32/p))
-    return t - __umulhi(t, magic) * p;
-}
-
 // floor(log2 x) of a positive double given by its bits.
 __device__ __forceinline__ int floor_log2_bits(uint64_t b) {
     int ex = int(b >> 52);
@@ -109,6 +101,17 @@ __device__ __forceinline__ uint32_t ceil_scaled_abs(T x, int shift) {
     if (r >= 64) return 1;
     uint64_t q = s.M >> r;
     return uint32_t(q + ((s.M & ((1ull << r) - 1)) != 0));
+}
+
+// floor(2^shift |x|) (the componentwise N rule's lower bound of 2^shift |x|).
+template <typename T>
+__device__ __forceinline__ uint32_t floor_scaled_abs(T x, int shift) {
+    Split s = split_bits(x);
+    if (s.M == 0) return 0;
+    int sh = s.e + shift;
+    if (sh >= 0) return sh > 10 ? 127u : uint32_t(s.M << sh);
+    const int r = -sh;
+    return r >= 64 ? 0u : uint32_t(s.M >> r);
 }
 
 // Algorithm 2: x' = trunc(2^shift x) = (-1)^neg * M * 2^E, E >= 0.
@@ -205,6 +208,7 @@ struct JobDesc {
     int m, n, k, k_pad, n_pad;
     int R_pad[2];                  // m_pad, n_pad
     int nmoduli, nmax, fast, inject, vec[2];
+    int cw;                        // componentwise N rule (OZ2_COMPONENTWISE)
     int absmax_lb;                 // lines per k_absmax item (kLineBlock or fewer, per launch)
     int accum;                     // CRT adds its result to C (the K ranges after the first)
     double target;
@@ -212,6 +216,8 @@ struct JobDesc {
     unsigned long long *rmax[2];   // per logical row maxima (bits)
     unsigned long long *l1[2];     // fixed-point 1-norms (PlaneArgs::l1)
     unsigned long long *red;       // bound reductions
+    float *cwv[2];                 // componentwise rule: (R_i 2^mu'_i, 2^alpha'_i 2^mu'_i) per row of A,
+                                   // (2^beta'_j 2^nu'_j, K_j 2^nu'_j) per column of B, rounded up
     int *cmax[2];                  // Cbar row / column maxima
     int *ss[2];                    // fast mode: sums of squares of Abar rows / Bbar columns
     int *ndev, *n_out;
@@ -443,6 +449,8 @@ struct PlaneArgs {
     int write;                            // quantisation: store the BF16 plane (accurate mode)
     unsigned long long *l1;               // quantisation: sum_h |x| 2^(mu'+57) per row, two 32-bit
                                           // halves (l1[2r] high, l1[2r+1] low; atomicAdd)
+    int floor_plane;                      // quantisation, componentwise rule: also store
+                                          // floor(2^mu' |x|) in plane 1
 };
 
 __device__ __forceinline__ int quant_shift(const unsigned long long *row_max, int r) {
@@ -493,7 +501,7 @@ __device__ __forceinline__ void flush_row(const PlaneArgs &a, RowAcc acc, int r,
 // lies in the significand's top word.  Zeros, subnormals and FP32 inputs take
 // the general path (ceil_scaled_abs, add_scaled_abs).
 template <typename T>
-__device__ __forceinline__ void quant_elem(T x, int shift, uint32_t &q, uint32_t &vhi, uint32_t &vlo) {
+__device__ __forceinline__ void quant_elem(T x, int shift, uint32_t &q, uint32_t &qf, uint32_t &vhi, uint32_t &vlo) {
     if constexpr (sizeof(T) == 8) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(x);
         const uint32_t hi = uint32_t(b >> 32), lo = uint32_t(b);
@@ -504,9 +512,11 @@ __device__ __forceinline__ void quant_elem(T x, int shift, uint32_t &q, uint32_t
             const int rr = r - 32;                              // >= 15
             if (rr >= 32) {
                 q = 1u;
+                qf = 0u;
             } else {
                 const uint32_t rest = (mh & ((1u << rr) - 1u)) | lo;
-                q = (mh >> rr) + (rest != 0u ? 1u : 0u);
+                qf = mh >> rr;
+                q = qf + (rest != 0u ? 1u : 0u);
             }
             if (r <= 57) {                                      // M << (57 - r), at most 10 bits
                 const int s = 57 - r;
@@ -526,6 +536,7 @@ __device__ __forceinline__ void quant_elem(T x, int shift, uint32_t &q, uint32_t
         }
     }
     q = ceil_scaled_abs(x, shift);
+    qf = floor_scaled_abs(x, shift);
     RowAcc t{0, 0, 0};
     add_scaled_abs(t, x, shift);
     vhi = uint32_t(t.hi);
@@ -540,15 +551,16 @@ __device__ __forceinline__ uint32_t pack_bf16x2_small(uint32_t a, uint32_t b) {
     return __byte_perm(__float_as_uint(fa), __float_as_uint(fb), 0x7632);
 }
 
-// Stores 8 values of Abar (accurate mode) and adds to the row sums.
+// Stores 8 values of Abar (accurate mode), and of floor(2^mu' |x|) in plane 1
+// under the componentwise rule, and adds to the row sums.
 template <typename T>
 __device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8], int shift, int r, int h0,
                                             RowAcc &acc) {
-    uint32_t q[8];
+    uint32_t q[8], qf[8];
 #pragma unroll
     for (int e = 0; e < 8; e++) {
         uint32_t vh, vl;
-        quant_elem(x[e], shift, q[e], vh, vl);
+        quant_elem(x[e], shift, q[e], qf[e], vh, vl);
         acc.ss += int(q[e] * q[e]);
         acc.hi += vh;
         acc.lo += vl;
@@ -561,12 +573,20 @@ __device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8],
         v.w = pack_bf16x2_small(q[6], q[7]);
         *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = v;
     }
+    if (a.floor_plane) {
+        uint4 v;
+        v.x = pack_bf16x2_small(qf[0], qf[1]);
+        v.y = pack_bf16x2_small(qf[2], qf[3]);
+        v.z = pack_bf16x2_small(qf[4], qf[5]);
+        v.w = pack_bf16x2_small(qf[6], qf[7]);
+        *reinterpret_cast<uint4 *>(a.out + a.plane + (long)r * a.k_pad + h0) = v;
+    }
 }
 
 template <typename T>
 __device__ __forceinline__ PlaneArgs quant_args(const JobDesc<T> &j, int X) {
     return PlaneArgs{j.res[X], j.plane[X], j.R_pad[X], j.k, j.k_pad, j.rmax[X], nullptr, nullptr,
-                     j.fast ? j.ss[X] : nullptr, !j.fast, j.l1[X]};
+                     j.fast ? j.ss[X] : nullptr, !j.fast, j.l1[X], j.cw};
 }
 
 // Eight consecutive elements src[0 .. 7] of a row, zero from index `valid` on:
@@ -628,6 +648,8 @@ __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGro
             if (h0 >= a.k_pad) break;
             if (!live) {
                 if (a.write) *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
+                if (a.floor_plane)
+                    *reinterpret_cast<uint4 *>(a.out + a.plane + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
                 continue;
             }
             T x[8];
@@ -827,7 +849,7 @@ __device__ __forceinline__ PlaneArgs resid_args(const JobDesc<T> &j, int X) {
     // the row maxima bound |A'|, |B'| (fixed-position limbs); they are not
     // computed when mu and nu are given
     return PlaneArgs{j.res[X], j.plane[X], j.R_pad[X], j.k, j.k_pad, j.inject ? nullptr : j.rmax[X],
-                     j.shift[X], j.ndev, nullptr, 1, nullptr};
+                     j.shift[X], j.ndev, nullptr, 1, nullptr, 0};
 }
 
 // K-contiguous source.  Item: 256 consecutive groups of 8 h in row-major order
@@ -948,7 +970,7 @@ struct Cfg {
 };
 }  // namespace gemm
 
-enum { EPI_MAX = 0, EPI_MOD = 1 };
+enum { EPI_MAX = 0, EPI_MOD = 1, EPI_CW = 2 };
 
 // One GEMM problem of a launch: X_l (rows l*m_pad ..) times Y_l^T for the planes
 // l < planes (and l < *n_dev when n_dev is set), 128 x BN output tiles.
@@ -956,11 +978,14 @@ struct GemmProblem {
     CUtensorMap tmA, tmB;      // BF16, K-major, 128B-swizzled boxes of 64 x 128 / 64 x BN
     int m_pad, n_pad, kb_total;
     int tiles_m, tiles_n, planes;
+    int plane0;                // first plane of the operands (EPI_CW: plane 1)
     long long item_begin;      // first work item of this problem in the launch
     const int *n_dev;          // EPI_MOD: planes l >= *n_dev are skipped
     int8_t *W;                 // EPI_MOD: W[l*w_plane + row*n_pad + col]
     long long w_plane;
     int *row_max, *col_max;    // EPI_MAX
+    const float *cw_row, *cw_col;   // EPI_CW: (a_i, b_i) per row, (c_j, d_j) per column
+    unsigned long long *cw_red;     // EPI_CW: maxima of X / L and Y / L (double bits) at [0], [2]
 };
 
 template <int CAP = gemm::kMaxGroup>
@@ -1043,49 +1068,58 @@ __device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, uint64
     }
 }
 
-// Epilogue of one output tile for one epilogue thread: NC INT32 sums of row
-// `row`, columns col0 .. col0+NC-1.
-template <int EPI, int NC>
-__device__ __forceinline__ void tile_epilogue(const GemmProblem &P, int l, int row, int col0, int lane,
-                                              const int (&acc)[NC]) {
-    if (EPI == EPI_MOD) {
-        int8_t *dst = P.W + (long long)l * P.w_plane + (long long)row * P.n_pad + col0;
-        if (l == 0) {                            // p = 256: low byte
+// 1.5 2^23 in both FP32 lanes, and its negative: x + 1.5 2^23 - 1.5 2^23 rounds
+// x to an integer for |x| < 2^22, and the low byte of the bits of r + 1.5 2^23
+// is r mod 256 for an integer |r| <= 256
+constexpr unsigned long long kMagic2 = 0x4B4000004B400000ull;
+constexpr unsigned long long kNegMagic2 = 0xCB400000CB400000ull;
+
+// EPI_MOD, per segment: x, an FP32 accumulator value (an integer, |x| <= 2^24),
+// becomes x - p q with q = rint(x RN(1/p)), a representative of x mod p_l with
+// |x - p q| <= p/2 + 1 (the FP32 quotient is within 1/2 + 1/p of x / p), two
+// elements per paired instruction; these add up exactly in FP32 over the <= 128
+// segments of a tile.
+__device__ __forceinline__ unsigned long long mod_rep2(unsigned long long x, unsigned long long ip,
+                                                        unsigned long long np) {
+    const unsigned long long q = f2::add(f2::fma(x, ip, kMagic2), kNegMagic2);
+    return f2::fma(q, np, x);
+}
+
+// EPI_MOD epilogue of one output tile for one epilogue thread: the NC sums of
+// segment representatives (|s| < 2^15) of row `row`, columns col0 .. col0+NC-1,
+// reduced to the balanced residue W_l = mod(C'_l, p_l) (exact: |s| < 2^23, and
+// s / p lies at least 1/(2p) from a half-integer for odd p; for p = 256 both
+// +-128 give the byte 0x80, the class -128) and stored as bytes.
+template <int NC>
+__device__ __forceinline__ void tile_epilogue_mod(const GemmProblem &P, int l, int row, int col0,
+                                                  const unsigned long long (&acc2)[NC / 2]) {
+    int8_t *dst = P.W + (long long)l * P.w_plane + (long long)row * P.n_pad + col0;
+    const unsigned long long ip = c_w13p[l][kFixLimbs], np = c_w13p[l][kFixLimbs + 1];
 #pragma unroll
-            for (int g = 0; g < NC / 16; g++) {
-                uint32_t w4[4];
+    for (int g = 0; g < NC / 16; g++) {
+        uint32_t w4[4];
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int b = g * 16 + j * 4;
-                    w4[j] = (uint32_t(acc[b]) & 255u) | ((uint32_t(acc[b + 1]) & 255u) << 8) |
-                            ((uint32_t(acc[b + 2]) & 255u) << 16) | ((uint32_t(acc[b + 3]) & 255u) << 24);
-                }
-                *reinterpret_cast<uint4 *>(dst + g * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        for (int j = 0; j < 4; j++) {
+            uint32_t b[4];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const unsigned long long t = f2::add(mod_rep2(acc2[g * 8 + j * 2 + h], ip, np), kMagic2);
+                b[2 * h] = uint32_t(t);
+                b[2 * h + 1] = uint32_t(t >> 32);
             }
-        } else {
-            const uint32_t p = uint32_t(c_p[l]), mg = c_magic[l], c16 = c_c16[l];
-            const int hp = int(p >> 1);
-#pragma unroll
-            for (int g = 0; g < NC / 16; g++) {
-                uint32_t w4[4];
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    uint32_t word = 0;
-#pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const int x = acc[g * 16 + j * 4 + e];
-                        const uint32_t u = uint32_t(x < 0 ? -x : x);
-                        uint32_t r = mod_small((u >> 16) * c16 + (u & 0xFFFFu), p, mg);
-                        int sr = int(r) > hp ? int(r) - int(p) : int(r);
-                        if (x < 0) sr = -sr;
-                        word |= (uint32_t(sr) & 255u) << (8 * e);
-                    }
-                    w4[j] = word;
-                }
-                *reinterpret_cast<uint4 *>(dst + g * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-            }
+            // the low bytes of four elements, in column order
+            w4[j] = __byte_perm(__byte_perm(b[0], b[1], 0x0040), __byte_perm(b[2], b[3], 0x0040), 0x5410);
         }
-    } else {
+        *reinterpret_cast<uint4 *>(dst + g * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    }
+}
+
+// EPI_MAX epilogue of one output tile for one epilogue thread: NC INT32 sums of
+// row `row`, columns col0 .. col0+NC-1, merged into the row and column maxima.
+template <int NC>
+__device__ __forceinline__ void tile_epilogue_max(const GemmProblem &P, int row, int col0, int lane,
+                                                  const int (&acc)[NC]) {
+    {
         int rm = 0;
 #pragma unroll
         for (int i = 0; i < NC; i++) rm = max(rm, acc[i]);
@@ -1100,6 +1134,41 @@ __device__ __forceinline__ void tile_epilogue(const GemmProblem &P, int l, int r
         }
 #pragma unroll
         for (int j = 0; j < NC / 32; j++) atomicMax(P.col_max + col0 + j * 32 + lane, mine[j]);
+    }
+}
+
+// EPI_CW epilogue (componentwise N rule): Chat_ij = (floor(2^mu' |A|) floor(|B| 2^nu'))_ij
+// as INT32 sums; L_ij = 2^-(mu'_i + nu'_j) Chat_ij <= (|A||B|)_ij.  With
+// (a, b) = (R_i, 2^alpha'_i) 2^mu'_i and (c, d) = (2^beta'_j, K_j) 2^nu'_j,
+//   X_ij / L_ij = (a c + b d) / Chat_ij,   Y_ij / L_ij = b c / Chat_ij,
+// the factors of t and t^2 in the N-dependent part of eq. thm:err-1 over L_ij,
+// rounded up; an entry with X or Y > 0 and Chat_ij = 0 gives +inf.  Their
+// maxima over the thread's entries, then the warp's, go to cw_red.
+template <int NC>
+__device__ __forceinline__ void tile_epilogue_cw(const GemmProblem &P, int row, int col0, const int (&acc)[NC]) {
+    const float2 ab = reinterpret_cast<const float2 *>(P.cw_row)[row];
+    const float2 *cd = reinterpret_cast<const float2 *>(P.cw_col) + col0;
+    float xm = 0.0f, ym = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+        const float2 v = cd[c];
+        const float X = __fadd_ru(__fmul_ru(ab.x, v.x), __fmul_ru(ab.y, v.y));
+        const float Y = __fmul_ru(ab.y, v.x);
+        if (X > 0.0f || Y > 0.0f) {
+            if (acc[c] == 0) {
+                xm = ym = __int_as_float(0x7f800000);
+            } else {
+                const float rc = __frcp_ru(__int2float_rd(acc[c]));
+                xm = fmaxf(xm, __fmul_ru(X, rc));
+                ym = fmaxf(ym, __fmul_ru(Y, rc));
+            }
+        }
+    }
+    const unsigned long long bx = warp_max_u64((unsigned long long)__double_as_longlong(double(xm)));
+    const unsigned long long by = warp_max_u64((unsigned long long)__double_as_longlong(double(ym)));
+    if ((threadIdx.x & 31) == 0) {
+        if (bx) atomicMax(P.cw_red, bx);
+        if (by) atomicMax(P.cw_red + 2, by);
     }
 }
 
@@ -1167,8 +1236,8 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
                 const WorkItem w = decode_item(G, g);
                 if (w.skip) continue;
                 const GemmProblem &P = G.p[w.p];
-                const int row_a = w.l * P.m_pad + w.tile_m * BM;
-                const int row_b = w.l * P.n_pad + w.tile_n * BN;
+                const int row_a = (P.plane0 + w.l) * P.m_pad + w.tile_m * BM;
+                const int row_b = (P.plane0 + w.l) * P.n_pad + w.tile_n * BN;
                 for (int kb = 0; kb < P.kb_total; kb++, kbc++) {
                     const int s = int(kbc % STAGES);
                     const uint32_t ph = (kbc / STAGES) & 1u;
@@ -1228,28 +1297,57 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
             if (w.skip) continue;
             const GemmProblem &P = G.p[w.p];
             const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
-            int acc[NC];
+            // EPI_MAX: INT32 sums of the segments; EPI_MOD: FP32 pairs holding the
+            // sum of the segments' representatives mod p_l (mod_rep2)
+            int acc[EPI == EPI_MOD ? 1 : NC];
+            unsigned long long acc2[EPI == EPI_MOD ? NC / 2 : 1];
+            unsigned long long ip = 0, np = 0;
+            if constexpr (EPI == EPI_MOD) {
 #pragma unroll
-            for (int i = 0; i < NC; i++) acc[i] = 0;
+                for (int i = 0; i < NC / 2; i++) acc2[i] = 0ull;
+                ip = c_w13p[w.l][kFixLimbs];
+                np = c_w13p[w.l][kFixLimbs + 1];
+            } else {
+#pragma unroll
+                for (int i = 0; i < NC; i++) acc[i] = 0;
+            }
             for (int seg = 0; seg < nseg; seg++, segc++) {
                 const int buf = int(segc & 1u);
                 if (!warp_wait(bar_accf(buf), (segc >> 1) & 1u, abort_flag, limit)) { ok = false; break; }
                 ptx::tc_fence_after();
                 const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + half * NC);
+                if constexpr (EPI == EPI_MOD) {
 #pragma unroll
-                for (int c = 0; c < NC / 32; c++) {
-                    uint32_t v[32];
-                    ptx::tmem_ld_32x32b_x32(taddr + uint32_t(c * 32), v);
-                    ptx::tmem_wait_ld();
+                    for (int c = 0; c < NC / 16; c++) {
+                        uint32_t v[16];
+                        ptx::tmem_ld_32x32b_x16(taddr + uint32_t(c * 16), v);
+                        ptx::tmem_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < 32; i++) acc[c * 32 + i] += __float2int_rn(__uint_as_float(v[i]));
+                        for (int i = 0; i < 8; i++) {
+                            const unsigned long long x = (unsigned long long)v[2 * i] |
+                                                         ((unsigned long long)v[2 * i + 1] << 32);
+                            acc2[c * 8 + i] = f2::add(acc2[c * 8 + i], mod_rep2(x, ip, np));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NC / 16; c++) {
+                        uint32_t v[16];
+                        ptx::tmem_ld_32x32b_x16(taddr + uint32_t(c * 16), v);
+                        ptx::tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; i++) acc[c * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
+                    }
                 }
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(bar_acce(buf));
             }
             if (!ok) break;
-            tile_epilogue<EPI, NC>(P, w.l, w.tile_m * BM + q * 32 + lane, w.tile_n * BN + half * NC, lane, acc);
+            const int row = w.tile_m * BM + q * 32 + lane, col0 = w.tile_n * BN + half * NC;
+            if constexpr (EPI == EPI_MOD) tile_epilogue_mod<NC>(P, w.l, row, col0, acc2);
+            else if constexpr (EPI == EPI_MAX) tile_epilogue_max<NC>(P, row, col0, lane, acc);
+            else tile_epilogue_cw<NC>(P, row, col0, acc);
         }
     }
     ptx::tc_fence_before();
@@ -1277,6 +1375,7 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
 // ============================================================= exponents and N
 // red[] holds bits of nonnegative doubles (order-independent atomicMax):
 // 0 max_i |A|v, 1 max_j v^T|B|, 2 max_i 2^alpha'_i, 3 max_j 2^beta'_j, 4 L;
+// 5 and 7 the componentwise rule's max X / L and max Y / L;
 // red[6] as two ints: fast mode's max_i ssA_i, max_j ssB_j.
 
 __device__ __forceinline__ double pow2_prime(unsigned long long rmax_bits, int cmax) {
@@ -1296,6 +1395,24 @@ __device__ __forceinline__ double row_l1(const unsigned long long *l1, const uns
     return ldexp(v, -(quant_shift(rmax, r) + 57));
 }
 
+// Componentwise rule: the row (X = 0) or column (X = 1) factors of X_ij / L_ij
+// and Y_ij / L_ij (tile_epilogue_cw), rounded up: the 1-norm times 2^mu' (the
+// fixed-point sum lies within k 2^-62 below it; the factor 1 + 2^-30 covers
+// that), and 2^alpha' 2^mu' = 2^5 sqrt(max cbar) (2^alpha' of Theorem 2).
+template <typename T>
+__device__ __forceinline__ void cw_vectors(const JobDesc<T> &j, int X, int t) {
+    const unsigned long long rb = j.rmax[X][t];
+    float s = 0.0f, w = 0.0f;
+    if (rb) {
+        const double l1 = (double(j.l1[X][2 * t]) * 4294967296.0 + double(j.l1[X][2 * t + 1])) * 0x1p-57;
+        s = __double2float_ru(l1 * (1.0 + 0x1p-30));
+        const int cm = j.cmax[X][t];
+        w = cm > 0 ? __double2float_ru(sqrt(double(cm)) * 32.0 * (1.0 + 0x1p-40)) : 0.0f;
+    }
+    // row of A: (a, b) = (R 2^mu', 2^alpha' 2^mu'); column of B: (c, d) = (2^beta' 2^nu', K 2^nu')
+    reinterpret_cast<float2 *>(j.cwv[X])[t] = X == 0 ? make_float2(s, w) : make_float2(w, s);
+}
+
 // The maxima that the N rule needs.  Item: 256 consecutive indices (one per
 // thread) of each of the ranges i < m, j < n, h < k, so that these short,
 // latency-bound reductions spread over many SMs.
@@ -1310,12 +1427,14 @@ __global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<
                 mR = v > mR ? v : mR;
                 v = (unsigned long long)__double_as_longlong(pow2_prime(j.rmax[0][t], j.cmax[0][t]));
                 m2a = v > m2a ? v : m2a;
+                if (j.cw) cw_vectors(j, 0, t);
             }
             if (t < j.n) {
                 unsigned long long v = (unsigned long long)__double_as_longlong(row_l1(j.l1[1], j.rmax[1], t));
                 mK = v > mK ? v : mK;
                 v = (unsigned long long)__double_as_longlong(pow2_prime(j.rmax[1][t], j.cmax[1][t]));
                 m2b = v > m2b ? v : m2b;
+                if (j.cw) cw_vectors(j, 1, t);
             }
             if (t < j.k) {
                 const double v = __longlong_as_double((long long)j.hmax[0][t]) *
@@ -1335,7 +1454,18 @@ __global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<
 // The N rule: smallest N in [2, nmax] with
 //   t_N (maxR max2b + max2a maxK) + (k + gN_N) t_N^2 max2a max2b <= tau * L,
 // else nmax.
-__device__ __forceinline__ int choose_n(const unsigned long long *red, int k, double tau, int nmax, int fp32) {
+__device__ __forceinline__ int choose_n(const unsigned long long *red, int k, double tau, int nmax, int fp32,
+                                        int cw) {
+    if (cw) {
+        // componentwise: t_N max(X / L) + (k + gN_N) t_N^2 max(Y / L) <= tau
+        const double xm = __longlong_as_double((long long)red[5]);
+        const double ym = __longlong_as_double((long long)red[7]);
+        for (int c = 2; c <= nmax; c++) {
+            const DevN &d = fp32 ? c_n32[c] : c_n64[c];
+            if (d.t * xm + (double(k) + d.gN) * d.t * d.t * ym <= tau) return c;
+        }
+        return nmax;
+    }
     const double maxR = __longlong_as_double((long long)red[0]);
     const double maxK = __longlong_as_double((long long)red[1]);
     const double m2a = __longlong_as_double((long long)red[2]);
@@ -1361,7 +1491,7 @@ __global__ void __launch_bounds__(256) k_exponents(const __grid_constant__ JobGr
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         __syncthreads();                     // the previous item has read sN
         if (threadIdx.x == 0) {
-            const int N = j.nmoduli > 0 ? j.nmoduli : choose_n(j.red, j.k, j.target, j.nmax, fp32);
+            const int N = j.nmoduli > 0 ? j.nmoduli : choose_n(j.red, j.k, j.target, j.nmax, fp32, j.cw);
             sN = N;
             if (li == 0) {
                 *j.ndev = N;

@@ -227,10 +227,6 @@ void build(Tables &T) {
     for (int l = 0; l < kNMax; l++) {
         uint32_t p = uint32_t(kModuli[l]);
         T.mod.p[l] = int(p);
-        T.mod.magic[l] = uint32_t(((uint64_t(1) << 32) + p - 1) / p);
-        T.mod.c16[l] = uint32_t((uint64_t(1) << 16) % p);
-        T.mod.c24[l] = uint32_t((uint64_t(1) << 24) % p);
-        T.mod.c48[l] = uint32_t((uint64_t(1) << 48) % p);
         uint32_t v = 1 % p;
         for (int e = 0; e < 256; e++) { T.mod.pow2[l][e] = uint8_t(v); v = (v * 2) % p; }
         v = 1 % p;

@@ -14,10 +14,6 @@ constexpr int kPairsLen = 625;                          // sum_{N=1}^{49} ceil(N
 // Per-modulus reduction constants (index l = 0..48).
 struct ModTable {
     int p[kNMax];
-    uint32_t magic[kNMax];   // ceil(2^32 / p): floor(t/p) = umulhi(t, magic) for t < 2^24
-    uint32_t c16[kNMax];     // 2^16 mod p
-    uint32_t c24[kNMax];     // 2^24 mod p
-    uint32_t c48[kNMax];     // 2^48 mod p
     uint8_t pow2[kNMax][256];// 2^E mod p, E = 0..255
     float w12[kNMax][kLimbs];     // balanced 2^(12 j) mod p, in [-(p-1)/2, (p-1)/2] (odd p)
     // {w, w} pairs of FP32 bits: balanced 2^(13 j) mod p (j < kFixLimbs), RN(1/p), -p
