@@ -22,10 +22,6 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 
-// Problems per GEMM launch of a single call: the residue GEMM of a fused call
-// runs its last partial wave of tiles as a second, unfused entry.
-constexpr int kGemmCap1 = 2;
-
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ------------------------------------------------------------------ per-device state
@@ -114,16 +110,16 @@ int ensure_device(int *dev_out) {
     if (!st.smem_attr) {
         const int s256 = int(gemm::Cfg<256>::kSmemBytes), s128 = int(gemm::Cfg<128>::kSmemBytes);
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        cudaError_t e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 256, kGemmCap1>, a, s256);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 256, kGemmCap1>, a, s256);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 128, kGemmCap1>, a, s128);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 128, kGemmCap1>, a, s128);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 256, 1>, a, s256);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 256, 1>, a, s256);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 128, 1>, a, s128);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 128, 1>, a, s128);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 256, gemm::kMaxGroup>, a, s256);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 256, gemm::kMaxGroup>, a, s256);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MAX, 128, gemm::kMaxGroup>, a, s128);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_MOD, 128, gemm::kMaxGroup>, a, s128);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 256, kGemmCap1>, a, s256);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 128, kGemmCap1>, a, s128);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 256, 1>, a, s256);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 128, 1>, a, s128);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 256, gemm::kMaxGroup>, a, s256);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm<EPI_CW, 128, gemm::kMaxGroup>, a, s128);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -203,11 +199,6 @@ int encode_bf16_2d(CUtensorMap *tm, const void *base, uint64_t rows, uint64_t co
 // __launch_bounds__ minimum).
 constexpr int kResidBlocksPerSM = 3;
 
-// k from which the residue GEMM runs the CRT in its epilogue: one output tile's
-// CRT (about 120-180 us of its eight epilogue warps) then fits between the
-// segment folds of the next tile's N planes.
-constexpr int kFuseK = 2048;
-
 // The residue GEMM's failure-path test hook (oz2_gemm_timeout_selftest sets it
 // for the duration of one call on its host thread): the k-block whose loads
 // each CTA skips on its first item (-1: none) and the limit of every wait.
@@ -225,7 +216,7 @@ int launch_gemm(GemmGroup<CAP> &G, int sms, cudaStream_t st) {
     for (int p = 0; p < G.count; p++) {
         GemmProblem &P = G.p[p];
         P.item_begin = items;
-        items += (long long)P.tile_count * (P.fused ? 1 : P.planes);
+        items += (long long)P.tiles_m * P.tiles_n * P.planes;
     }
     G.total_items = items;
     G.wait_limit_ns = EPI == EPI_MOD ? g_hook.limit_ns : kWaitLimitNs;
@@ -286,7 +277,6 @@ struct Job {
     int32_t *mu_out = nullptr, *nu_out = nullptr;
     const int32_t *mu_in = nullptr, *nu_in = nullptr;
     bool accum = false;            // CRT adds to C (split-K ranges after the first)
-    bool fused = false;            // CRT in the residue GEMM's epilogue (set by run_group)
     // workspace views
     Dims d{};
     Layout L{};
@@ -359,11 +349,9 @@ struct Job {
         P.kb_total = d.k_pad / gemm::BK;
         P.tiles_m = d.m_pad / gemm::BM;
         P.tiles_n = d.n_pad / bn;
-        P.tile_begin = 0;
-        P.tile_count = P.tiles_m * P.tiles_n;
-        P.fused = 0;
-        P.crt = CrtOut{};
         P.plane0 = 0;
+        P.cw_row = P.cw_col = nullptr;
+        P.cw_red = nullptr;
         return OZ2_OK;
     }
     void as_scale_gemm(GemmProblem &P) const {
@@ -378,17 +366,15 @@ struct Job {
         P.n_dev = ndev;
         P.W = W;
         P.w_plane = w_plane;
-        P.crt = CrtOut{C, mu_use(), nu_use(), ldc, m, n, fp32 ? 1 : 0, accum ? 1 : 0};
+        P.row_max = P.col_max = nullptr;
     }
-    // the residue GEMM runs this problem's CRT in its epilogue when the tiles'
-    // MMA work leaves the epilogue warps room for it (k >= kFuseK)
-    bool fuse_crt() const { return d.k_pad >= kFuseK; }
     // componentwise rule: floor(2^mu' |A|) floor(|B| 2^nu') from plane 1
     void as_cw_gemm(GemmProblem &P) const {
         P.planes = 1;
         P.plane0 = 1;
         P.n_dev = nullptr;
         P.W = nullptr;
+        P.row_max = P.col_max = nullptr;
         P.cw_row = cwA;
         P.cw_col = cwB;
         P.cw_red = red + 5;
@@ -415,7 +401,6 @@ struct Job {
         j.cwv[1] = cwB;
         j.inject = inject() ? 1 : 0;
         j.accum = accum ? 1 : 0;
-        j.fused = fused ? 1 : 0;
         auto aligned = [](const Operand<T> &op) {
             return (reinterpret_cast<uintptr_t>(op.ptr) % 16 == 0 && (op.ld * long(sizeof(T))) % 16 == 0) ? 1 : 0;
         };
@@ -473,22 +458,9 @@ int managed_workspace(int dev, size_t bytes, uint8_t **out) {
 // persistent launch over the tiles of all problems (heaviest first).
 template <typename T, int CAP, class Mark>
 int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&mark) {
-    constexpr int GCAP = CAP < kGemmCap1 ? kGemmCap1 : CAP;
-    static_assert(sizeof(JobGroup<T, CAP>) < 30000 && sizeof(GemmGroup<GCAP>) < 30000, "kernel parameter space");
+    static_assert(sizeof(JobGroup<T, CAP>) < 30000 && sizeof(GemmGroup<CAP>) < 30000, "kernel parameter space");
     static thread_local JobGroup<T, CAP> J;      // passed by value as the kernel parameter
-    static thread_local GemmGroup<GCAP> G;
-    // the CRT in the residue GEMM's epilogue: every problem of a batch with k >=
-    // kFuseK; a single call also needs two waves of tiles (a tile's CRT runs
-    // during the next tile), and runs its last partial wave unfused (rem tiles,
-    // plane by plane, their CRT by k_crt_tiles) so that no CTA holds a whole
-    // tile of N planes while the others idle
-    int rem1 = 0;
-    for (int p = 0; p < count; p++) {
-        Job<T> &job = *jobs[p];
-        const int tiles = (job.d.m_pad / gemm::BM) * (job.d.n_pad / job.bn);
-        job.fused = job.fuse_crt() && (count > 1 || tiles >= 2 * sms);
-        if (count == 1 && job.fused) rem1 = tiles % sms;
-    }
+    static thread_local GemmGroup<CAP> G;
     std::memset(&J, 0, sizeof J);
     J.count = count;
     for (int p = 0; p < count; p++) J.j[p] = jobs[p]->desc();
@@ -553,23 +525,9 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
                 GemmProblem &P = G.p[G.count++];
                 int r = job.describe(P);
                 if (r) return r;
-                if (epi == EPI_MAX) {
-                    job.as_scale_gemm(P);
-                } else if (epi == EPI_CW) {
-                    job.as_cw_gemm(P);
-                } else {
-                    job.as_residue_gemm(P);
-                    P.fused = job.fused ? 1 : 0;
-                    if (job.fused && count == 1 && rem1 > 0) {
-                        // the last rem1 tiles of the raster as plane-by-plane items
-                        GemmProblem &Q = G.p[G.count++];
-                        Q = P;
-                        P.tile_count -= rem1;
-                        Q.tile_begin = P.tile_count;
-                        Q.tile_count = rem1;
-                        Q.fused = 0;
-                    }
-                }
+                if (epi == EPI_MAX) job.as_scale_gemm(P);
+                else if (epi == EPI_CW) job.as_cw_gemm(P);
+                else job.as_residue_gemm(P);
             }
             if (!G.count) continue;
             int r;
@@ -606,17 +564,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
     if ((rc = gemms(EPI_MOD))) return rc;
     if ((rc = mark(OZ2_PHASE_CRT))) return rc;
-    if (count == 1 && jobs[0]->fused) {
-        if (rem1 > 0) {
-            const JobDesc<T> &j = J.j[0];
-            const int bn = jobs[0]->bn, tiles_m = j.R_pad[0] / gemm::BM, tiles_n = j.n_pad / bn;
-            const int bpt = gemm::BM / (256 / (bn / 4));
-            k_crt_tiles<T><<<unsigned(rem1 * bpt), 256, 0, st>>>(j.W, j.w_plane, long(j.n_pad), j.ndev, j.shift[0],
-                                                                 j.shift[1], j.C, j.ldc, j.m, j.n, j.accum, tiles_m,
-                                                                 tiles_n, bn, tiles_m * tiles_n - rem1);
-            if ((rc = launched())) return rc;
-        }
-    } else if (count == 1) {
+    if (count == 1) {
         const JobDesc<T> &j = J.j[0];
         dim3 grid(unsigned(cdiv(j.n, kCrtCols)), unsigned(std::min(j.m, 65535)));
         k_crt_one<T><<<grid, 256, 0, st>>>(j.W, j.w_plane, long(j.n_pad), j.ndev, j.shift[0], j.shift[1], j.C,

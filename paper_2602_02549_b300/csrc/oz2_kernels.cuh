@@ -211,7 +211,6 @@ struct JobDesc {
     int cw;                        // componentwise N rule (OZ2_COMPONENTWISE)
     int absmax_lb;                 // lines per k_absmax item (kLineBlock or fewer, per launch)
     int accum;                     // CRT adds its result to C (the K ranges after the first)
-    int fused;                     // the residue GEMM's epilogue runs the CRT (no k_crt items)
     double target;
     unsigned long long *hmax[2];   // per-k maxima of |A|, |B|
     unsigned long long *rmax[2];   // per logical row maxima (bits)
@@ -326,7 +325,6 @@ template <typename T> struct Items {
     __host__ __device__ static long long resid_kc(const JobDesc<T> &j) { return items_kc_x(j, 0) + items_kc_x(j, 1); }
     __host__ __device__ static long long resid_rc(const JobDesc<T> &j) { return items_rc_x(j, 0) + items_rc_x(j, 1); }
     __host__ __device__ static long long crt(const JobDesc<T> &j) {
-        if (j.fused) return 0;
         const int tpr = crt_tpr(j.n);
         return cdiv(j.m, 256 / tpr) * cdiv(j.n, tpr * 4);
     }
@@ -950,214 +948,6 @@ __global__ void __launch_bounds__(256, 3) k_resid_rc(const __grid_constant__ Job
     });
 }
 
-// ============================================================= CRT
-// Algorithm 3 after the products, then Algorithm 1's inverse scaling:
-//   C'(1) = sum_l s_l1 W_l, C'(2) = sum_l s_l2 W_l, each the exact sum rounded
-//           once to FP64 (b = 64: C'(1) is exact, Lemma 2; b = 32: s_l2 = 0),
-//   Q = rint(P_inv C'(1)),  C'' = fma(-Q, P2, fma(-Q, P1, C'(1)) + C'(2)),
-//   C = RN(2^-(mu_i + nu_j) C'')  (b = 32: rounded once to FP32).
-
-// ------------------------------------------------------------------ the epilogue's helpers
-
-// RN(x 2^e) for an integer-valued x with |x| < 2^400 (an exponent add, on the
-// integer units, whenever the result stays normal)
-__device__ __forceinline__ double scale_pow2(double x, int e) {
-    const long long b = __double_as_longlong(x);
-    const bool zero = ((unsigned long long)b << 1) == 0;          // +-0, tested on the integer units
-    const int ex = int((b >> 52) & 0x7FF);
-    if (zero || (ex + e >= 1 && ex + e <= 2046))
-        return zero ? x : __longlong_as_double((long long)((unsigned long long)b + ((unsigned long long)(long long)e << 52)));   // exact
-    if (e > 1023) return x * 0x1p1023 * 0x1p1023;                 // overflows to +-inf as ldexp does
-    if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
-    const double y = x * 0x1p-1022;                               // exact: |x| >= 1
-    const int e2 = e + 1022;
-    if (e2 < -1022) return copysign(0.0, x);
-    return y * __longlong_as_double((long long)(e2 + 1023) << 52);
-}
-
-// RN((hi 2^S + lo) 2^e) as a double, from integer operations only (S = 31 or
-// 32).  Requires |hi|, |lo| < 2^61 and a result in the normal range (the tables
-// check both for every N).  An exact zero gives +0.
-template <int S>
-__device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
-    // written without branches (selects only); every shift amount stays in [0, 63]
-    const long long t = hi + (lo >> S);            // value = t 2^S + r, 0 <= r < 2^S
-    const unsigned long long r = (unsigned long long)lo & ((1ull << S) - 1);
-    const bool neg = t < 0;
-    // |value| = T 2^S + R
-    const unsigned long long T = neg ? ~(unsigned long long)t + (r == 0 ? 1ull : 0ull) : (unsigned long long)t;
-    const unsigned long long R = neg ? ((1ull << S) - r) & ((1ull << S) - 1) : r;
-    // X 2^s with the bits below 2^s folded into a sticky bit 0 of X (T < 2^63, so s < S)
-    const int bt = 64 - __clzll((long long)T);
-    const int s = max(bt - (64 - S), 0);
-    const unsigned long long X = (T << (S - s)) | (R >> s) | ((R & ((1ull << s) - 1)) != 0 ? 1ull : 0ull);
-    const int bl = 64 - __clzll((long long)X);
-    const int sh = max(bl - 53, 0);
-    unsigned long long mant = bl <= 53 ? X << min(53 - bl, 63) : X >> sh;
-    const unsigned long long rem = X & ((1ull << sh) - 1), half = (1ull << sh) >> 1;
-    mant += (sh > 0 && (rem > half || (rem == half && (mant & 1ull)))) ? 1ull : 0ull;
-    const int carry = int(mant >> 53);
-    mant >>= carry;
-    const int ex = bl - 1 + s + e + carry;
-    const unsigned long long bits = (neg ? (1ull << 63) : 0ull) | ((unsigned long long)(ex + 1023) << 52) |
-                                    (mant & ((1ull << 52) - 1));
-    return X == 0 ? 0.0 : __longlong_as_double((long long)bits);
-}
-
-// H 2^e as a double for |H| < 2^53 (exact, on the integer units; the result is normal).
-__device__ __forceinline__ double exact_i53(long long H, int e) {
-    const unsigned long long a = H < 0 ? 0ull - (unsigned long long)H : (unsigned long long)H;
-    const int bl = 64 - __clzll((long long)a);                     // <= 53 (0 for H = 0)
-    const unsigned long long bits = ((unsigned long long)(bl + 1021 + e) << 52) + (a << (53 - bl));
-    return H == 0 ? 0.0 : __longlong_as_double((long long)(bits | (H < 0 ? (1ull << 63) : 0ull)));
-}
-
-// rint(x) (round half to even, as FP64 rint) on the integer units: the
-// fraction bits are rounded off in place, a carry into the exponent field
-// giving the next power of two.
-__device__ __forceinline__ double rint_bits(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = int((b >> 52) & 0x7FF);
-    const unsigned long long sign = b & (1ull << 63);
-    const int f = min(max(1075 - e, 1), 52);                     // fraction bits where 1 <= |x| < 2^52
-    const unsigned long long t = (b + ((1ull << (f - 1)) - 1) + ((b >> f) & 1ull)) & ~((1ull << f) - 1);
-    // |x| < 1: 0, or 1 above 1/2 (1/2 itself goes to the even 0)
-    const unsigned long long small = sign | ((b & ~(1ull << 63)) > 0x3FE0000000000000ull ? 0x3FF0000000000000ull : 0ull);
-    return __longlong_as_double((long long)(e >= 1075 ? b : (e < 1023 ? small : t)));   // |x| >= 2^52: x
-}
-
-// c + a.lo16 b.byte0 + a.hi16 b.byte1 (dp2a.lo) or with b's bytes 2, 3
-// (dp2a.hi): unsigned 16-bit pieces of a, signed bytes of b.
-__device__ __forceinline__ int dp2a_lo(uint32_t a, uint32_t b, int c) {
-    int d;
-    asm("dp2a.lo.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-__device__ __forceinline__ int dp2a_hi(uint32_t a, uint32_t b, int c) {
-    int d;
-    asm("dp2a.hi.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-
-// One row i, columns j0 .. j0+3 of one thread; load(l) gives the four W_l
-// bytes of those columns (zero for l >= N).  C'(1) and C'(2) are sums of
-// integer multiples of fixed grids, taken exactly: each constant is cut into
-// four 16-bit pieces, and one dp2a adds piece * W for two planes of one column
-// into a 32-bit sum (|sum| < 2^16 128 49 < 2^31).  The piece sums are then put
-// together in 64-bit integers and rounded once.
-template <typename T, typename Load>
-__device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, const int32_t *mu,
-                                        const int32_t *nu, T *C, long ldc, int n, int i, int j0, bool accum) {
-    constexpr int B = sizeof(T) == 8 ? 64 : 32;
-    int s1[4][4], s2[4][4];                    // [column][piece]: C'(1) (b = 64 only), C'(2) / b = 32 C'(1)
-#pragma unroll
-    for (int e = 0; e < 4; e++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) s1[e][q] = s2[e][q] = 0;
-    const int pairs = (N + 1) / 2;
-    // software pipeline: the next pair's loads are in flight while a pair is summed
-    uint32_t w0 = load(0), w1 = load(1);
-    for (int pi = 0; pi < pairs; pi++) {
-        const uint32_t p0 = w0, p1 = w1;
-        w0 = load(2 * pi + 2);
-        w1 = load(2 * pi + 3);
-        // bytes of columns (0, 1) and (2, 3), planes 2 pi and 2 pi + 1 side by side
-        const uint32_t x01 = __byte_perm(p0, p1, 0x5140), x23 = __byte_perm(p0, p1, 0x7362);
-        const uint4 c2 = B == 64 ? c_dp64[d.poff + pi][1] : c_dp32[d.poff + pi];
-        const uint32_t cc2[4] = {c2.x, c2.y, c2.z, c2.w};
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            s2[0][q] = dp2a_lo(cc2[q], x01, s2[0][q]);
-            s2[1][q] = dp2a_hi(cc2[q], x01, s2[1][q]);
-            s2[2][q] = dp2a_lo(cc2[q], x23, s2[2][q]);
-            s2[3][q] = dp2a_hi(cc2[q], x23, s2[3][q]);
-        }
-        if (B == 64) {
-            const uint4 c1 = c_dp64[d.poff + pi][0];
-            const uint32_t cc1[4] = {c1.x, c1.y, c1.z, c1.w};
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                s1[0][q] = dp2a_lo(cc1[q], x01, s1[0][q]);
-                s1[1][q] = dp2a_hi(cc1[q], x01, s1[1][q]);
-                s1[2][q] = dp2a_lo(cc1[q], x23, s1[2][q]);
-                s1[3][q] = dp2a_hi(cc1[q], x23, s1[3][q]);
-            }
-        }
-    }
-    const int mi = mu[i];
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-        const int j = j0 + e;
-        if (j >= n) break;
-        // the second sum as hi 2^32 + lo: pieces 0, 1 and 2, 3 (shifted as unsigned:
-        // the sums may be negative)
-        const long long lo2 = (long long)((unsigned long long)(long long)s2[e][0] +
-                                          ((unsigned long long)(long long)s2[e][1] << 16));
-        const long long hi2 = (long long)((unsigned long long)(long long)s2[e][2] +
-                                          ((unsigned long long)(long long)s2[e][3] << 16));
-        double cpp;
-        if (B == 64) {
-            // C'(1) = H g exactly, |H| < 2^53 (Lemma 2): the four piece sums added
-            // modulo 2^64, which is exact because H fits
-            const unsigned long long Hu = (unsigned long long)(long long)s1[e][0] +
-                                          ((unsigned long long)(long long)s1[e][1] << 16) +
-                                          ((unsigned long long)(long long)s1[e][2] << 32) +
-                                          ((unsigned long long)(long long)s1[e][3] << 48);
-            const double c1 = exact_i53((long long)Hu, d.eg);
-            const double q = rint_bits(d.Pinv * c1);
-            cpp = fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum<32>(hi2, lo2, d.esum));
-        } else {
-            const double c1 = rn_sum<32>(hi2, lo2, d.esum);
-            const double q = rint_bits(d.Pinv * c1);
-            // P2 = 0 and C'(2) = +0, so fma(-q, 0, x + 0) = x + 0 as in the b = 64 form
-            cpp = fma(-q, d.P1, c1) + 0.0;
-        }
-        const double v = scale_pow2(cpp, -(mi + nu[j]));
-        const T c = B == 64 ? T(v) : T(__double2float_rn(v));
-        T *dst = C + (long)i * ldc + j;
-        *dst = accum ? *dst + c : c;            // one rounding per added K range
-    }
-}
-
-// One problem: block (x, y) takes columns 1024 x .. 1024 x + 1023 of rows y,
-// y + gridDim.y, ...
-constexpr int kCrtCols = 1024;
-template <typename T>
-__global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, long n_pad, const int *n_dev,
-                                                 const int32_t *mu, const int32_t *nu, T *C, long ldc, int m, int n,
-                                                 int accum) {
-    const int N = *n_dev;
-    const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
-    const long col0 = (long)blockIdx.x * kCrtCols;
-    const int j0 = int(col0) + threadIdx.x * 4;
-    for (int i = blockIdx.y; i < m; i += gridDim.y) {
-        if (j0 >= n) continue;
-        const int8_t *wp = W + (long)i * n_pad + j0;
-        crt_row<T>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane)) : 0u; },
-                   N, d, mu, nu, C, ldc, n, i, j0, accum != 0);
-    }
-}
-
-// A group of problems.  Item: 256 / tpr rows of tpr x 4 columns (4 per thread,
-// tpr threads per row).
-template <typename T, int CAP>
-__global__ void __launch_bounds__(256, 4) k_crt(const __grid_constant__ JobGroup<T, CAP> G) {
-    for_items(G, [&](const JobDesc<T> &jd, long long li) {
-        const int tpr = crt_tpr(jd.n), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
-        const unsigned ncb = unsigned(cdiv(jd.n, tpr * 4)), ui = unsigned(li);
-        const int rb = int(ui / ncb);
-        const int i = rb * (256 / tpr) + ly;
-        const int j0 = int(ui - unsigned(rb) * ncb) * tpr * 4 + tx * 4;
-        if (ly >= 256 / tpr || j0 >= jd.n || i >= jd.m) return;
-        const int N = *jd.ndev;
-        const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
-        const int8_t *wp = jd.W + (long)i * jd.n_pad + j0;
-        const long wpl = jd.w_plane;
-        crt_row<T>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)) : 0u; },
-                   N, d, jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0, jd.accum != 0);
-    });
-}
-
 // ============================================================= tcgen05 GEMM
 namespace gemm {
 constexpr int BM = 128, BK = 64;
@@ -1182,42 +972,20 @@ struct Cfg {
 
 enum { EPI_MAX = 0, EPI_MOD = 1, EPI_CW = 2 };
 
-// The fused CRT of a residue GEMM (EPI_MOD with GemmProblem::fused): where
-// Algorithm 3's sums, Q, C'' and the inverse scaling write C.
-struct CrtOut {
-    void *C;                   // double or float (fp32), row-major
-    const int32_t *mu, *nu;
-    int ldc, m, n;
-    int fp32, accum;           // accum: C += (the K ranges after the first)
-};
-
 // One GEMM problem of a launch: X_l (rows l*m_pad ..) times Y_l^T for the planes
-// l < planes (and l < *n_dev when n_dev is set), 128 x BN output tiles: the
-// tiles tile_begin .. tile_begin + tile_count - 1 of the grouped raster order
-// (raster_tile).  A fused problem (EPI_MOD) has one work item per tile, which
-// runs all N planes of that tile and then its CRT; otherwise an item is one
-// (plane, tile) pair, the planes in order.
+// l < planes (and l < *n_dev when n_dev is set), 128 x BN output tiles.
 struct GemmProblem {
     CUtensorMap tmA, tmB;      // BF16, K-major, 128B-swizzled boxes of 64 x 128 / 64 x BN
     int m_pad, n_pad, kb_total;
     int tiles_m, tiles_n, planes;
     int plane0;                // first plane of the operands (EPI_CW: plane 1)
-    int tile_begin, tile_count;
-    int fused;                 // EPI_MOD: items are tiles with all planes, CRT in the epilogue
     long long item_begin;      // first work item of this problem in the launch
     const int *n_dev;          // EPI_MOD: planes l >= *n_dev are skipped
     int8_t *W;                 // EPI_MOD: W[l*w_plane + row*n_pad + col]
     long long w_plane;
-    union {                    // what each epilogue writes besides W
-        struct {
-            int *row_max, *col_max;          // EPI_MAX
-        };
-        struct {
-            const float *cw_row, *cw_col;    // EPI_CW: (a_i, b_i) per row, (c_j, d_j) per column
-            unsigned long long *cw_red;      // EPI_CW: maxima of X / L and Y / L (double bits) at [0], [2]
-        };
-        CrtOut crt;                          // EPI_MOD, fused
-    };
+    int *row_max, *col_max;    // EPI_MAX
+    const float *cw_row, *cw_col;   // EPI_CW: (a_i, b_i) per row, (c_j, d_j) per column
+    unsigned long long *cw_red;     // EPI_CW: maxima of X / L and Y / L (double bits) at [0], [2]
 };
 
 template <int CAP = gemm::kMaxGroup>
@@ -1231,27 +999,14 @@ struct GemmGroup {
                                         // but loads nothing, so the MMA warp's wait expires
 };
 
-// The planes [l0, l1) of one tile (l1 <= l0: nothing to do).
 struct WorkItem {
-    int p, l0, l1, tile_m, tile_n;
+    int p, l, tile_m, tile_n;
+    bool skip;
 };
 
-// Tile t of the grouped raster order: column by column through groups of
-// GROUP_M row tiles, so the CTAs working at the same time share few A and B
-// panels (L2 reuse).
-__host__ __device__ __forceinline__ void raster_tile(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
-    const int span = gemm::GROUP_M * tiles_n;
-    const int grp = t / span;
-    const int first_m = grp * gemm::GROUP_M;
-    const int gm = min(gemm::GROUP_M, tiles_m - first_m);
-    const int tin = t - grp * span;
-    tm = first_m + tin % gm;
-    tn = tin / gm;
-}
-
-// Work item g -> (problem, planes, tile): one plane of one tile, planes in
-// order (tiles inside a plane in raster order), or for a fused problem one tile
-// with the planes 0 .. N-1.
+// Work item g -> (problem, plane, tile).  Planes run in order; inside a plane
+// the tiles go column by column through groups of GROUP_M row tiles, so the
+// CTAs working at the same time share few A and B panels (L2 reuse).
 template <int CAP>
 __device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long long g) {
     WorkItem w;
@@ -1259,56 +1014,19 @@ __device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long lo
     while (p + 1 < G.count && G.p[p + 1].item_begin <= g) p++;
     const GemmProblem &P = G.p[p];
     const long long li = g - P.item_begin;
-    const int nl = P.n_dev != nullptr ? *P.n_dev : P.planes;
+    const int per_plane = P.tiles_m * P.tiles_n;
     w.p = p;
-    int t;
-    if (P.fused) {
-        t = int(li);
-        w.l0 = 0;
-        w.l1 = nl;
-    } else {
-        w.l0 = int(li / P.tile_count);
-        t = int(li - (long long)w.l0 * P.tile_count);
-        w.l1 = w.l0 < nl ? w.l0 + 1 : w.l0;
-    }
-    raster_tile(P.tile_begin + t, P.tiles_m, P.tiles_n, w.tile_m, w.tile_n);
+    w.l = int(li / per_plane);
+    const int t = int(li - (long long)w.l * per_plane);
+    const int span = gemm::GROUP_M * P.tiles_n;
+    const int grp = t / span;
+    const int first_m = grp * gemm::GROUP_M;
+    const int gm = min(gemm::GROUP_M, P.tiles_m - first_m);
+    const int tin = t - grp * span;
+    w.tile_m = first_m + tin % gm;
+    w.tile_n = tin / gm;
+    w.skip = P.n_dev != nullptr && w.l >= *P.n_dev;
     return w;
-}
-
-// The fused CRT of one output tile, for one epilogue thread: its row `row` and
-// NC columns from col0, as crt_row groups of 4 columns (Algorithm 3's sums from
-// W_l as this thread stored them, Q, C'', the inverse scaling).
-struct CrtSlice {
-    int p, row, col0, next, N;    // next: the next group of 4 columns; next == NC / 4: done
-};
-
-template <int NC, int CAP>
-__device__ __noinline__ void crt_groups(const GemmGroup<CAP> &G, CrtSlice &c, int count) {
-    const GemmProblem &P = G.p[c.p];
-    const CrtOut &o = P.crt;
-    const int end = min(c.next + count, NC / 4);
-    if (c.row >= o.m) {
-        c.next = end;
-        return;
-    }
-    const int8_t *wrow = P.W + (long long)c.row * P.n_pad;
-    for (; c.next < end; c.next++) {
-        const int j0 = c.col0 + 4 * c.next;
-        if (j0 >= o.n) {
-            c.next = NC / 4;
-            break;
-        }
-        // plain loads: this thread stored these bytes earlier in this kernel
-        auto load = [&](int l) {
-            return l < c.N ? *reinterpret_cast<const uint32_t *>(wrow + (long long)l * P.w_plane + j0) : 0u;
-        };
-        if (o.fp32)
-            crt_row<float>(load, c.N, c_n32[c.N], o.mu, o.nu, static_cast<float *>(o.C), o.ldc, o.n, c.row, j0,
-                           o.accum != 0);
-        else
-            crt_row<double>(load, c.N, c_n64[c.N], o.mu, o.nu, static_cast<double *>(o.C), o.ldc, o.n, c.row,
-                            j0, o.accum != 0);
-    }
 }
 
 __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
@@ -1516,24 +1234,20 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
             bool ok = true, first = true;
             for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
                 const WorkItem w = decode_item(G, g);
+                if (w.skip) continue;
                 const GemmProblem &P = G.p[w.p];
-                for (int l = w.l0; l < w.l1 && ok; l++) {
-                    const int row_a = (P.plane0 + l) * P.m_pad + w.tile_m * BM;
-                    const int row_b = (P.plane0 + l) * P.n_pad + w.tile_n * BN;
-                    for (int kb = 0; kb < P.kb_total; kb++, kbc++) {
-                        const int s = int(kbc % STAGES);
-                        const uint32_t ph = (kbc / STAGES) & 1u;
-                        if (kbc >= STAGES && !bounded_wait(bar_empty(s), ph ^ 1u, abort_flag, limit)) {
-                            ok = false;
-                            break;
-                        }
-                        ptx::mbar_arrive_expect_tx(bar_full(s), STAGE_BYTES);
-                        if (first && kb == G.hook_kb) continue;      // test hook: armed, never loaded
-                        ptx::tma_load_2d(sA(s), &P.tmA, kb * BK, row_a, bar_full(s));
-                        ptx::tma_load_2d(sB(s), &P.tmB, kb * BK, row_b, bar_full(s));
-                    }
-                    first = false;
+                const int row_a = (P.plane0 + w.l) * P.m_pad + w.tile_m * BM;
+                const int row_b = (P.plane0 + w.l) * P.n_pad + w.tile_n * BN;
+                for (int kb = 0; kb < P.kb_total; kb++, kbc++) {
+                    const int s = int(kbc % STAGES);
+                    const uint32_t ph = (kbc / STAGES) & 1u;
+                    if (kbc >= STAGES && !bounded_wait(bar_empty(s), ph ^ 1u, abort_flag, limit)) { ok = false; break; }
+                    ptx::mbar_arrive_expect_tx(bar_full(s), STAGE_BYTES);
+                    if (first && kb == G.hook_kb) continue;      // test hook: armed, never loaded
+                    ptx::tma_load_2d(sA(s), &P.tmA, kb * BK, row_a, bar_full(s));
+                    ptx::tma_load_2d(sB(s), &P.tmB, kb * BK, row_b, bar_full(s));
                 }
+                first = false;
             }
             issued = kbc;
         }
@@ -1543,10 +1257,10 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
             bool ok = true;
             for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
                 const WorkItem w = decode_item(G, g);
+                if (w.skip) continue;
                 const GemmProblem &P = G.p[w.p];
                 const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
-                for (int pseg = 0; pseg < (w.l1 - w.l0) * nseg && ok; pseg++, segc++) {
-                    const int seg = pseg % nseg;
+                for (int seg = 0; seg < nseg && ok; seg++, segc++) {
                     const int buf = int(segc & 1u);
                     if (segc >= 2 && !bounded_wait(bar_acce(buf), ((segc >> 1) - 1) & 1u, abort_flag, limit)) {
                         ok = false;
@@ -1578,81 +1292,62 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         const int half = (warp - 2) >> 2;       // columns [NC half, NC half + NC)
         uint32_t segc = 0;
         bool ok = true;
-        // EPI_MOD, fused problems: the CRT of the previous tile, in slices after
-        // each plane of the current one (next == NC / 4: nothing pending)
-        CrtSlice pend{0, 0, 0, NC / 4, 0};
         for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
             const WorkItem w = decode_item(G, g);
+            if (w.skip) continue;
             const GemmProblem &P = G.p[w.p];
             const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
-            const int row = w.tile_m * BM + q * 32 + lane, col0 = w.tile_n * BN + half * NC;
-            for (int l = w.l0; l < w.l1 && ok; l++) {
-                // EPI_MAX: INT32 sums of the segments; EPI_MOD: FP32 pairs holding the
-                // sum of the segments' representatives mod p_l (mod_rep2)
-                int acc[EPI == EPI_MOD ? 1 : NC];
-                unsigned long long acc2[EPI == EPI_MOD ? NC / 2 : 1];
-                unsigned long long ip = 0, np = 0;
+            // EPI_MAX: INT32 sums of the segments; EPI_MOD: FP32 pairs holding the
+            // sum of the segments' representatives mod p_l (mod_rep2)
+            int acc[EPI == EPI_MOD ? 1 : NC];
+            unsigned long long acc2[EPI == EPI_MOD ? NC / 2 : 1];
+            unsigned long long ip = 0, np = 0;
+            if constexpr (EPI == EPI_MOD) {
+#pragma unroll
+                for (int i = 0; i < NC / 2; i++) acc2[i] = 0ull;
+                ip = c_w13p[w.l][kFixLimbs];
+                np = c_w13p[w.l][kFixLimbs + 1];
+            } else {
+#pragma unroll
+                for (int i = 0; i < NC; i++) acc[i] = 0;
+            }
+            for (int seg = 0; seg < nseg; seg++, segc++) {
+                const int buf = int(segc & 1u);
+                if (!warp_wait(bar_accf(buf), (segc >> 1) & 1u, abort_flag, limit)) { ok = false; break; }
+                ptx::tc_fence_after();
+                const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + half * NC);
                 if constexpr (EPI == EPI_MOD) {
 #pragma unroll
-                    for (int i = 0; i < NC / 2; i++) acc2[i] = 0ull;
-                    ip = c_w13p[l][kFixLimbs];
-                    np = c_w13p[l][kFixLimbs + 1];
-                } else {
+                    for (int c = 0; c < NC / 16; c++) {
+                        uint32_t v[16];
+                        ptx::tmem_ld_32x32b_x16(taddr + uint32_t(c * 16), v);
+                        ptx::tmem_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < NC; i++) acc[i] = 0;
-                }
-                for (int seg = 0; seg < nseg; seg++, segc++) {
-                    const int buf = int(segc & 1u);
-                    if (!warp_wait(bar_accf(buf), (segc >> 1) & 1u, abort_flag, limit)) { ok = false; break; }
-                    ptx::tc_fence_after();
-                    const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * BN + half * NC);
-                    if constexpr (EPI == EPI_MOD) {
-#pragma unroll
-                        for (int c = 0; c < NC / 16; c++) {
-                            uint32_t v[16];
-                            ptx::tmem_ld_32x32b_x16(taddr + uint32_t(c * 16), v);
-                            ptx::tmem_wait_ld();
-#pragma unroll
-                            for (int i = 0; i < 8; i++) {
-                                const unsigned long long x = (unsigned long long)v[2 * i] |
-                                                             ((unsigned long long)v[2 * i + 1] << 32);
-                                acc2[c * 8 + i] = f2::add(acc2[c * 8 + i], mod_rep2(x, ip, np));
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < NC / 16; c++) {
-                            uint32_t v[16];
-                            ptx::tmem_ld_32x32b_x16(taddr + uint32_t(c * 16), v);
-                            ptx::tmem_wait_ld();
-#pragma unroll
-                            for (int i = 0; i < 16; i++) acc[c * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
+                        for (int i = 0; i < 8; i++) {
+                            const unsigned long long x = (unsigned long long)v[2 * i] |
+                                                         ((unsigned long long)v[2 * i + 1] << 32);
+                            acc2[c * 8 + i] = f2::add(acc2[c * 8 + i], mod_rep2(x, ip, np));
                         }
                     }
-                    ptx::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(bar_acce(buf));
-                }
-                if (!ok) break;
-                if constexpr (EPI == EPI_MOD) {
-                    tile_epilogue_mod<NC>(P, l, row, col0, acc2);
-                    // a slice of the previous tile's CRT: spread over this tile's planes
-                    if (pend.next < NC / 4) crt_groups<NC>(G, pend, (NC / 4 + w.l1 - w.l0 - 1) / (w.l1 - w.l0));
-                } else if constexpr (EPI == EPI_MAX) {
-                    tile_epilogue_max<NC>(P, row, col0, lane, acc);
                 } else {
-                    tile_epilogue_cw<NC>(P, row, col0, acc);
+#pragma unroll
+                    for (int c = 0; c < NC / 16; c++) {
+                        uint32_t v[16];
+                        ptx::tmem_ld_32x32b_x16(taddr + uint32_t(c * 16), v);
+                        ptx::tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; i++) acc[c * 16 + i] += __float2int_rn(__uint_as_float(v[i]));
+                    }
                 }
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(bar_acce(buf));
             }
-            if constexpr (EPI == EPI_MOD) {
-                if (ok && P.fused && w.l1 > w.l0) {
-                    if (pend.next < NC / 4) crt_groups<NC>(G, pend, NC / 4);     // finish the older tile first
-                    pend = CrtSlice{w.p, row, col0, 0, w.l1};
-                }
-            }
-        }
-        if constexpr (EPI == EPI_MOD) {
-            if (ok && pend.next < NC / 4) crt_groups<NC>(G, pend, NC / 4);      // the last tile's CRT
+            if (!ok) break;
+            const int row = w.tile_m * BM + q * 32 + lane, col0 = w.tile_n * BN + half * NC;
+            if constexpr (EPI == EPI_MOD) tile_epilogue_mod<NC>(P, w.l, row, col0, acc2);
+            else if constexpr (EPI == EPI_MAX) tile_epilogue_max<NC>(P, row, col0, lane, acc);
+            else tile_epilogue_cw<NC>(P, row, col0, acc);
         }
     }
     ptx::tc_fence_before();
@@ -1675,31 +1370,6 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         ptx::tc_fence_after();
         ptx::tmem_dealloc<2 * BN>(tmem);
     }
-}
-
-// The CRT of the tiles tile_begin .. tile_begin + gridDim.x / (blocks per tile) - 1
-// (raster order) of one problem whose other tiles ran theirs in the residue
-// GEMM's epilogue: each thread takes 4 columns of one row (crt_row), a block
-// 1024 outputs of one tile.
-template <typename T>
-__global__ void __launch_bounds__(256) k_crt_tiles(const int8_t *W, long w_plane, long n_pad, const int *n_dev,
-                                                   const int32_t *mu, const int32_t *nu, T *C, long ldc, int m,
-                                                   int n, int accum, int tiles_m, int tiles_n, int bn,
-                                                   int tile_begin) {
-    const int N = *n_dev;
-    const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
-    const int per_row = bn / 4;                 // threads per row of a tile
-    const int rows_pb = 256 / per_row;          // rows per block
-    const int bpt = gemm::BM / rows_pb;         // blocks per tile
-    const int t = tile_begin + int(blockIdx.x) / bpt, sub = int(blockIdx.x) % bpt;
-    int tm, tn;
-    raster_tile(t, tiles_m, tiles_n, tm, tn);
-    const int i = tm * gemm::BM + sub * rows_pb + int(threadIdx.x) / per_row;
-    const int j0 = tn * bn + (int(threadIdx.x) % per_row) * 4;
-    if (i >= m || j0 >= n) return;
-    const int8_t *wp = W + (long)i * n_pad + j0;
-    crt_row<T>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane)) : 0u; },
-               N, d, mu, nu, C, ldc, n, i, j0, accum != 0);
 }
 
 // ============================================================= exponents and N
@@ -1894,6 +1564,214 @@ __global__ void __launch_bounds__(256) k_fast_cmax(const __grid_constant__ JobGr
             if (t < j.m) j.cmax[0][t] = ceil_sqrt_u64((unsigned long long)j.ss[0][t] * mB);
             else j.cmax[1][t - j.m] = ceil_sqrt_u64(mA * (unsigned long long)j.ss[1][t - j.m]);
         }
+    });
+}
+
+// ============================================================= CRT
+// Algorithm 3 after the products, then Algorithm 1's inverse scaling:
+//   C'(1) = sum_l s_l1 W_l, C'(2) = sum_l s_l2 W_l, each the exact sum rounded
+//           once to FP64 (b = 64: C'(1) is exact, Lemma 2; b = 32: s_l2 = 0),
+//   Q = rint(P_inv C'(1)),  C'' = fma(-Q, P2, fma(-Q, P1, C'(1)) + C'(2)),
+//   C = RN(2^-(mu_i + nu_j) C'')  (b = 32: rounded once to FP32).
+
+// ------------------------------------------------------------------ the epilogue's helpers
+
+// RN(x 2^e) for an integer-valued x with |x| < 2^400 (an exponent add, on the
+// integer units, whenever the result stays normal)
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+    const long long b = __double_as_longlong(x);
+    const bool zero = ((unsigned long long)b << 1) == 0;          // +-0, tested on the integer units
+    const int ex = int((b >> 52) & 0x7FF);
+    if (zero || (ex + e >= 1 && ex + e <= 2046))
+        return zero ? x : __longlong_as_double((long long)((unsigned long long)b + ((unsigned long long)(long long)e << 52)));   // exact
+    if (e > 1023) return x * 0x1p1023 * 0x1p1023;                 // overflows to +-inf as ldexp does
+    if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+    const double y = x * 0x1p-1022;                               // exact: |x| >= 1
+    const int e2 = e + 1022;
+    if (e2 < -1022) return copysign(0.0, x);
+    return y * __longlong_as_double((long long)(e2 + 1023) << 52);
+}
+
+// RN((hi 2^S + lo) 2^e) as a double, from integer operations only (S = 31 or
+// 32).  Requires |hi|, |lo| < 2^61 and a result in the normal range (the tables
+// check both for every N).  An exact zero gives +0.
+template <int S>
+__device__ __forceinline__ double rn_sum(long long hi, long long lo, int e) {
+    // written without branches (selects only); every shift amount stays in [0, 63]
+    const long long t = hi + (lo >> S);            // value = t 2^S + r, 0 <= r < 2^S
+    const unsigned long long r = (unsigned long long)lo & ((1ull << S) - 1);
+    const bool neg = t < 0;
+    // |value| = T 2^S + R
+    const unsigned long long T = neg ? ~(unsigned long long)t + (r == 0 ? 1ull : 0ull) : (unsigned long long)t;
+    const unsigned long long R = neg ? ((1ull << S) - r) & ((1ull << S) - 1) : r;
+    // X 2^s with the bits below 2^s folded into a sticky bit 0 of X (T < 2^63, so s < S)
+    const int bt = 64 - __clzll((long long)T);
+    const int s = max(bt - (64 - S), 0);
+    const unsigned long long X = (T << (S - s)) | (R >> s) | ((R & ((1ull << s) - 1)) != 0 ? 1ull : 0ull);
+    const int bl = 64 - __clzll((long long)X);
+    const int sh = max(bl - 53, 0);
+    unsigned long long mant = bl <= 53 ? X << min(53 - bl, 63) : X >> sh;
+    const unsigned long long rem = X & ((1ull << sh) - 1), half = (1ull << sh) >> 1;
+    mant += (sh > 0 && (rem > half || (rem == half && (mant & 1ull)))) ? 1ull : 0ull;
+    const int carry = int(mant >> 53);
+    mant >>= carry;
+    const int ex = bl - 1 + s + e + carry;
+    const unsigned long long bits = (neg ? (1ull << 63) : 0ull) | ((unsigned long long)(ex + 1023) << 52) |
+                                    (mant & ((1ull << 52) - 1));
+    return X == 0 ? 0.0 : __longlong_as_double((long long)bits);
+}
+
+// H 2^e as a double for |H| < 2^53 (exact, on the integer units; the result is normal).
+__device__ __forceinline__ double exact_i53(long long H, int e) {
+    const unsigned long long a = H < 0 ? 0ull - (unsigned long long)H : (unsigned long long)H;
+    const int bl = 64 - __clzll((long long)a);                     // <= 53 (0 for H = 0)
+    const unsigned long long bits = ((unsigned long long)(bl + 1021 + e) << 52) + (a << (53 - bl));
+    return H == 0 ? 0.0 : __longlong_as_double((long long)(bits | (H < 0 ? (1ull << 63) : 0ull)));
+}
+
+// rint(x) (round half to even, as FP64 rint) on the integer units: the
+// fraction bits are rounded off in place, a carry into the exponent field
+// giving the next power of two.
+__device__ __forceinline__ double rint_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = int((b >> 52) & 0x7FF);
+    const unsigned long long sign = b & (1ull << 63);
+    const int f = min(max(1075 - e, 1), 52);                     // fraction bits where 1 <= |x| < 2^52
+    const unsigned long long t = (b + ((1ull << (f - 1)) - 1) + ((b >> f) & 1ull)) & ~((1ull << f) - 1);
+    // |x| < 1: 0, or 1 above 1/2 (1/2 itself goes to the even 0)
+    const unsigned long long small = sign | ((b & ~(1ull << 63)) > 0x3FE0000000000000ull ? 0x3FF0000000000000ull : 0ull);
+    return __longlong_as_double((long long)(e >= 1075 ? b : (e < 1023 ? small : t)));   // |x| >= 2^52: x
+}
+
+// c + a.lo16 b.byte0 + a.hi16 b.byte1 (dp2a.lo) or with b's bytes 2, 3
+// (dp2a.hi): unsigned 16-bit pieces of a, signed bytes of b.
+__device__ __forceinline__ int dp2a_lo(uint32_t a, uint32_t b, int c) {
+    int d;
+    asm("dp2a.lo.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ int dp2a_hi(uint32_t a, uint32_t b, int c) {
+    int d;
+    asm("dp2a.hi.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// One row i, columns j0 .. j0+3 of one thread; load(l) gives the four W_l
+// bytes of those columns (zero for l >= N).  C'(1) and C'(2) are sums of
+// integer multiples of fixed grids, taken exactly: each constant is cut into
+// four 16-bit pieces, and one dp2a adds piece * W for two planes of one column
+// into a 32-bit sum (|sum| < 2^16 128 49 < 2^31).  The piece sums are then put
+// together in 64-bit integers and rounded once.
+template <typename T, typename Load>
+__device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, const int32_t *mu,
+                                        const int32_t *nu, T *C, long ldc, int n, int i, int j0, bool accum) {
+    constexpr int B = sizeof(T) == 8 ? 64 : 32;
+    int s1[4][4], s2[4][4];                    // [column][piece]: C'(1) (b = 64 only), C'(2) / b = 32 C'(1)
+#pragma unroll
+    for (int e = 0; e < 4; e++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) s1[e][q] = s2[e][q] = 0;
+    const int pairs = (N + 1) / 2;
+    // software pipeline: the next pair's loads are in flight while a pair is summed
+    uint32_t w0 = load(0), w1 = load(1);
+    for (int pi = 0; pi < pairs; pi++) {
+        const uint32_t p0 = w0, p1 = w1;
+        w0 = load(2 * pi + 2);
+        w1 = load(2 * pi + 3);
+        // bytes of columns (0, 1) and (2, 3), planes 2 pi and 2 pi + 1 side by side
+        const uint32_t x01 = __byte_perm(p0, p1, 0x5140), x23 = __byte_perm(p0, p1, 0x7362);
+        const uint4 c2 = B == 64 ? c_dp64[d.poff + pi][1] : c_dp32[d.poff + pi];
+        const uint32_t cc2[4] = {c2.x, c2.y, c2.z, c2.w};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            s2[0][q] = dp2a_lo(cc2[q], x01, s2[0][q]);
+            s2[1][q] = dp2a_hi(cc2[q], x01, s2[1][q]);
+            s2[2][q] = dp2a_lo(cc2[q], x23, s2[2][q]);
+            s2[3][q] = dp2a_hi(cc2[q], x23, s2[3][q]);
+        }
+        if (B == 64) {
+            const uint4 c1 = c_dp64[d.poff + pi][0];
+            const uint32_t cc1[4] = {c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                s1[0][q] = dp2a_lo(cc1[q], x01, s1[0][q]);
+                s1[1][q] = dp2a_hi(cc1[q], x01, s1[1][q]);
+                s1[2][q] = dp2a_lo(cc1[q], x23, s1[2][q]);
+                s1[3][q] = dp2a_hi(cc1[q], x23, s1[3][q]);
+            }
+        }
+    }
+    const int mi = mu[i];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const int j = j0 + e;
+        if (j >= n) break;
+        // the second sum as hi 2^32 + lo: pieces 0, 1 and 2, 3 (shifted as unsigned:
+        // the sums may be negative)
+        const long long lo2 = (long long)((unsigned long long)(long long)s2[e][0] +
+                                          ((unsigned long long)(long long)s2[e][1] << 16));
+        const long long hi2 = (long long)((unsigned long long)(long long)s2[e][2] +
+                                          ((unsigned long long)(long long)s2[e][3] << 16));
+        double cpp;
+        if (B == 64) {
+            // C'(1) = H g exactly, |H| < 2^53 (Lemma 2): the four piece sums added
+            // modulo 2^64, which is exact because H fits
+            const unsigned long long Hu = (unsigned long long)(long long)s1[e][0] +
+                                          ((unsigned long long)(long long)s1[e][1] << 16) +
+                                          ((unsigned long long)(long long)s1[e][2] << 32) +
+                                          ((unsigned long long)(long long)s1[e][3] << 48);
+            const double c1 = exact_i53((long long)Hu, d.eg);
+            const double q = rint_bits(d.Pinv * c1);
+            cpp = fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum<32>(hi2, lo2, d.esum));
+        } else {
+            const double c1 = rn_sum<32>(hi2, lo2, d.esum);
+            const double q = rint_bits(d.Pinv * c1);
+            // P2 = 0 and C'(2) = +0, so fma(-q, 0, x + 0) = x + 0 as in the b = 64 form
+            cpp = fma(-q, d.P1, c1) + 0.0;
+        }
+        const double v = scale_pow2(cpp, -(mi + nu[j]));
+        const T c = B == 64 ? T(v) : T(__double2float_rn(v));
+        T *dst = C + (long)i * ldc + j;
+        *dst = accum ? *dst + c : c;            // one rounding per added K range
+    }
+}
+
+// One problem: block (x, y) takes columns 1024 x .. 1024 x + 1023 of rows y,
+// y + gridDim.y, ...
+constexpr int kCrtCols = 1024;
+template <typename T>
+__global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, long n_pad, const int *n_dev,
+                                                 const int32_t *mu, const int32_t *nu, T *C, long ldc, int m, int n,
+                                                 int accum) {
+    const int N = *n_dev;
+    const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
+    const long col0 = (long)blockIdx.x * kCrtCols;
+    const int j0 = int(col0) + threadIdx.x * 4;
+    for (int i = blockIdx.y; i < m; i += gridDim.y) {
+        if (j0 >= n) continue;
+        const int8_t *wp = W + (long)i * n_pad + j0;
+        crt_row<T>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane)) : 0u; },
+                   N, d, mu, nu, C, ldc, n, i, j0, accum != 0);
+    }
+}
+
+// A group of problems.  Item: 256 / tpr rows of tpr x 4 columns (4 per thread,
+// tpr threads per row).
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256, 4) k_crt(const __grid_constant__ JobGroup<T, CAP> G) {
+    for_items(G, [&](const JobDesc<T> &jd, long long li) {
+        const int tpr = crt_tpr(jd.n), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
+        const unsigned ncb = unsigned(cdiv(jd.n, tpr * 4)), ui = unsigned(li);
+        const int rb = int(ui / ncb);
+        const int i = rb * (256 / tpr) + ly;
+        const int j0 = int(ui - unsigned(rb) * ncb) * tpr * 4 + tx * 4;
+        if (ly >= 256 / tpr || j0 >= jd.n || i >= jd.m) return;
+        const int N = *jd.ndev;
+        const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
+        const int8_t *wp = jd.W + (long)i * jd.n_pad + j0;
+        const long wpl = jd.w_plane;
+        crt_row<T>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)) : 0u; },
+                   N, d, jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0, jd.accum != 0);
     });
 }
 

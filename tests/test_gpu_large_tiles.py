@@ -1,14 +1,13 @@
-"""The CRT in the residue GEMM's epilogue (k >= 2048: each CTA takes one tile
-through all N planes, stores W_l, and runs that tile's Algorithm 3 sums, Q, C''
-and inverse scaling between the next tile's planes).
+"""Parity on problems with more than two waves of output tiles and k >= 2048,
+the regime of the longest residue GEMMs:
 
-* a single call with more than two waves of tiles (tiles >= 2 x SMs), where the
-  last partial wave runs plane by plane with its CRT in k_crt_tiles: sampled
-  entries recomputed by the oracle with the GPU's exponents, bit for bit, and
-  the W_l of sampled rows and columns equal the oracle's;
-* fused problems inside a batch equal the same problems as single calls (which
-  run the separate CRT kernel), bit for bit;
-* an SGEMM single call through the fused path, sampled entries bit for bit.
+* a single call with 333 tiles of 128 x 256 (two full waves of 148 and a
+  partial one): sampled entries recomputed by the oracle with the GPU's
+  exponents, bit for bit, and the W_l of sampled rows and columns equal the
+  oracle's, for a fixed N and the bound rule;
+* problems with k >= 2048 inside a batch equal the same problems as single
+  calls, bit for bit;
+* an SGEMM single call of 320 tiles, sampled entries bit for bit.
 """
 import numpy as np
 import pytest
@@ -28,10 +27,10 @@ def _cuda():
 
 
 @pytest.mark.parametrize("N", [14, 0])
-def test_fused_single_call_with_tail(oracle, N):
+def test_single_call_many_waves(oracle, N):
     import torch
     from paper_2602_02549_b300 import binding as B
-    # 37 x 9 = 333 tiles of 128 x 256 (148 SMs: two fused waves and a tail of 37)
+    # 37 x 9 = 333 tiles of 128 x 256 (148 SMs: two full waves and a partial one of 37)
     m, n, k = 128 * 37 - 5, 256 * 8 + 100, 2100
     A, Bm = paper_pair(m, n, k, 1.0, seed=5)
     At, Bt = torch.tensor(A, device="cuda"), torch.tensor(Bm, device="cuda")
@@ -45,7 +44,7 @@ def test_fused_single_call_with_tail(oracle, N):
     assert B.sync() == 0
     Nu = int(nout.item())
     rng = np.random.default_rng(7)
-    # rows and columns from the fused waves and the tail (the last tiles of the raster)
+    # rows and columns from the first tiles of the raster and from the last ones
     ii = np.unique(np.concatenate([[0, m - 1, m - 130], rng.integers(0, m, 20)]))
     jj = np.unique(np.concatenate([[0, n - 1, n - 257], rng.integers(0, n, 20)]))
     A_rows, B_cols = np.ascontiguousarray(A[ii]), np.ascontiguousarray(Bm[:, jj])
@@ -60,7 +59,7 @@ def test_fused_single_call_with_tail(oracle, N):
     assert np.array_equal(Wg, Wref)
 
 
-def test_fused_batch_equals_single_calls():
+def test_long_k_batch_equals_single_calls():
     import torch
     from paper_2602_02549_b300 import binding as B
     shapes = [(300, 500, 2500, 1.0), (1000, 700, 3000, 2.0), (200, 300, 400, 0.5), (130, 260, 4097, 4.0)]
@@ -78,7 +77,7 @@ def test_fused_batch_equals_single_calls():
         assert torch.equal(q["C"], ref)
 
 
-def test_fused_sgemm_single_call(oracle):
+def test_sgemm_many_waves(oracle):
     import torch
     from paper_2602_02549_b300 import binding as B
     m, n, k = 128 * 40, 256 * 8, 2048
