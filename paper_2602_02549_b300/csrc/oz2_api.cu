@@ -159,7 +159,7 @@ Layout make_layout(const Dims &d) {
     L.hmaxB = take(sizeof(unsigned long long) * size_t(d.k_pad));
     L.cmax_row = take(sizeof(int) * size_t(d.m_pad));
     L.cmax_col = take(sizeof(int) * size_t(d.n_pad));
-    L.red = take(sizeof(unsigned long long) * 8);
+    L.red = take(sizeof(unsigned long long) * 16);
     L.ssA = take(sizeof(int) * size_t(d.m_pad));
     L.ssB = take(sizeof(int) * size_t(d.n_pad));
     L.rmaxA = take(sizeof(unsigned long long) * size_t(d.m_pad));
@@ -582,6 +582,13 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
     OZ2_LAUNCH(k_bound, bound, one_each)
     if ((rc = gemms(EPI_CW))) return rc;
+    {
+        bool any_cw = false;
+        for (int p = 0; p < count; p++) any_cw = any_cw || (jobs[p]->cw() && jobs[p]->nmoduli == 0);
+        if (any_cw && (rc = launch_k(true, k_choose<T, CAP>, dim3(count), dim3(32), 0, st,
+                                     static_cast<const JobGroup<T, CAP> &>(J))))
+            return rc;
+    }
     if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
     OZ2_LAUNCH(k_resid_kc, resid_kc, resident)
     OZ2_LAUNCH(k_resid_rc, resid_rc, resident)

@@ -216,7 +216,7 @@ struct JobDesc {
     unsigned long long *hmax[2];   // per-k maxima of |A|, |B|
     unsigned long long *rmax[2];   // per logical row maxima (bits)
     unsigned long long *l1[2];     // fixed-point 1-norms (PlaneArgs::l1)
-    unsigned long long *red;       // bound reductions
+    unsigned long long *red;       // bound reductions (red[8]: items of k_bound done)
     float *cwv[2];                 // componentwise rule: (R_i 2^mu'_i, 2^alpha'_i 2^mu'_i) per row of A,
                                    // (2^beta'_j 2^nu'_j, K_j 2^nu'_j) per column of B, rounded up
     int *cmax[2];                  // Cbar row / column maxima
@@ -712,43 +712,34 @@ __global__ void __launch_bounds__(256) k_quant_rc(const __grid_constant__ JobGro
 }
 
 // The N rule: smallest N in [2, nmax] with
-//   t_N (maxR max2b + max2a maxK) + (k + gN_N) t_N^2 max2a max2b <= tau * L,
-// else nmax.
-__device__ __forceinline__ int choose_n(const unsigned long long *red, int k, double tau, int nmax, int fp32,
-                                        int cw) {
-    if (cw) {
-        // componentwise: t_N max(X / L) + (k + gN_N) t_N^2 max(Y / L) <= tau
-        const double xm = __longlong_as_double((long long)red[5]);
-        const double ym = __longlong_as_double((long long)red[7]);
-        for (int c = 2; c <= nmax; c++) {
-            const DevN &d = fp32 ? c_n32[c] : c_n64[c];
-            if (d.t * xm + (double(k) + d.gN) * d.t * d.t * ym <= tau) return c;
-        }
-        return nmax;
-    }
-    const double maxR = __longlong_as_double((long long)red[0]);
-    const double maxK = __longlong_as_double((long long)red[1]);
-    const double m2a = __longlong_as_double((long long)red[2]);
-    const double m2b = __longlong_as_double((long long)red[3]);
-    const double L = __longlong_as_double((long long)red[4]);
-    for (int c = 2; c <= nmax; c++) {
+//   t_N (maxR max2b + max2a maxK) + (k + gN_N) t_N^2 max2a max2b <= tau * L
+// (componentwise, cw: t_N max(X / L) + (k + gN_N) t_N^2 max(Y / L) <= tau),
+// else nmax.  red[] holds the maxima as bits of nonnegative doubles.
+// Evaluated by the 32 lanes of a warp at once: lane t tests
+// N = 2 + t and N = 34 + t (<= nmax), and the smallest N that qualifies wins
+// (nmax if none does).  All 32 lanes must be
+// active.
+__device__ __forceinline__ int choose_n_warp(const unsigned long long *red, int k, double tau, int nmax, int fp32,
+                                             int cw) {
+    const int lane = threadIdx.x & 31;
+    auto ok = [&](int c) {
+        if (c > nmax) return false;
         const DevN &d = fp32 ? c_n32[c] : c_n64[c];
-        const double T = d.t * (maxR * m2b + m2a * maxK) + (double(k) + d.gN) * d.t * d.t * m2a * m2b;
-        if (T <= tau * L) return c;
-    }
-    return nmax;
-}
-
-// N of job j for the residue kernels: fixed, or the rule above from the
-// reductions of k_bound (and of the componentwise rule's second product).
-// Lane 0 of each warp evaluates it and the warp shares it, so all 32 lanes
-// must be active.
-template <typename T>
-__device__ __forceinline__ int job_n_warp(const JobDesc<T> &j) {
-    constexpr int fp32 = sizeof(T) == 4 ? 1 : 0;
-    int N = j.nmoduli;
-    if (N == 0 && (threadIdx.x & 31) == 0) N = choose_n(j.red, j.k, j.target, j.nmax, fp32, j.cw);
-    return __shfl_sync(0xffffffffu, N, 0);
+        if (cw) {
+            const double xm = __longlong_as_double((long long)red[5]);
+            const double ym = __longlong_as_double((long long)red[7]);
+            return d.t * xm + (double(k) + d.gN) * d.t * d.t * ym <= tau;
+        }
+        const double maxR = __longlong_as_double((long long)red[0]);
+        const double maxK = __longlong_as_double((long long)red[1]);
+        const double m2a = __longlong_as_double((long long)red[2]);
+        const double m2b = __longlong_as_double((long long)red[3]);
+        const double L = __longlong_as_double((long long)red[4]);
+        return d.t * (maxR * m2b + m2a * maxK) + (double(k) + d.gN) * d.t * d.t * m2a * m2b <= tau * L;
+    };
+    const unsigned lo = __ballot_sync(0xffffffffu, ok(2 + lane));
+    const unsigned hi = __ballot_sync(0xffffffffu, ok(34 + lane));
+    return lo ? 2 + __ffs(lo) - 1 : (hi ? 34 + __ffs(hi) - 1 : nmax);
 }
 
 // Algorithm 2's mu_i (X = 0, row i of A) or nu_j (X = 1, column j of B) for N
@@ -937,15 +928,10 @@ __global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ Job
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     load_pow2(pow2, kNMax);
     __syncthreads();
-    const JobDesc<T> *cur = nullptr;           // the job whose N is in curN
-    int curN = 0;
     for_items(G, [&](const JobDesc<T> &j, long long li) {
-        if (&j != cur) {                       // block-uniform: every lane is here
-            cur = &j;
-            curN = job_n_warp(j);
-        }
-        const int N = curN;
-        if (li == 0 && threadIdx.x == 0) {     // the N used, for the GEMM, the CRT and the caller
+        // fixed N, or the bound rule's (k_bound's last block or k_choose)
+        const int N = j.nmoduli > 0 ? j.nmoduli : *j.ndev;
+        if (j.nmoduli > 0 && li == 0 && threadIdx.x == 0) {   // a fixed N, for the GEMM, the CRT and the caller
             *j.ndev = N;
             if (j.n_out) *j.n_out = N;
         }
@@ -992,15 +978,10 @@ __global__ void __launch_bounds__(256, 3) k_resid_rc(const __grid_constant__ Job
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     __shared__ T tile[64][65];               // [r][swizzled h]
     load_pow2(pow2, kNMax);
-    const JobDesc<T> *cur = nullptr;           // the job whose N is in curN
-    int curN = 0;
     for_items(G, [&](const JobDesc<T> &j, long long li) {
-        if (&j != cur) {                       // block-uniform: every lane is here
-            cur = &j;
-            curN = job_n_warp(j);
-        }
-        const int N = curN;
-        if (li == 0 && threadIdx.x == 0) {
+        // fixed N, or the bound rule's (k_bound's last block or k_choose)
+        const int N = j.nmoduli > 0 ? j.nmoduli : *j.ndev;
+        if (j.nmoduli > 0 && li == 0 && threadIdx.x == 0) {
             *j.ndev = N;
             if (j.n_out) *j.n_out = N;
         }
@@ -1552,7 +1533,43 @@ __global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<
         block_max_to(m2a, j.red + 2);
         block_max_to(m2b, j.red + 3);
         block_max_to(mL, j.red + 4);
+        // the job's last item (counted in red[8]) has every maximum: it picks N
+        // (the componentwise rule waits for its second product: k_choose)
+        __shared__ int last;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last = atomicAdd(j.red + 8, 1ull) == (unsigned long long)(Items<T>::bound(j) - 1) ? 1 : 0;
+            __threadfence();
+        }
+        __syncthreads();
+        if (last && !j.cw && threadIdx.x < 32) {
+            const unsigned long long *red = j.red;
+            unsigned long long r[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) r[i] = __ldcg(red + i);
+            const int N = choose_n_warp(r, j.k, j.target, j.nmax, sizeof(T) == 4 ? 1 : 0, 0);
+            if (threadIdx.x == 0) {
+                *j.ndev = N;
+                if (j.n_out) *j.n_out = N;
+            }
+        }
     });
+}
+
+// The componentwise rule's N, once its second product has the ratio maxima:
+// one warp per job (block p takes job p).
+template <typename T, int CAP>
+__global__ void __launch_bounds__(32) k_choose(const __grid_constant__ JobGroup<T, CAP> G) {
+    ptx::grid_dep_wait();
+    ptx::grid_dep_launch();
+    const JobDesc<T> &j = G.j[blockIdx.x];
+    if (!j.cw || j.nmoduli > 0 || j.inject) return;
+    const int N = choose_n_warp(j.red, j.k, j.target, j.nmax, sizeof(T) == 4 ? 1 : 0, 1);
+    if (threadIdx.x == 0) {
+        *j.ndev = N;
+        if (j.n_out) *j.n_out = N;
+    }
 }
 
 // Fast mode (a reading; the paper only names the mode): Cbar is replaced by
