@@ -12,7 +12,6 @@
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
-#include <utility>
 #include <vector>
 
 #include "oz2.h"
@@ -159,7 +158,7 @@ Layout make_layout(const Dims &d) {
     L.hmaxB = take(sizeof(unsigned long long) * size_t(d.k_pad));
     L.cmax_row = take(sizeof(int) * size_t(d.m_pad));
     L.cmax_col = take(sizeof(int) * size_t(d.n_pad));
-    L.red = take(sizeof(unsigned long long) * 16);
+    L.red = take(sizeof(unsigned long long) * 8);
     L.ssA = take(sizeof(int) * size_t(d.m_pad));
     L.ssB = take(sizeof(int) * size_t(d.n_pad));
     L.rmaxA = take(sizeof(unsigned long long) * size_t(d.m_pad));
@@ -209,26 +208,6 @@ struct GemmHook {
 };
 thread_local GemmHook g_hook;
 
-// Launches kernel<<<grid, block, smem, st>>>(args...), with programmatic stream
-// serialization when `pdl` (the kernel may then start launching while the
-// previous kernel of the stream finishes; every kernel of the pipeline waits
-// for its predecessor with grid_dep_wait before touching memory).
-template <typename... KArgs, typename... Args>
-int launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-             Args &&...args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = pdl ? attr : nullptr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cuda_fail(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
-}
-
 // One persistent launch over the problems of `G` (item counts filled in here):
 // one CTA per SM, or fewer when there are fewer work items.
 template <int EPI, int BN, int CAP>
@@ -244,8 +223,8 @@ int launch_gemm(GemmGroup<CAP> &G, int sms, cudaStream_t st) {
     G.hook_kb = EPI == EPI_MOD ? g_hook.kb : -1;
     if (items == 0) return OZ2_OK;
     const int grid = int(std::min<long long>(items, sms));
-    return launch_k(true, k_gemm<EPI, BN, CAP>, dim3(grid), dim3(gemm::kThreads), gemm::Cfg<BN>::kSmemBytes, st,
-                    static_cast<const GemmGroup<CAP> &>(G));
+    k_gemm<EPI, BN, CAP><<<grid, gemm::kThreads, gemm::Cfg<BN>::kSmemBytes, st>>>(G);
+    return cuda_fail(cudaGetLastError());
 }
 
 // ------------------------------------------------------------------ validation
@@ -517,16 +496,12 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     // kResidBlocksPerSM blocks per SM (their launch bound)
     const long long one_each = (1ll << 31) - 1, resident = (long long)sms * kResidBlocksPerSM;
     int rc, g;
-    // the call's first kernel waits for everything before it on the stream;
-    // the others may start launching while their predecessor finishes
-    bool first_launch = true;
-#define OZ2_LAUNCH(kernel, items, cap)                                                        \
-    if ((g = plan(Items<T>::items, cap)) < 0) return OZ2_ENOTSUP;                             \
-    if (g > 0) {                                                                              \
-        rc = launch_k(!first_launch, kernel<T, CAP>, dim3(g), dim3(256), 0, st,               \
-                      static_cast<const JobGroup<T, CAP> &>(J));                              \
-        first_launch = false;                                                                 \
-        if (rc) return rc;                                                                    \
+    auto launched = [&]() { return cuda_fail(cudaGetLastError()); };
+#define OZ2_LAUNCH(kernel, items, cap)                              \
+    if ((g = plan(Items<T>::items, cap)) < 0) return OZ2_ENOTSUP;   \
+    if (g > 0) {                                                    \
+        kernel<T, CAP><<<g, 256, 0, st>>>(J);                       \
+        if ((rc = launched())) return rc;                           \
     }
     // heaviest problems first: the longest-processing-time order balances the
     // static assignment of GEMM work items to CTAs
@@ -582,13 +557,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
     OZ2_LAUNCH(k_bound, bound, one_each)
     if ((rc = gemms(EPI_CW))) return rc;
-    {
-        bool any_cw = false;
-        for (int p = 0; p < count; p++) any_cw = any_cw || (jobs[p]->cw() && jobs[p]->nmoduli == 0);
-        if (any_cw && (rc = launch_k(true, k_choose<T, CAP>, dim3(count), dim3(32), 0, st,
-                                     static_cast<const JobGroup<T, CAP> &>(J))))
-            return rc;
-    }
+    OZ2_LAUNCH(k_exponents, exponents, one_each)
     if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
     OZ2_LAUNCH(k_resid_kc, resid_kc, resident)
     OZ2_LAUNCH(k_resid_rc, resid_rc, resident)
@@ -598,10 +567,9 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     if (count == 1) {
         const JobDesc<T> &j = J.j[0];
         dim3 grid(unsigned(cdiv(j.n, kCrtCols)), unsigned(std::min(j.m, 65535)));
-        if ((rc = launch_k(true, k_crt_one<T>, grid, dim3(256), 0, st, (const int8_t *)j.W, j.w_plane, long(j.n_pad),
-                           (const int *)j.ndev, (const int32_t *)j.shift[0], (const int32_t *)j.shift[1], j.C, j.ldc,
-                           j.m, j.n, j.accum)))
-            return rc;
+        k_crt_one<T><<<grid, 256, 0, st>>>(j.W, j.w_plane, long(j.n_pad), j.ndev, j.shift[0], j.shift[1], j.C,
+                                             j.ldc, j.m, j.n, j.accum);
+        if ((rc = launched())) return rc;
     } else {
         OZ2_LAUNCH(k_crt, crt, one_each)
     }

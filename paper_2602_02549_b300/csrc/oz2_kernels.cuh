@@ -10,9 +10,8 @@
 //                             also |A| v and v^T |B| for the N rule
 //   k_gemm<EPI_MAX>           Cbar = Abar Bbar on tcgen05, keeping only the row
 //                             and column maxima of Cbar
-//   k_bound                   the maxima of the N rule
-//   k_resid_kc / k_resid_rc   N, mu, nu (Algorithm 2: Dbar, e, f), then
-//                             A'_l = mod(trunc(2^mu A), p_l) as BF16, N planes
+//   k_bound, k_exponents      the N rule; Dbar, e, f, mu, nu (Algorithm 2)
+//   k_resid_kc / k_resid_rc   A'_l = mod(trunc(2^mu A), p_l) as BF16, N planes
 //   k_gemm<EPI_MOD>           C'_l = A'_l B'_l on tcgen05, W_l = mod(C'_l, p_l)
 //   k_crt                     C'(1), C'(2), Q, C'' (Algorithm 3) and the
 //                             inverse scaling of Algorithm 1
@@ -216,13 +215,13 @@ struct JobDesc {
     unsigned long long *hmax[2];   // per-k maxima of |A|, |B|
     unsigned long long *rmax[2];   // per logical row maxima (bits)
     unsigned long long *l1[2];     // fixed-point 1-norms (PlaneArgs::l1)
-    unsigned long long *red;       // bound reductions (red[8]: items of k_bound done)
+    unsigned long long *red;       // bound reductions
     float *cwv[2];                 // componentwise rule: (R_i 2^mu'_i, 2^alpha'_i 2^mu'_i) per row of A,
                                    // (2^beta'_j 2^nu'_j, K_j 2^nu'_j) per column of B, rounded up
     int *cmax[2];                  // Cbar row / column maxima
     int *ss[2];                    // fast mode: sums of squares of Abar rows / Bbar columns
     int *ndev, *n_out;
-    int32_t *expo[2];              // mu, nu computed by the residue kernels
+    int32_t *expo[2];              // mu, nu computed by k_exponents
     const int32_t *shift[2];       // mu, nu as used (computed or injected)
     int32_t *expo_out[2];          // optional exports
     __nv_bfloat16 *res[2];
@@ -322,6 +321,7 @@ template <typename T> struct Items {
         const int mx = j.m > j.n ? (j.m > j.k ? j.m : j.k) : (j.n > j.k ? j.n : j.k);
         return !j.inject && j.nmoduli == 0 ? cdiv(mx, 256) : 0;
     }
+    __host__ __device__ static long long exponents(const JobDesc<T> &j) { return cdiv(j.m + j.n, 256); }
     __host__ __device__ static long long resid_kc(const JobDesc<T> &j) { return items_kc_x(j, 0) + items_kc_x(j, 1); }
     __host__ __device__ static long long resid_rc(const JobDesc<T> &j) { return items_rc_x(j, 0) + items_rc_x(j, 1); }
     __host__ __device__ static long long crt(const JobDesc<T> &j) {
@@ -343,8 +343,6 @@ __device__ __forceinline__ void for_items(const JobGroup<T, CAP> &G, F &&f) {
 
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_clear(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         const long long v = li * 256 + threadIdx.x;
         if (v < j.zero_vec) j.zero[v] = make_uint4(0, 0, 0, 0);
@@ -377,8 +375,6 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 // the lines ly, ly + lines-per-pass, ...; each warp lies in one line group.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         int X = 0;
         const long long n0 = items_absmax_x(j, 0);
@@ -448,6 +444,7 @@ struct PlaneArgs {
     int R_pad, k, k_pad;
     const unsigned long long *row_max;   // quantisation: shift = 5 - floor(log2 max)
     const int32_t *shift;                 // residues: mu or nu
+    const int *n_dev;                     // residues: number of planes
     int *sumsq;                           // quantisation, fast mode: sum_h xbar^2 per row (atomicAdd)
     int write;                            // quantisation: store the BF16 plane (accurate mode)
     unsigned long long *l1;               // quantisation: sum_h |x| 2^(mu'+57) per row, two 32-bit
@@ -588,7 +585,7 @@ __device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8],
 
 template <typename T>
 __device__ __forceinline__ PlaneArgs quant_args(const JobDesc<T> &j, int X) {
-    return PlaneArgs{j.res[X], j.plane[X], j.R_pad[X], j.k, j.k_pad, j.rmax[X], nullptr,
+    return PlaneArgs{j.res[X], j.plane[X], j.R_pad[X], j.k, j.k_pad, j.rmax[X], nullptr, nullptr,
                      j.fast ? j.ss[X] : nullptr, !j.fast, j.l1[X], j.cw};
 }
 
@@ -630,8 +627,6 @@ __device__ __forceinline__ void load8(const float *src, int valid, float (&x)[8]
 // the item (the row sums are reduced across the warp).
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         int X = 0;
         const long long n0 = items_quant_kc_x(j, 0);
@@ -669,8 +664,6 @@ __global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGro
 // shared memory.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_quant_rc(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     __shared__ T tile[64][65];
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         int X = 0;
@@ -709,65 +702,6 @@ __global__ void __launch_bounds__(256) k_quant_rc(const __grid_constant__ JobGro
         }
         flush_row(a, acc, r, 4, live);   // the 4 threads of row rr are adjacent lanes
     });
-}
-
-// The N rule: smallest N in [2, nmax] with
-//   t_N (maxR max2b + max2a maxK) + (k + gN_N) t_N^2 max2a max2b <= tau * L
-// (componentwise, cw: t_N max(X / L) + (k + gN_N) t_N^2 max(Y / L) <= tau),
-// else nmax.  red[] holds the maxima as bits of nonnegative doubles.
-// Evaluated by the 32 lanes of a warp at once: lane t tests
-// N = 2 + t and N = 34 + t (<= nmax), and the smallest N that qualifies wins
-// (nmax if none does).  All 32 lanes must be
-// active.
-__device__ __forceinline__ int choose_n_warp(const unsigned long long *red, int k, double tau, int nmax, int fp32,
-                                             int cw) {
-    const int lane = threadIdx.x & 31;
-    auto ok = [&](int c) {
-        if (c > nmax) return false;
-        const DevN &d = fp32 ? c_n32[c] : c_n64[c];
-        if (cw) {
-            const double xm = __longlong_as_double((long long)red[5]);
-            const double ym = __longlong_as_double((long long)red[7]);
-            return d.t * xm + (double(k) + d.gN) * d.t * d.t * ym <= tau;
-        }
-        const double maxR = __longlong_as_double((long long)red[0]);
-        const double maxK = __longlong_as_double((long long)red[1]);
-        const double m2a = __longlong_as_double((long long)red[2]);
-        const double m2b = __longlong_as_double((long long)red[3]);
-        const double L = __longlong_as_double((long long)red[4]);
-        return d.t * (maxR * m2b + m2a * maxK) + (double(k) + d.gN) * d.t * d.t * m2a * m2b <= tau * L;
-    };
-    const unsigned lo = __ballot_sync(0xffffffffu, ok(2 + lane));
-    const unsigned hi = __ballot_sync(0xffffffffu, ok(34 + lane));
-    return lo ? 2 + __ffs(lo) - 1 : (hi ? 34 + __ffs(hi) - 1 : nmax);
-}
-
-// Algorithm 2's mu_i (X = 0, row i of A) or nu_j (X = 1, column j of B) for N
-// moduli: d = single_up(max cbar) (1 for an empty row), e = log2f(d) with
-// CUDA's __log2f as in the paper, mu = mu' + floor(fl_down(fma(c, e, P'))).
-template <typename T>
-__device__ __forceinline__ int expo_of(const JobDesc<T> &j, int X, int r, int N) {
-    constexpr int fp32 = sizeof(T) == 4 ? 1 : 0;
-    const float Pp = fp32 ? c_n32[N].Pprime : c_n64[N].Pprime;
-    const unsigned long long bits = j.rmax[X][r];
-    const int mp = bits ? 5 - floor_log2_bits(bits) : 0;
-    const int cm = j.cmax[X][r];
-    const float d = cm > 0 ? __int2float_ru(cm) : 1.0f;
-    return mp + int(floorf(__fmaf_rd(c_cneg, __log2f(d), Pp)));
-}
-
-// The exponent of row r of operand X as the residues use it: injected, or
-// computed (and then stored for the CRT and the optional export by the thread
-// that takes the row's first positions, `first`).
-template <typename T>
-__device__ __forceinline__ int row_shift(const JobDesc<T> &j, int X, int r, int N, bool first) {
-    if (j.inject) return j.shift[X][r];
-    const int v = expo_of(j, X, r, N);
-    if (first) {
-        j.expo[X][r] = v;
-        if (j.expo_out[X]) j.expo_out[X][r] = v;
-    }
-    return v;
 }
 
 // ------------------------------------------------------------------ residues
@@ -915,7 +849,7 @@ __device__ __forceinline__ PlaneArgs resid_args(const JobDesc<T> &j, int X) {
     // the row maxima bound |A'|, |B'| (fixed-position limbs); they are not
     // computed when mu and nu are given
     return PlaneArgs{j.res[X], j.plane[X], j.R_pad[X], j.k, j.k_pad, j.inject ? nullptr : j.rmax[X],
-                     j.shift[X], nullptr, 1, nullptr, 0};
+                     j.shift[X], j.ndev, nullptr, 1, nullptr, 0};
 }
 
 // K-contiguous source.  Item: 256 consecutive groups of 8 h in row-major order
@@ -923,23 +857,16 @@ __device__ __forceinline__ PlaneArgs resid_args(const JobDesc<T> &j, int X) {
 // per thread, one 16-byte store per plane.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     load_pow2(pow2, kNMax);
     __syncthreads();
     for_items(G, [&](const JobDesc<T> &j, long long li) {
-        // fixed N, or the bound rule's (k_bound's last block or k_choose)
-        const int N = j.nmoduli > 0 ? j.nmoduli : *j.ndev;
-        if (j.nmoduli > 0 && li == 0 && threadIdx.x == 0) {   // a fixed N, for the GEMM, the CRT and the caller
-            *j.ndev = N;
-            if (j.n_out) *j.n_out = N;
-        }
         int X = 0;
         const long long n0 = items_kc_x(j, 0);
         if (li >= n0) { X = 1; li -= n0; }
         const PlaneArgs a = resid_args(j, X);
         const Operand<T> &op = j.op[X];
+        const int N = *a.n_dev;
         const long pw16 = a.plane / 8;
         const unsigned k8 = unsigned(a.k_pad / 8);
         const unsigned long long g = (unsigned long long)li * 256u + threadIdx.x;
@@ -951,7 +878,7 @@ __global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ Job
             for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
             return;
         }
-        const int shift = row_shift(j, X, r, N, h0 == 0);
+        const int shift = a.shift[r];
         // this row's own bound: where a warp spans several short rows, lanes on
         // both sides of a limb-count limit diverge (rare: the scaling gives
         // neighbouring rows nearly the same bit length; a warp-wide maximum
@@ -973,23 +900,16 @@ __device__ __forceinline__ int resid_swz(int hh) {
 
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256, 3) k_resid_rc(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     __shared__ __align__(16) uint8_t pow2[kNMax][256];
     __shared__ T tile[64][65];               // [r][swizzled h]
     load_pow2(pow2, kNMax);
     for_items(G, [&](const JobDesc<T> &j, long long li) {
-        // fixed N, or the bound rule's (k_bound's last block or k_choose)
-        const int N = j.nmoduli > 0 ? j.nmoduli : *j.ndev;
-        if (j.nmoduli > 0 && li == 0 && threadIdx.x == 0) {
-            *j.ndev = N;
-            if (j.n_out) *j.n_out = N;
-        }
         int X = 0;
         const long long n0 = items_rc_x(j, 0);
         if (li >= n0) { X = 1; li -= n0; }
         const PlaneArgs a = resid_args(j, X);
         const Operand<T> &op = j.op[X];
+        const int N = *a.n_dev;
         const long pw16 = a.plane / 8;
         const unsigned nrb = unsigned(a.R_pad / 64), ui = unsigned(li);
         const int hb = int(ui / nrb);
@@ -1013,7 +933,7 @@ __global__ void __launch_bounds__(256, 3) k_resid_rc(const __grid_constant__ Job
             const int rr = (threadIdx.x >> 3) + 32 * i;
             const int r = r_base + rr;
             const bool live = r < op.R;
-            const int shift = live ? row_shift(j, X, r, N, h_base == 0 && tc == 0) : 0;
+            const int shift = live ? a.shift[r] : 0;
             const int need = warp_max(live ? (a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20) : 0);
             uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
             if (!live) {
@@ -1304,9 +1224,6 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    // set-up done: wait for the previous kernel (its outputs are this one's inputs)
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     const uint32_t tmem = *tmem_slot;
     const long long total = G.total_items;
     uint32_t issued = 0;                         // producer: stages armed (lane 0 of warp 0)
@@ -1501,8 +1418,6 @@ __device__ __forceinline__ void cw_vectors(const JobDesc<T> &j, int X, int t) {
 // latency-bound reductions spread over many SMs.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         unsigned long long mR = 0, mK = 0, m2a = 0, m2b = 0, mL = 0;
         {
@@ -1533,43 +1448,76 @@ __global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<
         block_max_to(m2a, j.red + 2);
         block_max_to(m2b, j.red + 3);
         block_max_to(mL, j.red + 4);
-        // the job's last item (counted in red[8]) has every maximum: it picks N
-        // (the componentwise rule waits for its second product: k_choose)
-        __shared__ int last;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            last = atomicAdd(j.red + 8, 1ull) == (unsigned long long)(Items<T>::bound(j) - 1) ? 1 : 0;
-            __threadfence();
+    });
+}
+
+// The N rule: smallest N in [2, nmax] with
+//   t_N (maxR max2b + max2a maxK) + (k + gN_N) t_N^2 max2a max2b <= tau * L,
+// else nmax.
+__device__ __forceinline__ int choose_n(const unsigned long long *red, int k, double tau, int nmax, int fp32,
+                                        int cw) {
+    if (cw) {
+        // componentwise: t_N max(X / L) + (k + gN_N) t_N^2 max(Y / L) <= tau
+        const double xm = __longlong_as_double((long long)red[5]);
+        const double ym = __longlong_as_double((long long)red[7]);
+        for (int c = 2; c <= nmax; c++) {
+            const DevN &d = fp32 ? c_n32[c] : c_n64[c];
+            if (d.t * xm + (double(k) + d.gN) * d.t * d.t * ym <= tau) return c;
         }
-        __syncthreads();
-        if (last && !j.cw && threadIdx.x < 32) {
-            const unsigned long long *red = j.red;
-            unsigned long long r[8];
-#pragma unroll
-            for (int i = 0; i < 8; i++) r[i] = __ldcg(red + i);
-            const int N = choose_n_warp(r, j.k, j.target, j.nmax, sizeof(T) == 4 ? 1 : 0, 0);
-            if (threadIdx.x == 0) {
+        return nmax;
+    }
+    const double maxR = __longlong_as_double((long long)red[0]);
+    const double maxK = __longlong_as_double((long long)red[1]);
+    const double m2a = __longlong_as_double((long long)red[2]);
+    const double m2b = __longlong_as_double((long long)red[3]);
+    const double L = __longlong_as_double((long long)red[4]);
+    for (int c = 2; c <= nmax; c++) {
+        const DevN &d = fp32 ? c_n32[c] : c_n64[c];
+        const double T = d.t * (maxR * m2b + m2a * maxK) + (double(k) + d.gN) * d.t * d.t * m2a * m2b;
+        if (T <= tau * L) return c;
+    }
+    return nmax;
+}
+
+// N (fixed, or the rule), then Algorithm 2's mu/nu lines: d = single_up(max
+// cbar) (1 for an empty row), e = log2f(d) with CUDA's fast __log2f as in the
+// paper, mu = mu' + floor(fl_down(fma(c, e, P'))).  Item: 256 of the m + n
+// rows and columns (one per thread); every item of a problem derives the same
+// N, and item 0 publishes it.
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_exponents(const __grid_constant__ JobGroup<T, CAP> G) {
+    constexpr int fp32 = sizeof(T) == 4 ? 1 : 0;
+    __shared__ int sN;
+    for_items(G, [&](const JobDesc<T> &j, long long li) {
+        __syncthreads();                     // the previous item has read sN
+        if (threadIdx.x == 0) {
+            const int N = j.nmoduli > 0 ? j.nmoduli : choose_n(j.red, j.k, j.target, j.nmax, fp32, j.cw);
+            sN = N;
+            if (li == 0) {
                 *j.ndev = N;
                 if (j.n_out) *j.n_out = N;
             }
         }
+        __syncthreads();
+        if (j.inject) return;
+        const int N = sN;
+        const float Pp = fp32 ? c_n32[N].Pprime : c_n64[N].Pprime;
+        const float c = c_cneg;
+        {
+            const int t = int(li) * 256 + threadIdx.x;
+            if (t >= j.m + j.n) return;
+            const int X = t < j.m ? 0 : 1;
+            const int i = X ? t - j.m : t;
+            const unsigned long long bits = j.rmax[X][i];
+            const int mp = bits ? 5 - floor_log2_bits(bits) : 0;
+            const int cm = j.cmax[X][i];
+            const float d = cm > 0 ? __int2float_ru(cm) : 1.0f;
+            const float ex = __log2f(d);
+            const int v = mp + int(floorf(__fmaf_rd(c, ex, Pp)));
+            j.expo[X][i] = v;
+            if (j.expo_out[X]) j.expo_out[X][i] = v;
+        }
     });
-}
-
-// The componentwise rule's N, once its second product has the ratio maxima:
-// one warp per job (block p takes job p).
-template <typename T, int CAP>
-__global__ void __launch_bounds__(32) k_choose(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
-    const JobDesc<T> &j = G.j[blockIdx.x];
-    if (!j.cw || j.nmoduli > 0 || j.inject) return;
-    const int N = choose_n_warp(j.red, j.k, j.target, j.nmax, sizeof(T) == 4 ? 1 : 0, 1);
-    if (threadIdx.x == 0) {
-        *j.ndev = N;
-        if (j.n_out) *j.n_out = N;
-    }
 }
 
 // Fast mode (a reading; the paper only names the mode): Cbar is replaced by
@@ -1579,8 +1527,6 @@ __global__ void __launch_bounds__(32) k_choose(const __grid_constant__ JobGroup<
 // maxima <= 2^12 k, which the majorant satisfies.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_fast_max(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         int a = 0, b = 0;
         const int base = int(li) * 2048 + threadIdx.x;
@@ -1608,8 +1554,6 @@ __device__ __forceinline__ int ceil_sqrt_u64(unsigned long long x) {
 
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_fast_cmax(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         const int *mx = reinterpret_cast<const int *>(j.red + 6);
         const unsigned long long mA = (unsigned long long)mx[0], mB = (unsigned long long)mx[1];
@@ -1799,8 +1743,6 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, long n_pad, const int *n_dev,
                                                  const int32_t *mu, const int32_t *nu, T *C, long ldc, int m, int n,
                                                  int accum) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     const int N = *n_dev;
     const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
     const long col0 = (long)blockIdx.x * kCrtCols;
@@ -1817,8 +1759,6 @@ __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, 
 // tpr threads per row).
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256, 4) k_crt(const __grid_constant__ JobGroup<T, CAP> G) {
-    ptx::grid_dep_wait();
-    ptx::grid_dep_launch();
     for_items(G, [&](const JobDesc<T> &jd, long long li) {
         const int tpr = crt_tpr(jd.n), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
         const unsigned ncb = unsigned(cdiv(jd.n, tpr * 4)), ui = unsigned(li);

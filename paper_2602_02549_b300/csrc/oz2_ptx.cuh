@@ -17,14 +17,6 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 
-// ---------------------------------------------------------------- dependent launches
-// A kernel launched with programmatic stream serialization may start while
-// the previous kernel of the stream still runs; grid_dep_wait blocks until that
-// kernel has completed and its memory is visible (a no-op without the launch
-// attribute).  grid_dep_launch lets the next such kernel start launching.
-__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 // ---------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
