@@ -161,6 +161,44 @@ OZ2_API int oz2_cgemm(int m, int n, int k, const float *A, int lda, const float 
 OZ2_API size_t oz2_zworkspace_size(int m, int n, int k, int nmax, int mode, int fp32);
 
 /*
+ * Row-sharded emulated DGEMM (the paper treats one product on one device):
+ * the ranks of a job each hold a block of rows of A and all of B and compute
+ * the same rows of C = OS_II(A, B), bit for bit as one unsharded call would.
+ * Algorithm 2's mu_i needs only row i, but nu_j needs max_h cbar_hj over ALL
+ * rows of A, and the bound rule (nmoduli == 0) needs the maxima over all rows
+ * of |A| v and 2^alpha' and the per-k maxima of |A|: one exchange, an
+ * element-wise MAX over the ranks of three arrays that live in the workspace.
+ *   1. oz2_gemm_rows_begin on every rank (its rows: m, A): scaling up to the
+ *      bound rule's reductions; *ex receives the three device arrays:
+ *        cmax_col  int32[n]   column maxima of Cbar over this rank's rows
+ *        kmax      int64[k]   per-k maxima of |A| (bits of nonnegative doubles,
+ *                             which order like the values)
+ *        red       int64[8]   the bound rule's maxima (bits, likewise)
+ *   2. the caller replaces each array by the element-wise maximum over the
+ *      ranks, in place (e.g. an NCCL all-reduce with ncclMax on opts->stream);
+ *   3. oz2_gemm_rows_end on every rank with the same arguments plus C: the
+ *      rest of Algorithms 2 and 3 and the inverse scaling for its rows.
+ * Both calls take the same m, n, k, A, lda, B, ldb, nmoduli, mode and opts;
+ * opts->workspace (oz2_workspace_size(m, n, k, nmax, mode, 0) bytes) is
+ * required and carries the state from one call to the other.  k <= 2^17;
+ * mode: OZ2_TRANS_A, OZ2_TRANS_B (OZ2_FAST, OZ2_COMPONENTWISE, mu_in/nu_in,
+ * w_out and phase_events: OZ2_ENOTSUP).  Returns as oz2_gemm_ex.
+ */
+typedef struct oz2_exchange {
+    int32_t *cmax_col;
+    size_t n;
+    int64_t *kmax;
+    size_t k;
+    int64_t *red;
+    size_t nred;
+} oz2_exchange;
+
+OZ2_API int oz2_gemm_rows_begin(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                                int nmoduli, int mode, const oz2_opts *opts, oz2_exchange *ex);
+OZ2_API int oz2_gemm_rows_end(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                              double *C, int ldc, int nmoduli, int mode, const oz2_opts *opts);
+
+/*
  * Batched emulated DGEMM: many independent problems of uneven shapes, each
  * with its own exponents and its own N (fixed, or the bound rule for its own
  * target).  The scaling GEMMs of all problems run as one persistent tcgen05

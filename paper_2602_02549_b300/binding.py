@@ -163,6 +163,105 @@ def gemm_timeout_selftest(A, B, C, nmoduli: int, limit_us: int = 5000, *, worksp
                                            _ld(C, "C"), int(nmoduli), int(limit_us), ctypes.byref(o))
 
 
+class oz2_exchange(ctypes.Structure):
+    _fields_ = [("cmax_col", ctypes.c_void_p), ("n", ctypes.c_size_t), ("kmax", ctypes.c_void_p),
+                ("k", ctypes.c_size_t), ("red", ctypes.c_void_p), ("nred", ctypes.c_size_t)]
+
+
+def _rows_opts(A, stream, workspace, target, nmax, n_out, mu_out, nu_out):
+    import torch
+    o = oz2_opts()
+    s = stream if stream is not None else torch.cuda.current_stream(A.device)
+    o.stream = ctypes.c_void_p(s.cuda_stream)
+    o.workspace = ctypes.c_void_p(workspace.data_ptr())
+    o.workspace_bytes = workspace.numel()
+    o.target = float(target)
+    o.nmax = int(nmax)
+    o.n_out, o.mu_out, o.nu_out = _ptr(n_out), _ptr(mu_out), _ptr(nu_out)
+    return o
+
+
+def _rows_dims(A, B, mode):
+    ta, tb = bool(mode & OZ2_TRANS_A), bool(mode & OZ2_TRANS_B)
+    m = A.size(1) if ta else A.size(0)
+    k = A.size(0) if ta else A.size(1)
+    n = B.size(0) if tb else B.size(1)
+    return m, n, k
+
+
+def gemm_rows_begin(A, B, nmoduli: int = 0, mode: int = 0, *, workspace, target: float = 0.0, nmax: int = 0,
+                    stream=None):
+    """oz2_gemm_rows_begin on float64 CUDA tensors (this rank's rows of A, all of
+    B): returns the three exchange arrays as int32 / int64 tensors that view the
+    workspace, to be replaced in place by their element-wise maximum over the
+    ranks before gemm_rows_end.  Raises on a non-OK status."""
+    import torch
+    m, n, k = _rows_dims(A, B, mode)
+    o = _rows_opts(A, stream, workspace, target, nmax, None, None, None)
+    ex = oz2_exchange()
+    L = lib()
+    L.oz2_gemm_rows_begin.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int] * 2 + \
+        [ctypes.c_int, ctypes.c_int, ctypes.POINTER(oz2_opts), ctypes.POINTER(oz2_exchange)]
+    L.oz2_gemm_rows_begin.restype = ctypes.c_int
+    with torch.cuda.device(A.device):
+        rc = L.oz2_gemm_rows_begin(m, n, k, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), int(nmoduli), int(mode),
+                                   ctypes.byref(o), ctypes.byref(ex))
+    if rc:
+        raise Oz2Error(rc, "oz2_gemm_rows_begin")
+    base = workspace.data_ptr()
+
+    def view(ptr, count, dtype, size):
+        off = ptr - base
+        return workspace[off:off + count * size].view(dtype)
+    return (view(ex.cmax_col, ex.n, torch.int32, 4), view(ex.kmax, ex.k, torch.int64, 8),
+            view(ex.red, ex.nred, torch.int64, 8))
+
+
+def gemm_rows_end(A, B, C, nmoduli: int = 0, mode: int = 0, *, workspace, target: float = 0.0, nmax: int = 0,
+                  stream=None, n_out=None, mu_out=None, nu_out=None) -> int:
+    """oz2_gemm_rows_end: this rank's rows of C once the exchange is done.
+    Returns the status code."""
+    import torch
+    m, n, k = _rows_dims(A, B, mode)
+    o = _rows_opts(A, stream, workspace, target, nmax, n_out, mu_out, nu_out)
+    L = lib()
+    L.oz2_gemm_rows_end.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int] * 3 + \
+        [ctypes.c_int, ctypes.c_int, ctypes.POINTER(oz2_opts)]
+    L.oz2_gemm_rows_end.restype = ctypes.c_int
+    with torch.cuda.device(A.device):
+        return L.oz2_gemm_rows_end(m, n, k, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), _ptr(C), _ld(C, "C"),
+                                   int(nmoduli), int(mode), ctypes.byref(o))
+
+
+def exchange_max(arrays, group=None) -> None:
+    """The exchange of a row-sharded call: every array replaced, in place, by
+    its element-wise maximum over the ranks of `group` (torch.distributed; NCCL
+    on CUDA tensors, gloo on CPU tensors)."""
+    import torch.distributed as dist
+    for t in arrays:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+
+
+def matmul_rows(A_rows, B, nmoduli: int = 0, *, target: float = 1e-15, nmax: int = 0, trans_a: bool = False,
+                trans_b: bool = False, group=None, out=None, n_out=None):
+    """This rank's rows of A @ B when the rows of A are split over the ranks of
+    `group` (B whole on every rank): begin, the exchange, end; bit-identical to
+    the same rows of the unsharded matmul."""
+    import torch
+    mode = (OZ2_TRANS_A if trans_a else 0) | (OZ2_TRANS_B if trans_b else 0)
+    m, n, k = _rows_dims(A_rows, B, mode)
+    nm = nmoduli if nmoduli else (nmax if nmax else 20)
+    ws = torch.empty(workspace_size(m, n, k, nm, mode, False), dtype=torch.uint8, device=A_rows.device)
+    tgt = target if nmoduli == 0 else 0.0
+    arrays = gemm_rows_begin(A_rows, B, nmoduli, mode, workspace=ws, target=tgt, nmax=nmax)
+    exchange_max(arrays, group)
+    C = out if out is not None else torch.empty((m, n), dtype=torch.float64, device=A_rows.device)
+    rc = gemm_rows_end(A_rows, B, C, nmoduli, mode, workspace=ws, target=tgt, nmax=nmax, n_out=n_out)
+    if rc:
+        raise Oz2Error(rc, "oz2_gemm_rows_end")
+    return C
+
+
 def sum_tables(N: int, fp32: bool = False) -> tuple:
     """The CRT-sum constants as the device holds them: (list of k_l, esum) with
     s_l2 (DGEMM) or s_l1 (SGEMM) = k_l 2^esum (host-only)."""

@@ -456,8 +456,12 @@ int managed_workspace(int dev, size_t bytes, uint8_t **out) {
 // Every phase of Algorithms 1-3 for a group of at most kMaxJobs problems:
 // each light phase is one launch over the items of all problems, each GEMM one
 // persistent launch over the tiles of all problems (heaviest first).
+// part: 0 the whole call; 1 the phases up to the N rule's reductions (a rank's
+// share before the exchange of a row-sharded call); 2 the rest, from the
+// reductions again (after the exchange)
+enum { kPartAll = 0, kPartBegin = 1, kPartEnd = 2 };
 template <typename T, int CAP, class Mark>
-int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&mark) {
+int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&mark, int part = kPartAll) {
     static_assert(sizeof(JobGroup<T, CAP>) < 30000 && sizeof(GemmGroup<CAP>) < 30000, "kernel parameter space");
     static thread_local JobGroup<T, CAP> J;      // passed by value as the kernel parameter
     static thread_local GemmGroup<CAP> G;
@@ -544,18 +548,24 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
         return OZ2_OK;
     };
 
-    if ((rc = mark(OZ2_PHASE_STATS))) return rc;
-    OZ2_LAUNCH(k_clear, clear, one_each)
-    OZ2_LAUNCH(k_absmax, absmax, one_each)
-    if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
-    OZ2_LAUNCH(k_quant_kc, quant_kc, one_each)
-    OZ2_LAUNCH(k_quant_rc, quant_rc, one_each)
-    OZ2_LAUNCH(k_fast_max, fast_max, one_each)
-    OZ2_LAUNCH(k_fast_cmax, fast_cmax, one_each)
-    if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
-    if ((rc = gemms(EPI_MAX))) return rc;
+    if (part != kPartEnd) {
+        if ((rc = mark(OZ2_PHASE_STATS))) return rc;
+        OZ2_LAUNCH(k_clear, clear, one_each)
+        OZ2_LAUNCH(k_absmax, absmax, one_each)
+        if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
+        OZ2_LAUNCH(k_quant_kc, quant_kc, one_each)
+        OZ2_LAUNCH(k_quant_rc, quant_rc, one_each)
+        OZ2_LAUNCH(k_fast_max, fast_max, one_each)
+        OZ2_LAUNCH(k_fast_cmax, fast_cmax, one_each)
+        if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;
+        if ((rc = gemms(EPI_MAX))) return rc;
+    }
     if ((rc = mark(OZ2_PHASE_EXPONENTS))) return rc;
+    // after the exchange the reductions run again: their atomic maxima over
+    // this rank's rows leave the exchanged maxima in place, and the terms that
+    // read the exchanged column maxima and per-k maxima come out global
     OZ2_LAUNCH(k_bound, bound, one_each)
+    if (part == kPartBegin) return OZ2_OK;
     if ((rc = gemms(EPI_CW))) return rc;
     OZ2_LAUNCH(k_exponents, exponents, one_each)
     if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
@@ -744,6 +754,48 @@ int run_complex(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T
     dim3 grid(unsigned(cdiv(n, 256)), unsigned(std::min(m, 65535)));
     k_zmerge<T><<<grid, 256, 0, st>>>(Cre, Cim, n, m, n, C, ldc);
     return cuda_fail(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ row-sharded calls
+// One rank's rows of a product whose A rows are split over ranks (B whole on
+// every rank): the phases up to the N rule's reductions, the exchange (by the
+// caller: an element-wise MAX over the ranks of three workspace arrays), then
+// the rest.  Algorithm 2's mu_i needs only row i; nu_j needs max_h cbar_hj over
+// all rows (the exchanged column maxima), and the bound rule the maxima over
+// all rows of |A| v and 2^alpha' and the per-k maxima of |A| (for L).
+int rows_check(int m, int n, int k, const double *A, int lda, const double *B, int ldb, int nmoduli, int mode,
+               const oz2_opts *o) {
+    int rc = validate(m, n, k, A, lda, B, ldb, B, n, nmoduli, mode, o);
+    if (rc) return rc;
+    if (!o || !o->workspace) return OZ2_EINVAL;                 // the state between the two calls
+    if (k > OZ2_K_MAX) return OZ2_ERANGE;
+    if ((mode & (OZ2_FAST | OZ2_COMPONENTWISE)) || o->mu_in || o->w_out || o->phase_events) return OZ2_ENOTSUP;
+    return OZ2_OK;
+}
+
+int rows_part(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+              int nmoduli, int mode, const oz2_opts *o, int part, oz2_exchange *ex) {
+    Job<double> job;
+    job.set(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o->target, o->nmax);
+    if (o->workspace_bytes < job.L.total) return OZ2_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(o->workspace) & 255u) return OZ2_EINVAL;
+    int dev = 0, rc = ensure_device(&dev);
+    if (rc) return rc;
+    job.n_out = o->n_out;
+    job.mu_out = o->mu_out;
+    job.nu_out = o->nu_out;
+    job.bind(static_cast<uint8_t *>(o->workspace));
+    if (ex) {
+        ex->cmax_col = job.cmax_col;
+        ex->n = size_t(n);
+        ex->kmax = reinterpret_cast<int64_t *>(job.hmaxA);
+        ex->k = size_t(k);
+        ex->red = reinterpret_cast<int64_t *>(job.red);
+        ex->nred = 8;
+    }
+    Job<double> *one = &job;
+    return run_group<double, 1>(&one, 1, static_cast<cudaStream_t>(o->stream), g_dev[dev].sms,
+                                [](int) { return OZ2_OK; }, part);
 }
 
 // ------------------------------------------------------------------ batches
@@ -990,6 +1042,22 @@ size_t oz2_zworkspace_size(int m, int n, int k, int nmax, int mode, int fp32) {
     if (m < 1 || n < 1 || k < 1 || k > (1 << 30) || nmax < OZ2_N_MIN || nmax > OZ2_N_MAX) return 0;
     const int rmode = mode & (OZ2_FAST | OZ2_TRANS_A | OZ2_TRANS_B | OZ2_COMPONENTWISE);
     return fp32 ? zlayout<float>(m, n, k, nmax, rmode).total : zlayout<double>(m, n, k, nmax, rmode).total;
+}
+
+int oz2_gemm_rows_begin(int m, int n, int k, const double *A, int lda, const double *B, int ldb, int nmoduli,
+                        int mode, const oz2_opts *opts, oz2_exchange *ex) {
+    if (!ex) return OZ2_EINVAL;
+    int rc = rows_check(m, n, k, A, lda, B, ldb, nmoduli, mode, opts);
+    if (rc) return rc;
+    return rows_part(m, n, k, A, lda, B, ldb, nullptr, n, nmoduli, mode, opts, kPartBegin, ex);
+}
+
+int oz2_gemm_rows_end(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+                      int nmoduli, int mode, const oz2_opts *opts) {
+    int rc = rows_check(m, n, k, A, lda, B, ldb, nmoduli, mode, opts);
+    if (rc) return rc;
+    if (!C || ldc < n) return OZ2_EINVAL;
+    return rows_part(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, opts, kPartEnd, nullptr);
 }
 
 int oz2_gemm_batched(int count, const oz2_problem *problems, const oz2_opts *opts) {

@@ -168,3 +168,26 @@ def test_batched_keeps_the_k_limit(lib):
     arr = (P * 1)(big)
     assert lib.oz2_gemm_batched(1, ctypes.cast(arr, ctypes.c_void_p), None) == B.OZ2_ERANGE
     assert lib.oz2_batched_workspace_size(1, ctypes.cast(arr, ctypes.c_void_p)) == 0
+
+
+def test_rows_argument_validation(lib):
+    # the row-sharded calls reject what they cannot carry before touching CUDA
+    lib.oz2_gemm_rows_begin.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int] * 2 + \
+        [ctypes.c_int, ctypes.c_int, ctypes.POINTER(B.oz2_opts), ctypes.POINTER(B.oz2_exchange)]
+    lib.oz2_gemm_rows_end.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int] * 3 + \
+        [ctypes.c_int, ctypes.c_int, ctypes.POINTER(B.oz2_opts)]
+    ex = B.oz2_exchange()
+    o = B.oz2_opts()
+    o.target = 1e-15
+    begin = lambda k=8, mode=0, N=0, opts=o, exch=ex: lib.oz2_gemm_rows_begin(   # noqa: E731
+        8, 8, k, FAKE, max(k, 8), FAKE, 8, N, mode, ctypes.byref(opts) if opts else None,
+        ctypes.byref(exch) if exch else None)
+    assert begin(exch=None) == B.OZ2_EINVAL
+    assert begin(opts=None) == B.OZ2_EINVAL
+    assert begin() == B.OZ2_EINVAL                      # no workspace: it carries the state
+    o.workspace = FAKE
+    o.workspace_bytes = 1 << 30
+    assert begin(k=B.K_MAX + 1) == B.OZ2_ERANGE
+    assert begin(mode=B.OZ2_FAST) == B.OZ2_ENOTSUP
+    assert begin(mode=B.OZ2_COMPONENTWISE) == B.OZ2_ENOTSUP
+    assert lib.oz2_gemm_rows_end(8, 8, 8, FAKE, 8, FAKE, 8, None, 8, 0, 0, ctypes.byref(o)) == B.OZ2_EINVAL
