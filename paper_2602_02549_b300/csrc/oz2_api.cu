@@ -86,8 +86,10 @@ int ensure_device(int *dev_out) {
         DevN n64[kNMax + 1], n32[kNMax + 1];
         for (int N = 0; N <= kNMax; N++) {
             const NTable &a = T.n64[N], &b = T.n32[N];
-            n64[N] = DevN{a.P1, a.P2, a.Pinv, a.g, a.t, a.gN, a.Pprime, a.eg, a.esum, a.poff};
-            n32[N] = DevN{b.P1, b.P2, b.Pinv, b.g, b.t, b.gN, b.Pprime, b.eg, b.esum, b.poff};
+            n64[N] = DevN{a.P1, a.P2, a.Pinv, a.g, a.t, a.gN, a.Pprime, a.eg, a.esum, a.poff,
+                          a.M1, a.eu1, a.sh, a.kq, a.sq};
+            n32[N] = DevN{b.P1, b.P2, b.Pinv, b.g, b.t, b.gN, b.Pprime, b.eg, b.esum, b.poff,
+                          b.M1, b.eu1, b.sh, b.kq, b.sq};
         }
         cudaError_t e = cudaSuccess;
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_n64, n64, sizeof n64);

@@ -31,6 +31,9 @@ struct DevN {
     int eg;       // b = 64: g = 2^eg
     int esum;     // grid exponent of the rounded CRT sum
     int poff;     // first plane pair of this N in c_dp64 / c_dp32
+    long long M1; // b = 64: P1 = M1 2^eu1, g = 2^(eu1 + sh)
+    int eu1, sh;
+    int kq, sq;   // b = 64: (H >> 22) kq 2^-sq estimates H g / P
 };
 
 __constant__ DevN c_n64[kNMax + 1];
@@ -1576,6 +1579,17 @@ __global__ void __launch_bounds__(256) k_fast_cmax(const __grid_constant__ JobGr
 
 // ------------------------------------------------------------------ the epilogue's helpers
 
+// RN(x 2^e) where the result leaves the normal range (a call, so that its FP64
+// multiplies stay off the common path)
+__device__ __noinline__ double scale_pow2_slow(double x, int e) {
+    if (e > 1023) return x * 0x1p1023 * 0x1p1023;                 // overflows to +-inf as ldexp does
+    if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+    const double y = x * 0x1p-1022;                               // exact: |x| >= 1
+    const int e2 = e + 1022;
+    if (e2 < -1022) return copysign(0.0, x);
+    return y * __longlong_as_double((long long)(e2 + 1023) << 52);
+}
+
 // RN(x 2^e) for an integer-valued x with |x| < 2^400 (an exponent add, on the
 // integer units, whenever the result stays normal)
 __device__ __forceinline__ double scale_pow2(double x, int e) {
@@ -1584,12 +1598,7 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
     const int ex = int((b >> 52) & 0x7FF);
     if (zero || (ex + e >= 1 && ex + e <= 2046))
         return zero ? x : __longlong_as_double((long long)((unsigned long long)b + ((unsigned long long)(long long)e << 52)));   // exact
-    if (e > 1023) return x * 0x1p1023 * 0x1p1023;                 // overflows to +-inf as ldexp does
-    if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
-    const double y = x * 0x1p-1022;                               // exact: |x| >= 1
-    const int e2 = e + 1022;
-    if (e2 < -1022) return copysign(0.0, x);
-    return y * __longlong_as_double((long long)(e2 + 1023) << 52);
+    return scale_pow2_slow(x, e);
 }
 
 // RN((hi 2^S + lo) 2^e) as a double, from integer operations only (S = 31 or
@@ -1641,6 +1650,12 @@ __device__ __forceinline__ double rint_bits(double x) {
     // |x| < 1: 0, or 1 above 1/2 (1/2 itself goes to the even 0)
     const unsigned long long small = sign | ((b & ~(1ull << 63)) > 0x3FE0000000000000ull ? 0x3FF0000000000000ull : 0ull);
     return __longlong_as_double((long long)(e >= 1075 ? b : (e < 1023 ? small : t)));   // |x| >= 2^52: x
+}
+
+// Q = rint(P_inv C'(1)) in FP64 as Algorithm 3 states it, for C'(1) = H g (a
+// call: taken only where the integer estimate cannot decide)
+__device__ __noinline__ long long crt_q_fp64(long long H, int eg, double Pinv) {
+    return (long long)rint_bits(Pinv * exact_i53(H, eg));
 }
 
 // c + a.lo16 b.byte0 + a.hi16 b.byte1 (dp2a.lo) or with b's bytes 2, 3
@@ -1720,9 +1735,24 @@ __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, 
                                           ((unsigned long long)(long long)s1[e][1] << 16) +
                                           ((unsigned long long)(long long)s1[e][2] << 32) +
                                           ((unsigned long long)(long long)s1[e][3] << 48);
-            const double c1 = exact_i53((long long)Hu, d.eg);
-            const double q = rint_bits(d.Pinv * c1);
-            cpp = fma(-q, d.P2, fma(-q, d.P1, c1) + rn_sum<32>(hi2, lo2, d.esum));
+            // Q: y = (H >> 22) kq 2^-sq is within 2^-15 of H g / P and FP64's
+            // P_inv C'(1) within 2^-38 of it, so both have the nearest integer
+            // of y unless y lies within 2^-14 of a half-integer (then FP64 decides)
+            const long long H = (long long)Hu;
+            const long long z = (long long)(int)(H >> 22) * (long long)d.kq;
+            const unsigned long long half = 1ull << (d.sq - 1);
+            const unsigned long long fr = (unsigned long long)z & ((half << 1) - 1);
+            long long q = (long long)((unsigned long long)z + half) >> d.sq;
+            if ((fr > half ? fr - half : half - fr) <= (half >> 13)) q = crt_q_fp64(H, d.eg, d.Pinv);
+            // fma(-Q, P1, C'(1)) is exact (|C'(1) - Q P1| < 2^53 ulp(P1), both
+            // multiples of ulp(P1) = 2^eu1): T1 2^eu1, taken modulo 2^64
+            const long long T1 = (long long)(((unsigned long long)H << d.sh) -
+                                             (unsigned long long)q * (unsigned long long)d.M1);
+            // C'(2) = RN(hi2 2^32 + lo2) 2^esum as the sum of two exact doubles
+            const long long th = hi2 + (lo2 >> 32);
+            const long long tl = lo2 & 0xFFFFFFFFll;
+            const double c2 = exact_i53(th, d.esum + 32) + exact_i53(tl, d.esum);
+            cpp = fma(-exact_i53(q, 0), d.P2, exact_i53(T1, d.eu1) + c2);
         } else {
             const double c1 = rn_sum<32>(hi2, lo2, d.esum);
             const double q = rint_bits(d.Pinv * c1);

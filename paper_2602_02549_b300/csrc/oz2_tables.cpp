@@ -290,12 +290,33 @@ void build(Tables &T) {
             P1b = e1 - 53 >= 0 ? P1b.shl(e1 - 53) : P1b.shr(53 - e1);
             n.P2 = cmp(P, P1b) >= 0 ? to_double(sub(P, P1b)) : -to_double(sub(P1b, P));
             n.Pinv = Pinv;
+            n.M1 = (long long)std::ldexp(f1, 53);
+            n.eu1 = e1 - 53;
             n.Pprime = Pprime;
             n.t = t;
             n.gN = double((1.0L + 3.0L * u64) * std::ldexp(1.0L, 1 + clr) * (N + 2) * u64 * u64 *
                           (long double)rho * PL) * (1.0 + 0x1p-40);
             const int eg = clr + (r.bits() - 1) - 52;
             n.g = std::ldexp(1.0, eg);
+            n.sh = eg - n.eu1;
+            {   // Q = rint(P_inv C'(1)) from C'(1) = H g, |H| < 2^53: the estimate
+                // (H >> 22) kq 2^-sq of H g / P (kq < 2^31, the product below 2^61)
+                // is within err of it; FP64's P_inv C'(1) is within ymax 2^-51.  The
+                // kernel takes the estimate's nearest integer unless it lies within
+                // 2^-14 of a half-integer, so err + ymax 2^-51 <= 2^-15 is required.
+                const long double ymax = std::ldexp(1.0L, 53 + eg) / PL;
+                int sq = 61;
+                long double K = 0;
+                for (; sq >= 16; sq--) {
+                    K = std::rint(std::ldexp(1.0L, 22 + eg + sq) / PL);
+                    if (K < 0x1p31L - 1 && ymax * std::ldexp(1.0L, sq) < 0x1p61L) break;
+                }
+                n.kq = int(K);
+                n.sq = sq;
+                const long double err = std::ldexp(1.0L, 22 + eg) / PL +
+                                        ymax * std::fabs(K * PL / std::ldexp(1.0L, 22 + eg + sq) - 1.0L);
+                T.sums_fit &= N < 2 || (n.sh >= 0 && n.sh < 64 && sq >= 16 && err + ymax * 0x1p-51L <= 0x1p-15L);
+            }
             n.offset = offset;
             for (int l = 0; l < N; l++) {
                 const Big &xl = x[size_t(l)];
@@ -338,6 +359,11 @@ void build(Tables &T) {
                 h += 128.0L * (long double)T.s1i[offset + l];
             }
             T.sums_fit &= hy < (1ll << 31) && h < 0x1p62L && T.n64[N].eg + 62 < 1023 && T.n64[N].eg > -960;
+            // |H| < 2^53 (Lemma 2), which the kernel's integer steps rely on:
+            // |W_l| <= floor(p_l / 2)
+            long double hb = 0;
+            for (int l = 0; l < N; l++) hb += (long double)(kModuli[l] / 2) * (long double)T.s1i[offset + l];
+            T.sums_fit &= N < 2 || (hb < 0x1p53L && T.n64[N].esum >= -1022);
             // the dp2a form rebuilds H from four 16-bit piece sums modulo 2^64, which is
             // exact while |H| < 2^63; each piece sum stays below 2^16 128 49 < 2^31
             T.sums_fit &= h < 0x1p62L;

@@ -34,6 +34,10 @@ struct NTable {
     int esum;                // grid of the rounded CRT sum: s_l2 (b = 64) or s_l1
                              // (b = 32) = (k[1] 2^31 + k[0]) 2^esum
     int poff;                // start of this N's plane pairs in dp64 / dp32
+    // b = 64, the CRT kernel's integer steps: P1 = M1 2^eu1 (M1 < 2^53), g = 2^(eu1 + sh);
+    // Q's estimate (H >> 22) kq 2^-sq ~ H g / P for C'(1) = H g
+    long long M1;
+    int eu1, sh, kq, sq;
 };
 
 struct Tables {
