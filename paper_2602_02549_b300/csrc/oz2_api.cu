@@ -426,6 +426,11 @@ struct Job {
         j.w_plane = w_plane;
         j.zero = reinterpret_cast<uint4 *>(ws);
         j.zero_vec = long(L.zero_end / 16);
+        for (int X = 0; X < 2; X++) {        // run_group may narrow these per launch
+            int S, Cl;
+            absmax_geom(j, X, S, Cl);
+            j.absmax_lw[X] = absmax_lw_min(Cl);
+        }
         return j;
     }
 };
@@ -470,20 +475,26 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     std::memset(&J, 0, sizeof J);
     J.count = count;
     for (int p = 0; p < count; p++) J.j[p] = jobs[p]->desc();
-    // k_absmax: fewer lines per item while the whole launch would give fewer than
-    // two blocks per SM (each item ends in one atomicMax per position, so large
-    // launches keep the full kLineBlock)
-    for (int lb = kLineBlock; lb > 8; lb /= 2) {
-        long long total = 0;
-        for (int p = 0; p < count; p++) {
-            J.j[p].absmax_lb = lb;
-            total += Items<T>::absmax(J.j[p]);
+    // k_absmax: items as wide as the lines allow (absmax_lw_min); while the whole
+    // launch would give fewer than two blocks per SM, narrower items (more line
+    // groups per block), and then, while it would give fewer than one, fewer
+    // lines per item.  Each item ends in one atomicMax per position and per
+    // line, and the items that share a position contend for it, so launches
+    // with enough items keep the widest items and the full kLineBlock lines.
+    {
+        auto total = [&]() {
+            long long t = 0;
+            for (int p = 0; p < count; p++) t += Items<T>::absmax(J.j[p]);
+            return t;
+        };
+        for (bool wider = true; wider && total() < 2ll * sms;) {
+            wider = false;
+            for (int p = 0; p < count; p++)
+                for (int X = 0; X < 2; X++)
+                    if (J.j[p].absmax_lw[X] < 8) { J.j[p].absmax_lw[X] *= 2; wider = true; }
         }
-        if (total >= 2ll * sms) break;
-        if (lb / 2 <= 8) {
-            for (int p = 0; p < count; p++) J.j[p].absmax_lb = lb / 2;
-            break;
-        }
+        while (total() < sms && J.j[0].absmax_lb > 8)
+            for (int p = 0; p < count; p++) J.j[p].absmax_lb /= 2;
     }
     // fills J.begin from the per-problem item counts; returns the grid size (0: nothing to do)
     // (the kernels decode a problem's items with 32-bit arithmetic; a count of
@@ -555,8 +566,16 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
         OZ2_LAUNCH(k_clear, clear, one_each)
         OZ2_LAUNCH(k_absmax, absmax, one_each)
         if ((rc = mark(OZ2_PHASE_QUANT))) return rc;
-        OZ2_LAUNCH(k_quant_kc, quant_kc, one_each)
-        OZ2_LAUNCH(k_quant_rc, quant_rc, one_each)
+        {   // one launch for both layouts where the two would each leave SMs idle
+            long long items = 0;
+            for (int p = 0; p < count; p++) items += Items<T>::quant(J.j[p]);
+            if (items < 4ll * sms) {
+                OZ2_LAUNCH(k_quant, quant, one_each)
+            } else {
+                OZ2_LAUNCH(k_quant_kc, quant_kc, one_each)
+                OZ2_LAUNCH(k_quant_rc, quant_rc, one_each)
+            }
+        }
         OZ2_LAUNCH(k_fast_max, fast_max, one_each)
         OZ2_LAUNCH(k_fast_cmax, fast_cmax, one_each)
         if ((rc = mark(OZ2_PHASE_SCALEGEMM))) return rc;

@@ -6,8 +6,9 @@
 //   k_absmax                  Algorithm 2 inputs: max |x| per row of A (per
 //                             column of B) -> mu', nu', and the per-k maxima
 //                             of the N rule (one HBM read)
-//   k_quant_kc / k_quant_rc   Abar = ceil(2^mu' |A|), Bbar likewise, as BF16;
-//                             also |A| v and v^T |B| for the N rule
+//   k_quant_kc / k_quant_rc   Abar = ceil(2^mu' |A|), Bbar likewise, as BF16
+//   (k_quant: both)           (K-contiguous rows, or transposed through shared
+//                             memory); also |A| v and v^T |B| for the N rule
 //   k_gemm<EPI_MAX>           Cbar = Abar Bbar on tcgen05, keeping only the row
 //                             and column maxima of Cbar
 //   k_bound, k_exponents      the N rule; Dbar, e, f, mu, nu (Algorithm 2)
@@ -213,6 +214,7 @@ struct JobDesc {
     int nmoduli, nmax, fast, inject, vec[2];
     int cw;                        // componentwise N rule (OZ2_COMPONENTWISE)
     int absmax_lb;                 // lines per k_absmax item (kLineBlock or fewer, per launch)
+    int absmax_lw[2];              // line groups per k_absmax block (1, 2, 4 or 8), per operand
     int accum;                     // CRT adds its result to C (the K ranges after the first)
     double target;
     unsigned long long *hmax[2];   // per-k maxima of |A|, |B|
@@ -252,17 +254,24 @@ __host__ __device__ __forceinline__ void absmax_geom(const JobDesc<T> &j, int X,
     if (j.op[X].kcontig) { S = j.op[X].R; C = j.k; }
     else { S = j.k; C = j.op[X].R; }
 }
-// threads per line: a multiple of 32 covering C / 8 positions, at most 256
-__host__ __device__ __forceinline__ int absmax_tpl(int C) {
-    int t = int(cdiv(cdiv(C, 8), 32) * 32);
-    return t < 32 ? 32 : (t > 256 ? 256 : t);
-}
+// k_absmax item: j.absmax_lb lines x 256 (8 / lw) positions, lw = j.absmax_lw[X]
+// line groups: a warp covers 256 positions of a line (8 per lane), the block's
+// 8 warps form 8 / lw position groups times lw line groups, and each line
+// group takes every lw-th line of the item.
 template <typename T>
 __host__ __device__ __forceinline__ long long items_absmax_x(const JobDesc<T> &j, int X) {
     if (j.inject) return 0;
     int S, C;
     absmax_geom(j, X, S, C);
-    return cdiv(S, j.absmax_lb) * cdiv(C, absmax_tpl(C) * 8);
+    return cdiv(S, j.absmax_lb) * cdiv(C, 2048 / j.absmax_lw[X]);
+}
+// the fewest line groups (widest items) that leave no warp of a block without
+// positions: 8 / lw position groups of 256 cover at most C rounded up to 256
+__host__ __device__ __forceinline__ int absmax_lw_min(int C) {
+    const long long pg = cdiv(C, 256);
+    int lw = 1;
+    while (lw < 8 && 8 / lw > pg) lw <<= 1;
+    return lw;
 }
 // Residues of K-contiguous rows: 256 consecutive groups of 8 positions per
 // item, in the row-major order of the R_pad x k_pad plane (R_pad x k_pad / 8
@@ -327,6 +336,7 @@ template <typename T> struct Items {
     __host__ __device__ static long long exponents(const JobDesc<T> &j) { return cdiv(j.m + j.n, 256); }
     __host__ __device__ static long long resid_kc(const JobDesc<T> &j) { return items_kc_x(j, 0) + items_kc_x(j, 1); }
     __host__ __device__ static long long resid_rc(const JobDesc<T> &j) { return items_rc_x(j, 0) + items_rc_x(j, 1); }
+    __host__ __device__ static long long quant(const JobDesc<T> &j) { return quant_kc(j) + quant_rc(j); }
     __host__ __device__ static long long crt(const JobDesc<T> &j) {
         const int tpr = crt_tpr(j.n);
         return cdiv(j.m, 256 / tpr) * cdiv(j.n, tpr * 4);
@@ -373,23 +383,26 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return ((unsigned long long)hi << 32) | lo;
 }
 
-// Item: j.absmax_lb lines x (threads per line x 8) positions of one operand.
-// Thread (line group ly, position group tx) takes 8 consecutive positions of
-// the lines ly, ly + lines-per-pass, ...; each warp lies in one line group.
+// Item: j.absmax_lb lines x PW = 256 (8 / lw) positions of one operand (see
+// items_absmax_x).  Each line's maximum over the item is one atomicMax per
+// warp; each position's maximum over the item's lines is reduced across the
+// lw line groups through shared memory first, so that a position takes one
+// atomicMax per item.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup<T, CAP> G) {
+    __shared__ unsigned long long part[2048];   // [line group][position group][e 32 + lane]
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         int X = 0;
         const long long n0 = items_absmax_x(j, 0);
         if (li >= n0) { X = 1; li -= n0; }
         int S, C;
         absmax_geom(j, X, S, C);
-        const int tpl = absmax_tpl(C), ppi = tpl * 8, lpp = 256 / tpl;
-        const unsigned ncb = unsigned(cdiv(C, ppi)), ui = unsigned(li);
+        const int lw = j.absmax_lw[X], npg = 8 / lw, PW = 256 * npg;
+        const unsigned ncb = unsigned(cdiv(C, PW)), ui = unsigned(li);
         const int lb = int(ui / ncb), cb = int(ui - unsigned(lb) * ncb);
-        const int ly = threadIdx.x / tpl, tx = threadIdx.x - ly * tpl;
-        if (ly >= lpp) return;                  // 256 % tpl threads left over (whole warps)
-        const int c0 = cb * ppi + tx * 8;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int pg = warp % npg, lg = warp / npg;
+        const int c0 = cb * PW + pg * 256 + lane * 8;
         const int LB = j.absmax_lb;
         const int s_end = min(S, (lb + 1) * LB);
         const bool kc = j.op[X].kcontig != 0;
@@ -399,7 +412,7 @@ __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup
         const long ld = j.op[X].ld;
         const bool full = c0 + 8 <= C, vec = full && j.vec[X];
         unsigned long long cm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int s = lb * LB + ly; s < s_end; s += lpp) {
+        for (int s = lb * LB + lg; s < s_end; s += lw) {
             const T *src = ptr + (long)s * ld + c0;
             T x[8];
             if (vec) {
@@ -429,11 +442,30 @@ __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup
                 lm = bits > lm ? bits : lm;
             }
             lm = warp_max_u64(lm);
-            if ((threadIdx.x & 31) == 0 && lm) atomicMax(smax + s, lm);
+            if (lane == 0 && lm) atomicMax(smax + s, lm);
         }
+        if (lw == 1) {                       // one line group: no reduction across warps
 #pragma unroll
-        for (int e = 0; e < 8; e++)
-            if (cm[e] && c0 + e < C) atomicMax(cmax + c0 + e, cm[e]);
+            for (int e = 0; e < 8; e++)
+                if (cm[e] && c0 + e < C) atomicMax(cmax + c0 + e, cm[e]);
+            return;
+        }
+        __syncthreads();                     // the previous item's reads of part are done
+#pragma unroll
+        for (int e = 0; e < 8; e++) part[lg * PW + pg * 256 + e * 32 + lane] = cm[e];
+        __syncthreads();
+        // thread t: positions u 256 + t of the item (u < npg), position q = t of
+        // position group u stored at u 256 + (q % 8) 32 + q / 8
+        const int t = threadIdx.x, slot = (t & 7) * 32 + (t >> 3);
+        for (int u = 0; u < npg; u++) {
+            unsigned long long v = 0;
+            for (int g = 0; g < lw; g++) {
+                const unsigned long long w = part[g * PW + u * 256 + slot];
+                v = w > v ? w : v;
+            }
+            const int c = cb * PW + u * 256 + t;
+            if (v && c < C) atomicMax(cmax + c, v);
+        }
     });
 }
 
@@ -564,9 +596,12 @@ __device__ __forceinline__ void emit_quant8(const PlaneArgs &a, const T (&x)[8],
     for (int e = 0; e < 8; e++) {
         uint32_t vh, vl;
         quant_elem(x[e], shift, q[e], qf[e], vh, vl);
-        acc.ss += int(q[e] * q[e]);
         acc.hi += vh;
         acc.lo += vl;
+    }
+    if (a.sumsq) {                          // fast mode only
+#pragma unroll
+        for (int e = 0; e < 8; e++) acc.ss += int(q[e] * q[e]);
     }
     if (a.write) {
         uint4 v;
@@ -628,82 +663,103 @@ __device__ __forceinline__ void load8(const float *src, int valid, float (&x)[8]
 // K-contiguous source.  Item: 256 / tpr rows of tpr x 8 h (8 per thread, tpr
 // threads per row; each warp lies in one row).  Every lane stays to the end of
 // the item (the row sums are reduced across the warp).
-template <typename T, int CAP>
-__global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGroup<T, CAP> G) {
-    for_items(G, [&](const JobDesc<T> &j, long long li) {
-        int X = 0;
-        const long long n0 = items_quant_kc_x(j, 0);
-        if (li >= n0) { X = 1; li -= n0; }
-        const PlaneArgs a = quant_args(j, X);
-        const Operand<T> &op = j.op[X];
-        const int tpr = quant_tpr(a.k_pad), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
-        const unsigned nhb = unsigned(cdiv(a.k_pad, tpr * 8 * kQuantGroups)), ui = unsigned(li);
-        const int rb = int(ui / nhb);
-        const int r = rb * (256 / tpr) + ly;
-        const int hb = int(ui - unsigned(rb) * nhb) * tpr * 8 * kQuantGroups + tx * 8;
-        if (ly >= 256 / tpr) return;            // 256 % tpr threads left over (whole warps)
-        RowAcc acc{0, 0, 0};
-        const bool live = r < op.R;
-        const int shift = live ? quant_shift(a.row_max, r) : 0;
+template <typename T>
+__device__ __forceinline__ void quant_kc_item(const JobDesc<T> &j, long long li) {
+    int X = 0;
+    const long long n0 = items_quant_kc_x(j, 0);
+    if (li >= n0) { X = 1; li -= n0; }
+    const PlaneArgs a = quant_args(j, X);
+    const Operand<T> &op = j.op[X];
+    const int tpr = quant_tpr(a.k_pad), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
+    const unsigned nhb = unsigned(cdiv(a.k_pad, tpr * 8 * kQuantGroups)), ui = unsigned(li);
+    const int rb = int(ui / nhb);
+    const int r = rb * (256 / tpr) + ly;
+    const int hb = int(ui - unsigned(rb) * nhb) * tpr * 8 * kQuantGroups + tx * 8;
+    if (ly >= 256 / tpr) return;            // 256 % tpr threads left over (whole warps)
+    RowAcc acc{0, 0, 0};
+    const bool live = r < op.R;
+    const int shift = live ? quant_shift(a.row_max, r) : 0;
 #pragma unroll 2
-        for (int g = 0; g < kQuantGroups; g++) {
-            const int h0 = hb + g * tpr * 8;    // each chunk coalesced across the row's threads
-            if (h0 >= a.k_pad) break;
-            if (!live) {
-                if (a.write) *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
-                if (a.floor_plane)
-                    *reinterpret_cast<uint4 *>(a.out + a.plane + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
-                continue;
-            }
-            T x[8];
-            load8(op.ptr + (long)r * op.ld + h0, a.k - h0, x);
-            emit_quant8(a, x, shift, r, h0, acc);
+    for (int g = 0; g < kQuantGroups; g++) {
+        const int h0 = hb + g * tpr * 8;    // each chunk coalesced across the row's threads
+        if (h0 >= a.k_pad) break;
+        if (!live) {
+            if (a.write) *reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
+            if (a.floor_plane)
+                *reinterpret_cast<uint4 *>(a.out + a.plane + (long)r * a.k_pad + h0) = make_uint4(0, 0, 0, 0);
+            continue;
         }
-        flush_row(a, acc, r, tpr < 32 ? tpr : 32, live);   // a row's lanes: tpr of them, or whole warps
-    });
+        T x[8];
+        load8(op.ptr + (long)r * op.ld + h0, a.k - h0, x);
+        emit_quant8(a, x, shift, r, h0, acc);
+    }
+    flush_row(a, acc, r, tpr < 32 ? tpr : 32, live);   // a row's lanes: tpr of them, or whole warps
 }
 
 // R-contiguous source.  Item: a 64 (h) x 64 (r) tile transposed through
 // shared memory.
+template <typename T>
+__device__ __forceinline__ void quant_rc_item(const JobDesc<T> &j, long long li, T (*tile)[65]) {
+    int X = 0;
+    const long long n0 = items_quant_rc_x(j, 0);
+    if (li >= n0) { X = 1; li -= n0; }
+    const PlaneArgs a = quant_args(j, X);
+    const Operand<T> &op = j.op[X];
+    const unsigned nrb = unsigned(a.R_pad / 64), ui = unsigned(li);
+    const int hb = int(ui / nrb);
+    const int h_base = hb * 64, r_base = int(ui - unsigned(hb) * nrb) * 64;
+    __syncthreads();                     // the previous item's reads of the tile are done
+    {
+        const int rr = threadIdx.x & 63;
+        const int r = r_base + rr;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int hh = (threadIdx.x >> 6) + 4 * i;
+            const int h = h_base + hh;
+            tile[hh][rr] = (r < op.R && h < a.k) ? op.ptr[(long)h * op.ld + r] : T(0);
+        }
+    }
+    __syncthreads();
+    const int rr = threadIdx.x >> 2, hq = threadIdx.x & 3;
+    const int r = r_base + rr;
+    const bool live = r < op.R;
+    const int shift = live ? quant_shift(a.row_max, r) : 0;
+    RowAcc acc{0, 0, 0};
+#pragma unroll
+    for (int g = 0; g < 2; g++) {
+        const int hh0 = hq * 16 + g * 8;
+        const int h0 = h_base + hh0;
+        T x[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[e] = live ? tile[hh0 + e][rr] : T(0);
+        emit_quant8(a, x, shift, r, h0, acc);
+    }
+    flush_row(a, acc, r, 4, live);   // the 4 threads of row rr are adjacent lanes
+}
+
+// Quantisation of K-contiguous rows.
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_quant_kc(const __grid_constant__ JobGroup<T, CAP> G) {
+    for_items(G, [&](const JobDesc<T> &j, long long li) { quant_kc_item(j, li); });
+}
+
+// Quantisation of transposed rows.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256) k_quant_rc(const __grid_constant__ JobGroup<T, CAP> G) {
     __shared__ T tile[64][65];
+    for_items(G, [&](const JobDesc<T> &j, long long li) { quant_rc_item(j, li, tile); });
+}
+
+// Both layouts in one launch, for launches too small to fill the GPU twice
+// over: the K-contiguous items of each problem come first, then the
+// transposed ones.
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256) k_quant(const __grid_constant__ JobGroup<T, CAP> G) {
+    __shared__ T tile[64][65];
     for_items(G, [&](const JobDesc<T> &j, long long li) {
-        int X = 0;
-        const long long n0 = items_quant_rc_x(j, 0);
-        if (li >= n0) { X = 1; li -= n0; }
-        const PlaneArgs a = quant_args(j, X);
-        const Operand<T> &op = j.op[X];
-        const unsigned nrb = unsigned(a.R_pad / 64), ui = unsigned(li);
-        const int hb = int(ui / nrb);
-        const int h_base = hb * 64, r_base = int(ui - unsigned(hb) * nrb) * 64;
-        __syncthreads();                     // the previous item's reads of the tile are done
-        {
-            const int rr = threadIdx.x & 63;
-            const int r = r_base + rr;
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const int hh = (threadIdx.x >> 6) + 4 * i;
-                const int h = h_base + hh;
-                tile[hh][rr] = (r < op.R && h < a.k) ? op.ptr[(long)h * op.ld + r] : T(0);
-            }
-        }
-        __syncthreads();
-        const int rr = threadIdx.x >> 2, hq = threadIdx.x & 3;
-        const int r = r_base + rr;
-        const bool live = r < op.R;
-        const int shift = live ? quant_shift(a.row_max, r) : 0;
-        RowAcc acc{0, 0, 0};
-#pragma unroll
-        for (int g = 0; g < 2; g++) {
-            const int hh0 = hq * 16 + g * 8;
-            const int h0 = h_base + hh0;
-            T x[8];
-#pragma unroll
-            for (int e = 0; e < 8; e++) x[e] = live ? tile[hh0 + e][rr] : T(0);
-            emit_quant8(a, x, shift, r, h0, acc);
-        }
-        flush_row(a, acc, r, 4, live);   // the 4 threads of row rr are adjacent lanes
+        const long long nkc = items_quant_kc_x(j, 0) + items_quant_kc_x(j, 1);
+        if (li < nkc) quant_kc_item(j, li);
+        else quant_rc_item(j, li - nkc, tile);
     });
 }
 
@@ -839,12 +895,6 @@ __device__ __forceinline__ void emit_resid8(uint4 *dst, long pw16, int N, const 
     else emit_resid8_general(dst, pw16, N, x, shift, pow2);
 }
 
-__device__ __forceinline__ void load_pow2(uint8_t (*s)[256], int N) {
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(g_pow2);
-    uint32_t *dst = reinterpret_cast<uint32_t *>(s);
-    for (int i = threadIdx.x; i < N * 64; i += blockDim.x) dst[i] = src[i];
-}
-
 __device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
 
 template <typename T>
@@ -858,39 +908,34 @@ __device__ __forceinline__ PlaneArgs resid_args(const JobDesc<T> &j, int X) {
 // K-contiguous source.  Item: 256 consecutive groups of 8 h in row-major order
 // (rows shorter than 2048 share an item, so no thread idles); 8 consecutive h
 // per thread, one 16-byte store per plane.
-template <typename T, int CAP>
-__global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ JobGroup<T, CAP> G) {
-    __shared__ __align__(16) uint8_t pow2[kNMax][256];
-    load_pow2(pow2, kNMax);
-    __syncthreads();
-    for_items(G, [&](const JobDesc<T> &j, long long li) {
-        int X = 0;
-        const long long n0 = items_kc_x(j, 0);
-        if (li >= n0) { X = 1; li -= n0; }
-        const PlaneArgs a = resid_args(j, X);
-        const Operand<T> &op = j.op[X];
-        const int N = *a.n_dev;
-        const long pw16 = a.plane / 8;
-        const unsigned k8 = unsigned(a.k_pad / 8);
-        const unsigned long long g = (unsigned long long)li * 256u + threadIdx.x;
-        const unsigned long long rq = (g >> 32) == 0 ? unsigned(g) / k8 : g / k8;
-        if (rq >= (unsigned long long)a.R_pad) return;   // the last item's tail (none while 256 | R_pad k_pad / 8)
-        const int r = int(rq), h0 = int(g - rq * k8) * 8;
-        uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
-        if (r >= op.R) {
-            for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
-            return;
-        }
-        const int shift = a.shift[r];
-        // this row's own bound: where a warp spans several short rows, lanes on
-        // both sides of a limb-count limit diverge (rare: the scaling gives
-        // neighbouring rows nearly the same bit length; a warp-wide maximum
-        // measured slower)
-        const int need = a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20;
-        T x[8];
-        load8(op.ptr + (long)r * op.ld + h0, a.k - h0, x);
-        emit_resid8(dst, pw16, N, x, shift, need, pow2);
-    });
+template <typename T>
+__device__ __forceinline__ void resid_kc_item(const JobDesc<T> &j, long long li, const uint8_t (*pow2)[256]) {
+    int X = 0;
+    const long long n0 = items_kc_x(j, 0);
+    if (li >= n0) { X = 1; li -= n0; }
+    const PlaneArgs a = resid_args(j, X);
+    const Operand<T> &op = j.op[X];
+    const int N = *a.n_dev;
+    const long pw16 = a.plane / 8;
+    const unsigned k8 = unsigned(a.k_pad / 8);
+    const unsigned long long g = (unsigned long long)li * 256u + threadIdx.x;
+    const unsigned long long rq = (g >> 32) == 0 ? unsigned(g) / k8 : g / k8;
+    if (rq >= (unsigned long long)a.R_pad) return;   // the last item's tail (none while 256 | R_pad k_pad / 8)
+    const int r = int(rq), h0 = int(g - rq * k8) * 8;
+    uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
+    if (r >= op.R) {
+        for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
+        return;
+    }
+    const int shift = a.shift[r];
+    // this row's own bound: where a warp spans several short rows, lanes on
+    // both sides of a limb-count limit diverge (rare: the scaling gives
+    // neighbouring rows nearly the same bit length; a warp-wide maximum
+    // measured slower)
+    const int need = a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20;
+    T x[8];
+    load8(op.ptr + (long)r * op.ld + h0, a.k - h0, x);
+    emit_resid8(dst, pw16, N, x, shift, need, pow2);
 }
 
 // R-contiguous source.  Item: a 64 (r) x 64 (h) tile transposed through shared
@@ -901,54 +946,63 @@ __device__ __forceinline__ int resid_swz(int hh) {
     return (hh & ~7) | (((((hh >> 1) & 3) ^ ((hh >> 4) & 3))) << 1) | (hh & 1);
 }
 
+template <typename T>
+__device__ __forceinline__ void resid_rc_item(const JobDesc<T> &j, long long li, const uint8_t (*pow2)[256],
+                                              T (*tile)[65]) {
+    int X = 0;
+    const long long n0 = items_rc_x(j, 0);
+    if (li >= n0) { X = 1; li -= n0; }
+    const PlaneArgs a = resid_args(j, X);
+    const Operand<T> &op = j.op[X];
+    const int N = *a.n_dev;
+    const long pw16 = a.plane / 8;
+    const unsigned nrb = unsigned(a.R_pad / 64), ui = unsigned(li);
+    const int hb = int(ui / nrb);
+    const int h_base = hb * 64, r_base = int(ui - unsigned(hb) * nrb) * 64;
+    __syncthreads();                     // the previous item's reads of the tile are done
+    {
+        const int rr = threadIdx.x & 63;
+        const int r = r_base + rr;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int hh = (threadIdx.x >> 6) + 4 * i;
+            const int h = h_base + hh;
+            tile[rr][resid_swz(hh)] = (r < op.R && h < a.k) ? op.ptr[(long)h * op.ld + r] : T(0);
+        }
+    }
+    __syncthreads();
+    const int tc = threadIdx.x & 7;
+    const int h0 = h_base + 8 * tc;
+#pragma unroll 1
+    for (int i = 0; i < 2; i++) {
+        const int rr = (threadIdx.x >> 3) + 32 * i;
+        const int r = r_base + rr;
+        const bool live = r < op.R;
+        const int shift = live ? a.shift[r] : 0;
+        const int need = warp_max(live ? (a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20) : 0);
+        uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
+        if (!live) {
+            for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
+            continue;
+        }
+        T x[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[e] = tile[rr][resid_swz(8 * tc + e)];
+        emit_resid8(dst, pw16, N, x, shift, need, pow2);
+    }
+}
+
+// Residues of K-contiguous rows (resident blocks looping over the items).
+template <typename T, int CAP>
+__global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ JobGroup<T, CAP> G) {
+    for_items(G, [&](const JobDesc<T> &j, long long li) { resid_kc_item(j, li, g_pow2); });
+}
+
+// Residues of transposed rows (resident blocks looping over the items).
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256, 3) k_resid_rc(const __grid_constant__ JobGroup<T, CAP> G) {
-    __shared__ __align__(16) uint8_t pow2[kNMax][256];
     __shared__ T tile[64][65];               // [r][swizzled h]
-    load_pow2(pow2, kNMax);
-    for_items(G, [&](const JobDesc<T> &j, long long li) {
-        int X = 0;
-        const long long n0 = items_rc_x(j, 0);
-        if (li >= n0) { X = 1; li -= n0; }
-        const PlaneArgs a = resid_args(j, X);
-        const Operand<T> &op = j.op[X];
-        const int N = *a.n_dev;
-        const long pw16 = a.plane / 8;
-        const unsigned nrb = unsigned(a.R_pad / 64), ui = unsigned(li);
-        const int hb = int(ui / nrb);
-        const int h_base = hb * 64, r_base = int(ui - unsigned(hb) * nrb) * 64;
-        __syncthreads();                     // pow2 is loaded; the previous item's reads are done
-        {
-            const int rr = threadIdx.x & 63;
-            const int r = r_base + rr;
-#pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const int hh = (threadIdx.x >> 6) + 4 * i;
-                const int h = h_base + hh;
-                tile[rr][resid_swz(hh)] = (r < op.R && h < a.k) ? op.ptr[(long)h * op.ld + r] : T(0);
-            }
-        }
-        __syncthreads();
-        const int tc = threadIdx.x & 7;
-        const int h0 = h_base + 8 * tc;
-#pragma unroll 1
-        for (int i = 0; i < 2; i++) {
-            const int rr = (threadIdx.x >> 3) + 32 * i;
-            const int r = r_base + rr;
-            const bool live = r < op.R;
-            const int shift = live ? a.shift[r] : 0;
-            const int need = warp_max(live ? (a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20) : 0);
-            uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
-            if (!live) {
-                for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
-                continue;
-            }
-            T x[8];
-#pragma unroll
-            for (int e = 0; e < 8; e++) x[e] = tile[rr][resid_swz(8 * tc + e)];
-            emit_resid8(dst, pw16, N, x, shift, need, pow2);
-        }
-    });
+    for_items(G, [&](const JobDesc<T> &j, long long li) { resid_rc_item(j, li, g_pow2, tile); });
 }
 
 // ============================================================= tcgen05 GEMM
@@ -1456,28 +1510,31 @@ __global__ void __launch_bounds__(256) k_bound(const __grid_constant__ JobGroup<
 
 // The N rule: smallest N in [2, nmax] with
 //   t_N (maxR max2b + max2a maxK) + (k + gN_N) t_N^2 max2a max2b <= tau * L,
-// else nmax.
-__device__ __forceinline__ int choose_n(const unsigned long long *red, int k, double tau, int nmax, int fp32,
-                                        int cw) {
+// else nmax.  Called by all lanes of one warp: lane c tests N = base + c for
+// 32 candidates at a time, and the lowest passing lane decides.
+__device__ __forceinline__ bool n_passes(const unsigned long long *red, int c, int k, double tau, int fp32, int cw) {
+    const DevN &d = fp32 ? c_n32[c] : c_n64[c];
     if (cw) {
         // componentwise: t_N max(X / L) + (k + gN_N) t_N^2 max(Y / L) <= tau
         const double xm = __longlong_as_double((long long)red[5]);
         const double ym = __longlong_as_double((long long)red[7]);
-        for (int c = 2; c <= nmax; c++) {
-            const DevN &d = fp32 ? c_n32[c] : c_n64[c];
-            if (d.t * xm + (double(k) + d.gN) * d.t * d.t * ym <= tau) return c;
-        }
-        return nmax;
+        return d.t * xm + (double(k) + d.gN) * d.t * d.t * ym <= tau;
     }
     const double maxR = __longlong_as_double((long long)red[0]);
     const double maxK = __longlong_as_double((long long)red[1]);
     const double m2a = __longlong_as_double((long long)red[2]);
     const double m2b = __longlong_as_double((long long)red[3]);
     const double L = __longlong_as_double((long long)red[4]);
-    for (int c = 2; c <= nmax; c++) {
-        const DevN &d = fp32 ? c_n32[c] : c_n64[c];
-        const double T = d.t * (maxR * m2b + m2a * maxK) + (double(k) + d.gN) * d.t * d.t * m2a * m2b;
-        if (T <= tau * L) return c;
+    const double T = d.t * (maxR * m2b + m2a * maxK) + (double(k) + d.gN) * d.t * d.t * m2a * m2b;
+    return T <= tau * L;
+}
+__device__ __forceinline__ int choose_n(const unsigned long long *red, int k, double tau, int nmax, int fp32,
+                                        int cw) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 2; base <= nmax; base += 32) {
+        const int c = base + lane;
+        const unsigned ok = __ballot_sync(0xffffffffu, c <= nmax && n_passes(red, c, k, tau, fp32, cw));
+        if (ok) return base + __ffs(int(ok)) - 1;
     }
     return nmax;
 }
@@ -1493,12 +1550,14 @@ __global__ void __launch_bounds__(256) k_exponents(const __grid_constant__ JobGr
     __shared__ int sN;
     for_items(G, [&](const JobDesc<T> &j, long long li) {
         __syncthreads();                     // the previous item has read sN
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             const int N = j.nmoduli > 0 ? j.nmoduli : choose_n(j.red, j.k, j.target, j.nmax, fp32, j.cw);
-            sN = N;
-            if (li == 0) {
-                *j.ndev = N;
-                if (j.n_out) *j.n_out = N;
+            if (threadIdx.x == 0) {
+                sN = N;
+                if (li == 0) {
+                    *j.ndev = N;
+                    if (j.n_out) *j.n_out = N;
+                }
             }
         }
         __syncthreads();
@@ -1674,25 +1733,37 @@ __device__ __forceinline__ int dp2a_hi(uint32_t a, uint32_t b, int c) {
 // One row i, columns j0 .. j0+3 of one thread; load(l) gives the four W_l
 // bytes of those columns (zero for l >= N).  C'(1) and C'(2) are sums of
 // integer multiples of fixed grids, taken exactly: each constant is cut into
-// four 16-bit pieces, and one dp2a adds piece * W for two planes of one column
-// into a 32-bit sum (|sum| < 2^16 128 49 < 2^31).  The piece sums are then put
+// 16-bit pieces (s_l1 / g, below 2^48, into three; s_l2 / 2^esum into four),
+// and one dp2a adds piece * W for two planes of one column into a 32-bit sum
+// (|sum| < 2^16 128 49 < 2^31).  The piece sums are then put
 // together in 64-bit integers and rounded once.
-template <typename T, typename Load>
+template <typename T, int AHEAD, typename Load>
 __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, const int32_t *mu,
                                         const int32_t *nu, T *C, long ldc, int n, int i, int j0, bool accum) {
     constexpr int B = sizeof(T) == 8 ? 64 : 32;
-    int s1[4][4], s2[4][4];                    // [column][piece]: C'(1) (b = 64 only), C'(2) / b = 32 C'(1)
+    int s1[4][3], s2[4][4];                    // [column][piece]: C'(1) (b = 64 only), C'(2) / b = 32 C'(1)
 #pragma unroll
-    for (int e = 0; e < 4; e++)
+    for (int e = 0; e < 4; e++) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) s1[e][q] = s2[e][q] = 0;
+        for (int q = 0; q < 3; q++) s1[e][q] = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) s2[e][q] = 0;
+    }
     const int pairs = (N + 1) / 2;
-    // software pipeline: the next pair's loads are in flight while a pair is summed
-    uint32_t w0 = load(0), w1 = load(1);
+    // software pipeline: the next AHEAD (1 or 2) pairs' loads are in flight while a pair is summed
+    static_assert(AHEAD == 1 || AHEAD == 2, "prefetch depth");
+    uint32_t w0 = load(0), w1 = load(1), v0 = AHEAD == 2 ? load(2) : 0u, v1 = AHEAD == 2 ? load(3) : 0u;
     for (int pi = 0; pi < pairs; pi++) {
         const uint32_t p0 = w0, p1 = w1;
-        w0 = load(2 * pi + 2);
-        w1 = load(2 * pi + 3);
+        if (AHEAD == 2) {
+            w0 = v0;
+            w1 = v1;
+            v0 = load(2 * pi + 4);
+            v1 = load(2 * pi + 5);
+        } else {
+            w0 = load(2 * pi + 2);
+            w1 = load(2 * pi + 3);
+        }
         // bytes of columns (0, 1) and (2, 3), planes 2 pi and 2 pi + 1 side by side
         const uint32_t x01 = __byte_perm(p0, p1, 0x5140), x23 = __byte_perm(p0, p1, 0x7362);
         const uint4 c2 = B == 64 ? c_dp64[d.poff + pi][1] : c_dp32[d.poff + pi];
@@ -1705,10 +1776,10 @@ __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, 
             s2[3][q] = dp2a_hi(cc2[q], x23, s2[3][q]);
         }
         if (B == 64) {
-            const uint4 c1 = c_dp64[d.poff + pi][0];
-            const uint32_t cc1[4] = {c1.x, c1.y, c1.z, c1.w};
+            const uint4 c1 = c_dp64[d.poff + pi][0];   // piece 3 is zero: s_l1 / g < 2^48
+            const uint32_t cc1[3] = {c1.x, c1.y, c1.z};
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
+            for (int q = 0; q < 3; q++) {
                 s1[0][q] = dp2a_lo(cc1[q], x01, s1[0][q]);
                 s1[1][q] = dp2a_hi(cc1[q], x01, s1[1][q]);
                 s1[2][q] = dp2a_lo(cc1[q], x23, s1[2][q]);
@@ -1729,12 +1800,11 @@ __device__ __forceinline__ void crt_row(const Load &load, int N, const DevN &d, 
                                           ((unsigned long long)(long long)s2[e][3] << 16));
         double cpp;
         if (B == 64) {
-            // C'(1) = H g exactly, |H| < 2^53 (Lemma 2): the four piece sums added
+            // C'(1) = H g exactly, |H| < 2^53 (Lemma 2): the three piece sums added
             // modulo 2^64, which is exact because H fits
             const unsigned long long Hu = (unsigned long long)(long long)s1[e][0] +
                                           ((unsigned long long)(long long)s1[e][1] << 16) +
-                                          ((unsigned long long)(long long)s1[e][2] << 32) +
-                                          ((unsigned long long)(long long)s1[e][3] << 48);
+                                          ((unsigned long long)(long long)s1[e][2] << 32);
             // Q: y = (H >> 22) kq 2^-sq is within 2^-15 of H g / P and FP64's
             // P_inv C'(1) within 2^-38 of it, so both have the nearest integer
             // of y unless y lies within 2^-14 of a half-integer (then FP64 decides)
@@ -1780,7 +1850,7 @@ __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, 
     for (int i = blockIdx.y; i < m; i += gridDim.y) {
         if (j0 >= n) continue;
         const int8_t *wp = W + (long)i * n_pad + j0;
-        crt_row<T>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane)) : 0u; },
+        crt_row<T, 2>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * w_plane)) : 0u; },
                    N, d, mu, nu, C, ldc, n, i, j0, accum != 0);
     }
 }
@@ -1800,7 +1870,7 @@ __global__ void __launch_bounds__(256, 4) k_crt(const __grid_constant__ JobGroup
         const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
         const int8_t *wp = jd.W + (long)i * jd.n_pad + j0;
         const long wpl = jd.w_plane;
-        crt_row<T>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)) : 0u; },
+        crt_row<T, 1>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)) : 0u; },
                    N, d, jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0, jd.accum != 0);
     });
 }

@@ -364,9 +364,11 @@ void build(Tables &T) {
             long double hb = 0;
             for (int l = 0; l < N; l++) hb += (long double)(kModuli[l] / 2) * (long double)T.s1i[offset + l];
             T.sums_fit &= N < 2 || (hb < 0x1p53L && T.n64[N].esum >= -1022);
-            // the dp2a form rebuilds H from four 16-bit piece sums modulo 2^64, which is
-            // exact while |H| < 2^63; each piece sum stays below 2^16 128 49 < 2^31
+            // the dp2a form rebuilds H from three 16-bit piece sums modulo 2^64, which is
+            // exact while |H| < 2^63; each piece sum stays below 2^16 128 49 < 2^31, and
+            // the fourth piece of every s_l1 / g is zero
             T.sums_fit &= h < 0x1p62L;
+            for (int l = 0; l < N; l++) T.sums_fit &= uint64_t(T.s1i[offset + l]) < (uint64_t(1) << 48);
         }
         {   // 16-bit pieces of the constants, two planes per word (the last pair of
             // an odd N pairs its plane with a zero)
