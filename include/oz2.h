@@ -357,6 +357,13 @@ OZ2_API int oz2_gemm_noalloc(int m, int n, int k, const double *A, int lda, cons
  * the library source line that caught it.  For diagnostics. */
 OZ2_API int oz2_last_error(int *line);
 
+/* The number of kernels this library has launched in this process so far (all
+ * host threads, all devices; diagnostic kernels included).  For accounting:
+ * the difference over a span of calls is the number of kernels they enqueued
+ * (a call's count depends on its sizes: small problems merge some phases into
+ * one launch).  Not part of the paper's method. */
+OZ2_API long long oz2_launch_count(void);
+
 /* Human-readable name of a status code (static string). */
 OZ2_API const char *oz2_status_str(int status);
 

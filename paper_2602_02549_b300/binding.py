@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         L.oz2_status_str.argtypes = [i]
         L.oz2_status_str.restype = ctypes.c_char_p
         L.oz2_version.restype = i
+        L.oz2_launch_count.argtypes = []
+        L.oz2_launch_count.restype = ctypes.c_longlong
         L.oz2_last_error.argtypes = [P]
         L.oz2_last_error.restype = i
         _lib = L
@@ -412,6 +414,11 @@ def zmatmul(A, B, nmoduli: int = 0, *, target: float = 1e-15, nmax: int = 0, tra
     if rc:
         raise Oz2Error(rc, "oz2 complex gemm")
     return C
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process so far (oz2_launch_count)."""
+    return int(lib().oz2_launch_count())
 
 
 def sync(stream=None) -> int:

@@ -47,6 +47,7 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 // Last CUDA failure seen by the library (for oz2_last_error): the error code
 // and the source line of the check that caught it.
 std::atomic<int> g_last_cuda_error{0};
+std::atomic<long long> g_launches{0};      // kernels launched (oz2_launch_count)
 std::atomic<int> g_last_cuda_line{0};
 
 int cuda_fail_at(cudaError_t e, int line) {
@@ -226,6 +227,7 @@ int launch_gemm(GemmGroup<CAP> &G, int sms, cudaStream_t st) {
     if (items == 0) return OZ2_OK;
     const int grid = int(std::min<long long>(items, sms));
     k_gemm<EPI, BN, CAP><<<grid, gemm::kThreads, gemm::Cfg<BN>::kSmemBytes, st>>>(G);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -342,15 +344,17 @@ struct Job {
     const int32_t *nu_use() const { return inject() ? nu_in : nu; }
 
     // the residue planes and their tensor maps (plane 0 holds Abar / Bbar first)
-    int describe(GemmProblem &P) const {
+    // tile width w: the problem's own (bn), or 128 where n_pad is a multiple of 256
+    int describe(GemmProblem &P, int w = 0) const {
+        if (w == 0) w = bn;
         int rc = encode_bf16_2d(&P.tmA, resA, uint64_t(nmax) * d.m_pad, uint64_t(d.k_pad), gemm::BM);
         if (rc) return rc;
-        if ((rc = encode_bf16_2d(&P.tmB, resB, uint64_t(nmax) * d.n_pad, uint64_t(d.k_pad), uint32_t(bn)))) return rc;
+        if ((rc = encode_bf16_2d(&P.tmB, resB, uint64_t(nmax) * d.n_pad, uint64_t(d.k_pad), uint32_t(w)))) return rc;
         P.m_pad = d.m_pad;
         P.n_pad = d.n_pad;
         P.kb_total = d.k_pad / gemm::BK;
         P.tiles_m = d.m_pad / gemm::BM;
-        P.tiles_n = d.n_pad / bn;
+        P.tiles_n = d.n_pad / w;
         P.plane0 = 0;
         P.cw_row = P.cw_col = nullptr;
         P.cw_red = nullptr;
@@ -518,6 +522,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     if ((g = plan(Items<T>::items, cap)) < 0) return OZ2_ENOTSUP;   \
     if (g > 0) {                                                    \
         kernel<T, CAP><<<g, 256, 0, st>>>(J);                       \
+        g_launches.fetch_add(1, std::memory_order_relaxed);         \
         if ((rc = launched())) return rc;                           \
     }
     // heaviest problems first: the longest-processing-time order balances the
@@ -532,15 +537,27 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
     // one persistent launch per GEMM phase and tile width: EPI_MAX the scaling
     // GEMM, EPI_CW the componentwise rule's second product, EPI_MOD the residues
+    // The scaling GEMM (one plane) of a launch with at most half as many 128 x 256
+    // tiles as SMs runs on 128 x 128 tiles: twice the CTAs at work, still one
+    // round (1024^3: 16 -> 13 us); larger launches keep each problem's width.
+    bool narrow_scale = true;
+    {
+        long long tiles = 0;
+        for (int p = 0; p < count; p++)
+            if (jobs[p]->needs_scale_gemm())
+                tiles += (long long)(jobs[p]->d.m_pad / gemm::BM) * (jobs[p]->d.n_pad / jobs[p]->bn);
+        narrow_scale = 2 * tiles <= sms;
+    }
+    auto width = [&](const Job<T> &job, int epi) { return epi == EPI_MAX && narrow_scale ? 128 : job.bn; };
     auto gemms = [&](int epi) -> int {
         for (int bn : {256, 128}) {
             std::memset(&G, 0, sizeof G);
             for (int idx = 0; idx < count; idx++) {
                 const Job<T> &job = *jobs[order[idx]];
-                if (job.bn != bn) continue;
+                if (width(job, epi) != bn) continue;
                 if ((epi == EPI_MAX && !job.needs_scale_gemm()) || (epi == EPI_CW && !job.cw())) continue;
                 GemmProblem &P = G.p[G.count++];
-                int r = job.describe(P);
+                int r = job.describe(P, bn);
                 if (r) return r;
                 if (epi == EPI_MAX) job.as_scale_gemm(P);
                 else if (epi == EPI_CW) job.as_cw_gemm(P);
@@ -600,6 +617,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
         dim3 grid(unsigned(cdiv(j.n, kCrtCols)), unsigned(std::min(j.m, 65535)));
         k_crt_one<T><<<grid, 256, 0, st>>>(j.W, j.w_plane, long(j.n_pad), j.ndev, j.shift[0], j.shift[1], j.C,
                                              j.ldc, j.m, j.n, j.accum);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
         if ((rc = launched())) return rc;
     } else {
         OZ2_LAUNCH(k_crt, crt, one_each)
@@ -745,6 +763,7 @@ int run_complex(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T
                      int ldy) {
         dim3 grid(unsigned(cdiv(L, 256)), unsigned(std::min(R, 65535)));
         k_zsplit<T><<<grid, 256, 0, st>>>(X, ldx, R, L, stacked ? 1 : 0, im0, neg0, im1, neg1, Y, ldy);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
         return cuda_fail(cudaGetLastError());
     };
     // A_s: m x 2k side by side, or (transposed) 2k x m stacked
@@ -774,6 +793,7 @@ int run_complex(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T
     }
     dim3 grid(unsigned(cdiv(n, 256)), unsigned(std::min(m, 65535)));
     k_zmerge<T><<<grid, 256, 0, st>>>(Cre, Cim, n, m, n, C, ldc);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -1178,6 +1198,7 @@ int oz2_check_log2f(void *stream, unsigned long long *dev_out) {
     rc = cuda_fail(cudaMemsetAsync(dev_out, 0, 2 * sizeof(unsigned long long), st));
     if (rc) return rc;
     k_log2f_check<<<148 * 8, 256, 0, st>>>(b0, b1 - b0 + 1, dev_out);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -1186,6 +1207,7 @@ int oz2_wait_selftest(void *stream, unsigned int limit_us) {
     int dev = 0, rc = ensure_device(&dev);
     if (rc) return rc;
     k_wait_selftest<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(uint64_t(limit_us) * 1000ull);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cuda_fail(cudaGetLastError());
 }
 
@@ -1216,6 +1238,8 @@ const char *oz2_status_str(int s) {
     default: return "unknown status";
     }
 }
+
+long long oz2_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int oz2_version(void) { return 100; }
 
