@@ -85,6 +85,16 @@ def test_argument_validation(lib, fp32):
     assert call(lib, N=0, opts=o, fp32=fp32) == E
 
 
+def test_argument_errors_launch_nothing(lib):
+    """Argument errors come back before any launch: the library's own kernel
+    count does not move."""
+    before = B.launch_count()
+    assert call(lib, m=0) == B.OZ2_EINVAL
+    assert call(lib, ldc=7, fp32=True) == B.OZ2_EINVAL
+    assert call(lib, N=50) == B.OZ2_EINVAL
+    assert B.launch_count() == before
+
+
 def test_workspace_size(lib):
     assert B.workspace_size(0, 8, 8, 14) == 0
     # k > 2^17: the ranges share one workspace sized for the longest range
