@@ -348,6 +348,14 @@ template <typename T, int CAP, class F>
 __device__ __forceinline__ void for_items(const JobGroup<T, CAP> &G, F &&f) {
     const long long total = G.begin[G.count];
     int p = 0;
+    if (CAP > 1 && blockIdx.x < total) {     // the first item's problem by bisection
+        int hi = G.count - 1;
+        while (p < hi) {
+            const int mid = (p + hi + 1) >> 1;
+            if (G.begin[mid] <= (long long)blockIdx.x) p = mid;
+            else hi = mid - 1;
+        }
+    }
     for (long long g = blockIdx.x; g < total; g += gridDim.x) {
         while (G.begin[p + 1] <= g) p++;
         f(G.j[p], g - G.begin[p]);
@@ -1064,10 +1072,11 @@ struct WorkItem {
 // Work item g -> (problem, plane, tile).  Planes run in order; inside a plane
 // the tiles go column by column through groups of GROUP_M row tiles, so the
 // CTAs working at the same time share few A and B panels (L2 reuse).
+// p: the problem of the caller's previous item (0 at first); a caller's items
+// increase, so the search for g's problem resumes there.
 template <int CAP>
-__device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long long g) {
+__device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long long g, int &p) {
     WorkItem w;
-    int p = 0;
     while (p + 1 < G.count && G.p[p + 1].item_begin <= g) p++;
     const GemmProblem &P = G.p[p];
     const long long li = g - P.item_begin;
@@ -1289,8 +1298,9 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         if (lane == 0) {
             uint32_t kbc = 0;                    // stage ring position, across items
             bool ok = true, first = true;
+            int pcur = 0;
             for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
-                const WorkItem w = decode_item(G, g);
+                const WorkItem w = decode_item(G, g, pcur);
                 if (w.skip) continue;
                 const GemmProblem &P = G.p[w.p];
                 const int row_a = (P.plane0 + w.l) * P.m_pad + w.tile_m * BM;
@@ -1312,8 +1322,9 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         if (lane == 0) {
             uint32_t kbc = 0, segc = 0;
             bool ok = true;
+            int pcur = 0;
             for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
-                const WorkItem w = decode_item(G, g);
+                const WorkItem w = decode_item(G, g, pcur);
                 if (w.skip) continue;
                 const GemmProblem &P = G.p[w.p];
                 const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
@@ -1349,8 +1360,9 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         const int half = (warp - 2) >> 2;       // columns [NC half, NC half + NC)
         uint32_t segc = 0;
         bool ok = true;
+        int pcur = 0;
         for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
-            const WorkItem w = decode_item(G, g);
+            const WorkItem w = decode_item(G, g, pcur);
             if (w.skip) continue;
             const GemmProblem &P = G.p[w.p];
             const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
