@@ -219,7 +219,9 @@ int launch_gemm(GemmGroup<CAP> &G, int sms, cudaStream_t st) {
     for (int p = 0; p < G.count; p++) {
         GemmProblem &P = G.p[p];
         P.item_begin = items;
-        items += (long long)P.tiles_m * P.tiles_n * P.planes;
+        const long long np = (long long)P.tiles_m * P.tiles_n * P.planes;
+        if (np >= (1ll << 31)) return OZ2_ENOTSUP;   // the kernel decodes a problem's items in 32 bits
+        items += np;
     }
     G.total_items = items;
     G.wait_limit_ns = EPI == EPI_MOD ? g_hook.limit_ns : kWaitLimitNs;

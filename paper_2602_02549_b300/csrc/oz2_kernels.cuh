@@ -1079,18 +1079,19 @@ __device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long lo
     WorkItem w;
     while (p + 1 < G.count && G.p[p + 1].item_begin <= g) p++;
     const GemmProblem &P = G.p[p];
-    const long long li = g - P.item_begin;
-    const int per_plane = P.tiles_m * P.tiles_n;
+    // a problem's items number below 2^31 (tiles x planes), so 32-bit division
+    const unsigned li = unsigned(g - P.item_begin);
+    const unsigned per_plane = unsigned(P.tiles_m * P.tiles_n);
     w.p = p;
     w.l = int(li / per_plane);
-    const int t = int(li - (long long)w.l * per_plane);
-    const int span = gemm::GROUP_M * P.tiles_n;
-    const int grp = t / span;
-    const int first_m = grp * gemm::GROUP_M;
-    const int gm = min(gemm::GROUP_M, P.tiles_m - first_m);
-    const int tin = t - grp * span;
-    w.tile_m = first_m + tin % gm;
-    w.tile_n = tin / gm;
+    const unsigned t = li - unsigned(w.l) * per_plane;
+    const unsigned span = unsigned(gemm::GROUP_M * P.tiles_n);
+    const unsigned grp = t / span;
+    const int first_m = int(grp) * gemm::GROUP_M;
+    const unsigned gm = unsigned(min(gemm::GROUP_M, P.tiles_m - first_m));
+    const unsigned tin = t - grp * span;
+    w.tile_m = first_m + int(tin % gm);
+    w.tile_n = int(tin / gm);
     w.skip = P.n_dev != nullptr && w.l >= *P.n_dev;
     return w;
 }
