@@ -481,7 +481,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     std::memset(&J, 0, sizeof J);
     J.count = count;
     for (int p = 0; p < count; p++) J.j[p] = jobs[p]->desc();
-    // k_absmax: items as wide as the lines allow (absmax_lw_min); while the whole
+    // k_absmax: items of the width that wastes the fewest positions (absmax_lw_min); while the whole
     // launch would give fewer than two blocks per SM, narrower items (more line
     // groups per block), and then, while it would give fewer than one, fewer
     // lines per item.  Each item ends in one atomicMax per position and per

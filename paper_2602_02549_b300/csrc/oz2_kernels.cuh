@@ -265,13 +265,19 @@ __host__ __device__ __forceinline__ long long items_absmax_x(const JobDesc<T> &j
     absmax_geom(j, X, S, C);
     return cdiv(S, j.absmax_lb) * cdiv(C, 2048 / j.absmax_lw[X]);
 }
-// the fewest line groups (widest items) that leave no warp of a block without
-// positions: 8 / lw position groups of 256 cover at most C rounded up to 256
+// the item width for lines of C positions: the one that leaves the fewest idle
+// positions (the host may narrow it further for small launches)
 __host__ __device__ __forceinline__ int absmax_lw_min(int C) {
-    const long long pg = cdiv(C, 256);
-    int lw = 1;
-    while (lw < 8 && 8 / lw > pg) lw <<= 1;
-    return lw;
+    // the fewest positions past C over the item columns (ties: fewer line
+    // groups, i.e. wider items)
+    int best = 8;
+    long long least = -1;
+    for (int lw = 8; lw >= 1; lw >>= 1) {
+        const long long pw = 2048 / lw;
+        const long long waste = cdiv(C, pw) * pw - C;
+        if (least < 0 || waste <= least) { least = waste; best = lw; }
+    }
+    return best;
 }
 // Residues of K-contiguous rows: 256 consecutive groups of 8 positions per
 // item, in the row-major order of the R_pad x k_pad plane (R_pad x k_pad / 8
@@ -296,10 +302,16 @@ __host__ __device__ __forceinline__ long long items_rc_x(const JobDesc<T> &j, in
 // threads idle
 constexpr int kQuantGroups = 4;
 __host__ __device__ __forceinline__ int quant_tpr(int k_pad) {
-    const long long need = cdiv(k_pad, 8 * kQuantGroups);
-    int t = 8;
-    while (t < 256 && t < need) t <<= 1;
-    return t;
+    // the width whose items leave the fewest h positions past k_pad (ties: the
+    // wider, with fewer items per row and so fewer atomic row sums)
+    int best = 8;
+    long long least = -1;
+    for (int t = 8; t <= 256; t <<= 1) {
+        const long long per = (long long)t * 8 * kQuantGroups;
+        const long long waste = cdiv(k_pad, per) * per - k_pad;
+        if (least < 0 || waste <= least) { least = waste; best = t; }
+    }
+    return best;
 }
 template <typename T>
 __host__ __device__ __forceinline__ long long items_quant_kc_x(const JobDesc<T> &j, int X) {
