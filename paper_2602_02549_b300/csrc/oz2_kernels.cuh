@@ -18,6 +18,7 @@
 //                             inverse scaling of Algorithm 1
 #pragma once
 #include <cuda_bf16.h>
+#include <climits>
 #include <cstdint>
 
 #include "oz2_ptx.cuh"
@@ -1084,13 +1085,23 @@ struct WorkItem {
 // Work item g -> (problem, plane, tile).  Planes run in order; inside a plane
 // the tiles go column by column through groups of GROUP_M row tiles, so the
 // CTAs working at the same time share few A and B panels (L2 reuse).
-// p: the problem of the caller's previous item (0 at first); a caller's items
-// increase, so the search for g's problem resumes there.
+// A role's position in the item space: the problem of its previous item and
+// that problem's plane count N (INT_MAX where all planes run).  A role's items
+// increase, so the search for the next item's problem resumes there, and N is
+// read once per problem.
+struct ItemCursor {
+    int p = -1, n = 0;
+};
 template <int CAP>
-__device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long long g, int &p) {
+__device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long long g, ItemCursor &c) {
     WorkItem w;
+    int p = c.p < 0 ? 0 : c.p;
     while (p + 1 < G.count && G.p[p + 1].item_begin <= g) p++;
     const GemmProblem &P = G.p[p];
+    if (p != c.p) {
+        c.p = p;
+        c.n = P.n_dev != nullptr ? *P.n_dev : INT_MAX;
+    }
     // a problem's items number below 2^31 (tiles x planes), so 32-bit division
     const unsigned li = unsigned(g - P.item_begin);
     const unsigned per_plane = unsigned(P.tiles_m * P.tiles_n);
@@ -1104,8 +1115,19 @@ __device__ __forceinline__ WorkItem decode_item(const GemmGroup<CAP> &G, long lo
     const unsigned tin = t - grp * span;
     w.tile_m = first_m + int(tin % gm);
     w.tile_n = int(tin / gm);
-    w.skip = P.n_dev != nullptr && w.l >= *P.n_dev;
+    w.skip = w.l >= c.n;
     return w;
+}
+
+// Planes l >= N come last in a problem's items: a role that meets one moves g
+// to the last of its items (g + j gridDim) before the next problem's first, so
+// that the loop's increment lands on that first one.
+template <int CAP>
+__device__ __forceinline__ long long skip_to_next_problem(const GemmGroup<CAP> &G, long long g, int p,
+                                                          long long total) {
+    const long long next = p + 1 < G.count ? G.p[p + 1].item_begin : total;
+    const unsigned steps = (unsigned(next - g) + gridDim.x - 1) / gridDim.x;   // >= 1
+    return g + (long long)(steps - 1) * gridDim.x;
 }
 
 __device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
@@ -1311,10 +1333,10 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         if (lane == 0) {
             uint32_t kbc = 0;                    // stage ring position, across items
             bool ok = true, first = true;
-            int pcur = 0;
+            ItemCursor cur;
             for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
-                const WorkItem w = decode_item(G, g, pcur);
-                if (w.skip) continue;
+                const WorkItem w = decode_item(G, g, cur);
+                if (w.skip) { g = skip_to_next_problem(G, g, w.p, total); continue; }
                 const GemmProblem &P = G.p[w.p];
                 const int row_a = (P.plane0 + w.l) * P.m_pad + w.tile_m * BM;
                 const int row_b = (P.plane0 + w.l) * P.n_pad + w.tile_n * BN;
@@ -1335,10 +1357,10 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         if (lane == 0) {
             uint32_t kbc = 0, segc = 0;
             bool ok = true;
-            int pcur = 0;
+            ItemCursor cur;
             for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
-                const WorkItem w = decode_item(G, g, pcur);
-                if (w.skip) continue;
+                const WorkItem w = decode_item(G, g, cur);
+                if (w.skip) { g = skip_to_next_problem(G, g, w.p, total); continue; }
                 const GemmProblem &P = G.p[w.p];
                 const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
                 for (int seg = 0; seg < nseg && ok; seg++, segc++) {
@@ -1373,10 +1395,10 @@ __global__ void __launch_bounds__(gemm::kThreads, 1) k_gemm(const __grid_constan
         const int half = (warp - 2) >> 2;       // columns [NC half, NC half + NC)
         uint32_t segc = 0;
         bool ok = true;
-        int pcur = 0;
+        ItemCursor cur;
         for (long long g = blockIdx.x; g < total && ok; g += gridDim.x) {
-            const WorkItem w = decode_item(G, g, pcur);
-            if (w.skip) continue;
+            const WorkItem w = decode_item(G, g, cur);
+            if (w.skip) { g = skip_to_next_problem(G, g, w.p, total); continue; }
             const GemmProblem &P = G.p[w.p];
             const int nseg = (P.kb_total + SEG_KB - 1) / SEG_KB;
             // EPI_MAX: INT32 sums of the segments; EPI_MOD: FP32 pairs holding the
