@@ -47,8 +47,10 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 // Last CUDA failure seen by the library (for oz2_last_error): the error code
 // and the source line of the check that caught it.
 std::atomic<int> g_last_cuda_error{0};
-std::atomic<long long> g_launches{0};      // kernels launched (oz2_launch_count)
 std::atomic<int> g_last_cuda_line{0};
+
+// Kernels launched by the library in this process (oz2_launch_count).
+std::atomic<long long> g_launches{0};
 
 int cuda_fail_at(cudaError_t e, int line) {
     if (e == cudaSuccess) return OZ2_OK;
