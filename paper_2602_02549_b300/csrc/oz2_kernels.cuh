@@ -288,11 +288,6 @@ __host__ __device__ __forceinline__ long long items_kc_x(const JobDesc<T> &j, in
     if (!j.op[X].kcontig) return 0;
     return cdiv((long long)j.R_pad[X] * (j.k_pad / 8), 256);
 }
-// CRT: threads per row covering n / 4 columns
-__host__ __device__ __forceinline__ int crt_tpr(int n) {
-    int t = int(cdiv(cdiv(n, 4), 32) * 32);
-    return t < 32 ? 32 : (t > 256 ? 256 : t);
-}
 template <typename T>
 __host__ __device__ __forceinline__ long long items_rc_x(const JobDesc<T> &j, int X) {
     return j.op[X].kcontig ? 0 : (long long)(j.k_pad / 64) * (j.R_pad[X] / 64);
@@ -351,8 +346,7 @@ template <typename T> struct Items {
     __host__ __device__ static long long resid_rc(const JobDesc<T> &j) { return items_rc_x(j, 0) + items_rc_x(j, 1); }
     __host__ __device__ static long long quant(const JobDesc<T> &j) { return quant_kc(j) + quant_rc(j); }
     __host__ __device__ static long long crt(const JobDesc<T> &j) {
-        const int tpr = crt_tpr(j.n);
-        return cdiv(j.m, 256 / tpr) * cdiv(j.n, tpr * 4);
+        return cdiv((long long)j.m * cdiv(j.n, 4), 256);
     }
 };
 
@@ -1902,22 +1896,22 @@ __global__ void __launch_bounds__(256) k_crt_one(const int8_t *W, long w_plane, 
     }
 }
 
-// A group of problems.  Item: 256 / tpr rows of tpr x 4 columns (4 per thread,
-// tpr threads per row).
+// A group of problems.  Item: 256 consecutive groups of 4 columns in the
+// problem's row-major order (ceil(n / 4) groups per row; rows shorter than 1024
+// share an item, so no thread idles), 4 columns per thread.
 template <typename T, int CAP>
 __global__ void __launch_bounds__(256, 4) k_crt(const __grid_constant__ JobGroup<T, CAP> G) {
     for_items(G, [&](const JobDesc<T> &jd, long long li) {
-        const int tpr = crt_tpr(jd.n), ly = threadIdx.x / tpr, tx = threadIdx.x - ly * tpr;
-        const unsigned ncb = unsigned(cdiv(jd.n, tpr * 4)), ui = unsigned(li);
-        const int rb = int(ui / ncb);
-        const int i = rb * (256 / tpr) + ly;
-        const int j0 = int(ui - unsigned(rb) * ncb) * tpr * 4 + tx * 4;
-        if (ly >= 256 / tpr || j0 >= jd.n || i >= jd.m) return;
+        const unsigned q = unsigned(cdiv(jd.n, 4));
+        const unsigned long long g = (unsigned long long)li * 256u + threadIdx.x;
+        const unsigned long long iq = (g >> 32) == 0 ? unsigned(g) / q : g / q;
+        if (iq >= (unsigned long long)jd.m) return;            // the last item's tail
+        const int i = int(iq), j0 = int(g - iq * q) * 4;
         const int N = *jd.ndev;
         const DevN d = sizeof(T) == 8 ? c_n64[N] : c_n32[N];
         const int8_t *wp = jd.W + (long)i * jd.n_pad + j0;
         const long wpl = jd.w_plane;
-        crt_row<T, 1>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)) : 0u; },
+        crt_row<T, 2>([&](int l) { return l < N ? __ldg(reinterpret_cast<const uint32_t *>(wp + (long)l * wpl)) : 0u; },
                    N, d, jd.shift[0], jd.shift[1], jd.C, jd.ldc, jd.n, i, j0, jd.accum != 0);
     });
 }
