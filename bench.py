@@ -62,6 +62,9 @@ def parse():
                         "splitk: k beyond 2^17 (K ranges added in FP64); zgemm: complex FP64")
     p.add_argument("--k", type=int, default=4 << 17, help="splitk: the contraction length")
     p.add_argument("--mode", default="accurate", choices=["accurate", "fast"])
+    p.add_argument("--policy", type=int, default=-1, choices=[-1, 0, 1, 2],
+                   help="batched: fixed tile policy (0 all 128x256, 1 all 128x128, 2 128x128 where "
+                        "n mod 256 <= 128); -1 autotunes")
     p.add_argument("--no-forms", action="store_true",
                    help="skip the other forms' sub-records (fast mode, small sizes, SGEMM, autograd, batched)")
     return p.parse_args()
@@ -473,11 +476,14 @@ def form_autograd(dev, target, nmax, fast, steps, warmup, peak, flush):
             "grad_rel_err_vs_fp64": err, "l2": "flushed (256 MiB write) before every timed step"}
 
 
-def form_batched(dev, target, fast, steps, warmup, peak, flush, samples_per_problem=4):
+def form_batched(dev, target, fast, steps, warmup, peak, flush, samples_per_problem=4, policy=-1):
     """64 uneven problems (m, n, k log-uniform in [128, 4096], phi ~ U(0.5, 4)),
     per-problem bound-chosen N for `target`, one oz2_gemm_batched call replayed
     from a CUDA graph, against 64 plain oz2_gemm_ex calls at the fixed N that
-    meets the target for every problem (the largest chosen N)."""
+    meets the target for every problem (the largest chosen N).  policy < 0: the
+    tile policy from oz2_batched_autotune; 0, 1 or 2: that policy, no autotuning
+    (the library's first launches are then the first call's, then the first
+    replay's)."""
     import torch
     from paper_2602_02549_b300 import binding as B
     from paper_2602_02549_b300.accuracy import sampled_errors
@@ -490,7 +496,11 @@ def form_batched(dev, target, fast, steps, warmup, peak, flush, samples_per_prob
                           fast=fast, n_out=torch.zeros(1, dtype=torch.int32, device=dev)))
         flops += 2.0 * m * n * k
     ws = torch.empty(B.batched_workspace_size(probs), dtype=torch.uint8, device=dev)
-    policy, policy_ms = B.batched_autotune(probs, workspace=ws)     # outside the capture
+    if policy < 0:
+        policy, policy_ms = B.batched_autotune(probs, workspace=ws)     # outside the capture
+    else:
+        assert B.batched_set_policy(probs, policy) == 0
+        policy_ms = None
     assert B.gemm_batched(probs, workspace=ws) == 0
     torch.cuda.synchronize()
     Ns = [int(q["n_out"].item()) for q in probs]
@@ -595,7 +605,7 @@ def run_workload(args):
     fast = args.mode == "fast"
     if args.workload == "batched":
         rec = form_batched(dev, 1e-14 if args.target == 1e-15 else args.target, fast, args.steps, args.warmup,
-                           peak, flush)
+                           peak, flush, policy=args.policy)
         metric = METRIC
     elif args.workload == "autograd":
         rec = form_autograd(dev, args.target, args.nmax, fast, args.steps, args.warmup, peak, flush)
