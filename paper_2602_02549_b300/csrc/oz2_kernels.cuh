@@ -281,16 +281,17 @@ __host__ __device__ __forceinline__ int absmax_lw_min(int C) {
     return best;
 }
 // Residues of K-contiguous rows: 256 consecutive groups of 8 positions per
-// item, in the row-major order of the R_pad x k_pad plane (R_pad x k_pad / 8
-// groups in all, a multiple of 256: R_pad is a multiple of 128, k_pad of 64)
+// item, in the row-major order of the plane's R live rows of k_pad positions
+// (R x k_pad / 8 groups in all; the last item may end early).  Transposed
+// rows: 64 x 64 tiles over the R live rows.
 template <typename T>
 __host__ __device__ __forceinline__ long long items_kc_x(const JobDesc<T> &j, int X) {
     if (!j.op[X].kcontig) return 0;
-    return cdiv((long long)j.R_pad[X] * (j.k_pad / 8), 256);
+    return cdiv((long long)j.op[X].R * (j.k_pad / 8), 256);
 }
 template <typename T>
 __host__ __device__ __forceinline__ long long items_rc_x(const JobDesc<T> &j, int X) {
-    return j.op[X].kcontig ? 0 : (long long)(j.k_pad / 64) * (j.R_pad[X] / 64);
+    return j.op[X].kcontig ? 0 : (long long)(j.k_pad / 64) * cdiv(j.op[X].R, 64);
 }
 // quantisation of K-contiguous rows: kQuantGroups chunks of tpr x 8 h per item;
 // tpr is a power of two in [8, 256] with tpr x 8 x kQuantGroups >= k_pad where
@@ -317,7 +318,8 @@ __host__ __device__ __forceinline__ long long items_quant_kc_x(const JobDesc<T> 
 }
 template <typename T>
 __host__ __device__ __forceinline__ long long items_quant_rc_x(const JobDesc<T> &j, int X) {
-    return j.inject ? 0 : items_rc_x(j, X);
+    // every row of R_pad: the scaling GEMM's maxima need zeros in the padding
+    return j.inject || j.op[X].kcontig ? 0 : (long long)(j.k_pad / 64) * (j.R_pad[X] / 64);
 }
 
 template <typename T> struct Items {
@@ -486,7 +488,9 @@ __global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ JobGroup
 
 // ============================================================= planes
 // k_quant_*: Abar = BF16(ceil(2^mu' |x|)), plane 0, K-major, zeros in the padding.
-// k_resid_*: planes l < N = BF16(mod(trunc(2^mu x), p_l)), K-major, zeros in padding.
+// k_resid_*: planes l < N = BF16(mod(trunc(2^mu x), p_l)), K-major, zeros past k in
+// each row; rows R .. R_pad-1 are not written (a padded row of A'_l or B'_l
+// reaches only rows or columns of C'_l past m or n, which the CRT never reads).
 // Output element (l, r, h) at out[l*plane + r*k_pad + h].
 struct PlaneArgs {
     __nv_bfloat16 *out;
@@ -935,13 +939,9 @@ __device__ __forceinline__ void resid_kc_item(const JobDesc<T> &j, long long li,
     const unsigned k8 = unsigned(a.k_pad / 8);
     const unsigned long long g = (unsigned long long)li * 256u + threadIdx.x;
     const unsigned long long rq = (g >> 32) == 0 ? unsigned(g) / k8 : g / k8;
-    if (rq >= (unsigned long long)a.R_pad) return;   // the last item's tail (none while 256 | R_pad k_pad / 8)
+    if (rq >= (unsigned long long)op.R) return;      // the last item's tail
     const int r = int(rq), h0 = int(g - rq * k8) * 8;
     uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
-    if (r >= op.R) {
-        for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
-        return;
-    }
     const int shift = a.shift[r];
     // this row's own bound: where a warp spans several short rows, lanes on
     // both sides of a limb-count limit diverge (rare: the scaling gives
@@ -971,7 +971,7 @@ __device__ __forceinline__ void resid_rc_item(const JobDesc<T> &j, long long li,
     const Operand<T> &op = j.op[X];
     const int N = *a.n_dev;
     const long pw16 = a.plane / 8;
-    const unsigned nrb = unsigned(a.R_pad / 64), ui = unsigned(li);
+    const unsigned nrb = unsigned(cdiv(op.R, 64)), ui = unsigned(li);
     const int hb = int(ui / nrb);
     const int h_base = hb * 64, r_base = int(ui - unsigned(hb) * nrb) * 64;
     __syncthreads();                     // the previous item's reads of the tile are done
@@ -996,10 +996,7 @@ __device__ __forceinline__ void resid_rc_item(const JobDesc<T> &j, long long li,
         const int shift = live ? a.shift[r] : 0;
         const int need = warp_max(live ? (a.row_max ? row_bits(a.row_max[r], shift) : 1 << 20) : 0);
         uint4 *dst = reinterpret_cast<uint4 *>(a.out + (long)r * a.k_pad + h0);
-        if (!live) {
-            for (int l = 0; l < N; l++) dst[(long)l * pw16] = make_uint4(0, 0, 0, 0);
-            continue;
-        }
+        if (!live) continue;
         T x[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) x[e] = tile[rr][resid_swz(8 * tc + e)];
