@@ -549,43 +549,27 @@ __device__ __forceinline__ void flush_row(const PlaneArgs &a, RowAcc acc, int r,
 }
 
 // One element of the quantisation from the bits of x: q = ceil(2^shift |x|)
-// and the 1-norm term floor(|x| 2^(shift+57)) as 32-bit halves (vhi, vlo).
-// A normal double takes 32-bit integer steps: |x| 2^shift = M 2^-r < 64 with
-// the 53-bit significand M >= 2^52 puts r >= 47, so the integer part of M 2^-r
-// lies in the significand's top word.  Zeros, subnormals and FP32 inputs take
-// the general path (ceil_scaled_abs, add_scaled_abs).
+// and the 1-norm term v = floor(|x| 2^(shift+57)) as 32-bit halves (vhi, vlo).
+// A normal double takes one 64-bit shift: |x| 2^shift = M 2^-r < 64 with the
+// 53-bit significand M >= 2^52 puts r >= 47, so v = M 2^(57-r) is M shifted
+// left by at most 10 (no bit lost: floor(2^shift |x|) = v >> 57 and q adds
+// one when any of v's low 57 bits is set) or shifted right (then 2^shift |x|
+// < 1/32, so q = 1).  Zeros, subnormals and FP32 inputs take the general path
+// (ceil_scaled_abs, add_scaled_abs).
 template <typename T>
 __device__ __forceinline__ void quant_elem(T x, int shift, uint32_t &q, uint32_t &qf, uint32_t &vhi, uint32_t &vlo) {
     if constexpr (sizeof(T) == 8) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-        const uint32_t hi = uint32_t(b >> 32), lo = uint32_t(b);
-        const int ex = int((hi >> 20) & 0x7FFu);
+        const int ex = int((b >> 52) & 0x7FFu);
         const int r = 1075 - ex - shift;
         if (ex != 0 && ex != 0x7FF && r >= 47) {
-            const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;   // M = mh 2^32 + lo
-            const int rr = r - 32;                              // >= 15
-            if (rr >= 32) {
-                q = 1u;
-                qf = 0u;
-            } else {
-                const uint32_t rest = (mh & ((1u << rr) - 1u)) | lo;
-                qf = mh >> rr;
-                q = qf + (rest != 0u ? 1u : 0u);
-            }
-            if (r <= 57) {                                      // M << (57 - r), at most 10 bits
-                const int s = 57 - r;
-                vhi = __funnelshift_l(lo, mh, s);
-                vlo = lo << s;
-            } else {
-                const int t = r - 57;
-                if (t < 32) {
-                    vlo = __funnelshift_r(lo, mh, t);
-                    vhi = mh >> t;
-                } else {
-                    vlo = t < 64 ? mh >> (t - 32) : 0u;
-                    vhi = 0u;
-                }
-            }
+            const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+            const int s = 57 - r;                               // <= 10
+            const unsigned long long v = (M << max(s, 0)) >> min(max(-s, 0), 63);
+            vhi = uint32_t(v >> 32);
+            vlo = uint32_t(v);
+            qf = vhi >> 25;
+            q = s < 0 ? 1u : qf + ((v << 7) != 0ull ? 1u : 0u);
             return;
         }
     }
