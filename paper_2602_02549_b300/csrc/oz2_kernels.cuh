@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "oz2_ptx.cuh"
 #include "oz2_tables.h"
@@ -819,11 +820,14 @@ __device__ __forceinline__ int row_bits(unsigned long long max_bits, int shift) 
 // fixed_limbs2: the limbs of two elements as FP32 pairs, the residues mod 256 as BF16x2.
 // Limb u (13 bits) becomes the float 2^23 + u by setting the exponent bits,
 // and one paired fma s (2^23 + u) - s 2^23 = s u (exact) applies the sign s.
-template <int L, typename T>
+// W64: |x'| < 2^64 (rows of at most 64 bits), so x' is formed in one 64-bit
+// word instead of 128 bits.
+template <int L, typename T, bool W64 = false>
 __device__ __forceinline__ uint32_t fixed_limbs2(T x0, T x1, int shift, unsigned long long (&dp)[L]) {
     const Int v0 = trunc_scaled(x0, shift), v1 = trunc_scaled(x1, shift);
-    const unsigned __int128 w0 = v0.M == 0 ? (unsigned __int128)0 : ((unsigned __int128)v0.M << v0.E);
-    const unsigned __int128 w1 = v1.M == 0 ? (unsigned __int128)0 : ((unsigned __int128)v1.M << v1.E);
+    using W = typename std::conditional<W64, unsigned long long, unsigned __int128>::type;
+    const W w0 = v0.M == 0 ? W(0) : (W(v0.M) << v0.E);
+    const W w1 = v1.M == 0 ? W(0) : (W(v1.M) << v1.E);
     const unsigned long long sg = f2::pack(v0.neg ? -1.0f : 1.0f, v1.neg ? -1.0f : 1.0f);
     const unsigned long long off = f2::pack(v0.neg ? 8388608.0f : -8388608.0f, v1.neg ? 8388608.0f : -8388608.0f);
 #pragma unroll
@@ -838,12 +842,12 @@ __device__ __forceinline__ uint32_t fixed_limbs2(T x0, T x1, int shift, unsigned
     return pack_bf16x2f(float(int(int8_t(b0))), float(int(int8_t(b1))));
 }
 
-template <int L, typename T>
+template <int L, typename T, bool W64 = false>
 __device__ __forceinline__ void emit_resid8_fixed(uint4 *dst, long pw16, int N, const T (&x)[8], int shift) {
     unsigned long long dp[4][L];
     uint32_t z[4];
 #pragma unroll
-    for (int j = 0; j < 4; j++) z[j] = fixed_limbs2<L>(x[2 * j], x[2 * j + 1], shift, dp[j]);
+    for (int j = 0; j < 4; j++) z[j] = fixed_limbs2<L, T, W64>(x[2 * j], x[2 * j + 1], shift, dp[j]);
     dst[0] = make_uint4(z[0], z[1], z[2], z[3]);
     const unsigned long long magic = f2::pack(12582912.0f, 12582912.0f);      // 1.5 2^23
     const unsigned long long nmagic = f2::pack(-12582912.0f, -12582912.0f);
@@ -892,7 +896,8 @@ __device__ __forceinline__ void emit_resid8_general(uint4 *dst, long pw16, int N
 template <typename T>
 __device__ __forceinline__ void emit_resid8(uint4 *dst, long pw16, int N, const T (&x)[8], int shift, int need,
                                             const uint8_t (*pow2)[256]) {
-    if (need <= 65) emit_resid8_fixed<5>(dst, pw16, N, x, shift);
+    if (need <= 64) emit_resid8_fixed<5, T, true>(dst, pw16, N, x, shift);
+    else if (need <= 65) emit_resid8_fixed<5>(dst, pw16, N, x, shift);
     else if (need <= 78) emit_resid8_fixed<6>(dst, pw16, N, x, shift);
     else if (need <= 104) emit_resid8_fixed<8>(dst, pw16, N, x, shift);
     else emit_resid8_general(dst, pw16, N, x, shift, pow2);

@@ -287,14 +287,15 @@ def test_vs_fma_chain_reading(oracle, b, N):
             assert (np.abs(oracle.exact_residual(A, Bm, C)) <= eb).all()
 
 
-@pytest.mark.parametrize("N,phi", [(16, 1.0), (17, 1.0), (17, 4.0), (18, 4.0), (20, 4.0), (21, 1.0),
-                                   (27, 1.0), (28, 0.5), (28, 1.0), (33, 1.0)])
+@pytest.mark.parametrize("N,phi", [(16, 1.0), (17, 0.5), (17, 1.0), (17, 4.0), (18, 4.0), (20, 4.0),
+                                   (21, 1.0), (27, 1.0), (28, 0.5), (28, 1.0), (33, 1.0)])
 def test_short_rows_limb_thresholds(oracle, N, phi):
     # k = 20 (k_pad = 64): one warp of the residue kernels covers four rows.
     # Across these N the bit length of the rows' largest |A'|, |B'| passes the
-    # 65 / 78 / 104 bit limits of the 5-, 6- and 8-limb forms; at N = 17 (65 or
-    # 66 bits) and N = 28, phi = 0.5 (104 to 106 bits) neighbouring rows lie on
-    # both sides of a limit.  W must stay bit-exact
+    # 64 / 65 / 78 / 104 bit limits of the 64-bit and 128-bit 5-limb forms and
+    # the 6- and 8-limb forms (N = 16: 61 to 62 bits); at N = 17, phi = 0.5 (64
+    # or 65 bits), N = 17, phi = 1 (65 or 66) and N = 28, phi = 0.5 (104 to 106)
+    # neighbouring rows lie on both sides of a limit.  W must stay bit-exact
     A, Bm = paper_pair(130, 70, 20, phi, seed=N)
     g = run_gpu(A, Bm, N)
     check_against_oracle(oracle, A, Bm, g)
