@@ -824,10 +824,28 @@ __device__ __forceinline__ int row_bits(unsigned long long max_bits, int shift) 
 // word instead of 128 bits.
 template <int L, typename T, bool W64 = false>
 __device__ __forceinline__ uint32_t fixed_limbs2(T x0, T x1, int shift, unsigned long long (&dp)[L]) {
-    const Int v0 = trunc_scaled(x0, shift), v1 = trunc_scaled(x1, shift);
+    Int v0, v1;
     using W = typename std::conditional<W64, unsigned long long, unsigned __int128>::type;
-    const W w0 = v0.M == 0 ? W(0) : (W(v0.M) << v0.E);
-    const W w1 = v1.M == 0 ? W(0) : (W(v1.M) << v1.E);
+    W w0, w1;
+    if constexpr (W64 && sizeof(T) == 8) {
+        // x' = trunc(2^shift |x|) < 2^64 straight from the bits: one shift of the
+        // significand (subnormals without the implicit bit, non-finite as zero)
+        auto one = [&](T x, Int &v) -> unsigned long long {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(double(x));
+            const int ex = int((b >> 52) & 0x7FFu);
+            const unsigned long long M = ex == 0x7FF ? 0ull : (b & 0xFFFFFFFFFFFFFull) | (ex != 0 ? 1ull << 52 : 0ull);
+            const int sh = (ex != 0 ? ex : 1) - 1075 + shift;
+            v.neg = (b >> 63) != 0;
+            return (M << min(max(sh, 0), 63)) >> min(max(-sh, 0), 63);
+        };
+        w0 = one(x0, v0);
+        w1 = one(x1, v1);
+    } else {
+        v0 = trunc_scaled(x0, shift);
+        v1 = trunc_scaled(x1, shift);
+        w0 = v0.M == 0 ? W(0) : (W(v0.M) << v0.E);
+        w1 = v1.M == 0 ? W(0) : (W(v1.M) << v1.E);
+    }
     const unsigned long long sg = f2::pack(v0.neg ? -1.0f : 1.0f, v1.neg ? -1.0f : 1.0f);
     const unsigned long long off = f2::pack(v0.neg ? 8388608.0f : -8388608.0f, v1.neg ? 8388608.0f : -8388608.0f);
 #pragma unroll

@@ -185,6 +185,27 @@ def test_wide_exponents_and_zeros(oracle):
     assert (g["C"][5] == 0).all() and (g["C"][:, 7] == 0).all()
 
 
+def test_subnormal_rows(oracle):
+    # rows made only of subnormal numbers (mu near 1074 + 60: the residue
+    # kernels shift significands without the implicit bit into x' of at most
+    # 64 bits), rows mixing subnormals with normal values, the smallest
+    # subnormals, a zero row and a subnormal column of B, at N where every
+    # row stays below 2^64; then the transposed layouts give the same bits
+    A, Bm = paper_pair(37, 29, 150, 1.0, seed=21)
+    A[3, :] = np.ldexp(A[3, :], -1040)
+    A[7, ::2] = np.ldexp(A[7, ::2], -1060)
+    A[11, :] = 0.0
+    A[13, :40] = 5e-324 * np.arange(1, 41)
+    A[13, 40:] = 0.0
+    Bm[:, 4] = np.ldexp(Bm[:, 4], -1050)
+    assert (np.abs(A[3]) < 2.0 ** -1022).all() and (A[3] != 0).any()
+    for N in (14, 16):
+        g = run_gpu(A, Bm, N)
+        check_against_oracle(oracle, A, Bm, g)
+        gt = run_gpu(np.ascontiguousarray(A.T), np.ascontiguousarray(Bm.T), N, trans_a=True, trans_b=True)
+        assert np.array_equal(gt["C"], g["C"]) and np.array_equal(gt["W"], g["W"])
+
+
 def test_subnormal_outputs(oracle):
     # tiny inputs make C subnormal: the single final rounding must match ldexp
     A, Bm = paper_pair(40, 30, 200, 1.0, seed=4)
