@@ -201,7 +201,7 @@ int encode_bf16_2d(CUtensorMap *tm, const void *base, uint64_t rows, uint64_t co
 }
 
 // Resident blocks of 256 threads per SM of the looping residue kernels (their
-// __launch_bounds__ minimum).
+// __launch_bounds__ minimum; the transposing one runs twice as many blocks of 128).
 constexpr int kResidBlocksPerSM = 3;
 
 // The residue GEMM's failure-path test hook (oz2_gemm_timeout_selftest sets it
@@ -517,18 +517,19 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
         return int(std::min<long long>(J.begin[count], cap));
     };
     // one item per block where a block has no setup to amortise; the residue
-    // kernels (which load a 12.5 KB table per block) stay resident and loop,
-    // kResidBlocksPerSM blocks per SM (their launch bound)
+    // kernels (the per-item N load and plane constants) stay resident and loop,
+    // kResidBlocksPerSM blocks of 256 threads per SM (their launch bound)
     const long long one_each = (1ll << 31) - 1, resident = (long long)sms * kResidBlocksPerSM;
     int rc, g;
     auto launched = [&]() { return cuda_fail(cudaGetLastError()); };
-#define OZ2_LAUNCH(kernel, items, cap)                              \
+#define OZ2_LAUNCH_B(kernel, items, cap, threads)                    \
     if ((g = plan(Items<T>::items, cap)) < 0) return OZ2_ENOTSUP;   \
     if (g > 0) {                                                    \
-        kernel<T, CAP><<<g, 256, 0, st>>>(J);                       \
+        kernel<T, CAP><<<g, threads, 0, st>>>(J);                   \
         g_launches.fetch_add(1, std::memory_order_relaxed);         \
         if ((rc = launched())) return rc;                           \
     }
+#define OZ2_LAUNCH(kernel, items, cap) OZ2_LAUNCH_B(kernel, items, cap, 256)
     // heaviest problems first: the longest-processing-time order balances the
     // static assignment of GEMM work items to CTAs
     std::vector<int> order;
@@ -612,7 +613,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
     OZ2_LAUNCH(k_exponents, exponents, one_each)
     if ((rc = mark(OZ2_PHASE_RESIDUES))) return rc;
     OZ2_LAUNCH(k_resid_kc, resid_kc, resident)
-    OZ2_LAUNCH(k_resid_rc, resid_rc, resident)
+    OZ2_LAUNCH_B(k_resid_rc, resid_rc, 2 * resident, 128)   // 128-thread blocks, twice as many
     if ((rc = mark(OZ2_PHASE_GEMM))) return rc;
     if ((rc = gemms(EPI_MOD))) return rc;
     if ((rc = mark(OZ2_PHASE_CRT))) return rc;
@@ -627,6 +628,7 @@ int run_group(Job<T> *const *jobs, int count, cudaStream_t st, int sms, Mark &&m
         OZ2_LAUNCH(k_crt, crt, one_each)
     }
 #undef OZ2_LAUNCH
+#undef OZ2_LAUNCH_B
     return mark(OZ2_NPHASES);
 }
 

@@ -284,7 +284,7 @@ __host__ __device__ __forceinline__ int absmax_lw_min(int C) {
 // Residues of K-contiguous rows: 256 consecutive groups of 8 positions per
 // item, in the row-major order of the plane's R live rows of k_pad positions
 // (R x k_pad / 8 groups in all; the last item may end early).  Transposed
-// rows: 32 x 128 tiles over the R live rows.
+// rows: 16 x 128 tiles over the R live rows.
 template <typename T>
 __host__ __device__ __forceinline__ long long items_kc_x(const JobDesc<T> &j, int X) {
     if (!j.op[X].kcontig) return 0;
@@ -292,7 +292,7 @@ __host__ __device__ __forceinline__ long long items_kc_x(const JobDesc<T> &j, in
 }
 template <typename T>
 __host__ __device__ __forceinline__ long long items_rc_x(const JobDesc<T> &j, int X) {
-    return j.op[X].kcontig ? 0 : cdiv(j.k_pad, 128) * cdiv(j.op[X].R, 32);
+    return j.op[X].kcontig ? 0 : cdiv(j.k_pad, 128) * cdiv(j.op[X].R, 16);
 }
 // quantisation of K-contiguous rows: kQuantGroups chunks of tpr x 8 h per item;
 // tpr is a power of two in [8, 256] with tpr x 8 x kQuantGroups >= k_pad where
@@ -960,13 +960,13 @@ __device__ __forceinline__ void resid_kc_item(const JobDesc<T> &j, long long li,
     emit_resid8(dst, pw16, N, x, shift, need, pow2);
 }
 
-// R-contiguous source.  Item: a 32 (r) x 128 (h) tile transposed through
-// shared memory (rows of 129 doubles), so that each row of a plane is written
-// in runs of 256 bytes.  Thread (row rr, group tc < 16) then takes h = 8 tc ..
-// 8 tc + 7 of row rr; within each group of eight the elements are stored
-// XOR-permuted by (tc >> 1) & 7, so that the 16 lanes of a half-warp reading
-// element e of their groups hit distinct banks (as do the 16 rows written per
-// h in the transposing stores).  The last tile of a row may reach past k_pad
+// R-contiguous source, blocks of 128 threads.  Item: a 16 (r) x 128 (h) tile
+// transposed through shared memory (rows of 129 doubles), so that each row of
+// a plane is written in runs of 256 bytes.  Thread (row rr, group tc < 16) then
+// takes h = 8 tc .. 8 tc + 7 of rows rr and rr + 8; within each group of eight
+// the elements are stored XOR-permuted by (tc >> 1) & 7, so that the 16 lanes
+// of a half-warp reading element e of their groups hit distinct banks (as do
+// the 16 rows written per h in the transposing stores).  The last tile of a row may reach past k_pad
 // (k_pad is a multiple of 64): those groups are not stored.
 __device__ __forceinline__ int resid_swz(int hh) { return hh ^ ((hh >> 4) & 7); }
 
@@ -980,16 +980,16 @@ __device__ __forceinline__ void resid_rc_item(const JobDesc<T> &j, long long li,
     const Operand<T> &op = j.op[X];
     const int N = *a.n_dev;
     const long pw16 = a.plane / 8;
-    const unsigned nrb = unsigned(cdiv(op.R, 32)), ui = unsigned(li);
+    const unsigned nrb = unsigned(cdiv(op.R, 16)), ui = unsigned(li);
     const int hb = int(ui / nrb);
-    const int h_base = hb * 128, r_base = int(ui - unsigned(hb) * nrb) * 32;
+    const int h_base = hb * 128, r_base = int(ui - unsigned(hb) * nrb) * 16;
     __syncthreads();                     // the previous item's reads of the tile are done
     {
-        const int rr = threadIdx.x & 31;
+        const int rr = threadIdx.x & 15;
         const int r = r_base + rr;
 #pragma unroll
         for (int i = 0; i < 16; i++) {
-            const int hh = (threadIdx.x >> 5) + 8 * i;
+            const int hh = (threadIdx.x >> 4) + 8 * i;
             const int h = h_base + hh;
             tile[rr][resid_swz(hh)] = (r < op.R && h < a.k) ? op.ptr[(long)h * op.ld + r] : T(0);
         }
@@ -999,7 +999,7 @@ __device__ __forceinline__ void resid_rc_item(const JobDesc<T> &j, long long li,
     const int h0 = h_base + 8 * tc;
 #pragma unroll 1
     for (int i = 0; i < 2; i++) {
-        const int rr = (threadIdx.x >> 4) + 16 * i;
+        const int rr = (threadIdx.x >> 4) + 8 * i;
         const int r = r_base + rr;
         const bool live = r < op.R;
         const int shift = live ? a.shift[r] : 0;
@@ -1021,8 +1021,8 @@ __global__ void __launch_bounds__(256, 3) k_resid_kc(const __grid_constant__ Job
 
 // Residues of transposed rows (resident blocks looping over the items).
 template <typename T, int CAP>
-__global__ void __launch_bounds__(256, 3) k_resid_rc(const __grid_constant__ JobGroup<T, CAP> G) {
-    __shared__ T tile[32][129];              // [r][swizzled h]
+__global__ void __launch_bounds__(128, 6) k_resid_rc(const __grid_constant__ JobGroup<T, CAP> G) {
+    __shared__ T tile[16][129];              // [r][swizzled h]
     for_items(G, [&](const JobDesc<T> &j, long long li) { resid_rc_item(j, li, g_pow2, tile); });
 }
 
