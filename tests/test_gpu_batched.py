@@ -136,6 +136,37 @@ def test_autotune_keeps_a_policy_and_results():
     assert B.batched_set_policy(probs, 5) == B.OZ2_EINVAL
 
 
+def test_more_problems_than_one_group():
+    # 70 problems: one group of 64 and one of 6, launched one after the other
+    # on the same workspace layout; every problem bit-identical to its single
+    # call, also under the autotuner's kept policy
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    rng = np.random.default_rng(70)
+    probs = []
+    for i in range(70):
+        m, n, k = (int(v) for v in rng.integers(1, 200, size=3))
+        Bm = paper_matrix(k, n, 1.0, 3 * i + 1)
+        probs.append(dict(A=torch.tensor(paper_matrix(m, k, 1.0, 3 * i), device="cuda"),
+                          B=torch.tensor(np.ascontiguousarray(Bm.T) if i % 4 == 0 else Bm, device="cuda"),
+                          C=torch.full((m, n), float("nan"), dtype=torch.float64, device="cuda"),
+                          nmoduli=0 if i % 3 else 12, target=1e-14 if i % 3 else 0.0, nmax=30 if i % 3 else 0,
+                          fast=i % 5 == 0, trans_a=False, trans_b=i % 4 == 0,
+                          n_out=torch.zeros(1, dtype=torch.int32, device="cuda")))
+    refs = [single_reference(q) for q in probs]
+    for tuned in (False, True):
+        if tuned:
+            B.batched_autotune(probs)
+        for q in probs:
+            q["C"].fill_(float("nan"))
+        assert B.gemm_batched(probs) == 0
+        torch.cuda.synchronize()
+        assert B.sync() == 0
+        for q, (C, nout) in zip(probs, refs):
+            assert int(q["n_out"].item()) == int(nout.item())
+            assert torch.equal(q["C"], C)
+
+
 def test_batched_benchmark_set(oracle):
     # the batched benchmark's 64 problems (m, n, k log-uniform in [128, 4096],
     # phi ~ U(0.5, 4), tau = 1e-14): autotuned tiles, graph-captured call, each
