@@ -253,6 +253,37 @@ OZ2_API int oz2_batched_autotune(int count, const oz2_problem *problems, const o
  * without timing.  Returns OZ2_OK or OZ2_EINVAL. */
 OZ2_API int oz2_batched_set_policy(int count, const oz2_problem *problems, int policy);
 
+/*
+ * C = OS_II(A, B) as oz2_gemm_ex / oz2_sgemm_ex, with A, B and C in host
+ * memory (the problem as the paper states it: FP64 or FP32 matrices, the
+ * product in the same format).  On opts->stream, in this order: A and B are
+ * copied into device memory (packed in their stored layout: A as (TRANS_A ?
+ * k x m : m x k), B as (TRANS_B ? n x k : k x n)), the emulation runs, and C
+ * is copied back into the host array (rows of n at stride ldc).  The device
+ * memory is carved from opts->workspace, which must hold
+ * oz2_host_workspace_size(...) bytes (NULL: the library-managed buffer, with
+ * the serialisation rule of oz2_opts.workspace).  With pinned (page-locked)
+ * host memory the call returns once everything is enqueued and C is valid when
+ * the stream has completed (oz2_sync): calls on two streams with two
+ * workspaces overlap one call's copies with the other's kernels.  With
+ * pageable host memory the copies are staged by the CUDA runtime and the call
+ * returns with C in place.  Any memory the CUDA runtime can address works as
+ * the source and destination (device pointers too).  The other options
+ * (n_out, mu/nu in/out, w_out, phase_events) are device pointers as in
+ * oz2_gemm_ex.  Returns as oz2_gemm_ex, plus OZ2_ENOMEM for a workspace below
+ * oz2_host_workspace_size.
+ */
+OZ2_API int oz2_gemm_host(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                          double *C, int ldc, int nmoduli, int mode, const oz2_opts *opts);
+OZ2_API int oz2_sgemm_host(int m, int n, int k, const float *A, int lda, const float *B, int ldb,
+                           float *C, int ldc, int nmoduli, int mode, const oz2_opts *opts);
+
+/* Bytes of device workspace oz2_gemm_host (fp32 = 0) or oz2_sgemm_host
+ * (fp32 = 1) needs: the packed device copies of A, B and C (each rounded up to
+ * 256 bytes) followed by oz2_workspace_size(m, n, k, nmax, mode, fp32).
+ * Returns 0 for invalid sizes.  Host-only. */
+OZ2_API size_t oz2_host_workspace_size(int m, int n, int k, int nmax, int mode, int fp32);
+
 /* Workspace bytes of oz2_gemm_batched for these problems (0 if any is invalid). */
 OZ2_API size_t oz2_batched_workspace_size(int count, const oz2_problem *problems);
 

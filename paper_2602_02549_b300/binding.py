@@ -66,11 +66,12 @@ def lib() -> ctypes.CDLL:
         for name in ("oz2_gemm", "oz2_sgemm"):
             getattr(L, name).argtypes = gemm_args
             getattr(L, name).restype = i
-        for name in ("oz2_gemm_ex", "oz2_sgemm_ex"):
+        for name in ("oz2_gemm_ex", "oz2_sgemm_ex", "oz2_gemm_host", "oz2_sgemm_host"):
             getattr(L, name).argtypes = gemm_args + [ctypes.POINTER(oz2_opts)]
             getattr(L, name).restype = i
-        L.oz2_workspace_size.argtypes = [i, i, i, i, i, i]
-        L.oz2_workspace_size.restype = sz
+        for name in ("oz2_workspace_size", "oz2_host_workspace_size"):
+            getattr(L, name).argtypes = [i, i, i, i, i, i]
+            getattr(L, name).restype = sz
         L.oz2_k_ranges.argtypes = [i, P, P]
         L.oz2_k_ranges.restype = i
         for name in ("oz2_zgemm", "oz2_cgemm"):
@@ -107,6 +108,11 @@ def status_str(status: int) -> str:
 
 def workspace_size(m: int, n: int, k: int, nmax: int, mode: int = 0, fp32: bool = False) -> int:
     return int(lib().oz2_workspace_size(m, n, k, nmax, mode, int(fp32)))
+
+
+def host_workspace_size(m: int, n: int, k: int, nmax: int, mode: int = 0, fp32: bool = False) -> int:
+    """oz2_host_workspace_size: device bytes of an oz2_gemm_host / oz2_sgemm_host call."""
+    return int(lib().oz2_host_workspace_size(m, n, k, nmax, mode, int(fp32)))
 
 
 def k_ranges(k: int) -> tuple[int, int]:
@@ -338,6 +344,49 @@ def gemm_ex(A, B, C, nmoduli: int = 0, mode: int = 0, *, target: float = 0.0, nm
         o.phase_events = ctypes.cast(arr, ctypes.c_void_p)
     fn = lib().oz2_sgemm_ex if fp32 else lib().oz2_gemm_ex
     with torch.cuda.device(A.device):
+        return fn(m, n, k, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), _ptr(C), _ld(C, "C"),
+                  nmoduli, mode, ctypes.byref(o))
+
+
+def gemm_host(A, B, C, nmoduli: int = 0, mode: int = 0, *, target: float = 0.0, nmax: int = 0,
+              workspace=None, stream=None, n_out=None, device=None) -> int:
+    """oz2_gemm_host / oz2_sgemm_host on torch CPU tensors (pinned or pageable):
+    the library copies A and B to the device, runs the emulation on `stream`
+    and copies C back.  Shapes as in gemm_ex; `workspace` is a CUDA uint8
+    tensor of >= host_workspace_size bytes (allocated here when omitted).
+    With pinned tensors C is valid once the stream has completed.  Returns the
+    status code."""
+    import torch
+    fp32 = A.dtype == torch.float32
+    if A.dtype not in (torch.float32, torch.float64) or B.dtype != A.dtype or C.dtype != A.dtype:
+        raise TypeError("A, B, C must all be float64 or all float32")
+    for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+        if t.is_cuda:
+            raise ValueError(f"{nm} must be a host (CPU) tensor; gemm_ex takes device tensors")
+    ta, tb = bool(mode & OZ2_TRANS_A), bool(mode & OZ2_TRANS_B)
+    m = A.size(1) if ta else A.size(0)
+    k = A.size(0) if ta else A.size(1)
+    n = B.size(0) if tb else B.size(1)
+    kb = B.size(1) if tb else B.size(0)
+    if kb != k or tuple(C.shape) != (m, n):
+        raise ValueError("shape mismatch")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    o = oz2_opts()
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    o.stream = ctypes.c_void_p(s.cuda_stream)
+    n_eff = nmoduli if nmoduli else (nmax if nmax else (14 if fp32 else 20))
+    if workspace is None and m > 0 and n > 0 and k > 0 and n_eff >= 2:
+        size = host_workspace_size(m, n, k, n_eff, mode, fp32)
+        if size:
+            workspace = torch.empty(size, dtype=torch.uint8, device=dev)
+    if workspace is not None:
+        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    o.target = float(target)
+    o.nmax = int(nmax)
+    o.n_out = _ptr(n_out)
+    fn = lib().oz2_sgemm_host if fp32 else lib().oz2_gemm_host
+    with torch.cuda.device(dev):
         return fn(m, n, k, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), _ptr(C), _ld(C, "C"),
                   nmoduli, mode, ctypes.byref(o))
 

@@ -689,6 +689,64 @@ int run(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int
     return OZ2_OK;
 }
 
+// ------------------------------------------------------------------ host arrays
+// oz2_gemm_host / oz2_sgemm_host: the device copies of A, B (packed in their
+// stored layout) and C, each rounded up to 256 bytes, then the emulation's own
+// workspace (laid out as run<T> lays it out for this call).
+struct HostSplit {
+    size_t a, b, c, inner, total;
+};
+
+template <typename T>
+HostSplit host_split(int m, int n, int k, int nmax) {
+    HostSplit h{};
+    h.a = round_up(size_t(m) * size_t(k) * sizeof(T), 256);
+    h.b = round_up(size_t(k) * size_t(n) * sizeof(T), 256);
+    h.c = round_up(size_t(m) * size_t(n) * sizeof(T), 256);
+    h.inner = make_layout(make_dims(m, n, k_split(k).kc, nmax)).total;
+    h.total = h.a + h.b + h.c + h.inner;
+    return h;
+}
+
+template <typename T>
+int run_host(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, int nmoduli, int mode,
+             const oz2_opts *o) {
+    int rc = validate(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o);
+    if (rc) return rc;
+    const int nmax = nmoduli ? nmoduli : (o && o->nmax ? o->nmax : (sizeof(T) == 4 ? 14 : 20));
+    const HostSplit h = host_split<T>(m, n, k, nmax);
+    int dev = 0;
+    if ((rc = ensure_device(&dev))) return rc;
+    cudaStream_t st = o ? static_cast<cudaStream_t>(o->stream) : nullptr;
+    uint8_t *ws = nullptr;
+    if (o && o->workspace) {
+        if (o->workspace_bytes < h.total) return OZ2_ENOMEM;
+        if (reinterpret_cast<uintptr_t>(o->workspace) & 255u) return OZ2_EINVAL;
+        ws = static_cast<uint8_t *>(o->workspace);
+    } else if ((rc = managed_workspace(dev, h.total, &ws))) {
+        return rc;
+    }
+    const bool ta = mode & OZ2_TRANS_A, tb = mode & OZ2_TRANS_B;
+    const int ra = ta ? k : m, ca = ta ? m : k;     // A as stored: ra rows of ca
+    const int rb = tb ? n : k, cb = tb ? k : n;     // B likewise
+    T *dA = reinterpret_cast<T *>(ws), *dB = reinterpret_cast<T *>(ws + h.a);
+    T *dC = reinterpret_cast<T *>(ws + h.a + h.b);
+    // cudaMemcpyDefault: the runtime tells host from device memory (unified addressing)
+    if ((rc = cuda_fail(cudaMemcpy2DAsync(dA, size_t(ca) * sizeof(T), A, size_t(lda) * sizeof(T),
+                                          size_t(ca) * sizeof(T), size_t(ra), cudaMemcpyDefault, st))))
+        return rc;
+    if ((rc = cuda_fail(cudaMemcpy2DAsync(dB, size_t(cb) * sizeof(T), B, size_t(ldb) * sizeof(T),
+                                          size_t(cb) * sizeof(T), size_t(rb), cudaMemcpyDefault, st))))
+        return rc;
+    oz2_opts inner = o ? *o : oz2_opts{};
+    inner.stream = st;
+    inner.workspace = ws + h.a + h.b + h.c;
+    inner.workspace_bytes = h.inner;
+    if ((rc = run<T>(m, n, k, dA, ca, dB, cb, dC, n, nmoduli, mode, &inner))) return rc;
+    return cuda_fail(cudaMemcpy2DAsync(C, size_t(ldc) * sizeof(T), dC, size_t(n) * sizeof(T), size_t(n) * sizeof(T),
+                                       size_t(m), cudaMemcpyDefault, st));
+}
+
 // ------------------------------------------------------------------ complex
 // ZGEMM / CGEMM: op(A) op(B) for interleaved complex A, B, C as two real
 // emulations over 2k (k_zsplit): Re C = A_s B_1, Im C = A_s B_2 with
@@ -1068,6 +1126,22 @@ int oz2_gemm(int m, int n, int k, const double *A, int lda, const double *B, int
 int oz2_sgemm_ex(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
                  int nmoduli, int mode, const oz2_opts *opts) {
     return run<float>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, opts);
+}
+
+int oz2_gemm_host(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+                  int nmoduli, int mode, const oz2_opts *opts) {
+    return run_host<double>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, opts);
+}
+
+int oz2_sgemm_host(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                   int nmoduli, int mode, const oz2_opts *opts) {
+    return run_host<float>(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, opts);
+}
+
+size_t oz2_host_workspace_size(int m, int n, int k, int nmax, int mode, int fp32) {
+    (void)mode;
+    if (m < 1 || n < 1 || k < 1 || nmax < OZ2_N_MIN || nmax > OZ2_N_MAX) return 0;
+    return fp32 ? host_split<float>(m, n, k, nmax).total : host_split<double>(m, n, k, nmax).total;
 }
 
 int oz2_sgemm(int m, int n, int k, const float *A, int lda, const float *B, int ldb, float *C, int ldc,

@@ -95,6 +95,41 @@ def test_argument_errors_launch_nothing(lib):
     assert B.launch_count() == before
 
 
+@pytest.mark.parametrize("fp32", [False, True])
+def test_host_arrays_argument_errors(lib, fp32):
+    """oz2_gemm_host / oz2_sgemm_host check their arguments as oz2_gemm_ex does,
+    before any copy or launch."""
+    fn = lib.oz2_sgemm_host if fp32 else lib.oz2_gemm_host
+    E = B.OZ2_EINVAL
+    before = B.launch_count()
+
+    def host(m=8, n=8, k=8, lda=8, ldb=8, ldc=8, N=14, mode=0, A=FAKE, Bp=FAKE, C=FAKE):
+        return fn(m, n, k, A, lda, Bp, ldb, C, ldc, N, mode, None)
+    assert host(m=0) == E
+    assert host(k=-3) == E
+    assert host(lda=7) == E
+    assert host(ldb=4, mode=B.OZ2_TRANS_B) == E
+    assert host(ldc=7) == E
+    assert host(N=50) == E
+    assert host(N=0) == E                      # the bound rule needs opts with a target
+    assert host(A=None) == E
+    assert host(mode=8) == E
+    assert B.launch_count() == before
+
+
+def test_host_workspace_size(lib):
+    """The device copies of A, B, C (each rounded up to 256 bytes) ahead of the
+    emulation's own workspace."""
+    r = lambda b: (b + 255) // 256 * 256   # noqa: E731
+    for m, n, k, N, fp32 in ((8, 8, 8, 14, False), (100, 37, 1001, 20, False), (33, 65, 17, 9, True),
+                             (5, 7, (1 << 17) + 1, 14, False)):
+        e = 4 if fp32 else 8
+        want = r(e * m * k) + r(e * k * n) + r(e * m * n) + B.workspace_size(m, n, k, N, 0, fp32)
+        assert B.host_workspace_size(m, n, k, N, 0, fp32) == want
+    assert B.host_workspace_size(0, 8, 8, 14) == 0
+    assert B.host_workspace_size(8, 8, 8, 1) == 0
+
+
 def test_workspace_size(lib):
     assert B.workspace_size(0, 8, 8, 14) == 0
     # k > 2^17: the ranges share one workspace sized for the longest range
