@@ -10,8 +10,10 @@
  * once P > 2^53, so the check is the normwise target: |C - AB| <=
  * 4 tau max_ij (|A||B|)_ij (the rule keeps the N-dependent part of the
  * Theorem 2 bound below tau times a lower bound of that maximum; the factor
- * leaves room for the N-independent rounding terms).  Exit status 0 on
- * success, a distinct nonzero code per failed check.
+ * leaves room for the N-independent rounding terms).  The third call,
+ * oz2_gemm_host, takes the host arrays themselves (malloc'd, pageable) and
+ * must give the exact product at N = 5 again.  Exit status 0 on success, a
+ * distinct nonzero code per failed check.
  */
 #include <math.h>
 #include <stdint.h>
@@ -120,7 +122,30 @@ int main(void)
         fprintf(stderr, "bound rule: error %.3g above %.3g\n", err, 4e-15 * absprod);
         return 8;
     }
-    printf("ok: %dx%dx%d exact at N = 5; N = %d by the bound rule, max error %.3g\n", m, n, k, N, err);
+
+    /* host arrays: the library uploads A and B, runs the emulation and downloads C */
+    const size_t hbytes = oz2_host_workspace_size(m, n, k, 5, OZ2_ACCURATE, 0);
+    void *hws;
+    CHECK_CUDA(cudaMalloc(&hws, hbytes));
+    for (int i = 0; i < m * n; i++) C[i] = -1.0;
+    oz2_opts h = {0};
+    h.stream = st;
+    h.workspace = hws;
+    h.workspace_bytes = hbytes;
+    if (oz2_gemm_host(m, n, k, A, k, B, n, C, n, 5, OZ2_ACCURATE, NULL) != OZ2_OK) return 9;   /* managed buffer */
+    if (oz2_sync(NULL) != OZ2_OK || check_exact(m, n, k, A, B, C)) return 10;
+    for (int i = 0; i < m * n; i++) C[i] = -1.0;
+    h.workspace_bytes = hbytes - 256;
+    if (oz2_gemm_host(m, n, k, A, k, B, n, C, n, 5, OZ2_ACCURATE, &h) != OZ2_ENOMEM) return 11;
+    h.workspace_bytes = hbytes;
+    rc = oz2_gemm_host(m, n, k, A, k, B, n, C, n, 5, OZ2_ACCURATE, &h);
+    if (rc == OZ2_OK) rc = oz2_sync(st);
+    if (rc != OZ2_OK) { fprintf(stderr, "oz2_gemm_host: %s\n", oz2_status_str(rc)); return 12; }
+    if (check_exact(m, n, k, A, B, C)) return 13;
+
+    printf("ok: %dx%dx%d exact at N = 5 (device and host arrays); N = %d by the bound rule, max error %.3g\n",
+           m, n, k, N, err);
+    cudaFree(hws);
     cudaFree(ws);
     cudaFree(dN);
     cudaFree(dA);
