@@ -255,8 +255,8 @@ OZ2_API int oz2_batched_set_policy(int count, const oz2_problem *problems, int p
 
 /*
  * C = OS_II(A, B) as oz2_gemm_ex / oz2_sgemm_ex, with A, B and C in host
- * memory (the problem as the paper states it: FP64 or FP32 matrices, the
- * product in the same format).  On opts->stream, in this order: A and B are
+ * memory (the problem as Section 3 states it: A in F_b^{m x k}, B in
+ * F_b^{k x n}, the product in the same format).  On opts->stream, in this order: A and B are
  * copied into device memory (packed in their stored layout: A as (TRANS_A ?
  * k x m : m x k), B as (TRANS_B ? n x k : k x n)), the emulation runs, and C
  * is copied back into the host array (rows of n at stride ldc).  The device
