@@ -92,6 +92,14 @@ def lib() -> ctypes.CDLL:
         L.oz2_launch_count.restype = ctypes.c_longlong
         L.oz2_last_error.argtypes = [P]
         L.oz2_last_error.restype = i
+        L.oz2_batched_workspace_size.argtypes = [i, P]
+        L.oz2_batched_workspace_size.restype = sz
+        L.oz2_gemm_batched.argtypes = [i, P, ctypes.POINTER(oz2_opts)]
+        L.oz2_gemm_batched.restype = i
+        L.oz2_batched_autotune.argtypes = [i, P, ctypes.POINTER(oz2_opts), ctypes.POINTER(i), P]
+        L.oz2_batched_autotune.restype = i
+        L.oz2_batched_set_policy.argtypes = [i, P, i]
+        L.oz2_batched_set_policy.restype = i
         _lib = L
     return _lib
 
@@ -544,8 +552,6 @@ def _problem_array(problems):
 
 def batched_workspace_size(problems) -> int:
     L = lib()
-    L.oz2_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p]
-    L.oz2_batched_workspace_size.restype = ctypes.c_size_t
     arr = _problem_array(problems)
     return int(L.oz2_batched_workspace_size(len(problems), ctypes.cast(arr, ctypes.c_void_p)))
 
@@ -556,16 +562,12 @@ def gemm_batched(problems, *, workspace=None, stream=None, phase_events=None) ->
     n_out (device int32[1]).  Returns the status code."""
     import torch
     L = lib()
-    L.oz2_gemm_batched.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(oz2_opts)]
-    L.oz2_gemm_batched.restype = ctypes.c_int
     arr = _problem_array(problems)
     o = oz2_opts()
     dev = problems[0]["A"].device
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     o.stream = ctypes.c_void_p(s.cuda_stream)
     if workspace is None:
-        L.oz2_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p]
-        L.oz2_batched_workspace_size.restype = ctypes.c_size_t
         size = int(L.oz2_batched_workspace_size(len(problems), ctypes.cast(arr, ctypes.c_void_p)))
         workspace = torch.empty(max(size, 256), dtype=torch.uint8, device=dev)
     o.workspace = ctypes.c_void_p(workspace.data_ptr())
@@ -586,9 +588,6 @@ def batched_autotune(problems, *, workspace=None, stream=None):
     fastest for later gemm_batched calls.  Returns (policy, [ms per policy])."""
     import torch
     L = lib()
-    L.oz2_batched_autotune.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(oz2_opts),
-                                       ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
-    L.oz2_batched_autotune.restype = ctypes.c_int
     arr = _problem_array(problems)
     o = oz2_opts()
     dev = problems[0]["A"].device
@@ -612,8 +611,6 @@ def batched_set_policy(problems, policy: int) -> int:
     """oz2_batched_set_policy: keep tile policy 0, 1 or 2 for this batch's shapes."""
     import torch
     L = lib()
-    L.oz2_batched_set_policy.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
-    L.oz2_batched_set_policy.restype = ctypes.c_int
     arr = _problem_array(problems)
     with torch.cuda.device(problems[0]["A"].device):
         return L.oz2_batched_set_policy(len(problems), ctypes.cast(arr, ctypes.c_void_p), int(policy))
