@@ -10,7 +10,8 @@
  *     A holds A^T (k x m, lda >= m); with OZ2_TRANS_B it holds B^T (n x k,
  *     ldb >= k).  These are the only transposes; there is no alpha/beta.
  *   - A, B, C, the workspace and every optional output are DEVICE pointers
- *     owned by the caller.  Nothing is freed by the library.
+ *     owned by the caller (oz2_gemm_host / oz2_sgemm_host: A, B and C in host
+ *     memory).  Nothing is freed by the library.
  *   - All work is enqueued on opts->stream (NULL: the legacy default stream)
  *     and the call returns without synchronising.  Argument errors are
  *     returned before anything is enqueued, and C is then left untouched.
