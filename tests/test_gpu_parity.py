@@ -206,6 +206,33 @@ def test_subnormal_rows(oracle):
         assert np.array_equal(gt["C"], g["C"]) and np.array_equal(gt["W"], g["W"])
 
 
+def test_non_finite_inputs_complete():
+    # NaN or Inf inputs break the paper's preconditions and their results are
+    # unspecified; the call must still complete (OZ2_OK, a clean sync) and
+    # leave the library working: the same finite call gives the same bits
+    # before and after
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    A, Bm = paper_pair(70, 50, 300, 1.0, seed=31)
+    At, Bt = torch.tensor(A, device="cuda"), torch.tensor(Bm, device="cuda")
+    C0 = B.matmul(At, Bt, 14)
+    torch.cuda.synchronize()
+    bad_A, bad_B = At.clone(), Bt.clone()
+    bad_A[3, :] = float("inf")
+    bad_A[9, 17] = float("nan")
+    bad_B[:, 5] = -float("inf")
+    bad_B[100, 20] = float("nan")
+    for X, Y in ((bad_A, Bt), (At, bad_B), (bad_A, bad_B)):
+        for N, mode in ((14, 0), (0, 0), (0, B.OZ2_FAST)):
+            C = torch.empty((70, 50), dtype=torch.float64, device="cuda")
+            assert B.gemm_ex(X, Y, C, N, mode, target=1e-15 if N == 0 else 0.0, nmax=20 if N == 0 else 0) == 0
+            torch.cuda.synchronize()
+            assert B.sync() == 0
+    C1 = B.matmul(At, Bt, 14)
+    torch.cuda.synchronize()
+    assert torch.equal(C0, C1)
+
+
 def test_subnormal_outputs(oracle):
     # tiny inputs make C subnormal: the single final rounding must match ldexp
     A, Bm = paper_pair(40, 30, 200, 1.0, seed=4)
