@@ -206,6 +206,24 @@ def test_subnormal_rows(oracle):
         assert np.array_equal(gt["C"], g["C"]) and np.array_equal(gt["W"], g["W"])
 
 
+def test_zero_operands(oracle):
+    # A = 0, B = 0 or both: every row uses Dbar = 1 (reading of Algorithm 2 for
+    # a zero Cbar row), every bound term and L vanish, so the rule takes N = 2
+    # as the oracle's does, W is zero and C exactly zero, in every mode
+    A, Bm = paper_pair(20, 30, 40, 1.0, seed=3)
+    Z, Zb = np.zeros_like(A), np.zeros_like(Bm)
+    for X, Y in ((Z, Bm), (A, Zb), (Z, Zb)):
+        s = oracle.scaling(X, Y, 14)
+        N_or, _ = oracle.choose_N(X, Y, s["alpha"], s["beta"], s["cmax_row"], s["cmax_col"], 1e-15, 20)
+        for N, fast in ((14, False), (0, False), (0, True)):
+            g = run_gpu(X, Y, N, target=1e-15, nmax=20, fast=fast)
+            if N == 0 and not fast:
+                assert g["N"] == N_or == 2
+            assert (g["C"] == 0).all() and not np.isnan(g["C"]).any()
+            assert (g["W"] == 0).all()
+            check_against_oracle(oracle, X, Y, g)
+
+
 def test_non_finite_inputs_complete():
     # NaN or Inf inputs break the paper's preconditions and their results are
     # unspecified; the call must still complete (OZ2_OK, a clean sync) and
