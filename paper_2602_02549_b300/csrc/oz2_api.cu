@@ -713,6 +713,8 @@ int run_host(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C
              const oz2_opts *o) {
     int rc = validate(m, n, k, A, lda, B, ldb, C, ldc, nmoduli, mode, o);
     if (rc) return rc;
+    // refused by run<T> too, but only after the uploads: refuse before them
+    if (k_split(k).count > 1 && o && (o->w_out || o->phase_events)) return OZ2_ENOTSUP;
     const int nmax = nmoduli ? nmoduli : (o && o->nmax ? o->nmax : (sizeof(T) == 4 ? 14 : 20));
     const HostSplit h = host_split<T>(m, n, k, nmax);
     int dev = 0;

@@ -114,6 +114,11 @@ def test_host_arrays_argument_errors(lib, fp32):
     assert host(N=0) == E                      # the bound rule needs opts with a target
     assert host(A=None) == E
     assert host(mode=8) == E
+    # k beyond 2^17 with per-call exports: refused before any upload
+    o = B.oz2_opts()
+    o.w_out = ctypes.c_void_p(0x10000)
+    K1 = (1 << 17) + 1
+    assert fn(8, 8, K1, FAKE, K1, FAKE, 8, FAKE, 8, 14, 0, ctypes.byref(o)) == B.OZ2_ENOTSUP
     assert B.launch_count() == before
 
 
