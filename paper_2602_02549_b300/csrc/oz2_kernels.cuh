@@ -555,8 +555,9 @@ __device__ __forceinline__ void flush_row(const PlaneArgs &a, RowAcc acc, int r,
 // 53-bit significand M >= 2^52 puts r >= 47, so v = M 2^(57-r) is M shifted
 // left by at most 10 (no bit lost: floor(2^shift |x|) = v >> 57 and q adds
 // one when any of v's low 57 bits is set) or shifted right (then 2^shift |x|
-// < 1/32, so q = 1).  Zeros, subnormals and FP32 inputs take the general path
-// (ceil_scaled_abs, add_scaled_abs).
+// < 1/32, so q = 1).  A normal float likewise, with its 24-bit significand
+// (r >= 18, a left shift by at most 39).  Zeros and subnormals take the
+// general path (ceil_scaled_abs, add_scaled_abs).
 template <typename T>
 __device__ __forceinline__ void quant_elem(T x, int shift, uint32_t &q, uint32_t &qf, uint32_t &vhi, uint32_t &vlo) {
     if constexpr (sizeof(T) == 8) {
@@ -566,6 +567,22 @@ __device__ __forceinline__ void quant_elem(T x, int shift, uint32_t &q, uint32_t
         if (ex != 0 && ex != 0x7FF && r >= 47) {
             const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
             const int s = 57 - r;                               // <= 10
+            const unsigned long long v = (M << max(s, 0)) >> min(max(-s, 0), 63);
+            vhi = uint32_t(v >> 32);
+            vlo = uint32_t(v);
+            qf = vhi >> 25;
+            q = s < 0 ? 1u : qf + ((v << 7) != 0ull ? 1u : 0u);
+            return;
+        }
+    } else {
+        // FP32: the 24-bit significand M with |x| 2^shift = M 2^-r < 64, r >= 18,
+        // so v = M 2^(57-r) is a left shift by at most 39 or a right shift
+        const uint32_t b = __float_as_uint(float(x));
+        const int ex = int((b >> 23) & 0xFFu);
+        const int r = 150 - ex - shift;
+        if (ex != 0 && ex != 0xFF && r >= 18) {
+            const unsigned long long M = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+            const int s = 57 - r;                               // <= 39
             const unsigned long long v = (M << max(s, 0)) >> min(max(-s, 0), 63);
             vhi = uint32_t(v >> 32);
             vlo = uint32_t(v);
