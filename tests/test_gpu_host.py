@@ -30,10 +30,10 @@ def _device_reference(A, Bm, N, mode, target, nmax):
     m = A.size(1) if ta else A.size(0)
     n = Bm.size(0) if tb else Bm.size(1)
     C = torch.empty((m, n), dtype=A.dtype, device="cuda")
-    nout = torch.zeros(1, dtype=torch.int32, device="cuda")
+    nout = torch.zeros(8, dtype=torch.int32, device="cuda")     # one N per K range (k <= 8 2^17)
     assert B.gemm_ex(dA.contiguous(), dB.contiguous(), C, N, mode, target=target, nmax=nmax, n_out=nout) == 0
     torch.cuda.synchronize()
-    return C.cpu(), int(nout.item())
+    return C.cpu(), int(nout[0].item())
 
 
 @pytest.mark.parametrize("pinned", [True, False])
@@ -111,3 +111,18 @@ def test_host_workspace_too_small():
     before = B.launch_count()
     assert B.gemm_host(A, Bm, C, 14, 0, workspace=small) == B.OZ2_ENOMEM
     assert B.launch_count() == before
+
+
+def test_host_arrays_split_k():
+    # k beyond 2^17: the ranges run in the emulation's workspace after the
+    # uploads, as in the device call
+    import torch
+    from paper_2602_02549_b300 import binding as B
+    m, n, k = 9, 7, (1 << 17) + 100
+    A = torch.tensor(paper_matrix(m, k, 1.0, 41)).pin_memory()
+    Bm = torch.tensor(paper_matrix(k, n, 1.0, 42)).pin_memory()
+    C = torch.empty((m, n), dtype=torch.float64).pin_memory()
+    assert B.gemm_host(A, Bm, C, 0, 0, target=1e-15, nmax=20) == 0
+    assert B.sync() == 0
+    ref, _ = _device_reference(A, Bm, 0, 0, 1e-15, 20)
+    assert torch.equal(C, ref)
